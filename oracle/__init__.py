@@ -1,0 +1,268 @@
+"""CPU oracle for exact Ball Mapper construction -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library never loads it.
+
+The arithmetic lives in ``bm_oracle.c`` (plain FP64 loops, one per definition
+of the paper); this module compiles it with gcc, loads it with ctypes and
+marshals numpy arrays.  ``brute.py`` is a second, differently written brute
+force (exact integer/rational arithmetic) used to pin this one.
+
+Functions and the passages they follow:
+  greedy             Sec. 2.2 greedy epsilon-net, smallest uncovered index first
+  range_query        Sec. 4 exact range set R_r(q) = {x : d(q,x) < r}, full scan
+  memberships        Sec. 2.3 X_i = X intersect B(l_i, eps), full balls
+  edges              Sec. 2.1 nerve / Sec. 4.2 G_r(L): edge iff X_i, X_j intersect
+  build              all of the above in order
+  kth_nn_dist        Sec. 5.1 target-occupancy rule (self counted first)
+  BallTree           Sec. 3.1 ball tree construction and pruned range query
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bm_oracle.c")
+_BUILD_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD_DIR, "libbm_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_f64p = ctypes.POINTER(ctypes.c_double)
+
+
+def compile_library(force: bool = False, src: str = _SRC, out: str = _LIB_PATH) -> str:
+    """Compile the oracle shared library with gcc (OpenMP, no FMA contraction)."""
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(src):
+        return out
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    tmp = out + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+           "-o", tmp, src, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, out)
+    return out
+
+
+def load_library(path: str):
+    """Load a compiled oracle library and declare its C signatures."""
+    lib = ctypes.CDLL(path)
+    lib.bmo_greedy.restype = ctypes.c_int64
+    lib.bmo_greedy.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int, ctypes.c_double, _i32p]
+    lib.bmo_range_count.restype = None
+    lib.bmo_range_count.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int, _f64p, ctypes.c_int64,
+                                    ctypes.c_double, _i64p]
+    lib.bmo_range_fill.restype = None
+    lib.bmo_range_fill.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int, _f64p, ctypes.c_int64,
+                                   ctypes.c_double, _i64p, _i32p]
+    lib.bmo_pair_sqdist.restype = None
+    lib.bmo_pair_sqdist.argtypes = [_f64p, ctypes.c_int, _f64p, ctypes.c_int64, _i32p, _i32p, _f64p]
+    lib.bmo_edges.restype = None
+    lib.bmo_edges.argtypes = [_f64p, ctypes.c_int, _i32p, ctypes.c_int64, ctypes.c_double,
+                              _i64p, _i32p, ctypes.c_int, _i64p, _i64p, _i32p]
+    lib.bmo_kth_nn_dist.restype = ctypes.c_int
+    lib.bmo_kth_nn_dist.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int, ctypes.c_int64, _f64p]
+    lib.bmo_bt_build.restype = ctypes.c_void_p
+    lib.bmo_bt_build.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int, ctypes.c_int]
+    lib.bmo_bt_free.restype = None
+    lib.bmo_bt_free.argtypes = [ctypes.c_void_p]
+    lib.bmo_bt_node_count.restype = ctypes.c_int64
+    lib.bmo_bt_node_count.argtypes = [ctypes.c_void_p]
+    lib.bmo_bt_range_count.restype = ctypes.c_int
+    lib.bmo_bt_range_count.argtypes = [ctypes.c_void_p, _f64p, ctypes.c_int64, ctypes.c_double, _i64p]
+    lib.bmo_bt_range_fill.restype = ctypes.c_int
+    lib.bmo_bt_range_fill.argtypes = [ctypes.c_void_p, _f64p, ctypes.c_int64, ctypes.c_double,
+                                      _i64p, _i32p]
+    lib.bmo_num_threads.restype = ctypes.c_int
+    lib.bmo_num_threads.argtypes = []
+    lib.bmo_set_num_threads.restype = None
+    lib.bmo_set_num_threads.argtypes = [ctypes.c_int]
+    return lib
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = load_library(compile_library())
+        return _lib
+
+
+def _f64(a) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a), dtype=np.float64)
+    if a.ndim == 1:
+        a = a.reshape(1, -1) if a.size else a.reshape(0, 1)
+    return a
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(t)
+
+
+def eps_squared(eps) -> float:
+    """eps^2 in FP64.  For a float32 eps the product is exact (24 x 24 bits < 53)."""
+    e = float(eps)
+    return e * e
+
+
+def num_threads() -> int:
+    return int(_load().bmo_num_threads())
+
+
+def set_num_threads(t: int) -> None:
+    _load().bmo_set_num_threads(int(t))
+
+
+def greedy(X, eps) -> np.ndarray:
+    """Landmark ids in greedy selection order (Sec. 2.2)."""
+    X = _f64(X)
+    n, d = X.shape
+    out = np.empty(max(n, 1), dtype=np.int32)
+    L = _load().bmo_greedy(_ptr(X, _f64p), n, d, eps_squared(eps), _ptr(out, _i32p))
+    if L < 0:
+        raise MemoryError("oracle greedy: allocation failed")
+    return out[:L].copy()
+
+
+def range_query(X, Q, eps):
+    """CSR (offsets int64 [m+1], ids int32) with row j = {i : D(X_i, Q_j) < eps^2}."""
+    X = _f64(X)
+    Q = _f64(Q)
+    n, d = X.shape
+    m = Q.shape[0]
+    if m and Q.shape[1] != d:
+        raise ValueError("dimension mismatch")
+    lib = _load()
+    counts = np.zeros(m, dtype=np.int64)
+    e2 = eps_squared(eps)
+    if m:
+        lib.bmo_range_count(_ptr(X, _f64p), n, d, _ptr(Q, _f64p), m, e2, _ptr(counts, _i64p))
+    offsets = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(counts, out=offsets[1:])
+    ids = np.empty(max(int(offsets[-1]), 1), dtype=np.int32)
+    if m:
+        lib.bmo_range_fill(_ptr(X, _f64p), n, d, _ptr(Q, _f64p), m, e2, _ptr(offsets, _i64p),
+                           _ptr(ids, _i32p))
+    return offsets, ids[: int(offsets[-1])].copy()
+
+
+def memberships(X, landmarks, eps):
+    """Full ball of every landmark (Sec. 2.3), CSR in landmark order."""
+    X = _f64(X)
+    lm = np.asarray(landmarks, dtype=np.int64)
+    Q = X[lm] if lm.size else np.zeros((0, X.shape[1]))
+    return range_query(X, Q, eps)
+
+
+def pair_sqdist(X, Q, qrow, xcol) -> np.ndarray:
+    """D(Q[qrow[k]], X[xcol[k]]) in FP64 for listed pairs."""
+    X = _f64(X)
+    Q = _f64(Q)
+    qrow = np.ascontiguousarray(qrow, dtype=np.int32)
+    xcol = np.ascontiguousarray(xcol, dtype=np.int32)
+    out = np.empty(qrow.size, dtype=np.float64)
+    if qrow.size:
+        _load().bmo_pair_sqdist(_ptr(X, _f64p), X.shape[1], _ptr(Q, _f64p), qrow.size,
+                                _ptr(qrow, _i32p), _ptr(xcol, _i32p), _ptr(out, _f64p))
+    return out
+
+
+def edges(X, landmarks, offsets, ids, eps, prune: bool = True) -> np.ndarray:
+    """Nerve 1-skeleton as an (E, 2) int32 array of landmark ordinals, i < j,
+    lexicographic: {i, j} is an edge iff membership rows i and j intersect."""
+    X = _f64(X)
+    lm = np.ascontiguousarray(landmarks, dtype=np.int32)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    ids = np.ascontiguousarray(ids, dtype=np.int32)
+    if ids.size == 0:
+        ids = np.zeros(1, dtype=np.int32)
+    L = lm.size
+    lib = _load()
+    counts = np.zeros(max(L, 1), dtype=np.int64)
+    if L:
+        lib.bmo_edges(_ptr(X, _f64p), X.shape[1], _ptr(lm, _i32p), L, eps_squared(eps),
+                      _ptr(offsets, _i64p), _ptr(ids, _i32p), int(prune), _ptr(counts, _i64p),
+                      None, None)
+    row_off = np.zeros(L + 1, dtype=np.int64)
+    np.cumsum(counts[:L], out=row_off[1:])
+    E = int(row_off[-1])
+    out = np.empty((max(E, 1), 2), dtype=np.int32)
+    if E:
+        lib.bmo_edges(_ptr(X, _f64p), X.shape[1], _ptr(lm, _i32p), L, eps_squared(eps),
+                      _ptr(offsets, _i64p), _ptr(ids, _i32p), int(prune), None,
+                      _ptr(row_off, _i64p), _ptr(out, _i32p))
+    return out[:E].copy()
+
+
+def build(X, eps, prune: bool = True) -> dict:
+    """Exact Ball Mapper: greedy landmarks, full-ball CSR memberships, nerve edges."""
+    lm = greedy(X, eps)
+    offsets, ids = memberships(X, lm, eps)
+    e = edges(X, lm, offsets, ids, eps, prune=prune)
+    return {"landmarks": lm, "offsets": offsets, "ids": ids, "edges": e}
+
+
+def kth_nn_dist(X, k: int) -> np.ndarray:
+    """Distance from each point to its k-th nearest neighbour, itself counted first."""
+    X = _f64(X)
+    n, d = X.shape
+    out = np.empty(n, dtype=np.float64)
+    rc = _load().bmo_kth_nn_dist(_ptr(X, _f64p), n, d, int(k), _ptr(out, _f64p))
+    if rc != 0:
+        raise ValueError("kth_nn_dist failed (k out of range or allocation failure)")
+    return out
+
+
+def occupancy_eps(X, k: int) -> float:
+    """Target-occupancy scale (Sec. 5.1): median over points of the k-th NN distance.
+    An even count takes the mean of the two middle values."""
+    return float(np.median(kth_nn_dist(X, k)))
+
+
+class BallTree:
+    """Independent exact range oracle through the ball tree of Sec. 3.1."""
+
+    def __init__(self, X, leaf_size: int = 40):
+        self._X = _f64(X)
+        n, d = self._X.shape
+        self._d = d
+        self._h = _load().bmo_bt_build(_ptr(self._X, _f64p), n, d, int(leaf_size))
+        if not self._h:
+            raise MemoryError("ball tree build failed")
+
+    @property
+    def node_count(self) -> int:
+        return int(_load().bmo_bt_node_count(self._h))
+
+    def range_query(self, Q, eps):
+        Q = _f64(Q)
+        m = Q.shape[0]
+        lib = _load()
+        counts = np.zeros(max(m, 1), dtype=np.int64)
+        if m and lib.bmo_bt_range_count(self._h, _ptr(Q, _f64p), m, float(eps), _ptr(counts, _i64p)):
+            raise RuntimeError("ball tree query failed")
+        offsets = np.zeros(m + 1, dtype=np.int64)
+        np.cumsum(counts[:m], out=offsets[1:])
+        ids = np.empty(max(int(offsets[-1]), 1), dtype=np.int32)
+        if m and lib.bmo_bt_range_fill(self._h, _ptr(Q, _f64p), m, float(eps), _ptr(offsets, _i64p),
+                                       _ptr(ids, _i32p)):
+            raise RuntimeError("ball tree query failed")
+        return offsets, ids[: int(offsets[-1])].copy()
+
+    def close(self):
+        if self._h:
+            _load().bmo_bt_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

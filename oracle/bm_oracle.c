@@ -1,0 +1,411 @@
+/*
+ * bm_oracle.c -- plain, slow CPU oracle for exact Ball Mapper construction.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library calls, links or
+ * loads this file; only the tests, the package's smoke check and the CPU
+ * baseline leg of the benchmark do.  It shares no code, header, table or
+ * helper with the CUDA path.
+ *
+ * Every routine follows a definition of the paper literally, in FP64:
+ *   - squared distance  D(a,b) = sum_i (a_i - b_i)^2, summed in index order
+ *     (Euclidean metric, Sec. 2.1 and Sec. 5.1);
+ *   - open ball / exact range set  R_r(q) = { x : d(q,x) < r }
+ *     (Sec. 2.1, ball definition; Sec. 4, Def. of the exact range oracle),
+ *     evaluated as D(q,x) < r^2 by a full scan over all points;
+ *   - greedy epsilon-net (Sec. 2.2 procedure): while a point is uncovered,
+ *     select one (the smallest uncovered index), add it to the landmark set
+ *     and mark every point of its open ball covered;
+ *   - ball membership X_i = X intersect B(l_i, eps), the full ball (Sec. 2.3);
+ *   - nerve 1-skeleton (Sec. 2.1 nerve definition, Sec. 4.2 Def. of N_r(L)):
+ *     edge {i,j} iff the two membership lists intersect;
+ *   - target-occupancy scale (Sec. 5.1): distance of each point to its k-th
+ *     nearest neighbour, the point itself counted first;
+ *   - ball tree construction and range query (Sec. 3.1), an independent
+ *     exact range oracle used to cross-check the brute force one.
+ *
+ * Parallelism: outer loops whose iterations are independent (one query row,
+ * one landmark pair row, one k-NN row) run under OpenMP.  This does not
+ * change any arithmetic: each value is still computed by the same sequential
+ * FP64 sum.  Compile with -ffp-contract=off so that no multiply-add is fused.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* D(a,b) = sum_{i<d} (a_i - b_i)^2 in FP64, index order. */
+static double sqdist(const double* a, const double* b, int d) {
+    double s = 0.0;
+    for (int i = 0; i < d; ++i) {
+        double t = a[i] - b[i];
+        s += t * t;
+    }
+    return s;
+}
+
+int bmo_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void bmo_set_num_threads(int t) {
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}
+
+/* ---------------------------------------------------------------------------
+ * Greedy epsilon-net, Sec. 2.2.  The selection rule "select an uncovered
+ * point" is read as: the smallest uncovered index.  Marking covers the open
+ * ball: D(x, y) < eps2.  Returns the landmark count; landmarks[] receives the
+ * landmark ids in selection order (hence strictly increasing).
+ * ------------------------------------------------------------------------- */
+int64_t bmo_greedy(const double* X, int64_t n, int d, double eps2, int32_t* landmarks) {
+    unsigned char* covered = (unsigned char*)calloc((size_t)(n > 0 ? n : 1), 1);
+    if (!covered) return -1;
+    int64_t L = 0;
+    for (int64_t x = 0; x < n; ++x) {
+        if (covered[x]) continue;
+        landmarks[L++] = (int32_t)x;
+        const double* px = X + (size_t)x * d;
+        #pragma omp parallel for schedule(static)
+        for (int64_t y = 0; y < n; ++y) {
+            if (sqdist(px, X + (size_t)y * d, d) < eps2) covered[y] = 1;
+        }
+    }
+    free(covered);
+    return L;
+}
+
+/* ---------------------------------------------------------------------------
+ * Exact range oracle R_r(q) by full scan (Sec. 4 definition), two phases.
+ * counts[j] = |{ i : D(X_i, Q_j) < eps2 }|.
+ * ------------------------------------------------------------------------- */
+void bmo_range_count(const double* X, int64_t n, int d, const double* Q, int64_t m,
+                     double eps2, int64_t* counts) {
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t j = 0; j < m; ++j) {
+        const double* q = Q + (size_t)j * d;
+        int64_t c = 0;
+        for (int64_t i = 0; i < n; ++i)
+            if (sqdist(q, X + (size_t)i * d, d) < eps2) ++c;
+        counts[j] = c;
+    }
+}
+
+/* ids[offsets[j] ..] = the members of R(Q_j) in ascending index order. */
+void bmo_range_fill(const double* X, int64_t n, int d, const double* Q, int64_t m,
+                    double eps2, const int64_t* offsets, int32_t* ids) {
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t j = 0; j < m; ++j) {
+        const double* q = Q + (size_t)j * d;
+        int64_t o = offsets[j];
+        for (int64_t i = 0; i < n; ++i)
+            if (sqdist(q, X + (size_t)i * d, d) < eps2) ids[o++] = (int32_t)i;
+    }
+}
+
+/* Exact squared distances for listed (row, col) pairs: out[k] = D(Q_row, X_col). */
+void bmo_pair_sqdist(const double* X, int d, const double* Q, int64_t npairs,
+                     const int32_t* qrow, const int32_t* xcol, double* out) {
+    #pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < npairs; ++k)
+        out[k] = sqdist(Q + (size_t)qrow[k] * d, X + (size_t)xcol[k] * d, d);
+}
+
+/* ---------------------------------------------------------------------------
+ * Nerve 1-skeleton (Sec. 2.1, Sec. 4.2): for landmark ordinals i < j the edge
+ * exists iff the sorted membership lists of rows i and j share an id.
+ *
+ * With prune != 0, pairs whose landmarks are at squared distance above
+ * 4*eps2 (with a relative margin of 1e-9) are skipped without intersecting:
+ * a common member x would give d(l_i,l_j) <= d(l_i,x) + d(x,l_j) < 2 eps by
+ * the triangle inequality (metric axiom 4, Sec. 2.1), so such pairs have no
+ * edge.  The tests check that pruning changes nothing.
+ *
+ * Two phases: edges == NULL counts per row i into row_counts (length L);
+ * otherwise edges (2 ints per edge, lexicographic) are written at
+ * row_offsets[i].
+ * ------------------------------------------------------------------------- */
+static int lists_intersect(const int32_t* a, int64_t na, const int32_t* b, int64_t nb) {
+    int64_t p = 0, q = 0;
+    while (p < na && q < nb) {
+        if (a[p] == b[q]) return 1;
+        if (a[p] < b[q]) ++p; else ++q;
+    }
+    return 0;
+}
+
+void bmo_edges(const double* X, int d, const int32_t* landmarks, int64_t L, double eps2,
+               const int64_t* offsets, const int32_t* ids, int prune,
+               int64_t* row_counts, const int64_t* row_offsets, int32_t* edges) {
+    const double lim = 4.0 * eps2 * (1.0 + 1e-9);
+    #pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t i = 0; i < L; ++i) {
+        const double* li = X + (size_t)landmarks[i] * d;
+        int64_t c = 0;
+        int64_t o = edges ? row_offsets[i] : 0;
+        for (int64_t j = i + 1; j < L; ++j) {
+            if (prune && sqdist(li, X + (size_t)landmarks[j] * d, d) > lim) continue;
+            if (lists_intersect(ids + offsets[i], offsets[i + 1] - offsets[i],
+                                ids + offsets[j], offsets[j + 1] - offsets[j])) {
+                if (edges) {
+                    edges[2 * o] = (int32_t)i;
+                    edges[2 * o + 1] = (int32_t)j;
+                    ++o;
+                } else {
+                    ++c;
+                }
+            }
+        }
+        if (!edges) row_counts[i] = c;
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * Target-occupancy scale, Sec. 5.1: for each point the distance to its k-th
+ * nearest neighbour, the point itself counted as the first.  Brute force:
+ * all n squared distances of the row, then the k-th smallest by selection.
+ * out[i] = sqrt(k-th smallest D(X_i, .)).
+ * ------------------------------------------------------------------------- */
+static double kth_smallest(double* v, int64_t n, int64_t k /* 0-based */) {
+    int64_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        double pivot = v[lo + (hi - lo) / 2];
+        int64_t i = lo, j = hi;
+        while (i <= j) {
+            while (v[i] < pivot) ++i;
+            while (v[j] > pivot) --j;
+            if (i <= j) { double t = v[i]; v[i] = v[j]; v[j] = t; ++i; --j; }
+        }
+        if (k <= j) hi = j;
+        else if (k >= i) lo = i;
+        else return v[k];
+    }
+    return v[k];
+}
+
+int bmo_kth_nn_dist(const double* X, int64_t n, int d, int64_t k, double* out) {
+    if (k < 1 || k > n) return -1;
+    int bad = 0;
+    #pragma omp parallel
+    {
+        double* row = (double*)malloc(sizeof(double) * (size_t)n);
+        if (!row) {
+            #pragma omp atomic write
+            bad = 1;
+        }
+        #pragma omp for schedule(dynamic, 16)
+        for (int64_t i = 0; i < n; ++i) {
+            if (!row) continue;
+            const double* p = X + (size_t)i * d;
+            for (int64_t j = 0; j < n; ++j) row[j] = sqdist(p, X + (size_t)j * d, d);
+            out[i] = sqrt(kth_smallest(row, n, k - 1));
+        }
+        free(row);
+    }
+    return bad ? -1 : 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Ball tree, Sec. 3.1.  Node centre c_i = (max_i + min_i)/2 over its points;
+ * radius R = max_x d(c, x); split by p_A = farthest point from c and
+ * p_B = farthest point from p_A; a point goes to X_A when it is closer to p_A
+ * than to p_B, otherwise (ties included) to X_B.  Recursion stops when the
+ * node holds at most leaf_size points, or the split leaves a side empty
+ * (all points identical).
+ *
+ * Range query: a node is discarded when d(q,c) - R > r (triangle
+ * inequality); a margin of 1e-9 (R + r) keeps FP64 square-root rounding from
+ * discarding a true member.  Leaves are scanned with the exact test
+ * D(q,x) < r^2, the same test as the brute-force oracle.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int64_t begin, end;     /* range in the permutation array */
+    int32_t left, right;    /* child node ids, -1 for leaves  */
+    double radius;
+    int64_t centre;         /* offset of the centre in the centre pool */
+} bt_node;
+
+typedef struct {
+    const double* X;
+    int d;
+    int64_t n;
+    int32_t* perm;
+    bt_node* nodes;
+    int64_t n_nodes, cap_nodes;
+    double* centres;
+    int leaf_size;
+} bt_tree;
+
+static int64_t bt_new_node(bt_tree* t) {
+    if (t->n_nodes == t->cap_nodes) {
+        int64_t nc = t->cap_nodes ? 2 * t->cap_nodes : 64;
+        bt_node* nn = (bt_node*)realloc(t->nodes, sizeof(bt_node) * (size_t)nc);
+        double* cc = (double*)realloc(t->centres, sizeof(double) * (size_t)nc * (size_t)t->d);
+        if (!nn || !cc) { if (nn) t->nodes = nn; if (cc) t->centres = cc; return -1; }
+        t->nodes = nn; t->centres = cc; t->cap_nodes = nc;
+    }
+    return t->n_nodes++;
+}
+
+static int bt_build_node(bt_tree* t, int64_t begin, int64_t end) {
+    int64_t id = bt_new_node(t);
+    if (id < 0) return -1;
+    const int d = t->d;
+    const double* X = t->X;
+    int32_t* perm = t->perm;
+    double* c = t->centres + (size_t)id * d;
+    for (int i = 0; i < d; ++i) {
+        double mx = -INFINITY, mn = INFINITY;
+        for (int64_t p = begin; p < end; ++p) {
+            double v = X[(size_t)perm[p] * d + i];
+            if (v > mx) mx = v;
+            if (v < mn) mn = v;
+        }
+        c[i] = (mx + mn) / 2.0;
+    }
+    double r2 = 0.0;
+    int64_t pa = begin;
+    for (int64_t p = begin; p < end; ++p) {
+        double s = sqdist(c, X + (size_t)perm[p] * d, d);
+        if (s > r2) { r2 = s; pa = p; }
+    }
+    bt_node* nd = &t->nodes[id];
+    nd->begin = begin; nd->end = end; nd->left = nd->right = -1;
+    nd->radius = sqrt(r2);
+    nd->centre = id * d;
+    if (end - begin <= t->leaf_size || r2 == 0.0) return (int)id;
+
+    const double* xa = X + (size_t)perm[pa] * d;
+    double far2 = -1.0;
+    int64_t pb = begin;
+    for (int64_t p = begin; p < end; ++p) {
+        double s = sqdist(xa, X + (size_t)perm[p] * d, d);
+        if (s > far2) { far2 = s; pb = p; }
+    }
+    const double* xb = X + (size_t)perm[pb] * d;
+    /* stable partition: X_A first (closer to p_A), then X_B */
+    int64_t cnt = end - begin;
+    int32_t* tmp = (int32_t*)malloc(sizeof(int32_t) * (size_t)cnt);
+    if (!tmp) return -1;
+    int64_t na = 0, nb = 0;
+    for (int64_t p = begin; p < end; ++p) {
+        const double* xp = X + (size_t)perm[p] * d;
+        if (sqdist(xp, xa, d) < sqdist(xp, xb, d)) perm[begin + na++] = perm[p];
+        else tmp[nb++] = perm[p];
+    }
+    memcpy(perm + begin + na, tmp, sizeof(int32_t) * (size_t)nb);
+    free(tmp);
+    if (na == 0 || nb == 0) return (int)id;   /* cannot split further */
+    int l = bt_build_node(t, begin, begin + na);
+    if (l < 0) return -1;
+    int r = bt_build_node(t, begin + na, end);
+    if (r < 0) return -1;
+    t->nodes[id].left = l;
+    t->nodes[id].right = r;
+    return (int)id;
+}
+
+void* bmo_bt_build(const double* X, int64_t n, int d, int leaf_size) {
+    bt_tree* t = (bt_tree*)calloc(1, sizeof(bt_tree));
+    if (!t) return NULL;
+    t->X = X; t->d = d; t->n = n; t->leaf_size = leaf_size > 0 ? leaf_size : 40;
+    t->perm = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    if (!t->perm) { free(t); return NULL; }
+    for (int64_t i = 0; i < n; ++i) t->perm[i] = (int32_t)i;
+    if (n > 0 && bt_build_node(t, 0, n) < 0) {
+        free(t->perm); free(t->nodes); free(t->centres); free(t);
+        return NULL;
+    }
+    return t;
+}
+
+void bmo_bt_free(void* h) {
+    bt_tree* t = (bt_tree*)h;
+    if (!t) return;
+    free(t->perm); free(t->nodes); free(t->centres); free(t);
+}
+
+int64_t bmo_bt_node_count(void* h) { return ((bt_tree*)h)->n_nodes; }
+
+static int cmp_i32(const void* a, const void* b) {
+    int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+    return (x > y) - (x < y);
+}
+
+/* Members of R_r(q) via the tree; returns the count, writes at most cap ids
+ * (sorted ascending when all fit).  Iterative traversal with an explicit stack. */
+static int64_t bt_query(const bt_tree* t, const double* q, double r, double r2,
+                        int32_t* out, int64_t cap) {
+    if (t->n == 0) return 0;
+    /* a depth-first stack never holds more entries than there are nodes */
+    int32_t* stack = (int32_t*)malloc(sizeof(int32_t) * (size_t)(t->n_nodes + 1));
+    if (!stack) return -1;
+    int64_t sp = 0;
+    int64_t cnt = 0;
+    stack[sp++] = 0;
+    while (sp > 0) {
+        const bt_node* nd = &t->nodes[stack[--sp]];
+        double dc = sqrt(sqdist(q, t->centres + nd->centre, t->d));
+        if (dc - nd->radius > r + 1e-9 * (nd->radius + r)) continue;   /* pruned */
+        if (nd->left < 0) {
+            for (int64_t p = nd->begin; p < nd->end; ++p) {
+                int32_t id = t->perm[p];
+                if (sqdist(q, t->X + (size_t)id * t->d, t->d) < r2) {
+                    if (cnt < cap) out[cnt] = id;
+                    ++cnt;
+                }
+            }
+        } else {
+            stack[sp++] = nd->right;
+            stack[sp++] = nd->left;
+        }
+    }
+    free(stack);
+    if (cnt <= cap) qsort(out, (size_t)cnt, sizeof(int32_t), cmp_i32);
+    return cnt;
+}
+
+/* Batched ball-tree range queries, two phases like bmo_range_count/fill. */
+int bmo_bt_range_count(void* h, const double* Q, int64_t m, double r, int64_t* counts) {
+    const bt_tree* t = (const bt_tree*)h;
+    int bad = 0;
+    const double r2 = r * r;
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t j = 0; j < m; ++j) {
+        int64_t c = bt_query(t, Q + (size_t)j * t->d, r, r2, NULL, 0);
+        if (c < 0) {
+            #pragma omp atomic write
+            bad = 1;
+        }
+        counts[j] = c;
+    }
+    return bad ? -1 : 0;
+}
+
+int bmo_bt_range_fill(void* h, const double* Q, int64_t m, double r, const int64_t* offsets,
+                      int32_t* ids) {
+    const bt_tree* t = (const bt_tree*)h;
+    int bad = 0;
+    const double r2 = r * r;
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t j = 0; j < m; ++j) {
+        int64_t cap = offsets[j + 1] - offsets[j];
+        int64_t c = bt_query(t, Q + (size_t)j * t->d, r, r2, ids + offsets[j], cap);
+        if (c != cap) {
+            #pragma omp atomic write
+            bad = 1;
+        }
+    }
+    return bad ? -1 : 0;
+}

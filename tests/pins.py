@@ -1,0 +1,207 @@
+"""Checks that pin the CPU oracle to facts fixed by the paper and by mathematics.
+
+Each ``pin_*`` raises AssertionError when the oracle disagrees.  They are used
+by ``test_oracle_pins.py`` on the real oracle and by ``test_oracle_mutants.py``
+on deliberately broken copies of it (every planted mistake must trip a pin).
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+
+import oracle
+from oracle import brute
+from paper_2601_01405_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def rows(offsets, ids):
+    return [ids[offsets[i]:offsets[i + 1]].tolist() for i in range(len(offsets) - 1)]
+
+
+def sqd(X, Y):
+    """All-pairs FP64 squared distances by the direct formula (numpy broadcasting)."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    return ((X[:, None, :] - Y[None, :, :]) ** 2).sum(axis=2)
+
+
+def _check_case(out, case):
+    assert out["landmarks"].tolist() == case["landmarks"], ("landmarks", out["landmarks"], case)
+    assert rows(out["offsets"], out["ids"]) == case["members"], ("members", case["eps"])
+    assert out["edges"].tolist() == case["edges"], ("edges", out["edges"], case)
+
+
+def pin_line():
+    g = golden("line.json")
+    for d in (1, 3):
+        X = W.line_points(10, d)
+        for case in g["cases"]:
+            _check_case(oracle.build(X, case["eps"]), case)
+
+
+def pin_grid():
+    g = golden("grid.json")
+    X = W.grid_points(3)
+    for case in g["cases"]:
+        _check_case(oracle.build(X, case["eps"]), case)
+
+
+def pin_degenerate():
+    # n = 0
+    out = oracle.build(np.zeros((0, 3), dtype=np.float32), 1.0)
+    assert out["landmarks"].size == 0 and out["edges"].size == 0 and out["offsets"].tolist() == [0]
+    # n = 1
+    out = oracle.build(np.ones((1, 4), dtype=np.float32), 0.5)
+    assert out["landmarks"].tolist() == [0] and rows(out["offsets"], out["ids"]) == [[0]]
+    # all points identical: one landmark, everyone a member (0 < eps), no edge
+    X = np.full((7, 2), 0.25, dtype=np.float32)
+    out = oracle.build(X, 1e-3)
+    assert out["landmarks"].tolist() == [0]
+    assert rows(out["offsets"], out["ids"]) == [list(range(7))]
+    assert out["edges"].shape[0] == 0
+    # eps larger than the diameter: a single ball holds everything
+    X = W.isotropic(50, 3, 10, seed=5)
+    out = oracle.build(X, 1e3)
+    assert out["landmarks"].tolist() == [0] and out["ids"].tolist() == list(range(50))
+    # d = 1, two far groups: two landmarks, no edge
+    X = np.array([[0.0], [0.5], [10.0], [10.25]], dtype=np.float32)
+    out = oracle.build(X, 1.0)
+    assert out["landmarks"].tolist() == [0, 2]
+    assert rows(out["offsets"], out["ids"]) == [[0, 1], [2, 3]]
+    assert out["edges"].shape[0] == 0
+
+
+def pin_brute(seeds=range(40)):
+    """Tiny tie-heavy clouds against the exact rational brute force (brute.py)."""
+    for s in seeds:
+        rng = np.random.default_rng(1000 + s)
+        n = int(rng.integers(1, 13))
+        d = int(rng.integers(1, 4))
+        k = 2
+        X = W.tiny_grid_cloud(n, d, k, span=6, seed=s)
+        eps = float(rng.choice([0.5, 0.75, 1.0, 1.25, 1.5, 2.0]))
+        ref = brute.build(X, eps, k)
+        out = oracle.build(X, eps)
+        assert out["landmarks"].tolist() == ref["landmarks"], (s, "landmarks")
+        assert rows(out["offsets"], out["ids"]) == ref["members"], (s, "members")
+        assert [tuple(e) for e in out["edges"].tolist()] == ref["edges"], (s, "edges")
+
+
+def pin_fixpoint(X, eps):
+    """The index-order greedy result is the unique L with
+    x in L  <=>  no l in L, l < x, has D(l, x) < eps^2."""
+    lm = oracle.greedy(X, eps)
+    D = sqd(X[lm], X)
+    inside = D < oracle.eps_squared(eps)
+    n = X.shape[0]
+    is_lm = np.zeros(n, dtype=bool)
+    is_lm[lm] = True
+    earlier = lm[:, None] < np.arange(n)[None, :]
+    covered_by_earlier = (inside & earlier).any(axis=0)
+    assert np.array_equal(is_lm, ~covered_by_earlier)
+
+
+def pin_invariants(X, eps):
+    """eps-net (Def. 2.1 / rho-cover and alpha-separation, Sec. 4.1 with delta = 0),
+    memberships equal to the full balls, CSR rows sorted and unique."""
+    out = oracle.build(X, eps)
+    lm, off, ids = out["landmarks"], out["offsets"], out["ids"]
+    e2 = oracle.eps_squared(eps)
+    assert np.all(np.diff(lm) > 0)
+    D = sqd(X[lm], X)
+    # membership = full open ball, in ascending id order
+    for i in range(lm.size):
+        assert ids[off[i]:off[i + 1]].tolist() == np.nonzero(D[i] < e2)[0].tolist()
+    # cover: every point within eps of some landmark; landmarks are members of their own balls
+    assert (D < e2).any(axis=0).all()
+    # separation: distinct landmarks at squared distance >= eps^2
+    DL = D[:, lm]
+    np.fill_diagonal(DL, np.inf)
+    assert (DL >= e2).all()
+    return out
+
+
+def pin_witness(X, eps):
+    """Edge {i,j} exists iff the witness radius tau_ij < eps (Sec. 4.2):
+    tau_ij^2 = min_x max(D(x,l_i), D(x,l_j))."""
+    out = oracle.build(X, eps)
+    lm = out["landmarks"]
+    D = sqd(X[lm], X)
+    e2 = oracle.eps_squared(eps)
+    L = lm.size
+    expect = []
+    for i in range(L):
+        tau2 = np.maximum(D[i][None, :], D[i + 1:]).min(axis=1) if i + 1 < L else np.zeros(0)
+        for off, t in enumerate(tau2):
+            if t < e2:
+                expect.append((i, i + 1 + off))
+    assert [tuple(e) for e in out["edges"].tolist()] == expect
+
+
+def pin_prune(X, eps):
+    out = oracle.build(X, eps, prune=True)
+    e0 = oracle.edges(X, out["landmarks"], out["offsets"], out["ids"], eps, prune=False)
+    assert np.array_equal(out["edges"], e0)
+
+
+def pin_balltree(X, eps, Q=None):
+    """An exact accelerated range query preserves every range set (Sec. 3.1 ball tree
+    against the Sec. 4 full scan)."""
+    if Q is None:
+        Q = X[oracle.greedy(X, eps)]
+    bt = oracle.BallTree(X, leaf_size=40)
+    o1, i1 = bt.range_query(Q, eps)
+    o2, i2 = oracle.range_query(X, Q, eps)
+    assert np.array_equal(o1, o2) and np.array_equal(i1, i2)
+    assert bt.node_count > 1 or X.shape[0] <= 40
+
+
+def pin_knn_scipy(X, k):
+    """k-th NN distance (self counted first) against scipy's kd-tree."""
+    from scipy.spatial import cKDTree
+    ref = cKDTree(np.asarray(X, dtype=np.float64)).query(np.asarray(X, dtype=np.float64), k=k)[0][:, -1]
+    got = oracle.kth_nn_dist(X, k)
+    assert np.allclose(got, ref, rtol=1e-12, atol=0.0)
+
+
+def pin_range_scipy(X, Q, eps):
+    """Range sets on continuous (tie-free) data against scipy's kd-tree ball query.
+    scipy's ball is closed; with no point at distance exactly eps it equals the open ball."""
+    from scipy.spatial import cKDTree
+    X64 = np.asarray(X, dtype=np.float64)
+    Q64 = np.asarray(Q, dtype=np.float64)
+    D = np.sqrt(sqd(Q64, X64))
+    assert not np.any(np.abs(D - eps) < 1e-9), "data has a near-tie; choose another eps"
+    ref = cKDTree(X64).query_ball_point(Q64, r=eps)
+    off, ids = oracle.range_query(X64, Q64, eps)
+    for j in range(Q64.shape[0]):
+        assert ids[off[j]:off[j + 1]].tolist() == sorted(ref[j])
+
+
+def pin_pair_sqdist(X):
+    """Squared distances of listed pairs equal the direct numpy formula."""
+    rng = np.random.default_rng(3)
+    qrow = rng.integers(0, X.shape[0], 200)
+    xcol = rng.integers(0, X.shape[0], 200)
+    got = oracle.pair_sqdist(X, X, qrow, xcol)
+    ref = ((X[qrow].astype(np.float64) - X[xcol].astype(np.float64)) ** 2).sum(axis=1)
+    assert np.array_equal(got, ref)
+
+
+def pin_paper():
+    g = golden("paper_gaussian.json")
+    X = W.paper_gaussian_fp64(g["n"], g["d"], seed=0)
+    eps = oracle.occupancy_eps(X, g["k"])
+    assert abs(eps - g["eps_printed"]) < g["eps_tolerance"], eps
+    out = oracle.build(X, eps)
+    assert out["landmarks"].size == g["landmarks"]
+    assert out["edges"].shape[0] == g["edges"]
