@@ -1,0 +1,144 @@
+/*
+ * ballmapper.h -- C-ABI of the GB300 exact Ball Mapper library (libballmapper.so).
+ *
+ * The operations follow the paper's statement of the problem:
+ *   - the exact range oracle R_r(q) = { x in X : d(q,x) < r }            (Sec. 4, Def. "exact range set")
+ *   - the greedy epsilon-net: while a point is uncovered, select one,     (Sec. 2.2)
+ *     add it to the landmark set and cover its open ball; the point
+ *     selected is always the smallest uncovered index
+ *   - ball memberships X_i = X intersect B(l_i, eps), full open balls     (Sec. 2.3; ball definition Sec. 2.1)
+ *   - the Ball Mapper graph = 1-skeleton of the nerve: an edge {i,j}      (Sec. 2.1 nerve; Sec. 4.2 N_r(L), G_r(L))
+ *     for every landmark pair whose balls share a data point
+ * The metric is Euclidean (Sec. 5.1).  Distances are decided exactly: the
+ * result equals the one obtained with FP64 squared distances summed in
+ * coordinate order, for any finite float32 input.
+ *
+ * Conventions shared by every entry point
+ *   - Points are float32, row-major, n rows of d contiguous coordinates.
+ *   - By default every pointer argument (inputs and outputs) is DEVICE
+ *     memory of the current CUDA device and all work is ordered on
+ *     opt->stream.  With opt->host_io != 0, inputs are host pointers (copied
+ *     in on the stream) and outputs are returned in host memory; the call
+ *     then returns only after the stream work is complete.
+ *   - Outputs are allocated by the library (opt->alloc / opt->free when
+ *     given, else cudaMallocAsync / cudaFreeAsync on the stream, or malloc
+ *     for host outputs) and released by the caller with bm_csr_free /
+ *     bm_graph_free, passing the same options.
+ *   - The caller keeps ownership of its inputs; they are only read.
+ *   - Every call returns a bm_status; nothing throws across the ABI.  On
+ *     error the output struct is zeroed, nothing is leaked, and
+ *     bm_last_error() returns a thread-local message.
+ *   - Ids are int32: n must be below 2^31.  Identical inputs give identical
+ *     output bytes.
+ */
+#ifndef BALLMAPPER_H
+#define BALLMAPPER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define BM_API __attribute__((visibility("default")))
+#else
+#define BM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BM_OK = 0,
+    BM_ERR_ARG = 1,        /* invalid argument (null pointer, n or d out of range, eps not finite > 0, NaN/Inf input) */
+    BM_ERR_CUDA = 2,       /* a CUDA runtime call failed; see bm_last_error() */
+    BM_ERR_NOMEM = 3,      /* an allocation failed */
+    BM_ERR_CAPACITY = 4,   /* an output exceeds a hard limit (e.g. more than 2^31-1 edges) */
+    BM_ERR_TIMEOUT = 5,    /* a bounded device-side wait expired; the context is still usable */
+    BM_ERR_UNSUPPORTED = 6 /* the device is not sm_103 (GB300) or lacks a needed feature */
+} bm_status;
+
+/* Distance-tile arithmetic.  Both are exact: pairs whose approximate value
+ * lies within the proven error band of eps^2 are re-decided in FP64. */
+typedef enum {
+    BM_PATH_TC_SPLIT3 = 0, /* tcgen05 tensor cores: BF16 hi/lo split products, FP32 accumulation in TMEM */
+    BM_PATH_FP32 = 1       /* plain FP32 CUDA-core tiles (comparison path) */
+} bm_path;
+
+/* Allocation callbacks: return device (or, for host outputs, ignored) memory
+ * of at least `bytes` bytes ordered on `stream`; NULL signals failure. */
+typedef void* (*bm_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*bm_free_fn)(void* ptr, void* stream, void* ctx);
+
+typedef struct {
+    void* stream;          /* cudaStream_t; NULL = legacy default stream */
+    int32_t path;          /* bm_path */
+    int32_t host_io;       /* 0: device pointers in and out; 1: host pointers in and out */
+    int32_t batch;         /* greedy candidates per step, 32..1024, multiple of 32; 0 = automatic */
+    int32_t reserved0;
+    bm_alloc_fn alloc;     /* optional device allocator for outputs and scratch */
+    bm_free_fn free;
+    void* alloc_ctx;
+} bm_options;
+
+typedef struct {
+    int64_t distance_evals;   /* algorithmic exact decisions: rows x n (memberships / range query) */
+    int64_t tile_pairs;       /* pairs evaluated by the distance tiles, speculative candidates included */
+    int64_t band_pairs;       /* pairs re-decided in FP64 (inside the error band) */
+    int64_t greedy_steps;     /* candidate batches processed by the greedy */
+    int64_t candidates;       /* candidates examined by the greedy */
+    int64_t edge_pairs;       /* (i<j) landmark pairs emitted by the nerve pass before deduplication */
+    double ms_prep, ms_greedy, ms_members, ms_edges, ms_total;  /* device time per phase */
+    float band_delta;         /* half-width of the error band used (in units of (eps^2 - D)/2) */
+    int32_t path;             /* bm_path actually used */
+} bm_stats;
+
+typedef struct {
+    int64_t rows;       /* number of rows */
+    int64_t nnz;        /* number of stored ids */
+    int64_t* offsets;   /* rows + 1 entries; row r is ids[offsets[r] .. offsets[r+1]) */
+    int32_t* ids;       /* point ids, ascending within each row */
+    int32_t on_host;    /* 1 when offsets/ids are host memory */
+    int32_t reserved0;
+} bm_csr;
+
+typedef struct {
+    int64_t n_landmarks;
+    int32_t* landmarks;   /* point ids in greedy order (strictly increasing) */
+    bm_csr members;       /* row i = R_eps(landmarks[i]), the full open ball */
+    int64_t n_edges;
+    int32_t* edges;       /* 2 * n_edges landmark ordinals (i, j), i < j, lexicographic, unique */
+    int32_t on_host;
+    int32_t reserved0;
+    bm_stats stats;
+} bm_graph;
+
+/* Fill *opt with defaults (default stream, tensor-core path, device I/O). */
+BM_API void bm_options_init(bm_options* opt);
+
+/* Exact range query, Sec. 4: out row j = { i : ||X_i - Q_j|| < eps }.
+ * X: n x d float32; Q: m x d float32; eps > 0 finite.  n = 0 or m = 0 give
+ * empty rows (X or Q may then be NULL).  stats may be NULL. */
+BM_API bm_status bm_range_query(const float* X, int64_t n, int32_t d, const float* Q, int64_t m,
+                         float eps, const bm_options* opt, bm_csr* out, bm_stats* stats);
+
+/* Ball Mapper construction, Sec. 2.2 (greedy epsilon-net in index order),
+ * Sec. 2.3 (full-ball memberships) and Sec. 2.1 / Sec. 4.2 (nerve edges).
+ * n = 0 gives an empty graph. */
+BM_API bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_options* opt,
+                   bm_graph* out);
+
+/* Release outputs (safe on zeroed structs); pass the options used to create them. */
+BM_API void bm_csr_free(bm_csr* csr, const bm_options* opt);
+BM_API void bm_graph_free(bm_graph* g, const bm_options* opt);
+
+BM_API const char* bm_status_string(bm_status s);
+BM_API const char* bm_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+BM_API int32_t bm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BALLMAPPER_H */

@@ -1,0 +1,266 @@
+"""ctypes binding of libballmapper's C-ABI (``include/ballmapper.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device inputs are torch CUDA tensors; the library's outputs and
+scratch are allocated through a callback into torch's caching allocator, so
+the returned device arrays are torch tensors that own their memory.  Host
+inputs (numpy arrays or CPU tensors) select the library's host I/O mode.
+
+There is no CPU fallback: if the library is not built, or no GB300 is
+present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libballmapper.so")
+
+BM_OK, BM_ERR_ARG, BM_ERR_CUDA, BM_ERR_NOMEM, BM_ERR_CAPACITY, BM_ERR_TIMEOUT, BM_ERR_UNSUPPORTED = range(7)
+BM_PATH_TC_SPLIT3, BM_PATH_FP32 = 0, 1
+PATHS = {"tc": BM_PATH_TC_SPLIT3, "fp32": BM_PATH_FP32}
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class bm_options(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_void_p), ("path", ctypes.c_int32), ("host_io", ctypes.c_int32),
+                ("batch", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("alloc", ALLOC_FN),
+                ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
+
+
+class bm_stats(ctypes.Structure):
+    _fields_ = [("distance_evals", ctypes.c_int64), ("tile_pairs", ctypes.c_int64), ("band_pairs", ctypes.c_int64),
+                ("greedy_steps", ctypes.c_int64), ("candidates", ctypes.c_int64), ("edge_pairs", ctypes.c_int64),
+                ("ms_prep", ctypes.c_double), ("ms_greedy", ctypes.c_double), ("ms_members", ctypes.c_double),
+                ("ms_edges", ctypes.c_double), ("ms_total", ctypes.c_double), ("band_delta", ctypes.c_float),
+                ("path", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class bm_csr(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int64), ("nnz", ctypes.c_int64), ("offsets", ctypes.c_void_p),
+                ("ids", ctypes.c_void_p), ("on_host", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+
+
+class bm_graph(ctypes.Structure):
+    _fields_ = [("n_landmarks", ctypes.c_int64), ("landmarks", ctypes.c_void_p), ("members", bm_csr),
+                ("n_edges", ctypes.c_int64), ("edges", ctypes.c_void_p), ("on_host", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("stats", bm_stats)]
+
+
+class BallMapperError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+STATUS_NAMES = {BM_OK: "BM_OK", BM_ERR_ARG: "BM_ERR_ARG", BM_ERR_CUDA: "BM_ERR_CUDA", BM_ERR_NOMEM: "BM_ERR_NOMEM",
+                BM_ERR_CAPACITY: "BM_ERR_CAPACITY", BM_ERR_TIMEOUT: "BM_ERR_TIMEOUT",
+                BM_ERR_UNSUPPORTED: "BM_ERR_UNSUPPORTED"}
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH):
+    """Load libballmapper.so (raises if it has not been built)."""
+    global _lib
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError("libballmapper.so is not built (%s); run __graft_entry__.build()" % path)
+        lib = ctypes.CDLL(path)
+        lib.bm_options_init.argtypes = [ctypes.POINTER(bm_options)]
+        lib.bm_options_init.restype = None
+        lib.bm_range_query.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_int64, ctypes.c_float, ctypes.POINTER(bm_options),
+                                       ctypes.POINTER(bm_csr), ctypes.POINTER(bm_stats)]
+        lib.bm_range_query.restype = ctypes.c_int
+        lib.bm_build.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_float,
+                                 ctypes.POINTER(bm_options), ctypes.POINTER(bm_graph)]
+        lib.bm_build.restype = ctypes.c_int
+        lib.bm_csr_free.argtypes = [ctypes.POINTER(bm_csr), ctypes.POINTER(bm_options)]
+        lib.bm_csr_free.restype = None
+        lib.bm_graph_free.argtypes = [ctypes.POINTER(bm_graph), ctypes.POINTER(bm_options)]
+        lib.bm_graph_free.restype = None
+        lib.bm_status_string.argtypes = [ctypes.c_int]
+        lib.bm_status_string.restype = ctypes.c_char_p
+        lib.bm_last_error.argtypes = []
+        lib.bm_last_error.restype = ctypes.c_char_p
+        lib.bm_version.argtypes = []
+        lib.bm_version.restype = ctypes.c_int32
+        _lib = lib
+        return lib
+
+
+def _check(lib, status):
+    if status != BM_OK:
+        raise BallMapperError(status, lib.bm_last_error().decode(errors="replace"))
+
+
+class _TorchAllocator:
+    """Routes the library's device allocations to torch's caching allocator."""
+
+    def __init__(self, device):
+        import torch
+        self._torch = torch
+        self._device = device
+        self.live = {}
+        self.failed = False
+
+        def _alloc(nbytes, stream, ctx):
+            try:
+                t = torch.empty(int(nbytes), dtype=torch.uint8, device=self._device)
+            except Exception:
+                self.failed = True
+                return None
+            p = t.data_ptr()
+            self.live[p] = t
+            return p
+
+        def _free(ptr, stream, ctx):
+            self.live.pop(ptr, None)
+
+        self.alloc_cb = ALLOC_FN(_alloc)
+        self.free_cb = FREE_FN(_free)
+
+    def tensor(self, ptr, count, dtype):
+        """Adopt a library output as a torch tensor of `count` elements."""
+        torch = self._torch
+        if not ptr:
+            return torch.empty(0, dtype=dtype, device=self._device)
+        raw = self.live.pop(ptr)
+        return raw.view(dtype)[:count]
+
+
+def _is_torch_cuda(x) -> bool:
+    try:
+        import torch
+    except ImportError:
+        return False
+    return isinstance(x, torch.Tensor) and x.is_cuda
+
+
+def _options(lib, path: str, batch: int, stream, host_io: bool, alloc: Optional[_TorchAllocator]):
+    opt = bm_options()
+    lib.bm_options_init(ctypes.byref(opt))
+    opt.path = PATHS[path]
+    opt.batch = int(batch)
+    opt.host_io = 1 if host_io else 0
+    opt.stream = stream or None
+    if alloc is not None:
+        opt.alloc = alloc.alloc_cb
+        opt.free = alloc.free_cb
+    return opt
+
+
+def _current_stream(device):
+    import torch
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _as_input(x, d_expected=None):
+    """(pointer, rows, d, keepalive, host) for a float32 matrix."""
+    if _is_torch_cuda(x):
+        import torch
+        if x.dtype != torch.float32 or x.dim() != 2:
+            raise ValueError("expected a 2-D float32 CUDA tensor")
+        x = x.contiguous()
+        return x.data_ptr(), x.shape[0], x.shape[1], x, False
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            x = x.numpy()
+    except ImportError:
+        pass
+    a = np.ascontiguousarray(x, dtype=np.float32)
+    if a.ndim != 2:
+        raise ValueError("expected a 2-D array")
+    return (a.ctypes.data if a.size else None), a.shape[0], a.shape[1], a, True
+
+
+def bm_range_query(X, Q, eps: float, path: str = "tc", stream=None):
+    """Exact range query R_eps(q) for every row q of Q over the points X.
+
+    Device tensors in -> torch CUDA tensors out; host arrays in -> numpy out.
+    Returns (offsets int64 [m+1], ids int32 [nnz], stats dict)."""
+    lib = load()
+    px, n, d, kx, hx = _as_input(X)
+    pq, m, dq, kq, hq = _as_input(Q)
+    if dq != d and m and n:
+        raise ValueError("dimension mismatch")
+    if hx != hq:
+        raise ValueError("X and Q must both be device tensors or both host arrays")
+    out = bm_csr()
+    st = bm_stats()
+    if hx:
+        opt = _options(lib, path, 0, stream, True, None)
+        _check(lib, lib.bm_range_query(px, n, d, pq, m, ctypes.c_float(eps), ctypes.byref(opt), ctypes.byref(out),
+                                       ctypes.byref(st)))
+        try:
+            off = np.ctypeslib.as_array((ctypes.c_int64 * (m + 1)).from_address(out.offsets)).copy()
+            ids = np.ctypeslib.as_array((ctypes.c_int32 * max(out.nnz, 1)).from_address(out.ids))[: out.nnz].copy()
+        finally:
+            lib.bm_csr_free(ctypes.byref(out), ctypes.byref(opt))
+        return off, ids, st.as_dict()
+    import torch
+    dev = kx.device
+    alloc = _TorchAllocator(dev)
+    opt = _options(lib, path, 0, stream or _current_stream(dev), False, alloc)
+    _check(lib, lib.bm_range_query(px, n, d, pq, m, ctypes.c_float(eps), ctypes.byref(opt), ctypes.byref(out),
+                                   ctypes.byref(st)))
+    off = alloc.tensor(out.offsets, m + 1, torch.int64)
+    ids = alloc.tensor(out.ids, out.nnz, torch.int32)
+    return off, ids, st.as_dict()
+
+
+def bm_build(X, eps: float, path: str = "tc", batch: int = 0, stream=None):
+    """Exact Ball Mapper: landmarks (greedy index order), CSR memberships, nerve edges.
+
+    Device tensor in -> dict of torch CUDA tensors; host array in -> dict of numpy arrays.
+    Keys: landmarks int32 [L], offsets int64 [L+1], ids int32 [nnz], edges int32 [E, 2], stats."""
+    lib = load()
+    px, n, d, kx, host = _as_input(X)
+    g = bm_graph()
+    if host:
+        opt = _options(lib, path, batch, stream, True, None)
+        _check(lib, lib.bm_build(px, n, d, ctypes.c_float(eps), ctypes.byref(opt), ctypes.byref(g)))
+        try:
+            L, nnz, E = g.n_landmarks, g.members.nnz, g.n_edges
+
+            def arr(ptr, ctype, count):
+                return np.ctypeslib.as_array((ctype * max(count, 1)).from_address(ptr))[:count].copy()
+
+            res = {"landmarks": arr(g.landmarks, ctypes.c_int32, L),
+                   "offsets": arr(g.members.offsets, ctypes.c_int64, L + 1),
+                   "ids": arr(g.members.ids, ctypes.c_int32, nnz),
+                   "edges": arr(g.edges, ctypes.c_int32, 2 * E).reshape(E, 2),
+                   "stats": g.stats.as_dict()}
+        finally:
+            lib.bm_graph_free(ctypes.byref(g), ctypes.byref(opt))
+        return res
+    import torch
+    dev = kx.device
+    alloc = _TorchAllocator(dev)
+    opt = _options(lib, path, batch, stream or _current_stream(dev), False, alloc)
+    _check(lib, lib.bm_build(px, n, d, ctypes.c_float(eps), ctypes.byref(opt), ctypes.byref(g)))
+    L, nnz, E = g.n_landmarks, g.members.nnz, g.n_edges
+    return {"landmarks": alloc.tensor(g.landmarks, L, torch.int32),
+            "offsets": alloc.tensor(g.members.offsets, L + 1, torch.int64),
+            "ids": alloc.tensor(g.members.ids, nnz, torch.int32),
+            "edges": alloc.tensor(g.edges, 2 * E, torch.int32).view(E, 2),
+            "stats": g.stats.as_dict()}
+
+
+def version() -> int:
+    return int(load().bm_version())

@@ -1,0 +1,648 @@
+// bm_api.cu -- the C-ABI of libballmapper: argument checks, buffer management,
+// phase orchestration on the caller's stream, and error reporting.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bm_host.h"
+
+namespace bm {
+
+thread_local std::string g_last_error;
+
+void device_free(const bm_options* opt, cudaStream_t s, void* p) {
+    if (!p) return;
+    if (opt && opt->free) opt->free(p, (void*)s, opt->alloc_ctx);
+    else cudaFreeAsync(p, s);
+}
+
+Arena::~Arena() {
+    for (void* p : ptrs_) device_free(opt_, stream_, p);
+}
+
+void* Arena::get(size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (bytes == 0) bytes = 256;
+    void* p = nullptr;
+    if (opt_ && opt_->alloc) {
+        p = opt_->alloc(bytes, (void*)stream_, opt_->alloc_ctx);
+    } else if (cudaMallocAsync(&p, bytes, stream_) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) ptrs_.push_back(p);
+    return p;
+}
+
+void Arena::release(void* p) {
+    if (!p) return;
+    auto it = std::find(ptrs_.begin(), ptrs_.end(), p);
+    if (it != ptrs_.end()) {
+        ptrs_.erase(it);
+        device_free(opt_, stream_, p);
+    }
+}
+
+void Arena::take(void* p) {
+    auto it = std::find(ptrs_.begin(), ptrs_.end(), p);
+    if (it != ptrs_.end()) ptrs_.erase(it);
+}
+
+namespace {
+
+struct Call {
+    bm_options opt;
+    cudaStream_t stream;
+};
+
+bm_status fail(bm_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+#define TRY_CUDA(expr)                                                                  \
+    do {                                                                                \
+        cudaError_t e__ = (expr);                                                       \
+        if (e__ != cudaSuccess) {                                                       \
+            cudaGetLastError();                                                         \
+            return fail(e__ == cudaErrorMemoryAllocation ? BM_ERR_NOMEM : BM_ERR_CUDA,  \
+                        std::string(#expr) + ": " + cudaGetErrorString(e__));           \
+        }                                                                               \
+    } while (0)
+
+#define ALLOC(ptr, type, count)                                                         \
+    do {                                                                                \
+        ptr = (type*)ar.get(sizeof(type) * (size_t)(count));                           \
+        if (!ptr) return fail(BM_ERR_NOMEM, "allocation of " #ptr " failed (" +         \
+                                                std::to_string(sizeof(type) * (size_t)(count)) + " bytes)"); \
+    } while (0)
+
+bm_status check_device(int path) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BM_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    }
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major != 10 || minor != 3)
+        return fail(BM_ERR_UNSUPPORTED, "libballmapper is built for sm_103 (GB300); device is sm_" +
+                                            std::to_string(major) + std::to_string(minor));
+    if (path != BM_PATH_FP32 && path != BM_PATH_TC_SPLIT3) return fail(BM_ERR_ARG, "unknown path");
+    return BM_OK;
+}
+
+bm_status validate_points(const float* X, long long n, int d, const char* name) {
+    if (n < 0 || n > 0x7fffffffLL) return fail(BM_ERR_ARG, std::string(name) + ": row count out of range [0, 2^31-1]");
+    if (d < 1 || d > 65536) return fail(BM_ERR_ARG, "d out of range [1, 65536]");
+    if (n > 0 && X == nullptr) return fail(BM_ERR_ARG, std::string(name) + " is NULL");
+    return BM_OK;
+}
+
+bm_status validate_eps(float eps) {
+    if (!std::isfinite(eps) || !(eps > 0.f)) return fail(BM_ERR_ARG, "eps must be finite and > 0");
+    return BM_OK;
+}
+
+struct Timer {
+    cudaEvent_t ev[8];
+    int used = 0;
+    cudaStream_t s;
+    explicit Timer(cudaStream_t st) : s(st) {
+        for (auto& e : ev) e = nullptr;
+    }
+    ~Timer() {
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+    void mark() {
+        if (used < 8 && cudaEventCreate(&ev[used]) == cudaSuccess) {
+            cudaEventRecord(ev[used], s);
+            ++used;
+        }
+    }
+    double ms(int a, int b) {
+        if (a >= used || b >= used) return 0.0;
+        float t = 0.f;
+        cudaEventSynchronize(ev[b]);
+        cudaEventElapsedTime(&t, ev[a], ev[b]);
+        return t;
+    }
+};
+
+// Copy `bytes` of device memory into a fresh host buffer (malloc).
+bool to_host(void** dst, const void* src, size_t bytes, cudaStream_t s) {
+    *dst = std::malloc(bytes ? bytes : 1);
+    if (!*dst) return false;
+    if (bytes && cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return false;
+    return true;
+}
+
+const float* stage_input(const float* X, long long rows, int d, bool host_io, Arena& ar, cudaStream_t s,
+                         bm_status* st) {
+    *st = BM_OK;
+    if (!host_io || rows == 0) return X;
+    float* dX = (float*)ar.get(sizeof(float) * (size_t)rows * d);
+    if (!dX) {
+        *st = fail(BM_ERR_NOMEM, "device copy of host input failed to allocate");
+        return nullptr;
+    }
+    if (cudaMemcpyAsync(dX, X, sizeof(float) * (size_t)rows * d, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        cudaGetLastError();
+        *st = fail(BM_ERR_CUDA, "host to device copy failed");
+        return nullptr;
+    }
+    return dX;
+}
+
+// Allocate and fill the tile operands of one point set.
+bm_status prepare(const float* x, long long rows, int d, double eps2, bool a_side, bool want_tc, Arena& ar,
+                  unsigned* max_norm_bits, int* bad, cudaStream_t s, Prepared& p) {
+    p.x = x;
+    p.rows = rows;
+    p.d = d;
+    p.d_pad = tc_pad_dim(d);
+    ALLOC(p.phi, float, std::max<long long>(rows, 1));
+    if (want_tc) {
+        ALLOC(p.hi, __nv_bfloat16, std::max<long long>(rows, 1) * p.d_pad);
+        ALLOC(p.lo, __nv_bfloat16, std::max<long long>(rows, 1) * p.d_pad);
+        ALLOC(p.aug, __nv_bfloat16, std::max<long long>(rows, 1) * 16);
+    }
+    TRY_CUDA(launch_prep(x, rows, d, eps2, a_side, want_tc, p, max_norm_bits, bad, s));
+    return BM_OK;
+}
+
+bm_status run_sweep(const SweepDesc& sd, int path, cudaStream_t s) {
+    if (path == BM_PATH_FP32) {
+        TRY_CUDA(launch_sweep_fp32(sd, s));
+        return BM_OK;
+    }
+    std::string why;
+    cudaError_t e = launch_sweep_tc(sd, s, &why);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BM_ERR_CUDA, "tensor-core sweep: " + why + " (" + cudaGetErrorString(e) + ")");
+    }
+    return BM_OK;
+}
+
+struct HostState {
+    DeviceState* pinned = nullptr;
+    HostState() {
+        if (cudaMallocHost(&pinned, sizeof(DeviceState)) != cudaSuccess) {
+            cudaGetLastError();
+            pinned = nullptr;
+        }
+    }
+    ~HostState() {
+        if (pinned) cudaFreeHost(pinned);
+    }
+};
+
+bm_status read_state(const DeviceState* dst, HostState& hs, DeviceState& out, cudaStream_t s) {
+    if (!hs.pinned) return fail(BM_ERR_NOMEM, "pinned state buffer");
+    TRY_CUDA(cudaMemcpyAsync(hs.pinned, dst, sizeof(DeviceState), cudaMemcpyDeviceToHost, s));
+    TRY_CUDA(cudaStreamSynchronize(s));
+    out = *hs.pinned;
+    return BM_OK;
+}
+
+// The greedy + membership part of bm_build.  Returns BM_OK with *retry set when
+// a buffer was too small (capacities are updated for the next attempt).
+bm_status greedy_pass(const Prepared& pts, double eps2, int path, int S, Arena& ar, cudaStream_t s,
+                      DeviceState* st, HostState& hs, unsigned long long& step_cap, unsigned long long& mem_cap,
+                      bool* retry, int** landmarks_out, unsigned long long** mem_keys_out, DeviceState& final_state) {
+    *retry = false;
+    const long long n = pts.rows;
+    const int d = pts.d;
+    const bool tc = path == BM_PATH_TC_SPLIT3;
+    GreedyBuffers g;
+    g.st = st;
+    const long long words_n = (n + 31) / 32;
+    const int words = S / 32;
+    ALLOC(g.covered, unsigned, words_n);
+    TRY_CUDA(cudaMemsetAsync(g.covered, 0, sizeof(unsigned) * words_n, s));
+    ALLOC(g.slot_of, int, n);
+    TRY_CUDA(cudaMemsetAsync(g.slot_of, 0xff, sizeof(int) * n, s));
+    ALLOC(g.cand_ids, int, S);
+    ALLOC(g.ordinal, int, S);
+    ALLOC(g.conflict, unsigned, (long long)S * words);
+    TRY_CUDA(cudaMemsetAsync(g.conflict, 0, sizeof(unsigned) * S * words, s));
+    ALLOC(g.row_any, unsigned, words);
+    TRY_CUDA(cudaMemsetAsync(g.row_any, 0, sizeof(unsigned) * words, s));
+    ALLOC(g.landmarks, int, n);
+    float* cx;
+    ALLOC(cx, float, (long long)S * d);
+    g.cand.x = cx;
+    g.cand.rows = S;
+    g.cand.d = d;
+    g.cand.d_pad = pts.d_pad;
+    ALLOC(g.cand.phi, float, S);
+    if (tc) {
+        ALLOC(g.cand.hi, __nv_bfloat16, (long long)S * pts.d_pad);
+        ALLOC(g.cand.lo, __nv_bfloat16, (long long)S * pts.d_pad);
+        ALLOC(g.cand.aug, __nv_bfloat16, (long long)S * 16);
+        TRY_CUDA(cudaMemsetAsync(g.cand.hi, 0, sizeof(__nv_bfloat16) * S * pts.d_pad, s));
+        TRY_CUDA(cudaMemsetAsync(g.cand.lo, 0, sizeof(__nv_bfloat16) * S * pts.d_pad, s));
+        TRY_CUDA(cudaMemsetAsync(g.cand.aug, 0, sizeof(__nv_bfloat16) * S * 16, s));
+    }
+    ALLOC(g.step_keys, unsigned long long, step_cap);
+    g.step_cap = step_cap;
+    ALLOC(g.mem_keys, unsigned long long, mem_cap);
+    g.mem_cap = mem_cap;
+
+    SweepDesc sd;
+    sd.a = &g.cand;
+    sd.b = &pts;
+    sd.a_rows_max = S;
+    sd.a_rows_dev = &st->cand_count;
+    sd.st = st;
+    sd.check_done = true;
+    sd.eps2 = eps2;
+    sd.sink.keys = g.step_keys;
+    sd.sink.count = &st->step_hits;
+    sd.sink.cap = step_cap;
+    sd.sink.slot_of = g.slot_of;
+    sd.sink.conflict = g.conflict;
+    sd.sink.row_any = g.row_any;
+    sd.sink.conflict_words = words;
+    sd.sink.band_count = &st->band_pairs;
+    sd.sink.pair_count = &st->tile_pairs;
+
+    DeviceState h;
+    int chunk = 2;
+    while (true) {
+        for (int i = 0; i < chunk; ++i) {
+            TRY_CUDA(launch_greedy_select(g, pts, S, tc, s));
+            bm_status rs = run_sweep(sd, path, s);
+            if (rs != BM_OK) return rs;
+            TRY_CUDA(launch_greedy_resolve(g, S, s));
+            TRY_CUDA(launch_greedy_apply(g, s));
+        }
+        bm_status rs = read_state(st, hs, h, s);
+        if (rs != BM_OK) return rs;
+        if (h.error & kErrTimeout) return fail(BM_ERR_TIMEOUT, "a bounded device wait expired in the distance tiles");
+        if (h.error & kErrStepOverflow) {
+            step_cap = std::max<unsigned long long>(2 * h.step_hits, 2 * step_cap);
+            *retry = true;
+            return BM_OK;
+        }
+        if (h.done) break;
+        chunk = std::min(chunk * 2, 64);
+    }
+    if (h.error & kErrMemberOverflow) {
+        mem_cap = h.mem_count + 1024;
+        *retry = true;
+        return BM_OK;
+    }
+    ar.release(g.step_keys);
+    *landmarks_out = g.landmarks;
+    *mem_keys_out = g.mem_keys;
+    final_state = h;
+    return BM_OK;
+}
+
+}  // namespace
+}  // namespace bm
+
+using namespace bm;
+
+extern "C" {
+
+void bm_options_init(bm_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->path = BM_PATH_TC_SPLIT3;
+}
+
+const char* bm_status_string(bm_status s) {
+    switch (s) {
+        case BM_OK: return "ok";
+        case BM_ERR_ARG: return "invalid argument";
+        case BM_ERR_CUDA: return "CUDA error";
+        case BM_ERR_NOMEM: return "out of memory";
+        case BM_ERR_CAPACITY: return "capacity exceeded";
+        case BM_ERR_TIMEOUT: return "device wait timed out";
+        case BM_ERR_UNSUPPORTED: return "unsupported device";
+    }
+    return "unknown status";
+}
+
+const char* bm_last_error(void) { return g_last_error.c_str(); }
+
+int32_t bm_version(void) { return 100; }
+
+void bm_csr_free(bm_csr* csr, const bm_options* opt) {
+    if (!csr) return;
+    if (csr->on_host) {
+        std::free(csr->offsets);
+        std::free(csr->ids);
+    } else {
+        cudaStream_t s = opt ? (cudaStream_t)opt->stream : nullptr;
+        device_free(opt, s, csr->offsets);
+        device_free(opt, s, csr->ids);
+    }
+    std::memset(csr, 0, sizeof(*csr));
+}
+
+void bm_graph_free(bm_graph* g, const bm_options* opt) {
+    if (!g) return;
+    if (g->on_host) {
+        std::free(g->landmarks);
+        std::free(g->edges);
+    } else {
+        cudaStream_t s = opt ? (cudaStream_t)opt->stream : nullptr;
+        device_free(opt, s, g->landmarks);
+        device_free(opt, s, g->edges);
+    }
+    bm_csr_free(&g->members, opt);
+    std::memset(g, 0, sizeof(*g));
+}
+
+bm_status bm_range_query(const float* X, int64_t n, int32_t d, const float* Q, int64_t m, float eps,
+                         const bm_options* opt_in, bm_csr* out, bm_stats* stats) {
+    if (!out) return fail(BM_ERR_ARG, "out is NULL");
+    std::memset(out, 0, sizeof(*out));
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    bm_options opt;
+    bm_options_init(&opt);
+    if (opt_in) opt = *opt_in;
+    bm_status vs = validate_points(X, n, d, "X");
+    if (vs != BM_OK) return vs;
+    vs = validate_points(Q, m, d, "Q");
+    if (vs != BM_OK) return vs;
+    vs = validate_eps(eps);
+    if (vs != BM_OK) return vs;
+    vs = check_device(opt.path);
+    if (vs != BM_OK) return vs;
+    cudaStream_t s = (cudaStream_t)opt.stream;
+    const bool host_io = opt.host_io != 0;
+    const double eps2 = (double)eps * (double)eps;
+    const bool tc = opt.path == BM_PATH_TC_SPLIT3;
+    Timer tm(s);
+    tm.mark();
+    bm_status rs = BM_OK;
+    long long nnz = 0;
+    long long* offsets = nullptr;
+    int* ids = nullptr;
+    unsigned long long band = 0, pairs = 0;
+    float delta = 0.f;
+    {
+        Arena ar(&opt, s);
+        const float* dX = stage_input(X, n, d, host_io, ar, s, &rs);
+        if (rs != BM_OK) return rs;
+        const float* dQ = stage_input(Q, m, d, host_io, ar, s, &rs);
+        if (rs != BM_OK) return rs;
+        ALLOC(offsets, long long, m + 1);
+        if (m == 0 || n == 0) {
+            TRY_CUDA(cudaMemsetAsync(offsets, 0, sizeof(long long) * (m + 1), s));
+            ALLOC(ids, int, 1);
+        } else {
+            DeviceState* st;
+            ALLOC(st, DeviceState, 1);
+            TRY_CUDA(cudaMemsetAsync(st, 0, sizeof(DeviceState), s));
+            int* bad;
+            ALLOC(bad, int, 1);
+            TRY_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+            Prepared px, pq;
+            rs = prepare(dX, n, d, eps2, false, tc, ar, &st->max_norm_bits, bad, s, px);
+            if (rs != BM_OK) return rs;
+            rs = prepare(dQ, m, d, eps2, true, tc, ar, &st->max_norm_q_bits, bad, s, pq);
+            if (rs != BM_OK) return rs;
+            TRY_CUDA(launch_delta(st, opt.path, d, px.d_pad, eps2, false, s));
+            int hbad = 0;
+            TRY_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+            TRY_CUDA(cudaStreamSynchronize(s));
+            if (hbad) return fail(BM_ERR_ARG, "input holds NaN or Inf");
+            unsigned long long cap = (unsigned long long)std::min<long long>(std::max<long long>(n, m) * 4 + (1 << 20),
+                                                                              (long long)n * m);
+            HostState hs;
+            DeviceState h;
+            unsigned long long* keys = nullptr;
+            for (int attempt = 0; attempt < 2; ++attempt) {
+                ALLOC(keys, unsigned long long, cap);
+                SweepDesc sd;
+                sd.a = &pq;
+                sd.b = &px;
+                sd.a_rows_max = m;
+                sd.a_rows_dev = nullptr;
+                sd.st = st;
+                sd.check_done = false;
+                sd.eps2 = eps2;
+                sd.sink = HitSink();
+                sd.sink.keys = keys;
+                sd.sink.count = &st->hit_count;
+                sd.sink.cap = cap;
+                sd.sink.band_count = &st->band_pairs;
+                sd.sink.pair_count = &st->tile_pairs;
+                rs = run_sweep(sd, opt.path, s);
+                if (rs != BM_OK) return rs;
+                rs = read_state(st, hs, h, s);
+                if (rs != BM_OK) return rs;
+                if (h.error & kErrTimeout) return fail(BM_ERR_TIMEOUT, "a bounded device wait expired");
+                if (h.hit_count <= cap) break;
+                ar.release(keys);
+                cap = h.hit_count;
+                TRY_CUDA(cudaMemsetAsync(&st->hit_count, 0, sizeof(unsigned long long), s));
+                TRY_CUDA(cudaMemsetAsync(&st->band_pairs, 0, sizeof(unsigned long long), s));
+                TRY_CUDA(cudaMemsetAsync(&st->tile_pairs, 0, sizeof(unsigned long long), s));
+            }
+            nnz = (long long)h.hit_count;
+            band = h.band_pairs;
+            pairs = h.tile_pairs;
+            delta = h.delta;
+            unsigned long long* tmp;
+            ALLOC(tmp, unsigned long long, std::max<long long>(nnz, 1));
+            unsigned long long* sorted = nullptr;
+            TRY_CUDA(radix_sort_u64(keys, tmp, nnz, digit_shifts(bits_for(n - 1), bits_for(m - 1)), ar, s, &sorted));
+            ALLOC(ids, int, std::max<long long>(nnz, 1));
+            TRY_CUDA(launch_csr_from_sorted(sorted, nnz, m, offsets, ids, s));
+        }
+        if (host_io) {
+            void *ho = nullptr, *hi = nullptr;
+            if (!to_host(&ho, offsets, sizeof(long long) * (m + 1), s) ||
+                !to_host(&hi, ids, sizeof(int) * std::max<long long>(nnz, 1), s)) {
+                std::free(ho);
+                std::free(hi);
+                return fail(BM_ERR_CUDA, "device to host copy of the result failed");
+            }
+            TRY_CUDA(cudaStreamSynchronize(s));
+            offsets = (long long*)ho;
+            ids = (int*)hi;
+            out->on_host = 1;
+        } else {
+            ar.take(offsets);
+            ar.take(ids);
+        }
+    }
+    tm.mark();
+    out->rows = m;
+    out->nnz = nnz;
+    out->offsets = (int64_t*)offsets;
+    out->ids = ids;
+    if (stats) {
+        stats->distance_evals = (int64_t)n * m;
+        stats->tile_pairs = (int64_t)pairs;
+        stats->band_pairs = (int64_t)band;
+        stats->ms_total = tm.ms(0, 1);
+        stats->band_delta = delta;
+        stats->path = opt.path;
+    }
+    return BM_OK;
+}
+
+bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_options* opt_in, bm_graph* out) {
+    if (!out) return fail(BM_ERR_ARG, "out is NULL");
+    std::memset(out, 0, sizeof(*out));
+    bm_options opt;
+    bm_options_init(&opt);
+    if (opt_in) opt = *opt_in;
+    bm_status vs = validate_points(X, n, d, "X");
+    if (vs != BM_OK) return vs;
+    vs = validate_eps(eps);
+    if (vs != BM_OK) return vs;
+    vs = check_device(opt.path);
+    if (vs != BM_OK) return vs;
+    int S = opt.batch;
+    if (S == 0) S = 1024;
+    if (S < 32 || S > 1024 || S % 32) return fail(BM_ERR_ARG, "batch must be a multiple of 32 in [32, 1024]");
+    cudaStream_t s = (cudaStream_t)opt.stream;
+    const bool host_io = opt.host_io != 0;
+    const double eps2 = (double)eps * (double)eps;
+    const bool tc = opt.path == BM_PATH_TC_SPLIT3;
+    Timer tm(s);
+    tm.mark();  // 0
+    bm_status rs = BM_OK;
+    bm_graph g;
+    std::memset(&g, 0, sizeof(g));
+    DeviceState fin;
+    std::memset(&fin, 0, sizeof(fin));
+    long long edge_pairs = 0;
+    {
+        Arena ar(&opt, s);
+        const float* dX = stage_input(X, n, d, host_io, ar, s, &rs);
+        if (rs != BM_OK) return rs;
+        int* landmarks = nullptr;
+        long long* offsets = nullptr;
+        int* ids = nullptr;
+        int* edges = nullptr;
+        long long L = 0, nnz = 0, E = 0;
+        if (n == 0) {
+            ALLOC(landmarks, int, 1);
+            ALLOC(offsets, long long, 1);
+            TRY_CUDA(cudaMemsetAsync(offsets, 0, sizeof(long long), s));
+            ALLOC(ids, int, 1);
+            ALLOC(edges, int, 2);
+            tm.mark(); tm.mark(); tm.mark(); tm.mark();
+        } else {
+            DeviceState* st;
+            ALLOC(st, DeviceState, 1);
+            int* bad;
+            ALLOC(bad, int, 1);
+            TRY_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+            TRY_CUDA(cudaMemsetAsync(st, 0, sizeof(DeviceState), s));
+            Prepared px;
+            rs = prepare(dX, n, d, eps2, false, tc, ar, &st->max_norm_bits, bad, s, px);
+            if (rs != BM_OK) return rs;
+            TRY_CUDA(launch_delta(st, opt.path, d, px.d_pad, eps2, true, s));
+            int hbad = 0;
+            TRY_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+            TRY_CUDA(cudaStreamSynchronize(s));
+            if (hbad) return fail(BM_ERR_ARG, "input holds NaN or Inf");
+            tm.mark();  // 1: prep done
+            unsigned long long step_cap = (unsigned long long)std::min<long long>((long long)S * n, 1LL << 22);
+            unsigned long long mem_cap = (unsigned long long)std::max<long long>(4 * n, 1LL << 20);
+            HostState hs;
+            unsigned long long* mem_keys = nullptr;
+            for (int attempt = 0; attempt < 6; ++attempt) {
+                bool retry = false;
+                TRY_CUDA(cudaMemsetAsync(st, 0, offsetof(DeviceState, max_norm_bits), s));
+                rs = greedy_pass(px, eps2, opt.path, S, ar, s, st, hs, step_cap, mem_cap, &retry, &landmarks,
+                                 &mem_keys, fin);
+                if (rs != BM_OK) return rs;
+                if (!retry) break;
+                if (attempt == 5) return fail(BM_ERR_CAPACITY, "greedy buffers kept overflowing");
+            }
+            tm.mark();  // 2: greedy (with memberships) done
+            L = fin.n_landmarks;
+            nnz = (long long)fin.mem_count;
+            unsigned long long* tmp;
+            ALLOC(tmp, unsigned long long, std::max<long long>(nnz, 1));
+            unsigned long long* sorted = nullptr;
+            TRY_CUDA(radix_sort_u64(mem_keys, tmp, nnz, digit_shifts(bits_for(n - 1), bits_for(L - 1)), ar, s,
+                                    &sorted));
+            ALLOC(offsets, long long, L + 1);
+            ALLOC(ids, int, std::max<long long>(nnz, 1));
+            TRY_CUDA(launch_csr_from_sorted(sorted, nnz, L, offsets, ids, s));
+            tm.mark();  // 3: CSR done
+            Failure f{BM_OK, ""};
+            EdgeResult er;
+            if (!build_edges(sorted, nnz, n, L, ar, s, er, f)) return fail(f.status, f.msg);
+            edges = er.edges;
+            E = er.n_edges;
+            edge_pairs = er.pairs;
+            if (!edges) ALLOC(edges, int, 2);
+            tm.mark();  // 4: edges done
+            ar.release(tmp);
+            ar.release(mem_keys);
+        }
+        if (host_io) {
+            void *hl = nullptr, *ho = nullptr, *hi = nullptr, *he = nullptr;
+            bool ok = to_host(&hl, landmarks, sizeof(int) * std::max<long long>(L, 1), s) &&
+                      to_host(&ho, offsets, sizeof(long long) * (L + 1), s) &&
+                      to_host(&hi, ids, sizeof(int) * std::max<long long>(nnz, 1), s) &&
+                      to_host(&he, edges, sizeof(int) * 2 * std::max<long long>(E, 1), s);
+            if (ok && cudaStreamSynchronize(s) != cudaSuccess) ok = false;
+            if (!ok) {
+                std::free(hl); std::free(ho); std::free(hi); std::free(he);
+                cudaGetLastError();
+                return fail(BM_ERR_CUDA, "device to host copy of the result failed");
+            }
+            g.landmarks = (int*)hl;
+            g.members.offsets = (int64_t*)ho;
+            g.members.ids = (int*)hi;
+            g.edges = (int*)he;
+            g.on_host = 1;
+            g.members.on_host = 1;
+        } else {
+            ar.take(landmarks);
+            ar.take(offsets);
+            ar.take(ids);
+            ar.take(edges);
+            g.landmarks = landmarks;
+            g.members.offsets = (int64_t*)offsets;
+            g.members.ids = ids;
+            g.edges = edges;
+        }
+        g.n_landmarks = L;
+        g.members.rows = L;
+        g.members.nnz = nnz;
+        g.n_edges = E;
+    }
+    tm.mark();  // 5
+    g.stats.distance_evals = (int64_t)g.n_landmarks * n;
+    g.stats.tile_pairs = (int64_t)fin.tile_pairs;
+    g.stats.band_pairs = (int64_t)fin.band_pairs;
+    g.stats.greedy_steps = (int64_t)fin.steps;
+    g.stats.candidates = (int64_t)fin.candidates;
+    g.stats.edge_pairs = edge_pairs;
+    g.stats.ms_prep = tm.ms(0, 1);
+    g.stats.ms_greedy = tm.ms(1, 2);
+    g.stats.ms_members = tm.ms(2, 3);
+    g.stats.ms_edges = tm.ms(3, 4);
+    g.stats.ms_total = tm.ms(0, 5);
+    g.stats.band_delta = fin.delta;
+    g.stats.path = opt.path;
+    *out = g;
+    return BM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,143 @@
+// bm_prep.cu -- K0: per-point preparation for the distance tiles.
+//
+// The decision d(q,x) < eps (open ball, Sec. 2.1; exact range set, Sec. 4) is
+// taken on the algebraic form of Sec. 3.2:
+//     D(q,x) = ||q||^2 + ||x||^2 - 2 q.x,
+// rewritten as   v = q.x - phi_q - phi_x,   phi = ||.||^2/2 - eps^2/4,
+// so that  x in R_eps(q)  <=>  v = (eps^2 - D)/2 > 0.
+// The norms are computed once per point here (the paper: computed once per
+// query, precomputed and stored per data point) and the inner product is left
+// to the tiles.
+//
+// For the tensor-core path each coordinate is split exactly-or-nearly into
+// two bf16 values, x = hi + lo (hi = bf16(x), lo = bf16(x - hi)), and phi is
+// carried into the K dimension by a 16-wide augmentation block so that the
+// FP32 accumulator already holds v:
+//   B side (points):   aug = [1, 1, 1, -p1, -p2, -p3, 0 ...]
+//   A side (queries):  aug = [-p1, -p2, -p3, 1, 1, 1, 0 ...]
+// with phi ~ p1 + p2 + p3 (three bf16 pieces of the FP64 value).
+#include "bm_host.h"
+
+namespace bm {
+
+int tc_pad_dim(int d) {
+    if (d <= 16) return 16;
+    if (d <= 32) return 32;
+    return (d + 63) / 64 * 64;
+}
+
+__global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ x, long long rows, int d,
+                                                   double eps2, int a_side, int want_tc,
+                                                   float* __restrict__ phi_out,
+                                                   __nv_bfloat16* __restrict__ hi,
+                                                   __nv_bfloat16* __restrict__ lo,
+                                                   __nv_bfloat16* __restrict__ aug, int d_pad,
+                                                   unsigned* max_norm_bits, int* bad_flag) {
+    __shared__ float s_max[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float my_max = 0.f;
+    const long long warps_total = (long long)gridDim.x * 8;
+    for (long long r = (long long)blockIdx.x * 8 + warp; r < rows; r += warps_total) {
+        const float* xr = x + r * d;
+        double s = 0.0;
+        bool bad = false;
+        for (int i = lane; i < (want_tc ? d_pad : d); i += 32) {
+            float v = i < d ? xr[i] : 0.f;
+            if (!isfinite(v)) bad = true;
+            s += (double)v * (double)v;
+            if (want_tc) {
+                __nv_bfloat16 h = __float2bfloat16_rn(v);
+                __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+                hi[r * d_pad + i] = h;
+                lo[r * d_pad + i] = l;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+        if (__any_sync(kFull, bad) && lane == 0) atomicExch(bad_flag, 1);
+        const double phi = 0.5 * s - 0.25 * eps2;
+        if (lane == 0) phi_out[r] = (float)phi;
+        if (want_tc && lane < 16) {
+            const __nv_bfloat16 p1 = __double2bfloat16(phi);
+            const double r1 = phi - (double)__bfloat162float(p1);
+            const __nv_bfloat16 p2 = __double2bfloat16(r1);
+            const double r2 = r1 - (double)__bfloat162float(p2);
+            const __nv_bfloat16 p3 = __double2bfloat16(r2);
+            const __nv_bfloat16 one = __float2bfloat16_rn(1.f);
+            const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+            __nv_bfloat16 v = zero;
+            const int pos = a_side ? lane : (lane < 3 ? lane + 3 : (lane < 6 ? lane - 3 : lane));
+            // pos < 3 : the -p pieces ; 3 <= pos < 6 : ones (A side layout; B side swaps halves)
+            if (pos == 0) v = __hneg(p1);
+            else if (pos == 1) v = __hneg(p2);
+            else if (pos == 2) v = __hneg(p3);
+            else if (pos < 6) v = one;
+            aug[r * 16 + lane] = v;
+        }
+        my_max = fmaxf(my_max, __double2float_ru(sqrt(s)));
+    }
+    // block max -> one atomic per block (norms are >= 0, so float bits order as unsigned)
+    for (int o = 16; o > 0; o >>= 1) my_max = fmaxf(my_max, __shfl_xor_sync(kFull, my_max, o));
+    if (lane == 0) s_max[warp] = my_max;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < 8; ++w) m = fmaxf(m, s_max[w]);
+        atomicMax(max_norm_bits, __float_as_uint(m));
+    }
+}
+
+cudaError_t launch_prep(const float* x, long long rows, int d, double eps2, bool a_side, bool want_tc,
+                        Prepared& out, unsigned* max_norm_bits, int* bad_flag, cudaStream_t s) {
+    if (rows == 0) return cudaSuccess;
+    long long blocks = (rows + 7) / 8;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    prep_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, rows, d, eps2, a_side ? 1 : 0, want_tc ? 1 : 0,
+                                                 out.phi, out.hi, out.lo, out.aug, out.d_pad,
+                                                 max_norm_bits, bad_flag);
+    return cudaGetLastError();
+}
+
+// Half-width of the error band, in units of v = (eps^2 - D)/2.
+//
+// N_a, N_b: max norms of the two sides; Phi = max |phi| <= max(N^2/2 - eps^2/4, eps^2/4).
+//
+// FP32 path: s = q.x by a chain of d FMAs, |s^ - s| <= gamma_d sum|q_i x_i| <= gamma_d N_a N_b
+// (u = 2^-24); phi rounded to float (u |phi| each) and two subtractions (u |.| each).
+//     delta = 2 (d + 8) 2^-23 (N_a N_b + Phi_a + Phi_b)
+//
+// Tensor-core path: K = 3 d_pad + 6 accumulated terms (hi.hi, lo.hi, hi.lo and the six
+// phi-piece products), each exact in FP32; the accumulation order and rounding of
+// tcgen05 are not specified, so every one of the K-1 additions (and one alignment
+// truncation per term) is charged 2^-23 of the sum of magnitudes:
+//     |acc - T| <= 2 K 2^-23 (1.02 N_a N_b + 1.01 (Phi_a + Phi_b)).
+// Dropped lo.lo products: <= 2^-16 N_a N_b.  bf16 rounding of lo (inputs that are not
+// multiples of 2^-k with |m| < 2^16): <= 2 * 2^-16 N_a N_b.  Three-piece phi: 2^-24 |phi|.
+//     delta = 2 [2 K 2^-23 (1.02 N_a N_b + 1.01 (Phi_a + Phi_b)) + 3 2^-16 N_a N_b
+//                + 2^-23 (Phi_a + Phi_b)]
+// Both bounds carry a safety factor of 2 and a tiny absolute term for underflow.
+__global__ void delta_kernel(DeviceState* st, int path, int d, int d_pad, double eps2, int same_sets) {
+    const double Nb = (double)__uint_as_float(st->max_norm_bits);
+    const double Na = same_sets ? Nb : (double)__uint_as_float(st->max_norm_q_bits);
+    const double Pa = fmax(Na * Na * 0.5 - 0.25 * eps2, 0.25 * eps2);
+    const double Pb = fmax(Nb * Nb * 0.5 - 0.25 * eps2, 0.25 * eps2);
+    const double u23 = 1.0 / 8388608.0, u16 = 1.0 / 65536.0;
+    double delta;
+    if (path == BM_PATH_FP32) {
+        delta = 2.0 * (d + 8) * u23 * (Na * Nb + Pa + Pb);
+    } else {
+        const double K = 3.0 * d_pad + 6.0;
+        delta = 2.0 * (2.0 * K * u23 * (1.02 * Na * Nb + 1.01 * (Pa + Pb)) + 3.0 * u16 * Na * Nb +
+                       u23 * (Pa + Pb));
+    }
+    delta += 1e-30;
+    st->delta = __double2float_ru(delta);
+}
+
+cudaError_t launch_delta(DeviceState* st, int path, int d, int d_pad, double eps2, bool same_sets,
+                         cudaStream_t s) {
+    delta_kernel<<<1, 1, 0, s>>>(st, path, d, d_pad, eps2, same_sets ? 1 : 0);
+    return cudaGetLastError();
+}
+
+}  // namespace bm

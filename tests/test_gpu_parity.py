@@ -1,0 +1,202 @@
+"""CUDA path (through the C-ABI) against the CPU oracle, element by element.
+
+Landmarks, membership CSR and nerve edges are integer / index results and must
+be bit-identical to the oracle on the same seeded inputs, on both distance-tile
+paths."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_01405_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PATHS = ["tc", "fp32"]
+
+
+@pytest.fixture(scope="module")
+def bm():
+    from paper_2601_01405_gb300 import _build, binding
+    _build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return binding
+
+
+def run_build(bm, X, eps, path, batch=0):
+    out = bm.bm_build(torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda(), eps, path=path, batch=batch)
+    torch.cuda.synchronize()
+    return {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in out.items()}
+
+
+def assert_same_graph(got, ref, tag=""):
+    assert np.array_equal(got["landmarks"], ref["landmarks"]), ("landmarks", tag)
+    assert np.array_equal(got["offsets"], ref["offsets"]), ("offsets", tag)
+    assert np.array_equal(got["ids"], ref["ids"]), ("ids", tag)
+    assert np.array_equal(got["edges"].reshape(-1, 2), ref["edges"].reshape(-1, 2)), ("edges", tag)
+
+
+# ------------------------------------------------------------------ range query
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("n,m,d,eps", [(10_000, 777, 16, 3.0), (4099, 300, 3, 0.4), (5000, 129, 17, 2.5),
+                                       (3000, 1000, 64, 9.5), (2500, 257, 100, 12.0), (1, 5, 8, 1.0),
+                                       (700, 1, 128, 14.0), (1000, 64, 1, 0.01)])
+def test_range_query_matches_oracle(bm, path, n, m, d, eps):
+    X = W.isotropic(n, d, 10, seed=n + d)
+    Q = W.isotropic(m, d, 10, seed=m + 3 * d)
+    off, ids, st = bm.bm_range_query(torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda(), eps, path=path)
+    torch.cuda.synchronize()
+    ro, ri = oracle.range_query(X, Q, eps)
+    assert np.array_equal(off.cpu().numpy(), ro)
+    assert np.array_equal(ids.cpu().numpy(), ri)
+    assert st["distance_evals"] == n * m
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_range_query_ties_on_grid(bm, path):
+    """Coarse grid data: many pairs at exactly eps; open balls exclude them."""
+    X = W.tiny_grid_cloud(6000, 3, 2, span=8, seed=1)
+    for eps in (0.5, 1.0, 1.25):
+        off, ids, st = bm.bm_range_query(torch.from_numpy(X).cuda(), torch.from_numpy(X[:900]).cuda(), eps, path=path)
+        ro, ri = oracle.range_query(X, X[:900], eps)
+        assert np.array_equal(off.cpu().numpy(), ro) and np.array_equal(ids.cpu().numpy(), ri), eps
+        assert st["band_pairs"] > 0   # the exact ties must have gone through the FP64 recheck
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_range_query_host_io(bm, path):
+    X = W.isotropic(3000, 32, 10, seed=5)
+    Q = X[::7]
+    off, ids, _ = bm.bm_range_query(X, Q, 4.0, path=path)
+    ro, ri = oracle.range_query(X, Q, 4.0)
+    assert isinstance(off, np.ndarray)
+    assert np.array_equal(off, ro) and np.array_equal(ids, ri)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_range_query_empty(bm, path):
+    X = W.isotropic(100, 4, 10, seed=1)
+    off, ids, _ = bm.bm_range_query(torch.from_numpy(X).cuda(), torch.zeros((0, 4)).cuda(), 1.0, path=path)
+    assert off.cpu().tolist() == [0] and ids.numel() == 0
+    off, ids, _ = bm.bm_range_query(torch.zeros((0, 4)).cuda(), torch.from_numpy(X[:5]).cuda(), 1.0, path=path)
+    assert off.cpu().tolist() == [0] * 6 and ids.numel() == 0
+
+
+# ------------------------------------------------------------------ build
+@pytest.mark.parametrize("path", PATHS)
+def test_build_golden_line_and_grid(bm, path):
+    import pins
+    for case in pins.golden("line.json")["cases"]:
+        got = run_build(bm, W.line_points(10, 3), case["eps"], path)
+        assert got["landmarks"].tolist() == case["landmarks"]
+        assert pins.rows(got["offsets"], got["ids"]) == case["members"]
+        assert got["edges"].tolist() == case["edges"]
+    for case in pins.golden("grid.json")["cases"]:
+        got = run_build(bm, W.grid_points(3), case["eps"], path)
+        assert got["landmarks"].tolist() == case["landmarks"]
+        assert pins.rows(got["offsets"], got["ids"]) == case["members"]
+        assert got["edges"].tolist() == case["edges"]
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_build_iso_n10k_d16(bm, path):
+    X = W.make("iso-n10k-d16")
+    ref = oracle.build(X, 3.0)
+    got = run_build(bm, X, 3.0, path)
+    assert_same_graph(got, ref)
+    assert got["stats"]["distance_evals"] == ref["landmarks"].size * X.shape[0]
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("batch", [32, 96, 1024])
+def test_build_batch_sizes(bm, path, batch):
+    X = W.isotropic(5003, 8, 10, seed=3)
+    ref = oracle.build(X, 2.0)
+    assert_same_graph(run_build(bm, X, 2.0, path, batch=batch), ref, batch)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_build_mixture_d64(bm, path):
+    X = W.mixture(8192, 64, 8, clusters=32, seed=0)
+    for eps in (6.0, 11.0, 12.5):
+        ref = oracle.build(X, eps)
+        assert_same_graph(run_build(bm, X, eps, path), ref, eps)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_build_swissroll_d128(bm, path):
+    X = W.swissroll(12000, 128, 12, seed=0)
+    for eps in (1.0, 2.0):
+        ref = oracle.build(X, eps)
+        assert_same_graph(run_build(bm, X, eps, path), ref, eps)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_build_degenerate(bm, path):
+    # n = 0
+    got = run_build(bm, np.zeros((0, 3), np.float32), 1.0, path)
+    assert got["landmarks"].size == 0 and got["offsets"].tolist() == [0] and got["edges"].size == 0
+    # n = 1
+    got = run_build(bm, np.ones((1, 5), np.float32), 0.5, path)
+    assert got["landmarks"].tolist() == [0] and got["ids"].tolist() == [0]
+    # identical points
+    got = run_build(bm, np.full((300, 2), 0.5, np.float32), 1e-3, path)
+    assert got["landmarks"].tolist() == [0] and got["ids"].tolist() == list(range(300))
+    # eps larger than the diameter
+    X = W.isotropic(2000, 6, 10, seed=2)
+    got = run_build(bm, X, 1e4, path)
+    assert got["landmarks"].tolist() == [0] and got["ids"].tolist() == list(range(2000))
+    # d = 1
+    X = W.isotropic(3000, 1, 10, seed=9)
+    assert_same_graph(run_build(bm, X, 0.05, path), oracle.build(X, 0.05))
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_build_grid_ties(bm, path):
+    X = W.tiny_grid_cloud(4000, 3, 2, span=8, seed=4)
+    for eps in (0.5, 1.0, 1.5):
+        assert_same_graph(run_build(bm, X, eps, path), oracle.build(X, eps), eps)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_build_unquantised_fp32(bm, path):
+    """Arbitrary float32 input: the FP64 recheck reproduces the oracle's arithmetic."""
+    X = np.random.default_rng(5).standard_normal((6000, 20)).astype(np.float32)
+    assert_same_graph(run_build(bm, X, 4.0, path), oracle.build(X, 4.0))
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_build_host_io_and_determinism(bm, path):
+    X = W.isotropic(4000, 16, 10, seed=11)
+    a = bm.bm_build(X, 3.0, path=path)
+    b = run_build(bm, X, 3.0, path)
+    c = run_build(bm, X, 3.0, path)
+    for k in ("landmarks", "offsets", "ids", "edges"):
+        assert np.array_equal(a[k], b[k]) and np.array_equal(b[k], c[k]), k
+
+
+def test_paths_agree_on_paper_gaussian_fp32(bm):
+    """The paper's worked example (Sec. 5.3) cast to float32: both paths agree with
+    each other and with the oracle on the same float32 data."""
+    X = W.paper_gaussian_fp64().astype(np.float32)
+    eps = float(np.float32(7.553576))
+    ref = oracle.build(X, eps)
+    for path in PATHS:
+        assert_same_graph(run_build(bm, X, eps, path), ref, path)
+
+
+# ------------------------------------------------------------------ errors
+def test_errors_are_reported(bm):
+    X = torch.from_numpy(W.isotropic(100, 4, 10, seed=1)).cuda()
+    for bad_eps in (0.0, -1.0, float("nan"), float("inf")):
+        with pytest.raises(bm.BallMapperError) as ei:
+            bm.bm_build(X, bad_eps)
+        assert ei.value.status == bm.BM_ERR_ARG
+    Xn = X.clone()
+    Xn[3, 1] = float("nan")
+    with pytest.raises(bm.BallMapperError) as ei:
+        bm.bm_build(Xn, 1.0)
+    assert ei.value.status == bm.BM_ERR_ARG
+    with pytest.raises(bm.BallMapperError) as ei:
+        bm.bm_build(X, 1.0, batch=33)
+    assert ei.value.status == bm.BM_ERR_ARG
