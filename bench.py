@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Benchmark: exact Ball Mapper construction on one GB300 (or N independent replicas).
+
+Workload (default): equal-weight 32-cluster Gaussian mixture, n = 1,000,000 points,
+d = 64, centres U[-10,10]^64, sigma = 1, coordinates quantised to multiples of 2^-8
+and stored as float32, eps in {2, 4, 6}, greedy in index order.  One step = one
+complete bm_build (prep, block-greedy with full-ball memberships, CSR, nerve edges)
+for each of the three eps values, inputs resident in HBM.
+
+Metric: exact distance evaluations per second, where one evaluation is one
+(landmark, point) membership decision: sum over eps of L_eps * n per step.
+The build seconds per eps, the plain FP32 CUDA-core path on the same workload,
+the roofline of the tensor-core distance tiles and the CPU oracle are reported
+beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Ball Mapper build s & distance evals/s (exact), TC split path vs plain FP32"
+UNIT = "evals/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="mix32-n1M-d64")
+    ap.add_argument("--path", choices=["tc", "fp32"], default="tc")
+    ap.add_argument("--compare-steps", type=int, default=1, help="timed steps of the FP32 comparison path (0: skip)")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(name):
+    from paper_2601_01405_gb300 import workloads as W
+    w = W.WORKLOADS[name]
+    return w, w.points(0)
+
+
+def config_of(w, extra=None):
+    cfg = {"workload": "%s: %s n=%d d=%d quantised 2^-%d, eps=%s, greedy in index order" %
+                       (w.name, w.kind, w.n, w.d, w.k, list(w.eps)),
+           "n": w.n, "d": w.d, "eps": list(w.eps), "quantisation": "2^-%d" % w.k,
+           "l2": "inputs larger than L2 (%.0f MB fp32 + %.0f MB bf16 split operands vs 129 MB)" %
+                 (w.n * w.d * 4 / 1e6, w.n * (2 * (w.d if w.d > 32 else 32) + 16) * 2 / 1e6),
+           "parallelism": "replicas"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def oracle_rate(X, eps_list, target_s, landmark_rows=None):
+    """Time the CPU oracle's full-scan membership query (the same exact decision per
+    (row, point) pair as the GPU sweep) on a bounded sample of rows.  Returns
+    (evals/s, evals, seconds, rows, threads)."""
+    import numpy as np
+    import oracle
+    n = X.shape[0]
+    rng = np.random.default_rng(1)
+    # calibration on a few rows, then size the sample to ~target_s
+    rows0 = 8
+    t0 = time.perf_counter()
+    oracle.range_query(X, X[rng.integers(0, n, rows0)], eps_list[0])
+    dt0 = max(time.perf_counter() - t0, 1e-3)
+    rows = max(len(eps_list), int(rows0 * target_s / dt0))
+    per = max(1, rows // len(eps_list))
+    evals = 0
+    t0 = time.perf_counter()
+    for e in eps_list:
+        q = X[rng.integers(0, n, per)] if landmark_rows is None else X[landmark_rows[:per]]
+        oracle.range_query(X, q, e)
+        evals += per * n
+    dt = time.perf_counter() - t0
+    return evals / dt, evals, dt, per * len(eps_list), oracle.num_threads()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    w, X = workload(args.workload)
+    eps_list = list(w.eps)
+    step_target = 6.0
+    import oracle
+    # warm-up steps (untimed) then K timed steps, each a bounded sample of the workload
+    rates = []
+    t_steps = []
+    evals_total = 0
+    for i in range(args.warmup + args.steps):
+        r, ev, dt, rows, thr = oracle_rate(X, eps_list, step_target)
+        if i >= args.warmup:
+            rates.append(r)
+            t_steps.append(dt)
+            evals_total += ev
+    value = evals_total / sum(t_steps)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(t_steps) / len(t_steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(w),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
+                             "sample": "per step ~%d random query rows x all %d points (full-scan FP64 "
+                                       "membership), split over eps %s" % (rows, w.n, eps_list)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2601_01405_gb300 import binding, _build
+
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device"}), flush=True)
+        return 1
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    _build.build()
+    binding.load()
+    w, X = workload(args.workload)
+    eps_list = list(w.eps)
+    Xd = torch.from_numpy(X).cuda()
+    n, d = X.shape
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def step(path):
+        stats = []
+        for e in eps_list:
+            out = binding.bm_build(Xd, e, path=path)
+            stats.append(out["stats"])
+            del out
+        return stats
+
+    def timed(path, warm, steps):
+        for _ in range(warm):
+            step(path)
+        barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        all_stats = []
+        for _ in range(steps):
+            all_stats.append(step(path))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        return ms, all_stats
+
+    sampler = ClockSampler(local)
+    for _ in range(args.warmup):
+        step(args.path)
+    sampler.start()
+    ms, stats = timed(args.path, 0, args.steps)
+    clocks = sampler.stop()
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    evals_per_step = sum(s["distance_evals"] for s in stats[0])
+    total_evals = evals_per_step * args.steps * ws
+    value = total_evals / (ms / 1000.0)
+    ms_step = ms / args.steps
+    flat = [s for st in stats for s in st]
+    build_s = {str(e): sum(st[i]["ms_total"] for st in stats) / len(stats) / 1000.0 for i, e in enumerate(eps_list)}
+    L_per_eps = {str(e): stats[0][i]["distance_evals"] // n for i, e in enumerate(eps_list)}
+    launches = sum(s["kernel_launches"] for s in flat)
+
+    # roofline of the dominant kernel: the tensor-core distance tiles
+    pk, pk_kind = peaks()
+    sweep_ms = sum(s["ms_sweep"] for s in flat)
+    sweep_n = sum(s["sweep_launches"] for s in flat)
+    tile_pairs = sum(s["tile_pairs"] for s in flat)
+    d_pad = 16 if d <= 16 else (32 if d <= 32 else (d + 63) // 64 * 64)
+    alg_flops = 2.0 * d * tile_pairs
+    issued_flops = 2.0 * (3 * d_pad + 16) * tile_pairs
+    achieved = alg_flops / (sweep_ms / 1000.0) / 1e12 if sweep_ms > 0 else 0.0
+    peak = pk.get("bf16_tflops_sustained", 1700.0)
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if peak else None, "traffic": None,
+                "kernel": "sweep_tc_kernel" if args.path == "tc" else "sweep_fp32_kernel",
+                "peak_kind": "%s bf16 sustained" % pk_kind,
+                "issued_tflops": issued_flops / (sweep_ms / 1000.0) / 1e12 if sweep_ms > 0 else 0.0,
+                "issued_frac": (issued_flops / (sweep_ms / 1000.0) / 1e12) / peak if sweep_ms > 0 and peak else None,
+                "avg_launch_ms": sweep_ms / sweep_n if sweep_n else None, "launches": sweep_n,
+                "sweep_share_of_step": sweep_ms / ms if ms else None}
+
+    extra = {}
+    # comparison: plain FP32 CUDA-core path, same workload
+    if args.compare_steps > 0 and args.path == "tc":
+        ms32, st32 = timed("fp32", 1, args.compare_steps)
+        ev32 = sum(s["distance_evals"] for s in st32[0])
+        f32 = [s for st in st32 for s in st]
+        extra["fp32_path"] = {"value": ev32 * args.compare_steps / (ms32 / 1000.0), "unit": UNIT,
+                              "ms_per_step": ms32 / args.compare_steps, "steps": args.compare_steps,
+                              "build_s": {str(e): f32[i]["ms_total"] / 1000.0 for i, e in enumerate(eps_list)},
+                              "band_pairs": sum(s["band_pairs"] for s in f32)}
+        extra["tc_speedup_vs_fp32"] = (ms32 / args.compare_steps) / ms_step
+
+    # end to end through the C-ABI with host buffers: H2D of the inputs and D2H of the graph inside
+    e2e = None
+    if args.e2e_steps > 0:
+        Xp = torch.from_numpy(X).pin_memory().numpy()
+        binding.bm_build(Xp, eps_list[0], path=args.path)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        d2h = 0
+        for _ in range(args.e2e_steps):
+            for e in eps_list:
+                out = binding.bm_build(Xp, e, path=args.path)
+                L, nnz, E = out["landmarks"].size, out["ids"].size, out["edges"].shape[0]
+                d2h += 4 * L + 8 * (L + 1) + 4 * nnz + 8 * E
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": evals_per_step * args.e2e_steps * ws / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(n * d * 4 * len(eps_list)),
+               "d2h_bytes_per_step": int(d2h // args.e2e_steps)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and args.cpu_seconds > 0:
+        r, ev, dt, rows, thr = oracle_rate(X, eps_list, args.cpu_seconds)
+        cpu = {"value": r, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": "%d random query rows x all %d points, full-scan FP64 membership, split over eps %s "
+                         "(%.1f s)" % (rows, n, eps_list, dt)}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16x3-split/fp32-acc/fp64-recheck" if args.path == "tc" else "f32/fp64-recheck",
+            "data": "synthetic (seeded generator, same recipe and sizes as the workload)",
+            "config": config_of(w, {"path": args.path, "landmarks": L_per_eps, "build_s": build_s,
+                                    "evals_per_step": evals_per_step,
+                                    "band_pairs": sum(s["band_pairs"] for s in flat),
+                                    "tile_pairs": tile_pairs}),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": launches}
+    line.update(extra)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

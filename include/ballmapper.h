@@ -90,6 +90,9 @@ typedef struct {
     double ms_prep, ms_greedy, ms_members, ms_edges, ms_total;  /* device time per phase */
     float band_delta;         /* half-width of the error band used (in units of (eps^2 - D)/2) */
     int32_t path;             /* bm_path actually used */
+    double ms_sweep;          /* device time of the distance-tile launches (CUDA events on the stream) */
+    int64_t sweep_launches;   /* distance-tile kernel launches */
+    int64_t kernel_launches;  /* all kernel launches of the call */
 } bm_stats;
 
 typedef struct {

@@ -40,7 +40,8 @@ class bm_stats(ctypes.Structure):
                 ("greedy_steps", ctypes.c_int64), ("candidates", ctypes.c_int64), ("edge_pairs", ctypes.c_int64),
                 ("ms_prep", ctypes.c_double), ("ms_greedy", ctypes.c_double), ("ms_members", ctypes.c_double),
                 ("ms_edges", ctypes.c_double), ("ms_total", ctypes.c_double), ("band_delta", ctypes.c_float),
-                ("path", ctypes.c_int32)]
+                ("path", ctypes.c_int32), ("ms_sweep", ctypes.c_double), ("sweep_launches", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

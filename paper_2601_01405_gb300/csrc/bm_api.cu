@@ -15,6 +15,7 @@
 namespace bm {
 
 thread_local std::string g_last_error;
+thread_local long long g_kernel_launches = 0;
 
 void device_free(const bm_options* opt, cudaStream_t s, void* p) {
     if (!p) return;
@@ -207,6 +208,44 @@ struct HostState {
     }
 };
 
+// Device time of the distance-tile launches: an event pair around each launch,
+// summed whenever the host synchronises with the stream anyway.
+struct SweepTimer {
+    std::vector<cudaEvent_t> ev;
+    size_t used = 0;
+    double ms = 0.0;
+    long long launches = 0;
+    cudaStream_t s;
+    explicit SweepTimer(cudaStream_t st) : s(st) {}
+    ~SweepTimer() {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+    void mark() {
+        if (used == ev.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                return;
+            }
+            ev.push_back(e);
+        }
+        cudaEventRecord(ev[used++], s);
+    }
+    void before() { mark(); }
+    void after() {
+        mark();
+        ++launches;
+    }
+    void collect() {  // the stream has been synchronised
+        for (size_t i = 0; i + 1 < used; i += 2) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, ev[i], ev[i + 1]) == cudaSuccess) ms += t;
+            else cudaGetLastError();
+        }
+        used = 0;
+    }
+};
+
 bm_status read_state(const DeviceState* dst, HostState& hs, DeviceState& out, cudaStream_t s) {
     if (!hs.pinned) return fail(BM_ERR_NOMEM, "pinned state buffer");
     TRY_CUDA(cudaMemcpyAsync(hs.pinned, dst, sizeof(DeviceState), cudaMemcpyDeviceToHost, s));
@@ -219,7 +258,8 @@ bm_status read_state(const DeviceState* dst, HostState& hs, DeviceState& out, cu
 // a buffer was too small (capacities are updated for the next attempt).
 bm_status greedy_pass(const Prepared& pts, double eps2, int path, int S, Arena& ar, cudaStream_t s,
                       DeviceState* st, HostState& hs, unsigned long long& step_cap, unsigned long long& mem_cap,
-                      bool* retry, int** landmarks_out, unsigned long long** mem_keys_out, DeviceState& final_state) {
+                      bool* retry, int** landmarks_out, unsigned long long** mem_keys_out, DeviceState& final_state,
+                      SweepTimer& stimer) {
     *retry = false;
     const long long n = pts.rows;
     const int d = pts.d;
@@ -282,13 +322,16 @@ bm_status greedy_pass(const Prepared& pts, double eps2, int path, int S, Arena& 
     while (true) {
         for (int i = 0; i < chunk; ++i) {
             TRY_CUDA(launch_greedy_select(g, pts, S, tc, s));
+            stimer.before();
             bm_status rs = run_sweep(sd, path, s);
+            stimer.after();
             if (rs != BM_OK) return rs;
             TRY_CUDA(launch_greedy_resolve(g, S, s));
             TRY_CUDA(launch_greedy_apply(g, s));
         }
         bm_status rs = read_state(st, hs, h, s);
         if (rs != BM_OK) return rs;
+        stimer.collect();
         if (h.error & kErrTimeout) return fail(BM_ERR_TIMEOUT, "a bounded device wait expired in the distance tiles");
         if (h.error & kErrStepOverflow) {
             step_cap = std::max<unsigned long long>(2 * h.step_hits, 2 * step_cap);
@@ -389,6 +432,8 @@ bm_status bm_range_query(const float* X, int64_t n, int32_t d, const float* Q, i
     const bool tc = opt.path == BM_PATH_TC_SPLIT3;
     Timer tm(s);
     tm.mark();
+    SweepTimer stimer(s);
+    const long long launches0 = g_kernel_launches;
     bm_status rs = BM_OK;
     long long nnz = 0;
     long long* offsets = nullptr;
@@ -443,10 +488,13 @@ bm_status bm_range_query(const float* X, int64_t n, int32_t d, const float* Q, i
                 sd.sink.cap = cap;
                 sd.sink.band_count = &st->band_pairs;
                 sd.sink.pair_count = &st->tile_pairs;
+                stimer.before();
                 rs = run_sweep(sd, opt.path, s);
+                stimer.after();
                 if (rs != BM_OK) return rs;
                 rs = read_state(st, hs, h, s);
                 if (rs != BM_OK) return rs;
+                stimer.collect();
                 if (h.error & kErrTimeout) return fail(BM_ERR_TIMEOUT, "a bounded device wait expired");
                 if (h.hit_count <= cap) break;
                 ar.release(keys);
@@ -495,6 +543,9 @@ bm_status bm_range_query(const float* X, int64_t n, int32_t d, const float* Q, i
         stats->ms_total = tm.ms(0, 1);
         stats->band_delta = delta;
         stats->path = opt.path;
+        stats->ms_sweep = stimer.ms;
+        stats->sweep_launches = stimer.launches;
+        stats->kernel_launches = g_kernel_launches - launches0;
     }
     return BM_OK;
 }
@@ -520,6 +571,8 @@ bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_opt
     const bool tc = opt.path == BM_PATH_TC_SPLIT3;
     Timer tm(s);
     tm.mark();  // 0
+    SweepTimer stimer(s);
+    const long long launches0 = g_kernel_launches;
     bm_status rs = BM_OK;
     bm_graph g;
     std::memset(&g, 0, sizeof(g));
@@ -566,7 +619,7 @@ bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_opt
                 bool retry = false;
                 TRY_CUDA(cudaMemsetAsync(st, 0, offsetof(DeviceState, max_norm_bits), s));
                 rs = greedy_pass(px, eps2, opt.path, S, ar, s, st, hs, step_cap, mem_cap, &retry, &landmarks,
-                                 &mem_keys, fin);
+                                 &mem_keys, fin, stimer);
                 if (rs != BM_OK) return rs;
                 if (!retry) break;
                 if (attempt == 5) return fail(BM_ERR_CAPACITY, "greedy buffers kept overflowing");
@@ -641,6 +694,9 @@ bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_opt
     g.stats.ms_total = tm.ms(0, 5);
     g.stats.band_delta = fin.delta;
     g.stats.path = opt.path;
+    g.stats.ms_sweep = stimer.ms;
+    g.stats.sweep_launches = stimer.launches;
+    g.stats.kernel_launches = g_kernel_launches - launches0;
     *out = g;
     return BM_OK;
 }

@@ -108,6 +108,26 @@ __device__ __forceinline__ void emit_hits_row(const HitSink& sink, unsigned row,
     }
 }
 
+// Same as emit_hits_row for a run of 32 consecutive columns col0 .. col0+31.
+__device__ __forceinline__ void emit_hits_run(const HitSink& sink, unsigned row, unsigned col0, unsigned mask) {
+    const unsigned cnt = __popc(mask);
+    unsigned long long pos = warp_reserve(sink.count, cnt);
+    while (mask) {
+        const int j = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const unsigned col = col0 + (unsigned)j;
+        if (pos < sink.cap) sink.keys[pos] = ((unsigned long long)row << 32) | col;
+        ++pos;
+        if (sink.slot_of) {
+            const int s = sink.slot_of[col];
+            if (s > (int)row) {
+                atomicOr(&sink.conflict[(size_t)row * sink.conflict_words + (s >> 5)], 1u << (s & 31));
+                atomicOr(&sink.row_any[row >> 5], 1u << (row & 31));
+            }
+        }
+    }
+}
+
 // Block-wide exclusive scan of one int per thread (blockDim.x multiple of 32, <= 1024).
 __device__ __forceinline__ int block_exclusive_scan(int v, int* smem32, int& total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;

@@ -112,9 +112,11 @@ unsigned grid_for(long long n, int threads) {
 cudaError_t launch_csr_from_sorted(const unsigned long long* keys, long long nnz, long long rows, long long* offsets,
                                    int* ids, cudaStream_t s) {
     if (nnz == 0) {
+        note_launch();
         fill_i64_kernel<<<grid_for(rows + 1, 256), 256, 0, s>>>(offsets, rows + 1, 0);
         return cudaGetLastError();
     }
+    note_launch();
     csr_offsets_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(keys, nnz, rows, offsets, ids);
     return cudaGetLastError();
 }
@@ -146,6 +148,7 @@ bool build_edges(const unsigned long long* keys, long long nnz, long long n, lon
     long long* cnt;
     BM_ALLOC(cnt, long long, n + 1);
     BM_TRY(cudaMemsetAsync(cnt, 0, sizeof(long long) * (n + 1), s));
+    note_launch();
     count_points_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(keys, nnz, cnt);
     BM_TRY(cudaGetLastError());
     long long* toff;
@@ -154,8 +157,10 @@ bool build_edges(const unsigned long long* keys, long long nnz, long long n, lon
     int* tlist;
     BM_ALLOC(tlist, int, nnz);
     BM_TRY(cudaMemsetAsync(cnt, 0, sizeof(long long) * (n + 1), s));
+    note_launch();
     scatter_transpose_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(keys, nnz, toff, cnt, tlist);
     BM_TRY(cudaGetLastError());
+    note_launch();
     pair_counts_kernel<<<grid_for(n, 256), 256, 0, s>>>(toff, n, cnt);
     BM_TRY(cudaGetLastError());
     long long* poff;
@@ -174,6 +179,7 @@ bool build_edges(const unsigned long long* keys, long long nnz, long long n, lon
     unsigned long long *pairs, *tmp;
     BM_ALLOC(pairs, unsigned long long, P);
     BM_ALLOC(tmp, unsigned long long, P);
+    note_launch();
     emit_pairs_kernel<<<grid_for(n * 32, 256), 256, 0, s>>>(toff, tlist, n, poff, pairs);
     BM_TRY(cudaGetLastError());
     ar.release(tlist);
@@ -184,6 +190,7 @@ bool build_edges(const unsigned long long* keys, long long nnz, long long n, lon
     BM_ALLOC(flags, long long, P);
     long long* pos;
     BM_ALLOC(pos, long long, P + 1);
+    note_launch();
     unique_flags_kernel<<<grid_for(P, 256), 256, 0, s>>>(sorted, P, flags);
     BM_TRY(cudaGetLastError());
     BM_TRY(exclusive_scan_i64(flags, pos, P, ar, s));
@@ -197,6 +204,7 @@ bool build_edges(const unsigned long long* keys, long long nnz, long long n, lon
     }
     int* edges;
     BM_ALLOC(edges, int, 2 * E);
+    note_launch();
     unique_scatter_kernel<<<grid_for(P, 256), 256, 0, s>>>(sorted, P, pos, edges);
     BM_TRY(cudaGetLastError());
     ar.release(pos);

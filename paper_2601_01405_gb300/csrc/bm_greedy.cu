@@ -34,6 +34,10 @@ __global__ void __launch_bounds__(kSelThreads) greedy_select_kernel(
     const __nv_bfloat16* __restrict__ Aug, int d_pad, __nv_bfloat16* cH, __nv_bfloat16* cLo,
     __nv_bfloat16* cAug) {
     if (st->done) return;
+    if (st->error & kErrTimeout) {  // a bounded wait expired in a previous step: stop the loop
+        if (threadIdx.x == 0) st->done = 1;
+        return;
+    }
     __shared__ int s_scan[33];
     __shared__ int s_found;
     __shared__ long long s_pos;
@@ -207,9 +211,10 @@ __global__ void __launch_bounds__(256) greedy_apply_kernel(DeviceState* st, cons
 cudaError_t launch_greedy_select(const GreedyBuffers& g, const Prepared& pts, int S, bool want_tc,
                                  cudaStream_t s) {
     const int words = S / 32;
+    note_launch();
     greedy_select_kernel<<<1, kSelThreads, 0, s>>>(
         g.st, g.covered, pts.rows, S, g.slot_of, g.cand_ids, g.conflict, g.row_any, words, pts.x, pts.phi,
-        pts.d, g.cand.phi == nullptr ? nullptr : const_cast<float*>(g.cand.x), g.cand.phi, want_tc ? 1 : 0,
+        pts.d, const_cast<float*>(g.cand.x), g.cand.phi, want_tc ? 1 : 0,
         pts.hi, pts.lo, pts.aug, pts.d_pad, g.cand.hi, g.cand.lo, g.cand.aug);
     return cudaGetLastError();
 }
@@ -224,12 +229,14 @@ cudaError_t launch_greedy_resolve(const GreedyBuffers& g, int S, cudaStream_t s)
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
+    note_launch();
     greedy_resolve_kernel<<<1, 256, smem, s>>>(g.st, g.conflict, g.row_any, words, g.cand_ids, g.ordinal,
                                                g.landmarks);
     return cudaGetLastError();
 }
 
 cudaError_t launch_greedy_apply(const GreedyBuffers& g, cudaStream_t s) {
+    note_launch();
     greedy_apply_kernel<<<152 * 8, 256, 0, s>>>(g.st, g.step_keys, g.step_cap, g.ordinal, g.covered, g.mem_keys,
                                                  g.mem_cap);
     return cudaGetLastError();

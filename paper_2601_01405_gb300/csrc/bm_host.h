@@ -31,6 +31,10 @@ private:
 
 void device_free(const bm_options* opt, cudaStream_t s, void* p);
 
+// Kernel launches issued by the current thread (reported in bm_stats).
+extern thread_local long long g_kernel_launches;
+inline void note_launch() { ++g_kernel_launches; }
+
 // Failure carried up to the C-ABI.
 struct Failure {
     bm_status status;

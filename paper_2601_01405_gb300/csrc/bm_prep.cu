@@ -92,6 +92,7 @@ cudaError_t launch_prep(const float* x, long long rows, int d, double eps2, bool
     if (rows == 0) return cudaSuccess;
     long long blocks = (rows + 7) / 8;
     if (blocks > 152 * 16) blocks = 152 * 16;
+    note_launch();
     prep_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, rows, d, eps2, a_side ? 1 : 0, want_tc ? 1 : 0,
                                                  out.phi, out.hi, out.lo, out.aug, out.d_pad,
                                                  max_norm_bits, bad_flag);
@@ -136,6 +137,7 @@ __global__ void delta_kernel(DeviceState* st, int path, int d, int d_pad, double
 
 cudaError_t launch_delta(DeviceState* st, int path, int d, int d_pad, double eps2, bool same_sets,
                          cudaStream_t s) {
+    note_launch();
     delta_kernel<<<1, 1, 0, s>>>(st, path, d, d_pad, eps2, same_sets ? 1 : 0);
     return cudaGetLastError();
 }

@@ -91,6 +91,7 @@ cudaError_t exclusive_scan(const T* in, T* out, long long n, Arena& ar, cudaStre
     const long long blocks = (n + kScanTile - 1) / kScanTile;
     T* sums = (T*)ar.get(sizeof(T) * (blocks + 1));
     if (!sums) return cudaErrorMemoryAllocation;
+    note_launch();
     scan_tile_kernel<T><<<(unsigned)blocks, kScanThreads, 0, s>>>(in, nullptr, n, sums, nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -102,6 +103,7 @@ cudaError_t exclusive_scan(const T* in, T* out, long long n, Arena& ar, cudaStre
         e = exclusive_scan<T>(sums, sums_scan, blocks, ar, s);
     }
     if (e != cudaSuccess) return e;
+    note_launch();
     scan_tile_kernel<T><<<(unsigned)blocks, kScanThreads, 0, s>>>(in, out, n, nullptr, sums_scan);
     e = cudaGetLastError();
     ar.release(sums_scan);
@@ -184,11 +186,13 @@ cudaError_t radix_sort_u64(unsigned long long* keys, unsigned long long* tmp, lo
     unsigned long long* src = keys;
     unsigned long long* dst = tmp;
     for (int sh : shifts) {
+        note_launch();
         radix_hist_kernel<<<(unsigned)tiles, kRadixThreads, 0, s>>>(src, n, sh, counts, tiles);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         e = exclusive_scan<unsigned>(counts, offs, cn, ar, s);
         if (e != cudaSuccess) return e;
+        note_launch();
         radix_scatter_kernel<<<(unsigned)tiles, kRadixThreads, 0, s>>>(src, dst, n, sh, offs, tiles);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -176,6 +176,7 @@ cudaError_t launch_sweep_fp32(const SweepDesc& s, cudaStream_t stream) {
     const long long b_tiles = (s.b->rows + BN - 1) / BN;
     const long long tiles = p.a_tiles * b_tiles;
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    note_launch();
     sweep_fp32_kernel<<<(unsigned)tiles, NT, 0, stream>>>(p);
     return cudaGetLastError();
 }

@@ -1,13 +1,546 @@
-// bm_tile_tc.cu -- K(b): tcgen05 tensor-core distance tiles (written next).
+// bm_tile_tc.cu -- K(b): distance tiles on the tcgen05 tensor cores.
+//
+// Decision rule (open ball, Sec. 2.1; exact range set, Sec. 4): x is in
+// R_eps(q) iff D(q,x) < eps^2.  Following the algebraic decomposition of
+// Sec. 3.2 the tile evaluates, for 128 query rows x NT points,
+//     v = q.x - phi_q - phi_x = (eps^2 - D)/2,      phi = ||.||^2/2 - eps^2/4
+// as one FP32 accumulation in tensor memory:
+//     q.x ~ hi_q.hi_x + lo_q.hi_x + hi_q.lo_x      (bf16 split products, exact in FP32)
+//     - phi_q - phi_x                              (the 16-wide augmentation block)
+// Pairs with v > delta are members, v < -delta are not, and the band in
+// between is re-decided in FP64 by the epilogue (verified range set, Sec. 4.3).
+//
+// Kernel organisation (one CTA per SM, persistent over work items):
+//   warp 0  TMA producer: one point tile (B, NT rows x all K) per work item,
+//           then the K chunks of up to 8 query tiles (A, 128 rows each)
+//           through a ring of shared-memory stages
+//   warp 1  allocates tensor memory; lane 0 issues tcgen05.mma (M=128, N=NT,
+//           K=16 per instruction) into one of two TMEM accumulators
+//   warps 2-5  epilogue: tcgen05.ld of the accumulator (one TMEM lane = one
+//           query row per thread), classification, FP64 band recheck and
+//           warp-aggregated hit emission
+// Every mbarrier wait is bounded in time; on expiry the kernel records
+// kErrTimeout, drains its in-flight copies and MMAs, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <string>
+
 #include "bm_host.h"
 
 namespace bm {
 
-bool tc_supported() { return false; }
+namespace {
 
-cudaError_t launch_sweep_tc(const SweepDesc&, cudaStream_t, std::string* why) {
-    if (why) *why = "tensor-core tiles not built in this version";
-    return cudaErrorNotSupported;
+constexpr int kThreads = 192;
+constexpr int kMaxGroup = 8;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
+constexpr unsigned long long kDrainNs = 200000000ull;  // 0.2 s
+
+struct TcArgs {
+    CUtensorMap a_hi, a_lo, a_aug, b_hi, b_lo, b_aug;
+    const float* ax;      // query rows, float32 (band recheck)
+    const float* bx;      // points, float32 (band recheck)
+    long long a_rows_max;
+    const int* a_rows_dev;
+    long long n;
+    int d;
+    int d_pad;
+    int check_done;
+    int pad0;
+    double eps2;
+    DeviceState* st;
+    HitSink sink;
+};
+
+struct Ctl {
+    unsigned long long b_full[2], b_empty[2];
+    unsigned long long a_full[16], a_empty[16];
+    unsigned long long t_full[2], t_empty[2];
+    unsigned long long drain;
+    unsigned tmem_base;
+    int abort_flag;
+};
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool bar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait.  Returns false when the CTA is aborting or the bound expired.
+__device__ __forceinline__ bool bar_wait(unsigned long long* b, uint32_t parity, volatile int* abort_flag,
+                                         int* gerr) {
+    const uint32_t bar = su32(b);
+    if (bar_try(bar, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    while (true) {
+        if (bar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (gtimer() - t0 > kWaitNs) {
+            *abort_flag = 1;
+            atomicOr(gerr, kErrTimeout);
+            return false;
+        }
+    }
+}
+
+// Bounded wait used while draining; ignores the abort flag.
+__device__ __forceinline__ void bar_drain(unsigned long long* b, uint32_t parity) {
+    const uint32_t bar = su32(b);
+    const unsigned long long t0 = gtimer();
+    while (!bar_try(bar, parity) && gtimer() - t0 < kDrainNs) {
+    }
+}
+
+__device__ __forceinline__ void bar_init(unsigned long long* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void bar_expect_tx(unsigned long long* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bar_arrive(unsigned long long* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+
+__device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, unsigned long long* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(su32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): K-major operand with a swizzle
+// atom of 8 rows x `span` bytes; atoms are stacked every 8*span bytes.
+__device__ __forceinline__ unsigned long long sdesc(uint32_t addr, uint32_t span) {
+    const uint32_t layout = span == 128 ? 2u : (span == 64 ? 4u : 6u);  // SW128 / SW64 / SW32
+    return (unsigned long long)((addr & 0x3FFFFu) >> 4) | (1ull << 16) |
+           ((unsigned long long)((8u * span) >> 4) << 32) | (1ull << 46) | ((unsigned long long)layout << 61);
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t d, unsigned long long a, unsigned long long b, uint32_t idesc,
+                                    uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(unsigned long long* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Byte sizes of the shared-memory regions for a configuration.
+struct Layout {
+    int CK, NT, BBUF, ASTG, nc;
+    uint32_t a_chunk, b_chunk, b_aug, b_bytes, b_stride, a_off, ctl_off, total;
+};
+
+__host__ __device__ inline Layout make_layout(int CK, int NT, int BBUF, int ASTG, int d_pad) {
+    Layout L;
+    L.CK = CK;
+    L.NT = NT;
+    L.BBUF = BBUF;
+    L.ASTG = ASTG;
+    L.nc = d_pad / CK;
+    L.a_chunk = 128u * CK * 2u;
+    L.b_chunk = (uint32_t)NT * CK * 2u;
+    L.b_aug = (uint32_t)NT * 32u;
+    L.b_bytes = 2u * L.nc * L.b_chunk + L.b_aug;
+    L.b_stride = (L.b_bytes + 1023u) & ~1023u;
+    L.a_off = BBUF * L.b_stride;
+    L.ctl_off = L.a_off + ASTG * L.a_chunk;
+    L.total = L.ctl_off + 1024u + 1024u;  // control block + alignment slack
+    return L;
+}
+
+template <int CK, int NT, int BBUF, int ASTG>
+__global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_constant__ TcArgs p) {
+    if (p.check_done && p.st->done) return;
+    const long long a_rows = p.a_rows_dev ? (long long)*p.a_rows_dev : p.a_rows_max;
+    if (a_rows <= 0 || p.n <= 0) return;
+
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const Layout L = make_layout(CK, NT, BBUF, ASTG, p.d_pad);
+    const int nc = L.nc;
+    Ctl* ctl = reinterpret_cast<Ctl*>(smem + L.ctl_off);
+    const uint32_t sbase = su32(smem);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long a_tiles = (a_rows + 127) / 128;
+    const int G = (int)(a_tiles < kMaxGroup ? a_tiles : kMaxGroup);
+    const long long n_groups = (a_tiles + G - 1) / G;
+    const long long b_tiles = (p.n + NT - 1) / NT;
+    const long long items = b_tiles * n_groups;
+    constexpr uint32_t kTmemCols = 2 * NT;
+    constexpr uint32_t kIdesc = idesc_bf16(128, NT);
+    constexpr uint32_t kSpan = CK * 2;
+    int* gerr = &p.st->error;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < BBUF; ++i) {
+            bar_init(&ctl->b_full[i], 1);
+            bar_init(&ctl->b_empty[i], 1);
+        }
+        for (int i = 0; i < ASTG; ++i) {
+            bar_init(&ctl->a_full[i], 1);
+            bar_init(&ctl->a_empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            bar_init(&ctl->t_full[i], 1);
+            bar_init(&ctl->t_empty[i], 4);
+        }
+        bar_init(&ctl->drain, 1);
+        ctl->abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&ctl->tmem_base)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = ctl->tmem_base;
+    volatile int* abort_flag = &ctl->abort_flag;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            uint32_t a_st = 0, a_ph = 0, b_buf = 0, b_ph = 0;
+            bool ok = true;
+            // parity of the last load issued into each stage / buffer (for draining)
+            int a_last[ASTG], b_last[BBUF];
+            for (int i = 0; i < ASTG; ++i) a_last[i] = -1;
+            for (int i = 0; i < BBUF; ++i) b_last[i] = -1;
+            for (long long item = blockIdx.x; ok && item < items; item += gridDim.x) {
+                const long long bt = item / n_groups, g = item % n_groups;
+                const long long at0 = g * G;
+                const long long at1 = (at0 + G < a_tiles) ? at0 + G : a_tiles;
+                const int yb = (int)(bt * NT);
+                if (!bar_wait(&ctl->b_empty[b_buf], b_ph ^ 1, abort_flag, gerr)) { ok = false; break; }
+                bar_expect_tx(&ctl->b_full[b_buf], L.b_bytes);
+                const uint32_t bb = sbase + b_buf * L.b_stride;
+                for (int c = 0; c < nc; ++c) {
+                    tma_load(bb + c * L.b_chunk, &p.b_hi, &ctl->b_full[b_buf], c * CK, yb);
+                    tma_load(bb + (nc + c) * L.b_chunk, &p.b_lo, &ctl->b_full[b_buf], c * CK, yb);
+                }
+                tma_load(bb + 2 * nc * L.b_chunk, &p.b_aug, &ctl->b_full[b_buf], 0, yb);
+                b_last[b_buf] = (int)b_ph;
+                if (++b_buf == BBUF) { b_buf = 0; b_ph ^= 1; }
+                for (long long at = at0; ok && at < at1; ++at) {
+                    const int ya = (int)(at * 128);
+                    for (int q = 0; q <= 2 * nc; ++q) {
+                        if (!bar_wait(&ctl->a_empty[a_st], a_ph ^ 1, abort_flag, gerr)) { ok = false; break; }
+                        const uint32_t dst = sbase + L.a_off + a_st * L.a_chunk;
+                        if (q < nc) {
+                            bar_expect_tx(&ctl->a_full[a_st], L.a_chunk);
+                            tma_load(dst, &p.a_hi, &ctl->a_full[a_st], q * CK, ya);
+                        } else if (q < 2 * nc) {
+                            bar_expect_tx(&ctl->a_full[a_st], L.a_chunk);
+                            tma_load(dst, &p.a_lo, &ctl->a_full[a_st], (q - nc) * CK, ya);
+                        } else {
+                            bar_expect_tx(&ctl->a_full[a_st], 128u * 32u);
+                            tma_load(dst, &p.a_aug, &ctl->a_full[a_st], 0, ya);
+                        }
+                        a_last[a_st] = (int)a_ph;
+                        if (++a_st == ASTG) { a_st = 0; a_ph ^= 1; }
+                    }
+                }
+            }
+            // drain: every issued copy has landed before shared memory is released
+            for (int i = 0; i < ASTG; ++i)
+                if (a_last[i] >= 0) bar_drain(&ctl->a_full[i], (uint32_t)a_last[i]);
+            for (int i = 0; i < BBUF; ++i)
+                if (b_last[i] >= 0) bar_drain(&ctl->b_full[i], (uint32_t)b_last[i]);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            uint32_t a_st = 0, a_ph = 0, b_buf = 0, b_ph = 0, t_buf = 0, t_ph = 0;
+            bool ok = true;
+            for (long long item = blockIdx.x; ok && item < items; item += gridDim.x) {
+                const long long g = item % n_groups;
+                const long long at0 = g * G;
+                const long long at1 = (at0 + G < a_tiles) ? at0 + G : a_tiles;
+                if (!bar_wait(&ctl->b_full[b_buf], b_ph, abort_flag, gerr)) { ok = false; break; }
+                fence_after();
+                const uint32_t bb = sbase + b_buf * L.b_stride;
+                for (long long at = at0; ok && at < at1; ++at) {
+                    if (!bar_wait(&ctl->t_empty[t_buf], t_ph ^ 1, abort_flag, gerr)) { ok = false; break; }
+                    fence_after();
+                    const uint32_t dacc = tmem + t_buf * NT;
+                    uint32_t acc = 0;
+                    for (int q = 0; q <= 2 * nc; ++q) {
+                        if (!bar_wait(&ctl->a_full[a_st], a_ph, abort_flag, gerr)) { ok = false; break; }
+                        fence_after();
+                        const uint32_t aa = sbase + L.a_off + a_st * L.a_chunk;
+                        if (q < nc) {
+#pragma unroll
+                            for (int k = 0; k < CK / 16; ++k) {
+                                const unsigned long long ad = sdesc(aa + k * 32, kSpan);
+                                mma(dacc, ad, sdesc(bb + q * L.b_chunk + k * 32, kSpan), kIdesc, acc);
+                                acc = 1;
+                                mma(dacc, ad, sdesc(bb + (nc + q) * L.b_chunk + k * 32, kSpan), kIdesc, 1);
+                            }
+                        } else if (q < 2 * nc) {
+                            const int c = q - nc;
+#pragma unroll
+                            for (int k = 0; k < CK / 16; ++k)
+                                mma(dacc, sdesc(aa + k * 32, kSpan), sdesc(bb + c * L.b_chunk + k * 32, kSpan),
+                                    kIdesc, 1);
+                        } else {
+                            mma(dacc, sdesc(aa, 32), sdesc(bb + 2 * nc * L.b_chunk, 32), kIdesc, 1);
+                        }
+                        mma_commit(&ctl->a_empty[a_st]);
+                        if (++a_st == ASTG) { a_st = 0; a_ph ^= 1; }
+                    }
+                    if (!ok) break;
+                    mma_commit(&ctl->t_full[t_buf]);
+                    if (++t_buf == 2) { t_buf = 0; t_ph ^= 1; }
+                }
+                if (!ok) break;
+                mma_commit(&ctl->b_empty[b_buf]);
+                if (++b_buf == BBUF) { b_buf = 0; b_ph ^= 1; }
+            }
+            // drain: all issued MMAs complete before TMEM / shared memory are released
+            mma_commit(&ctl->drain);
+            bar_drain(&ctl->drain, 0);
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int quarter = warp & 3;               // TMEM lanes 32*quarter .. +31
+        const float delta = p.st->delta;
+        uint32_t t_buf = 0, t_ph = 0;
+        unsigned long long band_local = 0, pairs_local = 0;
+        bool ok = true;
+        for (long long item = blockIdx.x; ok && item < items; item += gridDim.x) {
+            const long long bt = item / n_groups, g = item % n_groups;
+            const long long at0 = g * G;
+            const long long at1 = (at0 + G < a_tiles) ? at0 + G : a_tiles;
+            const long long col_base = bt * NT;
+            for (long long at = at0; at < at1; ++at) {
+                const bool w = __all_sync(kFull, bar_wait(&ctl->t_full[t_buf], t_ph, abort_flag, gerr));
+                if (!w) { ok = false; break; }
+                fence_after();
+                const long long row = at * 128 + quarter * 32 + lane;
+                const bool row_ok = row < a_rows;
+                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + t_buf * NT;
+#pragma unroll 1
+                for (int j = 0; j < NT / 32; ++j) {
+                    uint32_t r[32];
+                    tmem_ld32(taddr + j * 32, r);
+                    const long long col0 = col_base + j * 32;
+                    float mx = __uint_as_float(r[0]);
+#pragma unroll
+                    for (int i = 1; i < 32; ++i) mx = fmaxf(mx, __uint_as_float(r[i]));
+                    unsigned hit = 0, band = 0;
+                    if (row_ok && mx >= -delta) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            const float v = __uint_as_float(r[i]);
+                            const bool in_range = col0 + i < p.n;
+                            if (in_range && v > delta) hit |= 1u << i;
+                            else if (in_range && v >= -delta) band |= 1u << i;
+                        }
+                    }
+                    if (band) {
+                        band_local += __popc(band);
+                        const float* arow = p.ax + row * p.d;
+                        unsigned bm_ = band;
+                        while (bm_) {
+                            const int i = __ffs(bm_) - 1;
+                            bm_ &= bm_ - 1;
+                            if (exact_sqdist(arow, p.bx + (col0 + i) * p.d, p.d) < p.eps2) hit |= 1u << i;
+                        }
+                    }
+                    if (__any_sync(kFull, hit != 0u)) emit_hits_run(p.sink, (unsigned)row, (unsigned)col0, hit);
+                }
+                if (threadIdx.x == 64) {
+                    const long long ra = (a_rows - at * 128) < 128 ? (a_rows - at * 128) : 128;
+                    const long long rb = (p.n - col_base) < NT ? (p.n - col_base) : NT;
+                    pairs_local += (unsigned long long)(ra * rb);
+                }
+                fence_before();
+                __syncwarp();
+                if (lane == 0) bar_arrive(&ctl->t_empty[t_buf]);
+                if (++t_buf == 2) { t_buf = 0; t_ph ^= 1; }
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) band_local += __shfl_xor_sync(kFull, band_local, o);
+        if (lane == 0 && band_local) atomicAdd(p.sink.band_count, band_local);
+        if (threadIdx.x == 64 && pairs_local) atomicAdd(p.sink.pair_count, pairs_local);
+    }
+
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------- host side
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* base, long long rows, int cols, int box_cols, int box_rows,
+              CUtensorMapSwizzle sw) {
+    auto enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)(rows > 0 ? rows : 1)};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+CUtensorMapSwizzle swizzle_for(int CK) {
+    return CK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : (CK == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
+}
+
+constexpr uint32_t kMaxSmem = 232448;
+
+template <int CK, int NT, int BBUF, int ASTG>
+cudaError_t launch_cfg(TcArgs& args, long long a_rows_max, cudaStream_t stream, std::string* why) {
+    const Layout L0 = make_layout(CK, NT, BBUF, ASTG, args.d_pad);
+    // at least 120 KB so that two CTAs never share an SM (each holds 2*NT TMEM columns)
+    Layout L = L0;
+    if (L.total < 120u * 1024u) L.total = 120u * 1024u;
+    auto kern = sweep_tc_kernel<CK, NT, BBUF, ASTG>;
+    static int attr_bytes = 0;
+    if (attr_bytes < (int)L.total) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+        if (e != cudaSuccess) {
+            if (why) *why = "cannot reserve shared memory";
+            return e;
+        }
+        attr_bytes = (int)L.total;
+    }
+    const long long a_tiles = (a_rows_max + 127) / 128;
+    const long long G = a_tiles < kMaxGroup ? a_tiles : kMaxGroup;
+    const long long items = ((args.n + NT - 1) / NT) * ((a_tiles + G - 1) / G);
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long grid = items < sms ? items : sms;
+    if (grid <= 0) return cudaSuccess;
+    note_launch();
+    kern<<<(unsigned)grid, kThreads, L.total, stream>>>(args);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_supported() { return encode_fn() != nullptr; }
+
+cudaError_t launch_sweep_tc(const SweepDesc& s, cudaStream_t stream, std::string* why) {
+    if (s.a_rows_max == 0 || s.b->rows == 0) return cudaSuccess;
+    const int d_pad = s.b->d_pad;
+    if (d_pad > 512) {
+        if (why) *why = "tensor-core tiles support d <= 512";
+        return cudaErrorNotSupported;
+    }
+    TcArgs args;
+    memset(&args, 0, sizeof(args));
+    const int CK = d_pad <= 16 ? 16 : (d_pad <= 32 ? 32 : 64);
+    // configuration: point-tile width NT and buffering chosen to fit shared memory
+    int NT = 256, BBUF = 2;
+    if (CK == 64) {
+        const int nc = d_pad / 64;
+        if (make_layout(64, 256, 2, 4, d_pad).total <= kMaxSmem) { NT = 256; BBUF = 2; }
+        else if (make_layout(64, 128, 2, 4, d_pad).total <= kMaxSmem) { NT = 128; BBUF = 2; }
+        else if (make_layout(64, 128, 1, 4, d_pad).total <= kMaxSmem) { NT = 128; BBUF = 1; }
+        else { NT = 64; BBUF = 1; }
+        (void)nc;
+    }
+    const CUtensorMapSwizzle sw = swizzle_for(CK);
+    const long long arows = s.a->rows, brows = s.b->rows;
+    bool ok = make_map(&args.a_hi, s.a->hi, arows, d_pad, CK, 128, sw) &&
+              make_map(&args.a_lo, s.a->lo, arows, d_pad, CK, 128, sw) &&
+              make_map(&args.a_aug, s.a->aug, arows, 16, 16, 128, CU_TENSOR_MAP_SWIZZLE_32B) &&
+              make_map(&args.b_hi, s.b->hi, brows, d_pad, CK, NT, sw) &&
+              make_map(&args.b_lo, s.b->lo, brows, d_pad, CK, NT, sw) &&
+              make_map(&args.b_aug, s.b->aug, brows, 16, 16, NT, CU_TENSOR_MAP_SWIZZLE_32B);
+    if (!ok) {
+        if (why) *why = "tensor map encoding failed";
+        return cudaErrorInvalidValue;
+    }
+    args.ax = s.a->x;
+    args.bx = s.b->x;
+    args.a_rows_max = s.a_rows_max;
+    args.a_rows_dev = s.a_rows_dev;
+    args.n = brows;
+    args.d = s.b->d;
+    args.d_pad = d_pad;
+    args.check_done = s.check_done ? 1 : 0;
+    args.eps2 = s.eps2;
+    args.st = const_cast<DeviceState*>(s.st);
+    args.sink = s.sink;
+    if (CK == 16) return launch_cfg<16, 256, 2, 8>(args, s.a_rows_max, stream, why);
+    if (CK == 32) return launch_cfg<32, 256, 2, 8>(args, s.a_rows_max, stream, why);
+    if (NT == 256) return launch_cfg<64, 256, 2, 4>(args, s.a_rows_max, stream, why);
+    if (NT == 128 && BBUF == 2) return launch_cfg<64, 128, 2, 4>(args, s.a_rows_max, stream, why);
+    if (NT == 128) return launch_cfg<64, 128, 1, 4>(args, s.a_rows_max, stream, why);
+    return launch_cfg<64, 64, 1, 4>(args, s.a_rows_max, stream, why);
 }
 
 }  // namespace bm
