@@ -181,19 +181,64 @@ bm_status prepare(const float* x, long long rows, int d, double eps2, bool a_sid
     return BM_OK;
 }
 
-bm_status run_sweep(const SweepDesc& sd, int path, cudaStream_t s) {
+bm_status run_sweep(const SweepDesc& sd, int path, cudaStream_t s, int* grid) {
+    *grid = 0;
     if (path == BM_PATH_FP32) {
         TRY_CUDA(launch_sweep_fp32(sd, s));
         return BM_OK;
     }
     std::string why;
-    cudaError_t e = launch_sweep_tc(sd, s, &why);
+    cudaError_t e = launch_sweep_tc(sd, s, &why, grid);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(BM_ERR_CUDA, "tensor-core sweep: " + why + " (" + cudaGetErrorString(e) + ")");
     }
     return BM_OK;
 }
+
+// Hit and band-pair buffers of one sweep.  The tensor-core tiles write per-CTA
+// segments (raw, raw_band) that are compacted into keys / band; the FP32 tiles
+// write keys / band directly.
+struct SweepOut {
+    unsigned long long* keys = nullptr;
+    unsigned long long* band = nullptr;
+    unsigned long long* raw = nullptr;
+    unsigned long long* raw_band = nullptr;
+    unsigned long long* seg_counts = nullptr;
+    unsigned long long* band_seg_counts = nullptr;
+    unsigned long long cap = 0;
+};
+
+bm_status alloc_sweep_out(Arena& ar, bool tc, unsigned long long cap, int sms, SweepOut& o) {
+    o.cap = cap;
+    ALLOC(o.keys, unsigned long long, cap);
+    ALLOC(o.band, unsigned long long, cap);
+    if (tc) {
+        ALLOC(o.raw, unsigned long long, cap);
+        ALLOC(o.raw_band, unsigned long long, cap);
+        ALLOC(o.seg_counts, unsigned long long, sms);
+        ALLOC(o.band_seg_counts, unsigned long long, sms);
+    }
+    return BM_OK;
+}
+
+void release_sweep_out(Arena& ar, SweepOut& o, bool keep_keys) {
+    if (!keep_keys) ar.release(o.keys);
+    ar.release(o.band);
+    ar.release(o.raw);
+    ar.release(o.raw_band);
+    ar.release(o.seg_counts);
+    ar.release(o.band_seg_counts);
+    o = SweepOut();
+}
+
+struct SweepTimer;
+
+}  // namespace
+}  // namespace bm
+
+namespace bm {
+namespace {
 
 struct HostState {
     DeviceState* pinned = nullptr;
@@ -246,6 +291,46 @@ struct SweepTimer {
     }
 };
 
+// One distance sweep: tiles, compaction of the per-CTA segments (tensor-core
+// path), FP64 recheck of the band pairs.  sd.sink must already carry the
+// greedy bookkeeping (or none) and the statistics pointers.  Hits end up in
+// o.keys with their number in *count.
+bm_status sweep_stage(SweepDesc& sd, DeviceState* st, int path, SweepOut& o, unsigned long long* count,
+                      int overflow_bit, bool greedy, int sms, SweepTimer& stimer, cudaStream_t s) {
+    const bool tc = path == BM_PATH_TC_SPLIT3;
+    sd.sink.count = count;
+    sd.sink.cap = o.cap;
+    sd.sink.band_n = &st->band_n;
+    sd.sink.band_cap = o.cap;
+    if (tc) {
+        sd.sink.keys = o.raw;
+        sd.sink.band_keys = o.raw_band;
+        sd.sink.seg_counts = o.seg_counts;
+        sd.sink.band_seg_counts = o.band_seg_counts;
+        sd.sink.seg_cap = o.cap / sms;
+    } else {
+        sd.sink.keys = o.keys;
+        sd.sink.band_keys = o.band;
+        sd.sink.seg_counts = nullptr;
+        sd.sink.band_seg_counts = nullptr;
+        sd.sink.seg_cap = 0;
+    }
+    stimer.before();
+    int grid = 0;
+    bm_status rs = run_sweep(sd, path, s, &grid);
+    stimer.after();
+    if (rs != BM_OK) return rs;
+    if (tc) {
+        TRY_CUDA(launch_compact_segments(o.raw, sd.sink.seg_cap, o.seg_counts, grid, o.keys, count, st, overflow_bit,
+                                         greedy, greedy, s));
+        TRY_CUDA(launch_compact_segments(o.raw_band, sd.sink.seg_cap, o.band_seg_counts, grid, o.band, &st->band_n,
+                                         st, overflow_bit, greedy, greedy, s));
+    }
+    TRY_CUDA(launch_band_recheck(st, o.band, o.cap, sd.a->x, sd.b->x, sd.b->d, sd.eps2, o.keys, count, o.cap, sd.sink,
+                                 greedy, overflow_bit, greedy, s));
+    return BM_OK;
+}
+
 bm_status read_state(const DeviceState* dst, HostState& hs, DeviceState& out, cudaStream_t s) {
     if (!hs.pinned) return fail(BM_ERR_NOMEM, "pinned state buffer");
     TRY_CUDA(cudaMemcpyAsync(hs.pinned, dst, sizeof(DeviceState), cudaMemcpyDeviceToHost, s));
@@ -294,7 +379,11 @@ bm_status greedy_pass(const Prepared& pts, double eps2, int path, int S, Arena& 
         TRY_CUDA(cudaMemsetAsync(g.cand.lo, 0, sizeof(__nv_bfloat16) * S * pts.d_pad, s));
         TRY_CUDA(cudaMemsetAsync(g.cand.aug, 0, sizeof(__nv_bfloat16) * S * 16, s));
     }
-    ALLOC(g.step_keys, unsigned long long, step_cap);
+    const int sms = device_sm_count();
+    SweepOut so;
+    bm_status ars = alloc_sweep_out(ar, tc, step_cap, sms, so);
+    if (ars != BM_OK) return ars;
+    g.step_keys = so.keys;
     g.step_cap = step_cap;
     ALLOC(g.mem_keys, unsigned long long, mem_cap);
     g.mem_cap = mem_cap;
@@ -307,9 +396,6 @@ bm_status greedy_pass(const Prepared& pts, double eps2, int path, int S, Arena& 
     sd.st = st;
     sd.check_done = true;
     sd.eps2 = eps2;
-    sd.sink.keys = g.step_keys;
-    sd.sink.count = &st->step_hits;
-    sd.sink.cap = step_cap;
     sd.sink.slot_of = g.slot_of;
     sd.sink.conflict = g.conflict;
     sd.sink.row_any = g.row_any;
@@ -319,12 +405,12 @@ bm_status greedy_pass(const Prepared& pts, double eps2, int path, int S, Arena& 
 
     DeviceState h;
     int chunk = 2;
+    int regrows = 0;
     while (true) {
         for (int i = 0; i < chunk; ++i) {
             TRY_CUDA(launch_greedy_select(g, pts, S, tc, s));
-            stimer.before();
-            bm_status rs = run_sweep(sd, path, s);
-            stimer.after();
+            TRY_CUDA(launch_greedy_gather(g, pts, S, tc, s));
+            bm_status rs = sweep_stage(sd, st, path, so, &st->step_hits, kErrStepOverflow, true, sms, stimer, s);
             if (rs != BM_OK) return rs;
             TRY_CUDA(launch_greedy_resolve(g, S, s));
             TRY_CUDA(launch_greedy_apply(g, s));
@@ -333,20 +419,38 @@ bm_status greedy_pass(const Prepared& pts, double eps2, int path, int S, Arena& 
         if (rs != BM_OK) return rs;
         stimer.collect();
         if (h.error & kErrTimeout) return fail(BM_ERR_TIMEOUT, "a bounded device wait expired in the distance tiles");
-        if (h.error & kErrStepOverflow) {
-            step_cap = std::max<unsigned long long>(2 * h.step_hits, 2 * step_cap);
-            *retry = true;
-            return BM_OK;
+        if (h.error & (kErrStepOverflow | kErrMemberOverflow)) {
+            // a step stopped before committing anything: grow the buffer and redo it
+            if (++regrows > 64) return fail(BM_ERR_CAPACITY, "greedy buffers kept overflowing");
+            if (h.error & kErrStepOverflow) {
+                const unsigned long long need =
+                    std::max<unsigned long long>(h.max_seg * (unsigned long long)sms, std::max(h.step_hits, h.band_n)) *
+                    3 / 2;
+                step_cap = std::max<unsigned long long>(need, 2 * step_cap);
+                release_sweep_out(ar, so, false);
+                bm_status rs2 = alloc_sweep_out(ar, tc, step_cap, sms, so);
+                if (rs2 != BM_OK) return rs2;
+                g.step_keys = so.keys;
+                g.step_cap = step_cap;
+            }
+            if (h.error & kErrMemberOverflow) {
+                const unsigned long long need = std::max<unsigned long long>(2 * mem_cap, (h.mem_count + h.step_hits) * 3 / 2);
+                unsigned long long* nk;
+                ALLOC(nk, unsigned long long, need);
+                if (h.mem_count)
+                    TRY_CUDA(cudaMemcpyAsync(nk, g.mem_keys, sizeof(unsigned long long) * h.mem_count,
+                                             cudaMemcpyDeviceToDevice, s));
+                ar.release(g.mem_keys);
+                g.mem_keys = nk;
+                g.mem_cap = mem_cap = need;
+            }
+            TRY_CUDA(launch_greedy_rollback(g, s));
+            continue;
         }
         if (h.done) break;
         chunk = std::min(chunk * 2, 64);
     }
-    if (h.error & kErrMemberOverflow) {
-        mem_cap = h.mem_count + 1024;
-        *retry = true;
-        return BM_OK;
-    }
-    ar.release(g.step_keys);
+    release_sweep_out(ar, so, false);
     *landmarks_out = g.landmarks;
     *mem_keys_out = g.mem_keys;
     final_state = h;
@@ -469,11 +573,15 @@ bm_status bm_range_query(const float* X, int64_t n, int32_t d, const float* Q, i
             if (hbad) return fail(BM_ERR_ARG, "input holds NaN or Inf");
             unsigned long long cap = (unsigned long long)std::min<long long>(std::max<long long>(n, m) * 4 + (1 << 20),
                                                                               (long long)n * m);
+            if (tc) cap = std::max<unsigned long long>(cap, (unsigned long long)device_sm_count() * 4096);
             HostState hs;
             DeviceState h;
             unsigned long long* keys = nullptr;
-            for (int attempt = 0; attempt < 2; ++attempt) {
-                ALLOC(keys, unsigned long long, cap);
+            const int sms = device_sm_count();
+            for (int attempt = 0; attempt < 3; ++attempt) {
+                SweepOut so;
+                rs = alloc_sweep_out(ar, tc, cap, sms, so);
+                if (rs != BM_OK) return rs;
                 SweepDesc sd;
                 sd.a = &pq;
                 sd.b = &px;
@@ -483,22 +591,24 @@ bm_status bm_range_query(const float* X, int64_t n, int32_t d, const float* Q, i
                 sd.check_done = false;
                 sd.eps2 = eps2;
                 sd.sink = HitSink();
-                sd.sink.keys = keys;
-                sd.sink.count = &st->hit_count;
-                sd.sink.cap = cap;
                 sd.sink.band_count = &st->band_pairs;
                 sd.sink.pair_count = &st->tile_pairs;
-                stimer.before();
-                rs = run_sweep(sd, opt.path, s);
-                stimer.after();
+                rs = sweep_stage(sd, st, opt.path, so, &st->hit_count, kErrHitOverflow, false, sms, stimer, s);
                 if (rs != BM_OK) return rs;
                 rs = read_state(st, hs, h, s);
                 if (rs != BM_OK) return rs;
                 stimer.collect();
                 if (h.error & kErrTimeout) return fail(BM_ERR_TIMEOUT, "a bounded device wait expired");
-                if (h.hit_count <= cap) break;
-                ar.release(keys);
-                cap = h.hit_count;
+                const bool overflow = (h.error & kErrHitOverflow) != 0 || h.hit_count > cap || h.band_n > cap;
+                keys = so.keys;
+                release_sweep_out(ar, so, !overflow);
+                if (!overflow) break;
+                if (attempt == 2) return fail(BM_ERR_CAPACITY, "range query hit buffer kept overflowing");
+                cap = std::max<unsigned long long>(
+                    2 * cap, std::max(h.max_seg * (unsigned long long)sms, std::max(h.hit_count, h.band_n)) * 5 / 4 + 1024);
+                TRY_CUDA(cudaMemsetAsync(&st->error, 0, sizeof(int), s));
+                TRY_CUDA(cudaMemsetAsync(&st->max_seg, 0, sizeof(unsigned long long), s));
+                TRY_CUDA(cudaMemsetAsync(&st->band_n, 0, sizeof(unsigned long long), s));
                 TRY_CUDA(cudaMemsetAsync(&st->hit_count, 0, sizeof(unsigned long long), s));
                 TRY_CUDA(cudaMemsetAsync(&st->band_pairs, 0, sizeof(unsigned long long), s));
                 TRY_CUDA(cudaMemsetAsync(&st->tile_pairs, 0, sizeof(unsigned long long), s));
@@ -612,6 +722,7 @@ bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_opt
             if (hbad) return fail(BM_ERR_ARG, "input holds NaN or Inf");
             tm.mark();  // 1: prep done
             unsigned long long step_cap = (unsigned long long)std::min<long long>((long long)S * n, 1LL << 22);
+            if (tc) step_cap = std::max<unsigned long long>(step_cap, (unsigned long long)device_sm_count() * 2048);
             unsigned long long mem_cap = (unsigned long long)std::max<long long>(4 * n, 1LL << 20);
             HostState hs;
             unsigned long long* mem_keys = nullptr;

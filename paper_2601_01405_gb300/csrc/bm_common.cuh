@@ -36,6 +36,9 @@ struct DeviceState {
     unsigned int max_norm_q_bits;    // float bits of max ||q|| over the queries
     float delta;                     // band half-width in units of (eps^2 - D)/2
     int pad0;
+    unsigned long long max_seg;      // largest per-CTA hit segment seen by a compaction
+    unsigned long long band_n;       // band pairs awaiting the FP64 recheck (current sweep)
+    long long step_start_pos;        // scan_pos at the start of the current greedy step
 };
 
 // Where a distance tile delivers its (row, point) hits.
@@ -53,6 +56,18 @@ struct HitSink {
     int pad0;
     unsigned long long* band_count;
     unsigned long long* pair_count;
+    // Segmented mode (persistent tile kernels): CTA b appends to
+    // keys[b * seg_cap ..) through a shared-memory counter and publishes its
+    // count in seg_counts[b]; a compaction pass makes the keys contiguous.
+    unsigned long long* seg_counts;
+    unsigned long long seg_cap;
+    // Pairs inside the error band, (row << 32 | point), re-decided in FP64 by
+    // the band recheck kernel: contiguous (band_keys/band_n/band_cap) or
+    // segmented like the hits (band_seg_counts, seg_cap per CTA).
+    unsigned long long* band_keys;
+    unsigned long long* band_n;
+    unsigned long long band_cap;
+    unsigned long long* band_seg_counts;
 };
 
 // FP64 squared distance in coordinate order with separately rounded multiply
@@ -82,6 +97,22 @@ __device__ __forceinline__ unsigned long long warp_reserve(unsigned long long* c
     const unsigned total = __shfl_sync(kFull, x, 31);
     unsigned long long base = 0;
     if (lane == 31 && total) base = atomicAdd(counter, (unsigned long long)total);
+    base = __shfl_sync(kFull, base, 31);
+    return base + (x - cnt);
+}
+
+// Same as warp_reserve for a 32-bit counter (the per-CTA shared-memory counters).
+__device__ __forceinline__ unsigned warp_reserve32(unsigned* counter, unsigned cnt) {
+    const unsigned lane = lane_id();
+    unsigned x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(kFull, x, o);
+        if (lane >= (unsigned)o) x += y;
+    }
+    const unsigned total = __shfl_sync(kFull, x, 31);
+    unsigned base = 0;
+    if (lane == 31 && total) base = atomicAdd(counter, total);
     base = __shfl_sync(kFull, base, 31);
     return base + (x - cnt);
 }
@@ -126,6 +157,62 @@ __device__ __forceinline__ void emit_hits_run(const HitSink& sink, unsigned row,
             }
         }
     }
+}
+
+// Segmented-mode emission: reserve from the CTA's shared-memory counter
+// `ctr` (generic pointer) and write into the CTA's own key segment.
+__device__ __forceinline__ void emit_hits_run_seg(const HitSink& sink, unsigned long long* seg_keys,
+                                                  unsigned* ctr, unsigned row, unsigned col0,
+                                                  unsigned mask) {
+    const unsigned cnt = __popc(mask);
+    unsigned long long pos = warp_reserve32(ctr, cnt);
+    while (mask) {
+        const int j = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const unsigned col = col0 + (unsigned)j;
+        if (pos < sink.seg_cap) seg_keys[pos] = ((unsigned long long)row << 32) | col;
+        ++pos;
+        if (sink.slot_of) {
+            const int s = sink.slot_of[col];
+            if (s > (int)row) {
+                atomicOr(&sink.conflict[(size_t)row * sink.conflict_words + (s >> 5)], 1u << (s & 31));
+                atomicOr(&sink.row_any[row >> 5], 1u << (row & 31));
+            }
+        }
+    }
+}
+
+// Append (row, col0 + j) for every set bit j of mask to keys, reserving from a
+// global 64-bit counter (ctr64) or a shared 32-bit one (ctr32), no bookkeeping.
+// All 32 lanes must call it.
+__device__ __forceinline__ void emit_plain_run(unsigned long long* keys, unsigned long long* ctr64, unsigned* ctr32,
+                                               unsigned long long cap, unsigned row, unsigned col0, unsigned mask) {
+    unsigned long long pos = ctr32 ? (unsigned long long)warp_reserve32(ctr32, __popc(mask))
+                                   : warp_reserve(ctr64, __popc(mask));
+    while (mask) {
+        const int j = __ffs(mask) - 1;
+        mask &= mask - 1;
+        if (pos < cap) keys[pos] = ((unsigned long long)row << 32) | (col0 + (unsigned)j);
+        ++pos;
+    }
+}
+
+// FP64 squared distance in coordinate order, four coordinates per load
+// (rows 16-byte aligned, d a multiple of 4); same arithmetic as exact_sqdist.
+__device__ __forceinline__ double exact_sqdist4(const float* __restrict__ a, const float* __restrict__ b, int d) {
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    const float4* b4 = reinterpret_cast<const float4*>(b);
+    double s = 0.0;
+#pragma unroll 4
+    for (int i = 0; i < d / 4; ++i) {
+        const float4 x = a4[i], y = b4[i];
+        double t;
+        t = __dsub_rn((double)x.x, (double)y.x); s = __dadd_rn(s, __dmul_rn(t, t));
+        t = __dsub_rn((double)x.y, (double)y.y); s = __dadd_rn(s, __dmul_rn(t, t));
+        t = __dsub_rn((double)x.z, (double)y.z); s = __dadd_rn(s, __dmul_rn(t, t));
+        t = __dsub_rn((double)x.w, (double)y.w); s = __dadd_rn(s, __dmul_rn(t, t));
+    }
+    return s;
 }
 
 // Block-wide exclusive scan of one int per thread (blockDim.x multiple of 32, <= 1024).

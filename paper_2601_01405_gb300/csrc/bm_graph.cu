@@ -100,6 +100,30 @@ __global__ void unique_scatter_kernel(const unsigned long long* keys, long long 
     }
 }
 
+__global__ void compact_segments_kernel(const unsigned long long* src, unsigned long long seg_cap,
+                                        const unsigned long long* seg_counts, int nseg, unsigned long long* dst,
+                                        unsigned long long* count_out, DeviceState* st, int overflow_bit,
+                                        int check_done, int stop_on_overflow) {
+    if (check_done && st->done) return;
+    __shared__ unsigned long long s_pre, s_cnt;
+    if (threadIdx.x == 0) {
+        unsigned long long pre = 0;
+        for (int q = 0; q < (int)blockIdx.x; ++q) pre += seg_counts[q] < seg_cap ? seg_counts[q] : seg_cap;
+        const unsigned long long c = seg_counts[blockIdx.x];
+        s_pre = pre;
+        s_cnt = c < seg_cap ? c : seg_cap;
+        if (c > seg_cap) {
+            atomicOr(&st->error, overflow_bit);
+            atomicMax(&st->max_seg, c);
+            if (stop_on_overflow) st->done = 1;
+        }
+        if ((int)blockIdx.x == nseg - 1) *count_out = pre + s_cnt;
+    }
+    __syncthreads();
+    const unsigned long long* in = src + (unsigned long long)blockIdx.x * seg_cap;
+    for (unsigned long long i = threadIdx.x; i < s_cnt; i += blockDim.x) dst[s_pre + i] = in[i];
+}
+
 unsigned grid_for(long long n, int threads) {
     long long b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -118,6 +142,17 @@ cudaError_t launch_csr_from_sorted(const unsigned long long* keys, long long nnz
     }
     note_launch();
     csr_offsets_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(keys, nnz, rows, offsets, ids);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact_segments(const unsigned long long* src, unsigned long long seg_cap,
+                                    const unsigned long long* seg_counts, int nseg, unsigned long long* dst,
+                                    unsigned long long* count_out, DeviceState* st, int overflow_bit,
+                                    bool check_done, bool stop_on_overflow, cudaStream_t s) {
+    if (nseg <= 0) return cudaSuccess;
+    note_launch();
+    compact_segments_kernel<<<nseg, 256, 0, s>>>(src, seg_cap, seg_counts, nseg, dst, count_out, st, overflow_bit,
+                                                  check_done ? 1 : 0, stop_on_overflow ? 1 : 0);
     return cudaGetLastError();
 }
 

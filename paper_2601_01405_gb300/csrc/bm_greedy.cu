@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(kSelThreads) greedy_select_kernel(
     if (tid == 0) {
         s_found = 0;
         s_pos = st->scan_pos;
+        st->step_start_pos = st->scan_pos;   // lets the host redo this step with larger buffers
     }
     __syncthreads();
 
@@ -94,82 +95,125 @@ __global__ void __launch_bounds__(kSelThreads) greedy_select_kernel(
         st->cand_count = found;
         st->scan_pos = s_pos < n ? s_pos : n;
         st->step_hits = 0;
+        st->band_n = 0;
         st->candidates += (unsigned long long)found;
         if (found == 0) st->done = 1;
         else st->steps += 1;
     }
-    // 3. register the candidates and gather their rows
+    // 3. register the candidates (their rows are gathered by greedy_gather_kernel)
     for (int s = tid; s < found; s += kSelThreads) slot_of[cand_ids[s]] = s;
-    for (long long e = tid; e < (long long)found * d; e += kSelThreads) {
-        const int s = (int)(e / d), i = (int)(e % d);
-        cand_x[e] = X[(long long)cand_ids[s] * d + i];
-    }
-    for (int s = tid; s < found; s += kSelThreads) cand_phi[s] = phi[cand_ids[s]];
+}
+
+// One warp per candidate: copy its float32 row, phi and, for the tensor-core
+// path, its bf16 hi/lo rows and A-side augmentation (the B-side row with the
+// halves [0,3) and [3,6) swapped) into the contiguous candidate operands.
+__global__ void __launch_bounds__(256) greedy_gather_kernel(
+    const DeviceState* st, const int* __restrict__ cand_ids, const float* __restrict__ X,
+    const float* __restrict__ phi, int d, float* __restrict__ cand_x, float* __restrict__ cand_phi, int want_tc,
+    const unsigned* __restrict__ H, const unsigned* __restrict__ Lo, const __nv_bfloat16* __restrict__ Aug,
+    int d_pad, unsigned* __restrict__ cH, unsigned* __restrict__ cLo, __nv_bfloat16* __restrict__ cAug) {
+    if (st->done) return;
+    const int s = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (s >= st->cand_count) return;
+    const long long id = cand_ids[s];
+    for (int i = lane; i < d; i += 32) cand_x[(long long)s * d + i] = X[id * d + i];
+    if (lane == 0) cand_phi[s] = phi[id];
     if (want_tc) {
-        for (long long e = tid; e < (long long)found * d_pad; e += kSelThreads) {
-            const int s = (int)(e / d_pad), i = (int)(e % d_pad);
-            const long long src = (long long)cand_ids[s] * d_pad + i;
-            cH[e] = H[src];
-            cLo[e] = Lo[src];
+        const int w = d_pad / 2;  // bf16 pairs per row
+        for (int i = lane; i < w; i += 32) {
+            cH[(long long)s * w + i] = H[id * w + i];
+            cLo[(long long)s * w + i] = Lo[id * w + i];
         }
-        // A-side augmentation = B-side row with its halves [0,3) and [3,6) swapped
-        for (long long e = tid; e < (long long)found * 16; e += kSelThreads) {
-            const int s = (int)(e >> 4), i = (int)(e & 15);
-            const int src = i < 3 ? i + 3 : (i < 6 ? i - 3 : i);
-            cAug[e] = Aug[(long long)cand_ids[s] * 16 + src];
+        if (lane < 16) {
+            const int src = lane < 3 ? lane + 3 : (lane < 6 ? lane - 3 : lane);
+            cAug[(long long)s * 16 + lane] = Aug[id * 16 + src];
         }
     }
 }
 
-// One warp.  Rows of the conflict matrix that hold any bit were flagged in
-// row_any by the sweep; they are staged in shared memory first, then walked
-// in index order.  Candidate k is a landmark iff no earlier landmark
-// candidate covers it (its bit is clear in the running 'killed' set).
+// Rows of the conflict matrix that hold any bit were flagged in row_any by
+// the sweep; only those rows are staged in shared memory.  One warp then walks
+// the flagged candidates in index order: candidate k is a landmark iff no
+// earlier landmark candidate covers it (its bit is clear in the running
+// 'killed' set).  Finally every thread assigns ordinals in parallel.
 __global__ void __launch_bounds__(256) greedy_resolve_kernel(DeviceState* st, const unsigned* conflict,
                                                              const unsigned* row_any, int words,
                                                              const int* cand_ids, int* ordinal,
-                                                             int* landmarks) {
+                                                             int* landmarks, unsigned long long mem_cap) {
     if (st->done) return;
-    extern __shared__ unsigned s_rows[];   // S x words
+    // the new memberships are a subset of this step's hits: stop before anything
+    // is committed if they might not fit (the host grows the buffer and redoes the step)
+    if (st->mem_count + st->step_hits > mem_cap) {
+        if (threadIdx.x == 0) {
+            atomicOr(&st->error, kErrMemberOverflow);
+            st->done = 1;
+        }
+        return;
+    }
+    extern __shared__ unsigned s_rows[];   // flagged rows, compacted: nflag x words
+    __shared__ int s_rank_of_word[33];
+    __shared__ int s_flag_row[1024];
+    __shared__ unsigned s_killed[32];
+    __shared__ int s_nflag;
     const int c = st->cand_count;
     const int tid = threadIdx.x, lane = tid & 31;
-    // stage flagged rows
-    for (int e = tid; e < c * words; e += blockDim.x) {
-        const int k = e / words;
-        s_rows[e] = ((row_any[k >> 5] >> (k & 31)) & 1u) ? conflict[e] : 0u;
-    }
-    __syncthreads();
-    if (tid >= 32) return;
-    unsigned killed = 0;  // lane owns word 'lane' of the killed set
-    for (int w = 0; w < words; ++w) {
-        unsigned m = row_any[w];
+    if (tid < 32) {
+        unsigned a = lane < words ? row_any[lane] : 0u;
+        // rows >= c never hold bits, but mask them anyway
+        if (lane * 32 >= c) a = 0u;
+        else if (lane * 32 + 32 > c) a &= (1u << (c - lane * 32)) - 1u;
+        int cnt = __popc(a), x = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        s_rank_of_word[lane] = x - cnt;          // index of the first flagged row of this word
+        if (lane == 31) s_nflag = x;
+        unsigned m = a;
+        int k = x - cnt;
         while (m) {
             const int b = __ffs(m) - 1;
             m &= m - 1;
-            const int k = w * 32 + b;
-            if (k >= c) break;
-            const unsigned kw = __shfl_sync(kFull, killed, w);
-            if ((kw >> b) & 1u) continue;
-            if (lane < words) killed |= s_rows[k * words + lane];
+            s_flag_row[k++] = lane * 32 + b;
         }
     }
-    // alive = not killed; ordinals by prefix count in slot order
+    __syncthreads();
+    const int nflag = s_nflag;
+    for (int e = tid; e < nflag * words; e += blockDim.x) {
+        const int f = e / words, wi = e - f * words;
+        s_rows[e] = conflict[(size_t)s_flag_row[f] * words + wi];
+    }
+    __syncthreads();
+    if (tid < 32) {
+        unsigned killed = 0;  // lane owns word 'lane' of the killed set
+        for (int f = 0; f < nflag; ++f) {
+            const int k = s_flag_row[f];
+            const unsigned kw = __shfl_sync(kFull, killed, k >> 5);
+            if ((kw >> (k & 31)) & 1u) continue;
+            if (lane < words) killed |= s_rows[f * words + lane];
+        }
+        unsigned valid = (lane * 32 + 32 <= c) ? kFull : (lane * 32 >= c ? 0u : ((1u << (c - lane * 32)) - 1u));
+        const unsigned alive = ~killed & valid;
+        s_killed[lane] = alive;
+        int cnt = __popc(alive), x = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        s_rank_of_word[lane] = x - cnt;          // now: alive count before this word
+        if (lane == 31) s_rank_of_word[32] = x;
+    }
+    __syncthreads();
     const int base = st->n_landmarks;
-    int running = 0;
-    for (int w = 0; w < words; ++w) {
-        const unsigned kw = __shfl_sync(kFull, killed, w);
-        unsigned valid = (w * 32 + 32 <= c) ? kFull : (w * 32 >= c ? 0u : ((1u << (c - w * 32)) - 1u));
-        const unsigned alive = ~kw & valid;
-        const int k = w * 32 + lane;
-        if (k < c) {
-            const bool a = (alive >> lane) & 1u;
-            const int rank = running + __popc(alive & ((1u << lane) - 1u));
-            ordinal[k] = a ? base + rank : -1;
-            if (a) landmarks[base + rank] = cand_ids[k];
-        }
-        running += __popc(alive);
+    for (int k = tid; k < c; k += blockDim.x) {
+        const unsigned aw = s_killed[k >> 5];
+        const bool a = (aw >> (k & 31)) & 1u;
+        const int rank = s_rank_of_word[k >> 5] + __popc(aw & ((1u << (k & 31)) - 1u));
+        ordinal[k] = a ? base + rank : -1;
+        if (a) landmarks[base + rank] = cand_ids[k];
     }
-    if (lane == 0) st->n_landmarks = base + running;
+    __syncthreads();
+    if (tid == 0) st->n_landmarks = base + s_rank_of_word[32];
 }
 
 __global__ void __launch_bounds__(256) greedy_apply_kernel(DeviceState* st, const unsigned long long* step_keys,
@@ -219,6 +263,34 @@ cudaError_t launch_greedy_select(const GreedyBuffers& g, const Prepared& pts, in
     return cudaGetLastError();
 }
 
+// Undo the bookkeeping of a step stopped by a buffer overflow so that the next
+// select kernel picks the same candidates again.
+__global__ void greedy_rollback_kernel(DeviceState* st) {
+    st->scan_pos = st->step_start_pos;
+    st->steps -= 1;
+    st->candidates -= (unsigned long long)st->cand_count;
+    st->done = 0;
+    st->error = 0;
+    st->max_seg = 0;
+    st->step_hits = 0;
+    st->band_n = 0;
+}
+
+cudaError_t launch_greedy_rollback(const GreedyBuffers& g, cudaStream_t s) {
+    note_launch();
+    greedy_rollback_kernel<<<1, 1, 0, s>>>(g.st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_greedy_gather(const GreedyBuffers& g, const Prepared& pts, int S, bool want_tc, cudaStream_t s) {
+    note_launch();
+    greedy_gather_kernel<<<(S + 7) / 8, 256, 0, s>>>(
+        g.st, g.cand_ids, pts.x, pts.phi, pts.d, const_cast<float*>(g.cand.x), g.cand.phi, want_tc ? 1 : 0,
+        reinterpret_cast<const unsigned*>(pts.hi), reinterpret_cast<const unsigned*>(pts.lo), pts.aug, pts.d_pad,
+        reinterpret_cast<unsigned*>(g.cand.hi), reinterpret_cast<unsigned*>(g.cand.lo), g.cand.aug);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_greedy_resolve(const GreedyBuffers& g, int S, cudaStream_t s) {
     const int words = S / 32;
     const size_t smem = (size_t)S * words * sizeof(unsigned);
@@ -231,7 +303,7 @@ cudaError_t launch_greedy_resolve(const GreedyBuffers& g, int S, cudaStream_t s)
     }
     note_launch();
     greedy_resolve_kernel<<<1, 256, smem, s>>>(g.st, g.conflict, g.row_any, words, g.cand_ids, g.ordinal,
-                                               g.landmarks);
+                                               g.landmarks, g.mem_cap);
     return cudaGetLastError();
 }
 

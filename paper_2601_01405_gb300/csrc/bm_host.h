@@ -76,7 +76,16 @@ cudaError_t launch_sweep_fp32(const SweepDesc& s, cudaStream_t stream);
 
 // tile_tc.cu
 bool tc_supported();             // device is sm_103 and the kernel loaded
-cudaError_t launch_sweep_tc(const SweepDesc& s, cudaStream_t stream, std::string* why);
+// grid_out: CTAs launched (= hit segments written when s.sink.seg_counts is set)
+cudaError_t launch_sweep_tc(const SweepDesc& s, cudaStream_t stream, std::string* why, int* grid_out);
+int device_sm_count();
+// Gather the per-CTA hit segments into dst; *count_out = hits kept.  A segment
+// longer than seg_cap sets overflow_bit in st->error (and st->done when
+// stop_on_overflow) and records the length in st->max_seg.
+cudaError_t launch_compact_segments(const unsigned long long* src, unsigned long long seg_cap,
+                                    const unsigned long long* seg_counts, int nseg, unsigned long long* dst,
+                                    unsigned long long* count_out, DeviceState* st, int overflow_bit,
+                                    bool check_done, bool stop_on_overflow, cudaStream_t s);
 
 // greedy.cu
 struct GreedyBuffers {
@@ -96,8 +105,10 @@ struct GreedyBuffers {
 };
 cudaError_t launch_greedy_select(const GreedyBuffers& g, const Prepared& pts, int S, bool want_tc,
                                  cudaStream_t s);
+cudaError_t launch_greedy_gather(const GreedyBuffers& g, const Prepared& pts, int S, bool want_tc, cudaStream_t s);
 cudaError_t launch_greedy_resolve(const GreedyBuffers& g, int S, cudaStream_t s);
 cudaError_t launch_greedy_apply(const GreedyBuffers& g, cudaStream_t s);
+cudaError_t launch_greedy_rollback(const GreedyBuffers& g, cudaStream_t s);
 
 // sort.cu
 cudaError_t exclusive_scan_i64(const long long* in, long long* out, long long n, Arena& ar,
@@ -107,6 +118,13 @@ cudaError_t radix_sort_u64(unsigned long long* keys, unsigned long long* tmp, lo
                            unsigned long long** result);
 int bits_for(long long v);  // bits needed to represent v (>= 0)
 std::vector<int> digit_shifts(int lo_bits, int hi_bits);  // 8-bit digit shifts covering [0,lo) and [32,32+hi)
+
+// recheck.cu: FP64 re-decision of the band pairs; confirmed hits are appended
+// to keys through *count (book: the greedy's candidate-conflict bookkeeping).
+cudaError_t launch_band_recheck(DeviceState* st, const unsigned long long* band, unsigned long long band_cap,
+                                const float* ax, const float* bx, int d, double eps2, unsigned long long* keys,
+                                unsigned long long* count, unsigned long long cap, const HitSink& book,
+                                bool check_done, int overflow_bit, bool stop_on_overflow, cudaStream_t s);
 
 // graph.cu
 cudaError_t launch_csr_from_sorted(const unsigned long long* keys, long long nnz, long long rows,

@@ -5,9 +5,9 @@
 // (Sec. 3.2: the inner product dominates the cost of a range query) and then
 //     v = a.b - phi_a - phi_b  =  (eps^2 - D)/2   up to rounding.
 // Pairs with v > delta are members of the open ball, pairs with v < -delta
-// are not, and the rest are re-decided by the FP64 squared distance in
-// coordinate order (the verified range set of Sec. 4.3: candidates plus an
-// exact check).  delta bounds the FP32 error (see the delta kernel).
+// are not, and the rest are listed for the FP64 recheck kernel (the verified
+// range set of Sec. 4.3: candidates plus an exact check).  delta bounds the
+// FP32 error (see the delta kernel).
 #include "bm_host.h"
 
 namespace bm {
@@ -132,22 +132,22 @@ __global__ void __launch_bounds__(NT, 2) sweep_fp32_kernel(Fp32Args p) {
             else if (ok && v >= -delta) band |= 1ull << (8 * i + j);
         }
     }
-    unsigned band_local = __popcll(band);
-    while (band) {
-        const int b = __ffsll(band) - 1;
-        band &= band - 1;
-        const int i = b >> 3, j = b & 7;
-        const long long r = a0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
-        if (exact_sqdist(p.A + r * d, p.B + (long long)cols[j] * d, d) < p.eps2) hit |= 1ull << b;
-    }
 #pragma unroll 1
     for (int i = 0; i < 8; ++i) {
         const long long r = a0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
-        emit_hits_row(p.sink, (unsigned)r, cols, (hit >> (8 * i)) & 0xffull);
+        const unsigned long long hm = (hit >> (8 * i)) & 0xffull, bmk = (band >> (8 * i)) & 0xffull;
+        if (__any_sync(kFull, hm != 0ull)) emit_hits_row(p.sink, (unsigned)r, cols, hm);
+        if (__any_sync(kFull, bmk != 0ull)) {   // band pairs go to the FP64 recheck kernel
+            unsigned long long pos = warp_reserve(p.sink.band_n, __popcll(bmk));
+            unsigned long long m = bmk;
+            while (m) {
+                const int j = __ffsll(m) - 1;
+                m &= m - 1;
+                if (pos < p.sink.band_cap) p.sink.band_keys[pos] = ((unsigned long long)r << 32) | cols[j];
+                ++pos;
+            }
+        }
     }
-    // statistics: one atomic per warp
-    for (int o = 16; o > 0; o >>= 1) band_local += __shfl_xor_sync(kFull, band_local, o);
-    if ((tid & 31) == 0 && band_local) atomicAdd(p.sink.band_count, (unsigned long long)band_local);
     if (tid == 0) {
         const long long ra_ = (a_rows - a0) < BM ? (a_rows - a0) : BM;
         const long long rb_ = (p.n - b0) < BN ? (p.n - b0) : BN;

@@ -8,7 +8,7 @@
 //     q.x ~ hi_q.hi_x + lo_q.hi_x + hi_q.lo_x      (bf16 split products, exact in FP32)
 //     - phi_q - phi_x                              (the 16-wide augmentation block)
 // Pairs with v > delta are members, v < -delta are not, and the band in
-// between is re-decided in FP64 by the epilogue (verified range set, Sec. 4.3).
+// between is listed for the FP64 recheck kernel (verified range set, Sec. 4.3).
 //
 // Kernel organisation (one CTA per SM, persistent over work items):
 //   warp 0  TMA producer: one point tile (B, NT rows x all K) per work item,
@@ -16,9 +16,10 @@
 //           through a ring of shared-memory stages
 //   warp 1  allocates tensor memory; lane 0 issues tcgen05.mma (M=128, N=NT,
 //           K=16 per instruction) into one of two TMEM accumulators
-//   warps 2-5  epilogue: tcgen05.ld of the accumulator (one TMEM lane = one
-//           query row per thread), classification, FP64 band recheck and
-//           warp-aggregated hit emission
+//   warps 2-9  epilogue: tcgen05.ld of the accumulator (one TMEM lane = one
+//           query row per thread; two warps per lane quarter, each on half of
+//           the columns, all loads in flight before one wait), classification
+//           and warp-aggregated emission of hits and band pairs
 // Every mbarrier wait is bounded in time; on expiry the kernel records
 // kErrTimeout, drains its in-flight copies and MMAs, frees TMEM and returns.
 #include <cuda.h>
@@ -32,7 +33,8 @@ namespace bm {
 
 namespace {
 
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;   // 2 control warps + 8 epilogue warps
+constexpr int kEpiWarps = 8;
 constexpr int kMaxGroup = 8;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
 constexpr unsigned long long kDrainNs = 200000000ull;  // 0.2 s
@@ -60,6 +62,8 @@ struct Ctl {
     unsigned long long drain;
     unsigned tmem_base;
     int abort_flag;
+    unsigned seg_used;   // hits appended by this CTA (segmented mode)
+    unsigned band_used;  // band pairs appended by this CTA (segmented mode)
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -155,7 +159,8 @@ __device__ __forceinline__ void mma_commit(unsigned long long* bar) {
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+// Issue one 32-column TMEM load (no wait).
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -165,8 +170,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr)
         : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Byte sizes of the shared-memory regions for a configuration.
 struct Layout {
@@ -194,6 +200,11 @@ __host__ __device__ inline Layout make_layout(int CK, int NT, int BBUF, int ASTG
 
 template <int CK, int NT, int BBUF, int ASTG>
 __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_constant__ TcArgs p) {
+    const bool seg_mode = p.sink.seg_counts != nullptr;
+    if (seg_mode && threadIdx.x == 0) {
+        p.sink.seg_counts[blockIdx.x] = 0;
+        p.sink.band_seg_counts[blockIdx.x] = 0;
+    }
     if (p.check_done && p.st->done) return;
     const long long a_rows = p.a_rows_dev ? (long long)*p.a_rows_dev : p.a_rows_max;
     if (a_rows <= 0 || p.n <= 0) return;
@@ -227,10 +238,12 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
         }
         for (int i = 0; i < 2; ++i) {
             bar_init(&ctl->t_full[i], 1);
-            bar_init(&ctl->t_empty[i], 4);
+            bar_init(&ctl->t_empty[i], kEpiWarps);
         }
         bar_init(&ctl->drain, 1);
         ctl->abort_flag = 0;
+        ctl->seg_used = 0;
+        ctl->band_used = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -308,7 +321,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
                 if (!bar_wait(&ctl->b_full[b_buf], b_ph, abort_flag, gerr)) { ok = false; break; }
                 fence_after();
                 const uint32_t bb = sbase + b_buf * L.b_stride;
-                for (long long at = at0; ok && at < at1; ++at) {
+                for (long long ia = 0; ok && ia < at1 - at0; ++ia) {
                     if (!bar_wait(&ctl->t_empty[t_buf], t_ph ^ 1, abort_flag, gerr)) { ok = false; break; }
                     fence_after();
                     const uint32_t dacc = tmem + t_buf * NT;
@@ -351,66 +364,82 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        const int quarter = warp & 3;               // TMEM lanes 32*quarter .. +31
+        // warp w reads TMEM lanes 32*(w%4) .. +31 (the tcgen05.ld lane rule);
+        // warps 2-5 take the first half of the columns, warps 6-9 the second.
+        constexpr int kChunks = NT / 64;            // 32-column loads per warp per tile
+        const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
         const float delta = p.st->delta;
+        const unsigned long long seg_off = seg_mode ? (unsigned long long)blockIdx.x * p.sink.seg_cap : 0ull;
+        unsigned long long* seg_keys = p.sink.keys + seg_off;
+        unsigned long long* band_keys = p.sink.band_keys + seg_off;
+        unsigned* band_ctr32 = seg_mode ? &ctl->band_used : nullptr;
+        const unsigned long long band_cap = seg_mode ? p.sink.seg_cap : p.sink.band_cap;
         uint32_t t_buf = 0, t_ph = 0;
-        unsigned long long band_local = 0, pairs_local = 0;
+        unsigned long long pairs_local = 0;
         bool ok = true;
         for (long long item = blockIdx.x; ok && item < items; item += gridDim.x) {
             const long long bt = item / n_groups, g = item % n_groups;
             const long long at0 = g * G;
             const long long at1 = (at0 + G < a_tiles) ? at0 + G : a_tiles;
-            const long long col_base = bt * NT;
+            const long long col_base = bt * NT + half * (NT / 2);
             for (long long at = at0; at < at1; ++at) {
                 const bool w = __all_sync(kFull, bar_wait(&ctl->t_full[t_buf], t_ph, abort_flag, gerr));
                 if (!w) { ok = false; break; }
                 fence_after();
                 const long long row = at * 128 + quarter * 32 + lane;
                 const bool row_ok = row < a_rows;
-                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + t_buf * NT;
-#pragma unroll 1
-                for (int j = 0; j < NT / 32; ++j) {
-                    uint32_t r[32];
-                    tmem_ld32(taddr + j * 32, r);
-                    const long long col0 = col_base + j * 32;
-                    float mx = __uint_as_float(r[0]);
+                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + t_buf * NT + half * (NT / 2);
+                uint32_t r[kChunks][32];
 #pragma unroll
-                    for (int i = 1; i < 32; ++i) mx = fmaxf(mx, __uint_as_float(r[i]));
-                    unsigned hit = 0, band = 0;
-                    if (row_ok && mx >= -delta) {
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            const float v = __uint_as_float(r[i]);
-                            const bool in_range = col0 + i < p.n;
-                            if (in_range && v > delta) hit |= 1u << i;
-                            else if (in_range && v >= -delta) band |= 1u << i;
-                        }
-                    }
-                    if (band) {
-                        band_local += __popc(band);
-                        const float* arow = p.ax + row * p.d;
-                        unsigned bm_ = band;
-                        while (bm_) {
-                            const int i = __ffs(bm_) - 1;
-                            bm_ &= bm_ - 1;
-                            if (exact_sqdist(arow, p.bx + (col0 + i) * p.d, p.d) < p.eps2) hit |= 1u << i;
-                        }
-                    }
-                    if (__any_sync(kFull, hit != 0u)) emit_hits_run(p.sink, (unsigned)row, (unsigned)col0, hit);
-                }
-                if (threadIdx.x == 64) {
-                    const long long ra = (a_rows - at * 128) < 128 ? (a_rows - at * 128) : 128;
-                    const long long rb = (p.n - col_base) < NT ? (p.n - col_base) : NT;
-                    pairs_local += (unsigned long long)(ra * rb);
-                }
+                for (int j = 0; j < kChunks; ++j) tmem_ld32_async(taddr + j * 32, r[j]);
+                tmem_ld_wait();
+                // the accumulator is read: hand the TMEM buffer back to the MMA warp
                 fence_before();
                 __syncwarp();
                 if (lane == 0) bar_arrive(&ctl->t_empty[t_buf]);
                 if (++t_buf == 2) { t_buf = 0; t_ph ^= 1; }
+#pragma unroll
+                for (int j = 0; j < kChunks; ++j) {
+                    const long long col0 = col_base + j * 32;
+                    float m16[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) m16[i] = fmaxf(__uint_as_float(r[j][i]), __uint_as_float(r[j][i + 16]));
+#pragma unroll
+                    for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+                        for (int i = 0; i < w; ++i) m16[i] = fmaxf(m16[i], m16[i + w]);
+                    const float mx = m16[0];
+                    unsigned hit = 0, band = 0;
+                    if (row_ok && mx >= -delta) {
+                        const long long left = p.n - col0;
+                        const unsigned valid = left >= 32 ? kFull : (left <= 0 ? 0u : (1u << left) - 1u);
+                        unsigned near_ = 0;
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            const float v = __uint_as_float(r[j][i]);
+                            hit |= (v > delta ? 1u : 0u) << i;
+                            near_ |= (v >= -delta ? 1u : 0u) << i;
+                        }
+                        hit &= valid;
+                        band = near_ & ~hit & valid;
+                    }
+                    // band pairs go to the FP64 recheck kernel
+                    if (__any_sync(kFull, band != 0u))
+                        emit_plain_run(band_keys, p.sink.band_n, band_ctr32, band_cap, (unsigned)row, (unsigned)col0,
+                                       band);
+                    if (__any_sync(kFull, hit != 0u)) {
+                        if (seg_mode) emit_hits_run_seg(p.sink, seg_keys, &ctl->seg_used, (unsigned)row, (unsigned)col0, hit);
+                        else emit_hits_run(p.sink, (unsigned)row, (unsigned)col0, hit);
+                    }
+                }
+                if (threadIdx.x == 64) {
+                    const long long ra = (a_rows - at * 128) < 128 ? (a_rows - at * 128) : 128;
+                    const long long rb = (p.n - bt * NT) < NT ? (p.n - bt * NT) : NT;
+                    pairs_local += (unsigned long long)(ra * rb);
+                }
             }
         }
-        for (int o = 16; o > 0; o >>= 1) band_local += __shfl_xor_sync(kFull, band_local, o);
-        if (lane == 0 && band_local) atomicAdd(p.sink.band_count, band_local);
         if (threadIdx.x == 64 && pairs_local) atomicAdd(p.sink.pair_count, pairs_local);
     }
 
@@ -419,6 +448,10 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
     fence_after();
     if (warp == 1) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+    if (seg_mode && threadIdx.x == 0) {
+        p.sink.seg_counts[blockIdx.x] = ctl->seg_used;
+        p.sink.band_seg_counts[blockIdx.x] = ctl->band_used;
     }
 }
 
@@ -460,7 +493,7 @@ CUtensorMapSwizzle swizzle_for(int CK) {
 constexpr uint32_t kMaxSmem = 232448;
 
 template <int CK, int NT, int BBUF, int ASTG>
-cudaError_t launch_cfg(TcArgs& args, long long a_rows_max, cudaStream_t stream, std::string* why) {
+cudaError_t launch_cfg(TcArgs& args, long long a_rows_max, cudaStream_t stream, std::string* why, int* grid_out) {
     const Layout L0 = make_layout(CK, NT, BBUF, ASTG, args.d_pad);
     // at least 120 KB so that two CTAs never share an SM (each holds 2*NT TMEM columns)
     Layout L = L0;
@@ -482,6 +515,7 @@ cudaError_t launch_cfg(TcArgs& args, long long a_rows_max, cudaStream_t stream, 
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long grid = items < sms ? items : sms;
+    *grid_out = (int)(grid > 0 ? grid : 0);
     if (grid <= 0) return cudaSuccess;
     note_launch();
     kern<<<(unsigned)grid, kThreads, L.total, stream>>>(args);
@@ -492,7 +526,15 @@ cudaError_t launch_cfg(TcArgs& args, long long a_rows_max, cudaStream_t stream, 
 
 bool tc_supported() { return encode_fn() != nullptr; }
 
-cudaError_t launch_sweep_tc(const SweepDesc& s, cudaStream_t stream, std::string* why) {
+int device_sm_count() {
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+cudaError_t launch_sweep_tc(const SweepDesc& s, cudaStream_t stream, std::string* why, int* grid_out) {
+    *grid_out = 0;
     if (s.a_rows_max == 0 || s.b->rows == 0) return cudaSuccess;
     const int d_pad = s.b->d_pad;
     if (d_pad > 512) {
@@ -506,23 +548,47 @@ cudaError_t launch_sweep_tc(const SweepDesc& s, cudaStream_t stream, std::string
     int NT = 256, BBUF = 2;
     if (CK == 64) {
         const int nc = d_pad / 64;
-        if (make_layout(64, 256, 2, 4, d_pad).total <= kMaxSmem) { NT = 256; BBUF = 2; }
-        else if (make_layout(64, 128, 2, 4, d_pad).total <= kMaxSmem) { NT = 128; BBUF = 2; }
+        if (make_layout(64, 256, 2, 5, d_pad).total <= kMaxSmem) { NT = 256; BBUF = 2; }
+        else if (make_layout(64, 128, 2, 5, d_pad).total <= kMaxSmem) { NT = 128; BBUF = 2; }
         else if (make_layout(64, 128, 1, 4, d_pad).total <= kMaxSmem) { NT = 128; BBUF = 1; }
         else { NT = 64; BBUF = 1; }
         (void)nc;
     }
     const CUtensorMapSwizzle sw = swizzle_for(CK);
     const long long arows = s.a->rows, brows = s.b->rows;
-    bool ok = make_map(&args.a_hi, s.a->hi, arows, d_pad, CK, 128, sw) &&
-              make_map(&args.a_lo, s.a->lo, arows, d_pad, CK, 128, sw) &&
-              make_map(&args.a_aug, s.a->aug, arows, 16, 16, 128, CU_TENSOR_MAP_SWIZZLE_32B) &&
-              make_map(&args.b_hi, s.b->hi, brows, d_pad, CK, NT, sw) &&
-              make_map(&args.b_lo, s.b->lo, brows, d_pad, CK, NT, sw) &&
-              make_map(&args.b_aug, s.b->aug, brows, 16, 16, NT, CU_TENSOR_MAP_SWIZZLE_32B);
-    if (!ok) {
-        if (why) *why = "tensor map encoding failed";
-        return cudaErrorInvalidValue;
+    // The greedy sweeps the same candidate and point buffers every step: reuse the
+    // encoded tensor maps while the buffers and shapes are unchanged.
+    struct MapCache {
+        const void* key[6];
+        long long arows, brows;
+        int d_pad, NT;
+        CUtensorMap maps[6];
+        bool valid;
+    };
+    static thread_local MapCache cache = {};
+    const void* key[6] = {s.a->hi, s.a->lo, s.a->aug, s.b->hi, s.b->lo, s.b->aug};
+    bool hit = cache.valid && cache.arows == arows && cache.brows == brows && cache.d_pad == d_pad && cache.NT == NT;
+    for (int i = 0; hit && i < 6; ++i) hit = cache.key[i] == key[i];
+    if (hit) {
+        args.a_hi = cache.maps[0]; args.a_lo = cache.maps[1]; args.a_aug = cache.maps[2];
+        args.b_hi = cache.maps[3]; args.b_lo = cache.maps[4]; args.b_aug = cache.maps[5];
+    } else {
+        bool ok = make_map(&args.a_hi, s.a->hi, arows, d_pad, CK, 128, sw) &&
+                  make_map(&args.a_lo, s.a->lo, arows, d_pad, CK, 128, sw) &&
+                  make_map(&args.a_aug, s.a->aug, arows, 16, 16, 128, CU_TENSOR_MAP_SWIZZLE_32B) &&
+                  make_map(&args.b_hi, s.b->hi, brows, d_pad, CK, NT, sw) &&
+                  make_map(&args.b_lo, s.b->lo, brows, d_pad, CK, NT, sw) &&
+                  make_map(&args.b_aug, s.b->aug, brows, 16, 16, NT, CU_TENSOR_MAP_SWIZZLE_32B);
+        if (!ok) {
+            cache.valid = false;
+            if (why) *why = "tensor map encoding failed";
+            return cudaErrorInvalidValue;
+        }
+        for (int i = 0; i < 6; ++i) cache.key[i] = key[i];
+        cache.arows = arows; cache.brows = brows; cache.d_pad = d_pad; cache.NT = NT;
+        cache.maps[0] = args.a_hi; cache.maps[1] = args.a_lo; cache.maps[2] = args.a_aug;
+        cache.maps[3] = args.b_hi; cache.maps[4] = args.b_lo; cache.maps[5] = args.b_aug;
+        cache.valid = true;
     }
     args.ax = s.a->x;
     args.bx = s.b->x;
@@ -535,12 +601,12 @@ cudaError_t launch_sweep_tc(const SweepDesc& s, cudaStream_t stream, std::string
     args.eps2 = s.eps2;
     args.st = const_cast<DeviceState*>(s.st);
     args.sink = s.sink;
-    if (CK == 16) return launch_cfg<16, 256, 2, 8>(args, s.a_rows_max, stream, why);
-    if (CK == 32) return launch_cfg<32, 256, 2, 8>(args, s.a_rows_max, stream, why);
-    if (NT == 256) return launch_cfg<64, 256, 2, 4>(args, s.a_rows_max, stream, why);
-    if (NT == 128 && BBUF == 2) return launch_cfg<64, 128, 2, 4>(args, s.a_rows_max, stream, why);
-    if (NT == 128) return launch_cfg<64, 128, 1, 4>(args, s.a_rows_max, stream, why);
-    return launch_cfg<64, 64, 1, 4>(args, s.a_rows_max, stream, why);
+    if (CK == 16) return launch_cfg<16, 256, 2, 8>(args, s.a_rows_max, stream, why, grid_out);
+    if (CK == 32) return launch_cfg<32, 256, 2, 8>(args, s.a_rows_max, stream, why, grid_out);
+    if (NT == 256) return launch_cfg<64, 256, 2, 5>(args, s.a_rows_max, stream, why, grid_out);
+    if (NT == 128 && BBUF == 2) return launch_cfg<64, 128, 2, 5>(args, s.a_rows_max, stream, why, grid_out);
+    if (NT == 128) return launch_cfg<64, 128, 1, 4>(args, s.a_rows_max, stream, why, grid_out);
+    return launch_cfg<64, 64, 1, 4>(args, s.a_rows_max, stream, why, grid_out);
 }
 
 }  // namespace bm

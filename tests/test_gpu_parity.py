@@ -200,3 +200,32 @@ def test_errors_are_reported(bm):
     with pytest.raises(bm.BallMapperError) as ei:
         bm.bm_build(X, 1.0, batch=33)
     assert ei.value.status == bm.BM_ERR_ARG
+
+
+# ------------------------------------------------------------------ buffer growth
+@pytest.mark.parametrize("path", PATHS)
+def test_range_query_dense_hits_regrow(bm, path):
+    """Every pair a hit (9M keys): the first hit buffer overflows and the query is redone."""
+    X = W.isotropic(3000, 8, 10, seed=21)
+    off, ids, st = bm.bm_range_query(torch.from_numpy(X).cuda(), torch.from_numpy(X).cuda(), 1e3, path=path)
+    assert ids.numel() == 3000 * 3000
+    assert np.array_equal(off.cpu().numpy(), np.arange(3001, dtype=np.int64) * 3000)
+    assert np.array_equal(ids.cpu().numpy().reshape(3000, 3000), np.tile(np.arange(3000, dtype=np.int32), (3000, 1)))
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_build_step_buffer_regrow(bm, path):
+    """Large balls: a greedy step produces more hits than the first step buffer holds."""
+    X = W.isotropic(20000, 2, 10, seed=22)
+    ref = oracle.build(X, 2.0)
+    assert_same_graph(run_build(bm, X, 2.0, path), ref)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_build_membership_buffer_regrow(bm, path):
+    """Cover multiplicity ~6 at n = 200k: the membership keys outgrow their first buffer
+    (4n keys) and the greedy grows it and redoes the step, with no restart."""
+    X = W.isotropic(200_000, 8, 10, seed=23)
+    ref = oracle.build(X, 3.0)
+    assert ref["ids"].size > 4 * X.shape[0]
+    assert_same_graph(run_build(bm, X, 3.0, path), ref)
