@@ -2,14 +2,14 @@
  * ballmapper.h -- C-ABI of the GB300 exact Ball Mapper library (libballmapper.so).
  *
  * The operations follow the paper's statement of the problem:
- *   - the exact range oracle R_r(q) = { x in X : d(q,x) < r }            (Sec. 4, Def. "exact range set")
+ *   - the exact range oracle R_r(q) = { x in X : d(q,x) < r }            (Sec. 5, Def. 5.1)     
  *   - the greedy epsilon-net: while a point is uncovered, select one,     (Sec. 2.2)
  *     add it to the landmark set and cover its open ball; the point
  *     selected is always the smallest uncovered index
  *   - ball memberships X_i = X intersect B(l_i, eps), full open balls     (Sec. 2.3; ball definition Sec. 2.1)
- *   - the Ball Mapper graph = 1-skeleton of the nerve: an edge {i,j}      (Sec. 2.1 nerve; Sec. 4.2 N_r(L), G_r(L))
+ *   - the Ball Mapper graph = 1-skeleton of the nerve: an edge {i,j}      (Sec. 2.1 nerve; Sec. 5.2, Def. 5.6)
  *     for every landmark pair whose balls share a data point
- * The metric is Euclidean (Sec. 5.1).  Distances are decided exactly: the
+ * The metric is Euclidean (Sec. 6.1).  Distances are decided exactly: the
  * result equals the one obtained with FP64 squared distances summed in
  * coordinate order, for any finite float32 input.
  *
@@ -118,14 +118,14 @@ typedef struct {
 /* Fill *opt with defaults (default stream, tensor-core path, device I/O). */
 BM_API void bm_options_init(bm_options* opt);
 
-/* Exact range query, Sec. 4: out row j = { i : ||X_i - Q_j|| < eps }.
+/* Exact range query, Sec. 5, Def. 5.1: out row j = { i : ||X_i - Q_j|| < eps }.
  * X: n x d float32; Q: m x d float32; eps > 0 finite.  n = 0 or m = 0 give
  * empty rows (X or Q may then be NULL).  stats may be NULL. */
 BM_API bm_status bm_range_query(const float* X, int64_t n, int32_t d, const float* Q, int64_t m,
                          float eps, const bm_options* opt, bm_csr* out, bm_stats* stats);
 
 /* Ball Mapper construction, Sec. 2.2 (greedy epsilon-net in index order),
- * Sec. 2.3 (full-ball memberships) and Sec. 2.1 / Sec. 4.2 (nerve edges).
+ * Sec. 2.3 (full-ball memberships) and Sec. 2.1 / Sec. 5.2 (nerve edges).
  * n = 0 gives an empty graph. */
 BM_API bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_options* opt,
                    bm_graph* out);

@@ -10,11 +10,11 @@ force (exact integer/rational arithmetic) used to pin this one.
 
 Functions and the passages they follow:
   greedy             Sec. 2.2 greedy epsilon-net, smallest uncovered index first
-  range_query        Sec. 4 exact range set R_r(q) = {x : d(q,x) < r}, full scan
+  range_query        Sec. 5 (Def. 5.1) exact range set R_r(q) = {x : d(q,x) < r}, full scan
   memberships        Sec. 2.3 X_i = X intersect B(l_i, eps), full balls
-  edges              Sec. 2.1 nerve / Sec. 4.2 G_r(L): edge iff X_i, X_j intersect
+  edges              Sec. 2.1 nerve / Sec. 5.2 G_r(L): edge iff X_i, X_j intersect
   build              all of the above in order
-  kth_nn_dist        Sec. 5.1 target-occupancy rule (self counted first)
+  kth_nn_dist        Sec. 6.1 target-occupancy rule (self counted first)
   BallTree           Sec. 3.1 ball tree construction and pruned range query
 """
 from __future__ import annotations
@@ -221,7 +221,7 @@ def kth_nn_dist(X, k: int) -> np.ndarray:
 
 
 def occupancy_eps(X, k: int) -> float:
-    """Target-occupancy scale (Sec. 5.1): median over points of the k-th NN distance.
+    """Target-occupancy scale (Sec. 6.1): median over points of the k-th NN distance.
     An even count takes the mean of the two middle values."""
     return float(np.median(kth_nn_dist(X, k)))
 

@@ -8,17 +8,17 @@
  *
  * Every routine follows a definition of the paper literally, in FP64:
  *   - squared distance  D(a,b) = sum_i (a_i - b_i)^2, summed in index order
- *     (Euclidean metric, Sec. 2.1 and Sec. 5.1);
+ *     (Euclidean metric, Sec. 2.1 and Sec. 6.1);
  *   - open ball / exact range set  R_r(q) = { x : d(q,x) < r }
- *     (Sec. 2.1, ball definition; Sec. 4, Def. of the exact range oracle),
+ *     (Sec. 2.1, ball definition; Sec. 5, Def. 5.1 of the exact range set),
  *     evaluated as D(q,x) < r^2 by a full scan over all points;
  *   - greedy epsilon-net (Sec. 2.2 procedure): while a point is uncovered,
  *     select one (the smallest uncovered index), add it to the landmark set
  *     and mark every point of its open ball covered;
  *   - ball membership X_i = X intersect B(l_i, eps), the full ball (Sec. 2.3);
- *   - nerve 1-skeleton (Sec. 2.1 nerve definition, Sec. 4.2 Def. of N_r(L)):
+ *   - nerve 1-skeleton (Sec. 2.1 nerve definition, Sec. 5.2, Def. 5.6 of N_r(L)):
  *     edge {i,j} iff the two membership lists intersect;
- *   - target-occupancy scale (Sec. 5.1): distance of each point to its k-th
+ *   - target-occupancy scale (Sec. 6.1): distance of each point to its k-th
  *     nearest neighbour, the point itself counted first;
  *   - ball tree construction and range query (Sec. 3.1), an independent
  *     exact range oracle used to cross-check the brute force one.
@@ -87,7 +87,7 @@ int64_t bmo_greedy(const double* X, int64_t n, int d, double eps2, int32_t* land
 }
 
 /* ---------------------------------------------------------------------------
- * Exact range oracle R_r(q) by full scan (Sec. 4 definition), two phases.
+ * Exact range oracle R_r(q) by full scan (Sec. 5, Def. 5.1), two phases.
  * counts[j] = |{ i : D(X_i, Q_j) < eps2 }|.
  * ------------------------------------------------------------------------- */
 void bmo_range_count(const double* X, int64_t n, int d, const double* Q, int64_t m,
@@ -123,7 +123,7 @@ void bmo_pair_sqdist(const double* X, int d, const double* Q, int64_t npairs,
 }
 
 /* ---------------------------------------------------------------------------
- * Nerve 1-skeleton (Sec. 2.1, Sec. 4.2): for landmark ordinals i < j the edge
+ * Nerve 1-skeleton (Sec. 2.1, Sec. 5.2): for landmark ordinals i < j the edge
  * exists iff the sorted membership lists of rows i and j share an id.
  *
  * With prune != 0, pairs whose landmarks are at squared distance above
@@ -172,7 +172,7 @@ void bmo_edges(const double* X, int d, const int32_t* landmarks, int64_t L, doub
 }
 
 /* ---------------------------------------------------------------------------
- * Target-occupancy scale, Sec. 5.1: for each point the distance to its k-th
+ * Target-occupancy scale, Sec. 6.1: for each point the distance to its k-th
  * nearest neighbour, the point itself counted as the first.  Brute force:
  * all n squared distances of the row, then the k-th smallest by selection.
  * out[i] = sqrt(k-th smallest D(X_i, .)).

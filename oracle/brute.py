@@ -13,7 +13,7 @@ rather than the C oracle's scans and list intersections:
   * membership of l: the set comprehension {y : D(l, y) < eps^2} (Sec. 2.3);
   * edge {i, j}: some point x is a witness, D(x,l_i) < eps^2 and
     D(x,l_j) < eps^2 (Sec. 2.1 nerve; equivalently witness radius < eps,
-    Sec. 4.2).
+    Sec. 5.2, Def. 5.9).
 """
 from __future__ import annotations
 

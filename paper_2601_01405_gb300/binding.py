@@ -265,3 +265,4 @@ def bm_build(X, eps: float, path: str = "tc", batch: int = 0, stream=None):
 
 def version() -> int:
     return int(load().bm_version())
+

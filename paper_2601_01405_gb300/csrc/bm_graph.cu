@@ -4,7 +4,7 @@
 // offsets are the positions where the row part changes, ids the low halves.
 //
 // K(d): the Ball Mapper graph is the 1-skeleton of the nerve (Sec. 2.1,
-// Sec. 4.2): {i, j} is an edge iff some point lies in both balls.  Every
+// Sec. 5.2, Def. 5.6): {i, j} is an edge iff some point lies in both balls.  Every
 // point x covered by c_x balls witnesses the c_x (c_x - 1) / 2 pairs of its
 // covering landmarks, so the edge set is the deduplicated union of those
 // pairs.  Steps: transpose the memberships (point -> covering landmarks),

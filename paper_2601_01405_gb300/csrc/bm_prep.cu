@@ -1,6 +1,6 @@
 // bm_prep.cu -- K0: per-point preparation for the distance tiles.
 //
-// The decision d(q,x) < eps (open ball, Sec. 2.1; exact range set, Sec. 4) is
+// The decision d(q,x) < eps (open ball, Sec. 2.1; exact range set, Sec. 5, Def. 5.1) is
 // taken on the algebraic form of Sec. 3.2:
 //     D(q,x) = ||q||^2 + ||x||^2 - 2 q.x,
 // rewritten as   v = q.x - phi_q - phi_x,   phi = ||.||^2/2 - eps^2/4,

@@ -4,7 +4,7 @@
 // [-delta, delta] (v = (eps^2 - D)/2) and list the rest.  Here each listed
 // pair gets the exact test D(q,x) < eps^2 with D summed in FP64 in coordinate
 // order -- the same arithmetic as the CPU oracle -- which turns the tiles into
-// an exact range oracle (verified range set, Sec. 4.3).  One thread per pair,
+// an exact range oracle (verified range set, Sec. 5.3).  One thread per pair,
 // four coordinates per load when the rows allow it; confirmed members are
 // appended to the hit keys (with the greedy's candidate-conflict bookkeeping).
 #include "bm_host.h"

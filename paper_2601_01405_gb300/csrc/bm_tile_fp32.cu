@@ -6,7 +6,7 @@
 //     v = a.b - phi_a - phi_b  =  (eps^2 - D)/2   up to rounding.
 // Pairs with v > delta are members of the open ball, pairs with v < -delta
 // are not, and the rest are listed for the FP64 recheck kernel (the verified
-// range set of Sec. 4.3: candidates plus an exact check).  delta bounds the
+// range set of Sec. 5.3: candidates plus an exact check).  delta bounds the
 // FP32 error (see the delta kernel).
 #include "bm_host.h"
 

@@ -1,6 +1,6 @@
 // bm_tile_tc.cu -- K(b): distance tiles on the tcgen05 tensor cores.
 //
-// Decision rule (open ball, Sec. 2.1; exact range set, Sec. 4): x is in
+// Decision rule (open ball, Sec. 2.1; exact range set, Sec. 5, Def. 5.1): x is in
 // R_eps(q) iff D(q,x) < eps^2.  Following the algebraic decomposition of
 // Sec. 3.2 the tile evaluates, for 128 query rows x NT points,
 //     v = q.x - phi_q - phi_x = (eps^2 - D)/2,      phi = ||.||^2/2 - eps^2/4
@@ -8,7 +8,7 @@
 //     q.x ~ hi_q.hi_x + lo_q.hi_x + hi_q.lo_x      (bf16 split products, exact in FP32)
 //     - phi_q - phi_x                              (the 16-wide augmentation block)
 // Pairs with v > delta are members, v < -delta are not, and the band in
-// between is listed for the FP64 recheck kernel (verified range set, Sec. 4.3).
+// between is listed for the FP64 recheck kernel (verified range set, Sec. 5.3).
 //
 // Kernel organisation (one CTA per SM, persistent over work items):
 //   warp 0  TMA producer: one point tile (B, NT rows x all K) per work item,

@@ -5,7 +5,7 @@ Mapper arithmetic, so both the CPU oracle (tests) and the CUDA path consume
 the very same bytes from it.
 
 The paper evaluates on synthetic isotropic, clustered and low-dimensional
-structured point clouds in R^d with the Euclidean distance (Sec. 5.1).  Its
+structured point clouds in R^d with the Euclidean distance (Sec. 6.1).  Its
 generator parameters are not printed, so the recipes below fix them:
 
 * ``isotropic``  X ~ N(0, I_d)
@@ -138,7 +138,7 @@ def make(name: str, seed: int = 0) -> np.ndarray:
 
 
 def paper_gaussian_fp64(n: int = 20_000, d: int = 50, seed: int = 0) -> np.ndarray:
-    """Unquantised FP64 isotropic Gaussian of the paper's worked example (Sec. 5.3)."""
+    """Unquantised FP64 isotropic Gaussian of the paper's worked example (Sec. 6.3)."""
     return np.random.default_rng(seed).standard_normal((n, d))
 
 

@@ -111,7 +111,7 @@ def pin_fixpoint(X, eps):
 
 
 def pin_invariants(X, eps):
-    """eps-net (Def. 2.1 / rho-cover and alpha-separation, Sec. 4.1 with delta = 0),
+    """eps-net (Def. 2.1 / rho-cover and alpha-separation, Sec. 5.1, Def. 5.4 and Thm. 5.5 with delta = 0),
     memberships equal to the full balls, CSR rows sorted and unique."""
     out = oracle.build(X, eps)
     lm, off, ids = out["landmarks"], out["offsets"], out["ids"]
@@ -131,7 +131,7 @@ def pin_invariants(X, eps):
 
 
 def pin_witness(X, eps):
-    """Edge {i,j} exists iff the witness radius tau_ij < eps (Sec. 4.2):
+    """Edge {i,j} exists iff the witness radius tau_ij < eps (Sec. 5.2, Def. 5.9):
     tau_ij^2 = min_x max(D(x,l_i), D(x,l_j))."""
     out = oracle.build(X, eps)
     lm = out["landmarks"]
@@ -155,7 +155,7 @@ def pin_prune(X, eps):
 
 def pin_balltree(X, eps, Q=None):
     """An exact accelerated range query preserves every range set (Sec. 3.1 ball tree
-    against the Sec. 4 full scan)."""
+    against the Sec. 5 (Def. 5.1) full scan)."""
     if Q is None:
         Q = X[oracle.greedy(X, eps)]
     bt = oracle.BallTree(X, leaf_size=40)

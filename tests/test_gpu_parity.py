@@ -176,7 +176,7 @@ def test_build_host_io_and_determinism(bm, path):
 
 
 def test_paths_agree_on_paper_gaussian_fp32(bm):
-    """The paper's worked example (Sec. 5.3) cast to float32: both paths agree with
+    """The paper's worked example (Sec. 6.3) cast to float32: both paths agree with
     each other and with the oracle on the same float32 data."""
     X = W.paper_gaussian_fp64().astype(np.float32)
     eps = float(np.float32(7.553576))

@@ -86,5 +86,5 @@ def test_iso_n10k_d16_counts():
 
 @pytest.mark.slow
 def test_paper_worked_example():
-    """Sec. 5.3: Gaussian n=20000, d=50, k=50 -> eps ~ 7.5536, 6361 landmarks, 936690 edges."""
+    """Sec. 6.3: Gaussian n=20000, d=50, k=50 -> eps ~ 7.5536, 6361 landmarks, 936690 edges."""
     pins.pin_paper()
