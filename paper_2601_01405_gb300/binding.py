@@ -100,6 +100,9 @@ def load(path: str = LIB_PATH):
         lib.bm_last_error.restype = ctypes.c_char_p
         lib.bm_version.argtypes = []
         lib.bm_version.restype = ctypes.c_int32
+        lib.bm_range_count_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                                               ctypes.c_int64, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]
+        lib.bm_range_count_noalloc.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -266,3 +269,21 @@ def bm_build(X, eps: float, path: str = "tc", batch: int = 0, stream=None):
 def version() -> int:
     return int(load().bm_version())
 
+
+def bm_range_count_noalloc(X, Q, eps: float, counts, stream=None):
+    """|R_eps(q)| for every row q of Q, written into the caller's int64 CUDA tensor
+    `counts` (length m).  The library allocates nothing for this call: it works in
+    a fixed scratch area compiled into it (see the C header for limits)."""
+    import torch
+    lib = load()
+    if not (_is_torch_cuda(X) and _is_torch_cuda(Q) and _is_torch_cuda(counts)):
+        raise ValueError("X, Q and counts must be CUDA tensors")
+    if counts.dtype != torch.int64 or not counts.is_contiguous() or counts.numel() != Q.shape[0]:
+        raise ValueError("counts must be a contiguous int64 tensor with one entry per query")
+    px, n, d, kx, _ = _as_input(X)
+    pq, m, dq, kq, _ = _as_input(Q)
+    if m and n and dq != d:
+        raise ValueError("dimension mismatch")
+    st = stream or _current_stream(kx.device)
+    _check(lib, lib.bm_range_count_noalloc(px, n, d, pq, m, ctypes.c_float(eps), st, counts.data_ptr()))
+    return counts
