@@ -73,7 +73,9 @@ typedef struct {
     void* stream;          /* cudaStream_t; NULL = legacy default stream */
     int32_t path;          /* bm_path */
     int32_t host_io;       /* 0: device pointers in and out; 1: host pointers in and out */
-    int32_t batch;         /* greedy candidates per step, 32..1024, multiple of 32; 0 = automatic */
+    int32_t batch;         /* largest greedy batch (candidates per step), 32..2048, multiple of 32; 0 = 2048.
+                              The batch starts at min(batch, 256) and doubles / halves with the share of
+                              candidates that become landmarks. */
     int32_t reserved0;
     bm_alloc_fn alloc;     /* optional device allocator for outputs and scratch */
     bm_free_fn free;

@@ -321,10 +321,8 @@ bm_status sweep_stage(SweepDesc& sd, DeviceState* st, int path, SweepOut& o, uns
     stimer.after();
     if (rs != BM_OK) return rs;
     if (tc) {
-        TRY_CUDA(launch_compact_segments(o.raw, sd.sink.seg_cap, o.seg_counts, grid, o.keys, count, st, overflow_bit,
-                                         greedy, greedy, s));
-        TRY_CUDA(launch_compact_segments(o.raw_band, sd.sink.seg_cap, o.band_seg_counts, grid, o.band, &st->band_n,
-                                         st, overflow_bit, greedy, greedy, s));
+        TRY_CUDA(launch_compact_segments(o.raw, o.raw_band, sd.sink.seg_cap, o.seg_counts, o.band_seg_counts, grid,
+                                         o.keys, o.band, count, &st->band_n, st, overflow_bit, greedy, greedy, s));
     }
     TRY_CUDA(launch_band_recheck(st, o.band, o.cap, sd.a->x, sd.b->x, sd.b->d, sd.eps2, o.keys, count, o.cap, sd.sink,
                                  greedy, overflow_bit, greedy, s));
@@ -673,8 +671,8 @@ bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_opt
     vs = check_device(opt.path);
     if (vs != BM_OK) return vs;
     int S = opt.batch;
-    if (S == 0) S = 1024;
-    if (S < 32 || S > 1024 || S % 32) return fail(BM_ERR_ARG, "batch must be a multiple of 32 in [32, 1024]");
+    if (S == 0) S = 2048;
+    if (S < 32 || S > 2048 || S % 32) return fail(BM_ERR_ARG, "batch must be a multiple of 32 in [32, 2048]");
     cudaStream_t s = (cudaStream_t)opt.stream;
     const bool host_io = opt.host_io != 0;
     const double eps2 = (double)eps * (double)eps;
@@ -729,6 +727,11 @@ bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_opt
             for (int attempt = 0; attempt < 6; ++attempt) {
                 bool retry = false;
                 TRY_CUDA(cudaMemsetAsync(st, 0, offsetof(DeviceState, max_norm_bits), s));
+                {
+                    const int s_first = S < 256 ? S : 256;   // the batch grows while candidates survive
+                    TRY_CUDA(cudaMemcpyAsync(&st->s_next, &s_first, sizeof(int), cudaMemcpyHostToDevice, s));
+                    TRY_CUDA(cudaStreamSynchronize(s));
+                }
                 rs = greedy_pass(px, eps2, opt.path, S, ar, s, st, hs, step_cap, mem_cap, &retry, &landmarks,
                                  &mem_keys, fin, stimer);
                 if (rs != BM_OK) return rs;

@@ -39,6 +39,8 @@ struct DeviceState {
     unsigned long long max_seg;      // largest per-CTA hit segment seen by a compaction
     unsigned long long band_n;       // band pairs awaiting the FP64 recheck (current sweep)
     long long step_start_pos;        // scan_pos at the start of the current greedy step
+    int s_cur;                       // candidates requested by the current step
+    int s_next;                      // candidates the next step requests (adapted to the survival rate)
 };
 
 // Where a distance tile delivers its (row, point) hits.

@@ -100,28 +100,48 @@ __global__ void unique_scatter_kernel(const unsigned long long* keys, long long 
     }
 }
 
-__global__ void compact_segments_kernel(const unsigned long long* src, unsigned long long seg_cap,
-                                        const unsigned long long* seg_counts, int nseg, unsigned long long* dst,
-                                        unsigned long long* count_out, DeviceState* st, int overflow_bit,
-                                        int check_done, int stop_on_overflow) {
+// Gathers per-CTA segments into one contiguous array.  Blocks [0, nseg) handle
+// the hit segments, blocks [nseg, 2 nseg) the band segments of the same sweep.
+// Each block first loads all segment counts into shared memory and takes its
+// prefix with a block scan.
+__global__ void __launch_bounds__(256) compact_segments_kernel(
+    const unsigned long long* src, const unsigned long long* band_src, unsigned long long seg_cap,
+    const unsigned long long* seg_counts, const unsigned long long* band_seg_counts, int nseg,
+    unsigned long long* dst, unsigned long long* band_dst, unsigned long long* count_out,
+    unsigned long long* band_count_out, DeviceState* st, int overflow_bit, int check_done, int stop_on_overflow) {
     if (check_done && st->done) return;
-    __shared__ unsigned long long s_pre, s_cnt;
-    if (threadIdx.x == 0) {
-        unsigned long long pre = 0;
-        for (int q = 0; q < (int)blockIdx.x; ++q) pre += seg_counts[q] < seg_cap ? seg_counts[q] : seg_cap;
-        const unsigned long long c = seg_counts[blockIdx.x];
-        s_pre = pre;
-        s_cnt = c < seg_cap ? c : seg_cap;
-        if (c > seg_cap) {
-            atomicOr(&st->error, overflow_bit);
-            atomicMax(&st->max_seg, c);
-            if (stop_on_overflow) st->done = 1;
+    __shared__ unsigned long long s_cnt[256];
+    __shared__ unsigned long long s_pre, s_mine;
+    const bool band = (int)blockIdx.x >= nseg;
+    const int seg = band ? (int)blockIdx.x - nseg : (int)blockIdx.x;
+    const unsigned long long* counts = band ? band_seg_counts : seg_counts;
+    for (int q = threadIdx.x; q < 256; q += blockDim.x) {
+        unsigned long long c = q < nseg ? counts[q] : 0ull;
+        if (q < nseg && c > seg_cap) {
+            if (q == seg) {
+                atomicOr(&st->error, overflow_bit);
+                atomicMax(&st->max_seg, c);
+                if (stop_on_overflow) st->done = 1;
+            }
+            c = seg_cap;
         }
-        if ((int)blockIdx.x == nseg - 1) *count_out = pre + s_cnt;
+        s_cnt[q] = c;
     }
     __syncthreads();
-    const unsigned long long* in = src + (unsigned long long)blockIdx.x * seg_cap;
-    for (unsigned long long i = threadIdx.x; i < s_cnt; i += blockDim.x) dst[s_pre + i] = in[i];
+    if (threadIdx.x == 0) {
+        unsigned long long pre = 0, tot = 0;
+        for (int q = 0; q < nseg; ++q) {
+            if (q < seg) pre += s_cnt[q];
+            tot += s_cnt[q];
+        }
+        s_pre = pre;
+        s_mine = s_cnt[seg];
+        if (seg == nseg - 1) *(band ? band_count_out : count_out) = tot;
+    }
+    __syncthreads();
+    const unsigned long long* in = (band ? band_src : src) + (unsigned long long)seg * seg_cap;
+    unsigned long long* out = (band ? band_dst : dst) + s_pre;
+    for (unsigned long long i = threadIdx.x; i < s_mine; i += blockDim.x) out[i] = in[i];
 }
 
 unsigned grid_for(long long n, int threads) {
@@ -145,14 +165,18 @@ cudaError_t launch_csr_from_sorted(const unsigned long long* keys, long long nnz
     return cudaGetLastError();
 }
 
-cudaError_t launch_compact_segments(const unsigned long long* src, unsigned long long seg_cap,
-                                    const unsigned long long* seg_counts, int nseg, unsigned long long* dst,
-                                    unsigned long long* count_out, DeviceState* st, int overflow_bit,
+cudaError_t launch_compact_segments(const unsigned long long* src, const unsigned long long* band_src,
+                                    unsigned long long seg_cap, const unsigned long long* seg_counts,
+                                    const unsigned long long* band_seg_counts, int nseg, unsigned long long* dst,
+                                    unsigned long long* band_dst, unsigned long long* count_out,
+                                    unsigned long long* band_count_out, DeviceState* st, int overflow_bit,
                                     bool check_done, bool stop_on_overflow, cudaStream_t s) {
     if (nseg <= 0) return cudaSuccess;
+    if (nseg > 256) return cudaErrorInvalidValue;
     note_launch();
-    compact_segments_kernel<<<nseg, 256, 0, s>>>(src, seg_cap, seg_counts, nseg, dst, count_out, st, overflow_bit,
-                                                  check_done ? 1 : 0, stop_on_overflow ? 1 : 0);
+    compact_segments_kernel<<<2 * nseg, 256, 0, s>>>(src, band_src, seg_cap, seg_counts, band_seg_counts, nseg, dst,
+                                                      band_dst, count_out, band_count_out, st, overflow_bit,
+                                                      check_done ? 1 : 0, stop_on_overflow ? 1 : 0);
     return cudaGetLastError();
 }
 

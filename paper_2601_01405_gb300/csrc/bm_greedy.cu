@@ -48,12 +48,18 @@ __global__ void __launch_bounds__(kSelThreads) greedy_select_kernel(
     for (int i = tid; i < prev; i += kSelThreads) slot_of[cand_ids[i]] = -1;
     for (int i = tid; i < prev * words; i += kSelThreads) conflict[i] = 0;
     for (int i = tid; i < words; i += kSelThreads) row_any[i] = 0;
+    __shared__ int s_req;
     if (tid == 0) {
         s_found = 0;
         s_pos = st->scan_pos;
         st->step_start_pos = st->scan_pos;   // lets the host redo this step with larger buffers
+        int req = st->s_next;
+        req = req < 32 ? 32 : (req > S ? S : req);
+        s_req = req;
+        st->s_cur = req;
     }
     __syncthreads();
+    S = s_req;   // this step's batch: adapted between 32 and the buffer size
 
     // 2. next S uncovered ids in index order (bitmap scan, 1024 words per round)
     while (true) {
@@ -132,14 +138,20 @@ __global__ void __launch_bounds__(256) greedy_gather_kernel(
 }
 
 // Rows of the conflict matrix that hold any bit were flagged in row_any by
-// the sweep; only those rows are staged in shared memory.  One warp then walks
-// the flagged candidates in index order: candidate k is a landmark iff no
-// earlier landmark candidate covers it (its bit is clear in the running
-// 'killed' set).  Finally every thread assigns ordinals in parallel.
+// the sweep; flagged rows are staged in shared memory (as many as fit; the rest
+// are read from global memory).  One warp then walks the flagged candidates in
+// index order: candidate k is a landmark iff no earlier landmark candidate
+// covers it (its bit is clear in the running 'killed' set, two words per
+// lane).  Finally every thread assigns ordinals in parallel, and the next
+// step's batch size follows the survival rate (fewer wasted candidate rows on
+// dense data, larger batches where balls are small).
+constexpr int kMaxWords = 64;   // batches of up to 2048 candidates
+
 __global__ void __launch_bounds__(256) greedy_resolve_kernel(DeviceState* st, const unsigned* conflict,
                                                              const unsigned* row_any, int words,
                                                              const int* cand_ids, int* ordinal,
-                                                             int* landmarks, unsigned long long mem_cap) {
+                                                             int* landmarks, unsigned long long mem_cap,
+                                                             int stage_rows, int s_max) {
     if (st->done) return;
     // the new memberships are a subset of this step's hits: stop before anything
     // is committed if they might not fit (the host grows the buffer and redoes the step)
@@ -150,70 +162,94 @@ __global__ void __launch_bounds__(256) greedy_resolve_kernel(DeviceState* st, co
         }
         return;
     }
-    extern __shared__ unsigned s_rows[];   // flagged rows, compacted: nflag x words
-    __shared__ int s_rank_of_word[33];
-    __shared__ int s_flag_row[1024];
-    __shared__ unsigned s_killed[32];
+    extern __shared__ unsigned s_rows[];   // staged flagged rows: min(nflag, stage_rows) x words
+    __shared__ int s_rank_of_word[kMaxWords + 1];
+    __shared__ int s_flag_row[kMaxWords * 32];
+    __shared__ unsigned s_alive[kMaxWords];
     __shared__ int s_nflag;
     const int c = st->cand_count;
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid < 32) {
-        unsigned a = lane < words ? row_any[lane] : 0u;
-        // rows >= c never hold bits, but mask them anyway
-        if (lane * 32 >= c) a = 0u;
-        else if (lane * 32 + 32 > c) a &= (1u << (c - lane * 32)) - 1u;
-        int cnt = __popc(a), x = cnt;
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(kFull, x, o);
-            if (lane >= o) x += y;
+        int base = 0;
+        for (int h = 0; h < 2; ++h) {
+            const int w = lane + 32 * h;
+            unsigned a = w < words ? row_any[w] : 0u;
+            if (w * 32 >= c) a = 0u;
+            else if (w * 32 + 32 > c) a &= (1u << (c - w * 32)) - 1u;
+            const int cnt = __popc(a);
+            int x = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, x, o);
+                if (lane >= o) x += y;
+            }
+            const int first = base + x - cnt;
+            unsigned m = a;
+            int k = first;
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                s_flag_row[k++] = w * 32 + b;
+            }
+            base += __shfl_sync(kFull, x, 31);
         }
-        s_rank_of_word[lane] = x - cnt;          // index of the first flagged row of this word
-        if (lane == 31) s_nflag = x;
-        unsigned m = a;
-        int k = x - cnt;
-        while (m) {
-            const int b = __ffs(m) - 1;
-            m &= m - 1;
-            s_flag_row[k++] = lane * 32 + b;
-        }
+        if (lane == 0) s_nflag = base;
     }
     __syncthreads();
     const int nflag = s_nflag;
-    for (int e = tid; e < nflag * words; e += blockDim.x) {
+    const int staged = nflag < stage_rows ? nflag : stage_rows;
+    for (int e = tid; e < staged * words; e += blockDim.x) {
         const int f = e / words, wi = e - f * words;
         s_rows[e] = conflict[(size_t)s_flag_row[f] * words + wi];
     }
     __syncthreads();
     if (tid < 32) {
-        unsigned killed = 0;  // lane owns word 'lane' of the killed set
+        unsigned killed0 = 0, killed1 = 0;  // words lane and lane + 32 of the killed set
         for (int f = 0; f < nflag; ++f) {
-            const int k = s_flag_row[f];
-            const unsigned kw = __shfl_sync(kFull, killed, k >> 5);
+            const int k = s_flag_row[f], w = k >> 5;
+            const unsigned kw = __shfl_sync(kFull, w < 32 ? killed0 : killed1, w & 31);
             if ((kw >> (k & 31)) & 1u) continue;
-            if (lane < words) killed |= s_rows[f * words + lane];
+            const unsigned* row = f < staged ? s_rows + (size_t)f * words : conflict + (size_t)k * words;
+            if (lane < words) killed0 |= row[lane];
+            if (lane + 32 < words) killed1 |= row[lane + 32];
         }
-        unsigned valid = (lane * 32 + 32 <= c) ? kFull : (lane * 32 >= c ? 0u : ((1u << (c - lane * 32)) - 1u));
-        const unsigned alive = ~killed & valid;
-        s_killed[lane] = alive;
-        int cnt = __popc(alive), x = cnt;
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(kFull, x, o);
-            if (lane >= o) x += y;
+        int base = 0;
+        for (int h = 0; h < 2; ++h) {
+            const int w = lane + 32 * h;
+            const unsigned valid = (w * 32 + 32 <= c) ? kFull : (w * 32 >= c ? 0u : ((1u << (c - w * 32)) - 1u));
+            const unsigned alive = ~(h ? killed1 : killed0) & valid;
+            if (w < kMaxWords) s_alive[w] = alive;
+            const int cnt = __popc(alive);
+            int x = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, x, o);
+                if (lane >= o) x += y;
+            }
+            s_rank_of_word[w] = base + x - cnt;   // alive count before word w
+            base += __shfl_sync(kFull, x, 31);
         }
-        s_rank_of_word[lane] = x - cnt;          // now: alive count before this word
-        if (lane == 31) s_rank_of_word[32] = x;
+        if (lane == 0) s_rank_of_word[kMaxWords] = base;
     }
     __syncthreads();
-    const int base = st->n_landmarks;
+    const int base_l = st->n_landmarks;
     for (int k = tid; k < c; k += blockDim.x) {
-        const unsigned aw = s_killed[k >> 5];
+        const unsigned aw = s_alive[k >> 5];
         const bool a = (aw >> (k & 31)) & 1u;
         const int rank = s_rank_of_word[k >> 5] + __popc(aw & ((1u << (k & 31)) - 1u));
-        ordinal[k] = a ? base + rank : -1;
-        if (a) landmarks[base + rank] = cand_ids[k];
+        ordinal[k] = a ? base_l + rank : -1;
+        if (a) landmarks[base_l + rank] = cand_ids[k];
     }
     __syncthreads();
-    if (tid == 0) st->n_landmarks = base + s_rank_of_word[32];
+    if (tid == 0) {
+        const int alive = s_rank_of_word[kMaxWords];
+        st->n_landmarks = base_l + alive;
+        // next batch: double while at least 90 % of a full batch survives, halve below 50 %
+        const int cur = st->s_cur;
+        int nxt = cur;
+        if (c == cur && 10 * alive >= 9 * c) nxt = cur * 2;
+        else if (2 * alive < c) nxt = cur / 2;
+        nxt = nxt < 32 ? 32 : (nxt > s_max ? s_max : nxt);
+        st->s_next = nxt;
+    }
 }
 
 __global__ void __launch_bounds__(256) greedy_apply_kernel(DeviceState* st, const unsigned long long* step_keys,
@@ -293,17 +329,19 @@ cudaError_t launch_greedy_gather(const GreedyBuffers& g, const Prepared& pts, in
 
 cudaError_t launch_greedy_resolve(const GreedyBuffers& g, int S, cudaStream_t s) {
     const int words = S / 32;
-    const size_t smem = (size_t)S * words * sizeof(unsigned);
+    constexpr size_t kStageBytes = 128 * 1024;
+    const int stage_rows = (int)(kStageBytes / (sizeof(unsigned) * words));
+    const size_t smem = (size_t)(stage_rows < S ? stage_rows : S) * words * sizeof(unsigned);
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(greedy_resolve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             32 * 1024 * 4);
+                                             (int)kStageBytes);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     note_launch();
     greedy_resolve_kernel<<<1, 256, smem, s>>>(g.st, g.conflict, g.row_any, words, g.cand_ids, g.ordinal,
-                                               g.landmarks, g.mem_cap);
+                                               g.landmarks, g.mem_cap, stage_rows < S ? stage_rows : S, S);
     return cudaGetLastError();
 }
 

@@ -79,12 +79,15 @@ bool tc_supported();             // device is sm_103 and the kernel loaded
 // grid_out: CTAs launched (= hit segments written when s.sink.seg_counts is set)
 cudaError_t launch_sweep_tc(const SweepDesc& s, cudaStream_t stream, std::string* why, int* grid_out);
 int device_sm_count();
-// Gather the per-CTA hit segments into dst; *count_out = hits kept.  A segment
-// longer than seg_cap sets overflow_bit in st->error (and st->done when
-// stop_on_overflow) and records the length in st->max_seg.
-cudaError_t launch_compact_segments(const unsigned long long* src, unsigned long long seg_cap,
-                                    const unsigned long long* seg_counts, int nseg, unsigned long long* dst,
-                                    unsigned long long* count_out, DeviceState* st, int overflow_bit,
+// Gather the per-CTA hit and band segments of one sweep into dst / band_dst
+// (one launch); *count_out / *band_count_out = entries kept.  A segment longer
+// than seg_cap sets overflow_bit in st->error (and st->done when
+// stop_on_overflow) and records its length in st->max_seg.
+cudaError_t launch_compact_segments(const unsigned long long* src, const unsigned long long* band_src,
+                                    unsigned long long seg_cap, const unsigned long long* seg_counts,
+                                    const unsigned long long* band_seg_counts, int nseg, unsigned long long* dst,
+                                    unsigned long long* band_dst, unsigned long long* count_out,
+                                    unsigned long long* band_count_out, DeviceState* st, int overflow_bit,
                                     bool check_done, bool stop_on_overflow, cudaStream_t s);
 
 // greedy.cu

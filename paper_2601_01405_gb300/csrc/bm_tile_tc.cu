@@ -12,7 +12,7 @@
 //
 // Kernel organisation (one CTA per SM, persistent over work items):
 //   warp 0  TMA producer: one point tile (B, NT rows x all K) per work item,
-//           then the K chunks of up to 8 query tiles (A, 128 rows each)
+//           then the K chunks of up to 16 query tiles (A, 128 rows each)
 //           through a ring of shared-memory stages
 //   warp 1  allocates tensor memory; lane 0 issues tcgen05.mma (M=128, N=NT,
 //           K=16 per instruction) into one of two TMEM accumulators
@@ -35,7 +35,7 @@ namespace {
 
 constexpr int kThreads = 320;   // 2 control warps + 8 epilogue warps
 constexpr int kEpiWarps = 8;
-constexpr int kMaxGroup = 8;
+constexpr int kMaxGroup = 16;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
 constexpr unsigned long long kDrainNs = 200000000ull;  // 0.2 s
 

@@ -1,0 +1,101 @@
+"""Full-size workloads in the configuration bench.py times, checked against the CPU
+oracle on sampled outputs (each sampled value computed by the oracle one by one) and
+through properties that hold at any size."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_01405_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bm():
+    from paper_2601_01405_gb300 import _build, binding
+    _build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return binding
+
+
+def sampled_checks(X, out, eps, rng, n_points=400, n_rows=120, n_edges=200):
+    """X: host float32 points; out: bm_build result moved to the host."""
+    n = X.shape[0]
+    lm, off, ids, edges = out["landmarks"], out["offsets"], out["ids"], out["edges"]
+    L = lm.size
+    # landmarks: strictly increasing ids; every point covered; each landmark in its own ball
+    assert L >= 1 and np.all(np.diff(lm) > 0)
+    assert np.bincount(ids, minlength=n).min() >= 1
+    assert off[0] == 0 and off[-1] == ids.size and np.all(np.diff(off) >= 1)
+    rows_sorted = np.all((np.diff(ids) > 0) | (np.diff(np.repeat(np.arange(L), np.diff(off))) != 0))
+    assert rows_sorted
+    # index-order greedy characterisation on sampled points:
+    # x is a landmark  <=>  no landmark l < x has d(l, x) < eps
+    xs = np.unique(np.concatenate([rng.integers(0, n, n_points), lm[rng.integers(0, L, 50)]]))
+    lo, li = oracle.range_query(X[lm], X[xs], eps)
+    is_lm = np.isin(xs, lm)
+    for k, x in enumerate(xs):
+        covered_earlier = np.any(lm[li[lo[k]:lo[k + 1]]] < x)
+        assert is_lm[k] == (not covered_earlier), x
+    # membership rows of sampled landmarks: full-scan oracle rows
+    rows = np.unique(rng.integers(0, L, n_rows))
+    ro, ri = oracle.range_query(X, X[lm[rows]], eps)
+    for k, r in enumerate(rows):
+        assert np.array_equal(ids[off[r]:off[r + 1]], ri[ro[k]:ro[k + 1]]), r
+    # sampled edges: both balls (oracle rows) share a point
+    if edges.shape[0]:
+        es = edges[rng.integers(0, edges.shape[0], min(n_edges, edges.shape[0]))]
+        eo, ei = oracle.range_query(X, X[lm[es.ravel()]], eps)
+        for k in range(es.shape[0]):
+            a = ei[eo[2 * k]:eo[2 * k + 1]]
+            b = ei[eo[2 * k + 1]:eo[2 * k + 2]]
+            assert np.intersect1d(a, b).size > 0, es[k]
+        assert np.all(edges[:, 0] < edges[:, 1])
+        keys = edges[:, 0].astype(np.int64) * L + edges[:, 1]
+        assert np.all(np.diff(keys) > 0)            # lexicographic, unique
+    # sampled non-edges among landmark pairs that are close (d < 2 eps): no shared point
+    cand = rng.integers(0, L, (400, 2))
+    cand = cand[cand[:, 0] < cand[:, 1]]
+    d2 = ((X[lm[cand[:, 0]]].astype(np.float64) - X[lm[cand[:, 1]]]) ** 2).sum(1)
+    close = cand[d2 < 4.0 * float(eps) ** 2][:60]
+    if close.shape[0]:
+        ekeys = set(map(tuple, edges.tolist()))
+        co, ci = oracle.range_query(X, X[lm[close.ravel()]], eps)
+        for k, (i, j) in enumerate(close):
+            shared = np.intersect1d(ci[co[2 * k]:co[2 * k + 1]], ci[co[2 * k + 1]:co[2 * k + 2]]).size > 0
+            assert shared == ((int(i), int(j)) in ekeys), (i, j)
+
+
+def run(bm, Xd, eps, path="tc"):
+    out = bm.bm_build(Xd, eps, path=path)
+    torch.cuda.synchronize()
+    return {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in out.items()}
+
+
+@pytest.fixture(scope="module")
+def mix():
+    return W.make("mix32-n1M-d64")
+
+
+@pytest.mark.parametrize("eps", [2.0, 4.0, 6.0])
+def test_mix32_n1M_d64_sampled(bm, mix, eps):
+    Xd = torch.from_numpy(mix).cuda()
+    out = run(bm, Xd, eps)
+    sampled_checks(mix, out, eps, np.random.default_rng(int(eps)))
+
+
+def test_mix32_n1M_d64_paths_identical(bm, mix):
+    """Both distance-tile paths give the same bytes at full size (eps = 6)."""
+    Xd = torch.from_numpy(mix).cuda()
+    a = run(bm, Xd, 6.0, "tc")
+    b = run(bm, Xd, 6.0, "fp32")
+    for k in ("landmarks", "offsets", "ids", "edges"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("eps", [0.5, 1.0])
+def test_roll_n2M_d128_sampled(bm, eps):
+    X = W.make("roll-n2M-d128")
+    out = run(bm, torch.from_numpy(X).cuda(), eps)
+    sampled_checks(X, out, eps, np.random.default_rng(7 + int(10 * eps)), n_points=200, n_rows=60)

@@ -108,7 +108,7 @@ def test_build_iso_n10k_d16(bm, path):
 
 
 @pytest.mark.parametrize("path", PATHS)
-@pytest.mark.parametrize("batch", [32, 96, 1024])
+@pytest.mark.parametrize("batch", [32, 96, 1024, 2048])
 def test_build_batch_sizes(bm, path, batch):
     X = W.isotropic(5003, 8, 10, seed=3)
     ref = oracle.build(X, 2.0)
