@@ -131,6 +131,19 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def aggregate(dist, device, seconds, evals):
+    """Whole-job rate over replicas: evaluations summed over ranks divided by the
+    slowest rank's time (max over ranks).  Returns (rate, seconds_max, evals_sum)."""
+    if dist is None:
+        return evals / seconds, seconds, evals
+    import torch
+    t_max = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    e_sum = torch.tensor([float(evals)], dtype=torch.float64, device=device)
+    dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    dist.all_reduce(e_sum, op=dist.ReduceOp.SUM)
+    return float(e_sum.item()) / float(t_max.item()), float(t_max.item()), float(e_sum.item())
+
+
 # --------------------------------------------------------------------------- CPU oracle
 def oracle_rate(X, eps_list, target_s, landmark_rows=None):
     """Time the CPU oracle's full-scan membership query (the same exact decision per
@@ -247,13 +260,9 @@ def run_ours(args):
     sampler.start()
     ms, stats = timed(args.path, 0, args.steps)
     clocks = sampler.stop()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     evals_per_step = sum(s["distance_evals"] for s in stats[0])
-    total_evals = evals_per_step * args.steps * ws
-    value = total_evals / (ms / 1000.0)
+    value, secs, _ = aggregate(dist, "cuda", ms / 1000.0, evals_per_step * args.steps)
+    ms = secs * 1000.0
     ms_step = ms / args.steps
     flat = [s for st in stats for s in st]
     build_s = {str(e): sum(st[i]["ms_total"] for st in stats) / len(stats) / 1000.0 for i, e in enumerate(eps_list)}
@@ -307,11 +316,8 @@ def run_ours(args):
                 d2h += 4 * L + 8 * (L + 1) + 4 * nnz + 8 * E
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": evals_per_step * args.e2e_steps * ws / dt, "unit": UNIT,
+        e2e_rate, _, _ = aggregate(dist, "cuda", dt, evals_per_step * args.e2e_steps)
+        e2e = {"value": e2e_rate, "unit": UNIT,
                "h2d_bytes_per_step": int(n * d * 4 * len(eps_list)),
                "d2h_bytes_per_step": int(d2h // args.e2e_steps)}
 

@@ -76,7 +76,7 @@ typedef struct {
     int32_t batch;         /* largest greedy batch (candidates per step), 32..2048, multiple of 32; 0 = 2048.
                               The batch starts at min(batch, 256) and doubles / halves with the share of
                               candidates that become landmarks. */
-    int32_t reserved0;
+    int32_t skip_edges;    /* bm_build: 1 = landmarks and memberships only (no nerve pass) */
     bm_alloc_fn alloc;     /* optional device allocator for outputs and scratch */
     bm_free_fn free;
     void* alloc_ctx;

@@ -31,7 +31,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void
 
 class bm_options(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("path", ctypes.c_int32), ("host_io", ctypes.c_int32),
-                ("batch", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("alloc", ALLOC_FN),
+                ("batch", ctypes.c_int32), ("skip_edges", ctypes.c_int32), ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
 
 
@@ -155,9 +155,11 @@ def _is_torch_cuda(x) -> bool:
     return isinstance(x, torch.Tensor) and x.is_cuda
 
 
-def _options(lib, path: str, batch: int, stream, host_io: bool, alloc: Optional[_TorchAllocator]):
+def _options(lib, path: str, batch: int, stream, host_io: bool, alloc: Optional[_TorchAllocator],
+             skip_edges: bool = False):
     opt = bm_options()
     lib.bm_options_init(ctypes.byref(opt))
+    opt.skip_edges = 1 if skip_edges else 0
     opt.path = PATHS[path]
     opt.batch = int(batch)
     opt.host_io = 1 if host_io else 0
@@ -228,7 +230,7 @@ def bm_range_query(X, Q, eps: float, path: str = "tc", stream=None):
     return off, ids, st.as_dict()
 
 
-def bm_build(X, eps: float, path: str = "tc", batch: int = 0, stream=None):
+def bm_build(X, eps: float, path: str = "tc", batch: int = 0, stream=None, skip_edges: bool = False):
     """Exact Ball Mapper: landmarks (greedy index order), CSR memberships, nerve edges.
 
     Device tensor in -> dict of torch CUDA tensors; host array in -> dict of numpy arrays.
@@ -237,7 +239,7 @@ def bm_build(X, eps: float, path: str = "tc", batch: int = 0, stream=None):
     px, n, d, kx, host = _as_input(X)
     g = bm_graph()
     if host:
-        opt = _options(lib, path, batch, stream, True, None)
+        opt = _options(lib, path, batch, stream, True, None, skip_edges)
         _check(lib, lib.bm_build(px, n, d, ctypes.c_float(eps), ctypes.byref(opt), ctypes.byref(g)))
         try:
             L, nnz, E = g.n_landmarks, g.members.nnz, g.n_edges
@@ -256,7 +258,7 @@ def bm_build(X, eps: float, path: str = "tc", batch: int = 0, stream=None):
     import torch
     dev = kx.device
     alloc = _TorchAllocator(dev)
-    opt = _options(lib, path, batch, stream or _current_stream(dev), False, alloc)
+    opt = _options(lib, path, batch, stream or _current_stream(dev), False, alloc, skip_edges)
     _check(lib, lib.bm_build(px, n, d, ctypes.c_float(eps), ctypes.byref(opt), ctypes.byref(g)))
     L, nnz, E = g.n_landmarks, g.members.nnz, g.n_edges
     return {"landmarks": alloc.tensor(g.landmarks, L, torch.int32),

@@ -752,7 +752,7 @@ bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_opt
             tm.mark();  // 3: CSR done
             Failure f{BM_OK, ""};
             EdgeResult er;
-            if (!build_edges(sorted, nnz, n, L, ar, s, er, f)) return fail(f.status, f.msg);
+            if (!opt.skip_edges && !build_edges(sorted, nnz, n, L, ar, s, er, f)) return fail(f.status, f.msg);
             edges = er.edges;
             E = er.n_edges;
             edge_pairs = er.pairs;

@@ -7,9 +7,12 @@
 // Sec. 5.2, Def. 5.6): {i, j} is an edge iff some point lies in both balls.  Every
 // point x covered by c_x balls witnesses the c_x (c_x - 1) / 2 pairs of its
 // covering landmarks, so the edge set is the deduplicated union of those
-// pairs.  Steps: transpose the memberships (point -> covering landmarks),
-// count and prefix-sum the pairs per point, emit (i << 32 | j) keys with
-// i < j, radix sort, keep the first key of every run.
+// pairs.  Steps: transpose the memberships (point -> ascending covering
+// landmarks, by a radix sort of swapped keys); count the witnessed pairs per
+// smaller landmark and cut the landmark range into chunks of at most 2^28
+// pairs; per chunk emit (i << 32 | j) keys, radix sort, keep the first key of
+// every run and append.  Chunks ascend in i, so the edges come out
+// lexicographic.
 #include "bm_host.h"
 
 namespace bm {
@@ -35,48 +38,70 @@ __global__ void fill_i64_kernel(long long* p, long long n, long long v) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) p[i] = v;
 }
 
-__global__ void count_points_kernel(const unsigned long long* keys, long long nnz, long long* cnt) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += stride)
-        atomicAdd((unsigned long long*)&cnt[keys[i] & 0xffffffffull], 1ull);
-}
-
-__global__ void scatter_transpose_kernel(const unsigned long long* keys, long long nnz, const long long* toff,
-                                         long long* cursor, int* tlist) {
+// (row << 32 | point) -> (point << 32 | row): the transposed membership keys.
+__global__ void swap_keys_kernel(const unsigned long long* keys, long long nnz, unsigned long long* out) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += stride) {
         const unsigned long long k = keys[i];
-        const long long pt = (long long)(k & 0xffffffffull);
-        const long long slot = (long long)atomicAdd((unsigned long long*)&cursor[pt], 1ull);
-        tlist[toff[pt] + slot] = (int)(k >> 32);
+        out[i] = (k << 32) | (k >> 32);
     }
 }
 
-__global__ void pair_counts_kernel(const long long* toff, long long n, long long* pc) {
+// Pairs (i, j), i < j, that point x witnesses with landmark i as the smaller
+// ordinal: entry a of x's sorted cover list (length c) starts c - 1 - a pairs.
+__global__ void landmark_pair_counts_kernel(const unsigned long long* tkeys, const long long* toff,
+                                            const int* tlist, long long nnz, unsigned long long* plc) {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const long long c = toff[i + 1] - toff[i];
-        pc[i] = c * (c - 1) / 2;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+        const long long x = (long long)(tkeys[e] >> 32);
+        const long long c = toff[x + 1] - toff[x], a = e - toff[x];
+        if (c - 1 - a > 0) atomicAdd(&plc[tlist[e]], (unsigned long long)(c - 1 - a));
     }
 }
 
-// One warp per point: all pairs (a < b) of its covering landmarks.
-__global__ void emit_pairs_kernel(const long long* toff, const int* tlist, long long n, const long long* poff,
-                                  unsigned long long* pairs) {
+// First position in sorted v[lo, hi) with v[pos] >= key.
+__device__ __forceinline__ long long lower_bound_i32(const int* v, long long lo, long long hi, int key) {
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (v[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Per point: the number of its pairs whose smaller landmark lies in [i0, i1).
+__global__ void chunk_pair_counts_kernel(const long long* toff, const int* tlist, long long n, int i0, int i1,
+                                         long long* pc) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
+        const long long b0 = toff[x], c = toff[x + 1] - b0;
+        long long cnt = 0;
+        if (c >= 2) {
+            const long long p0 = lower_bound_i32(tlist, b0, b0 + c, i0) - b0;
+            const long long p1 = lower_bound_i32(tlist, b0, b0 + c, i1) - b0;
+            const long long k = p1 - p0;   // entries p0 .. p1-1 start (c-1-a) pairs each
+            cnt = k * (c - 1) - (p0 + p1 - 1) * k / 2;
+        }
+        pc[x] = cnt;
+    }
+}
+
+// One warp per point: keys ((i - i0) << 32 | j) for the pairs counted above.
+__global__ void emit_chunk_pairs_kernel(const long long* toff, const int* tlist, long long n, int i0, int i1,
+                                        const long long* poff, unsigned long long* pairs) {
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     const int lane = threadIdx.x & 31;
-    for (long long pt = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); pt < n; pt += warps) {
-        const long long b0 = toff[pt];
-        const int c = (int)(toff[pt + 1] - b0);
+    for (long long x = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); x < n; x += warps) {
+        const long long b0 = toff[x];
+        const int c = (int)(toff[x + 1] - b0);
         if (c < 2) continue;
-        long long o = poff[pt];
-        for (int a = 0; a < c - 1; ++a) {
-            const unsigned la = (unsigned)tlist[b0 + a];
-            for (int b = a + 1 + lane; b < c; b += 32) {
-                const unsigned lb = (unsigned)tlist[b0 + b];
-                const unsigned lo = la < lb ? la : lb, hi = la < lb ? lb : la;
-                pairs[o + (b - a - 1)] = ((unsigned long long)lo << 32) | hi;
-            }
+        const int p0 = (int)(lower_bound_i32(tlist, b0, b0 + c, i0) - b0);
+        const int p1 = (int)(lower_bound_i32(tlist, b0, b0 + c, i1) - b0);
+        long long o = poff[x];
+        for (int a = p0; a < p1; ++a) {
+            const unsigned hi = (unsigned)(tlist[b0 + a] - i0);
+            for (int b = a + 1 + lane; b < c; b += 32)
+                pairs[o + (b - a - 1)] = ((unsigned long long)hi << 32) | (unsigned)tlist[b0 + b];
             o += c - 1 - a;
         }
     }
@@ -88,13 +113,13 @@ __global__ void unique_flags_kernel(const unsigned long long* keys, long long n,
         flags[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
 }
 
-__global__ void unique_scatter_kernel(const unsigned long long* keys, long long n, const long long* pos,
+__global__ void unique_scatter_kernel(const unsigned long long* keys, long long n, const long long* pos, int i0,
                                       int* edges) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         if (i == 0 || keys[i] != keys[i - 1]) {
             const long long o = pos[i];
-            edges[2 * o] = (int)(keys[i] >> 32);
+            edges[2 * o] = i0 + (int)(keys[i] >> 32);
             edges[2 * o + 1] = (int)(keys[i] & 0xffffffffull);
         }
     }
@@ -204,75 +229,121 @@ bool build_edges(const unsigned long long* keys, long long nnz, long long n, lon
                  cudaStream_t s, EdgeResult& out, Failure& f) {
     out = EdgeResult();
     if (nnz == 0 || L < 2) return true;
-    long long* cnt;
-    BM_ALLOC(cnt, long long, n + 1);
-    BM_TRY(cudaMemsetAsync(cnt, 0, sizeof(long long) * (n + 1), s));
+    // 1. point -> covering landmarks, ascending (transpose by a radix sort of swapped keys)
+    unsigned long long *tk, *tk2;
+    BM_ALLOC(tk, unsigned long long, nnz);
+    BM_ALLOC(tk2, unsigned long long, nnz);
     note_launch();
-    count_points_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(keys, nnz, cnt);
+    swap_keys_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(keys, nnz, tk);
     BM_TRY(cudaGetLastError());
+    unsigned long long* tsorted = nullptr;
+    BM_TRY(radix_sort_u64(tk, tk2, nnz, digit_shifts(bits_for(L - 1), bits_for(n - 1)), ar, s, &tsorted));
     long long* toff;
     BM_ALLOC(toff, long long, n + 1);
-    BM_TRY(exclusive_scan_i64(cnt, toff, n, ar, s));
     int* tlist;
     BM_ALLOC(tlist, int, nnz);
-    BM_TRY(cudaMemsetAsync(cnt, 0, sizeof(long long) * (n + 1), s));
+    BM_TRY(launch_csr_from_sorted(tsorted, nnz, n, toff, tlist, s));
+    // 2. pairs per smaller landmark -> landmark-range chunks of bounded size
+    unsigned long long* plc;
+    BM_ALLOC(plc, unsigned long long, L + 1);
+    BM_TRY(cudaMemsetAsync(plc, 0, sizeof(unsigned long long) * (L + 1), s));
     note_launch();
-    scatter_transpose_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(keys, nnz, toff, cnt, tlist);
+    landmark_pair_counts_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(tsorted, toff, tlist, nnz, plc);
     BM_TRY(cudaGetLastError());
-    note_launch();
-    pair_counts_kernel<<<grid_for(n, 256), 256, 0, s>>>(toff, n, cnt);
-    BM_TRY(cudaGetLastError());
-    long long* poff;
-    BM_ALLOC(poff, long long, n + 1);
-    BM_TRY(exclusive_scan_i64(cnt, poff, n, ar, s));
-    long long P = 0;
-    BM_TRY(cudaMemcpyAsync(&P, poff + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    long long* lpre;
+    BM_ALLOC(lpre, long long, L + 1);
+    BM_TRY(exclusive_scan_i64((const long long*)plc, lpre, L, ar, s));
+    std::vector<long long> hpre((size_t)L + 1);
+    BM_TRY(cudaMemcpyAsync(hpre.data(), lpre, sizeof(long long) * (L + 1), cudaMemcpyDeviceToHost, s));
     BM_TRY(cudaStreamSynchronize(s));
+    ar.release(lpre);
+    ar.release(plc);
+    ar.release(tk2);
+    ar.release(tk);
+    const long long P = hpre[(size_t)L];
     out.pairs = P;
     if (P == 0) return true;
-    if (P >= (1LL << 32)) {
-        f.status = BM_ERR_CAPACITY;
-        f.msg = "nerve pass: " + std::to_string(P) + " witnessed pairs exceed one sort (2^32 keys)";
-        return false;
+    const long long kBudget = 1LL << 28;   // emitted pairs per chunk (32 B of scratch each)
+    std::vector<std::pair<int, int>> chunks;
+    for (long long i0 = 0; i0 < L;) {
+        long long i1 = i0 + 1;
+        // largest i1 with pairs(i0, i1) <= budget (at least one landmark)
+        long long lo = i0 + 1, hi = L;
+        while (lo < hi) {
+            const long long mid = (lo + hi + 1) / 2;
+            if (hpre[(size_t)mid] - hpre[(size_t)i0] <= kBudget) lo = mid;
+            else hi = mid - 1;
+        }
+        i1 = lo;
+        if (hpre[(size_t)i1] - hpre[(size_t)i0] >= (1LL << 32)) {
+            f.status = BM_ERR_CAPACITY;
+            f.msg = "nerve pass: one landmark witnesses more than 2^32 pairs";
+            return false;
+        }
+        chunks.emplace_back((int)i0, (int)i1);
+        i0 = i1;
     }
-    unsigned long long *pairs, *tmp;
-    BM_ALLOC(pairs, unsigned long long, P);
-    BM_ALLOC(tmp, unsigned long long, P);
-    note_launch();
-    emit_pairs_kernel<<<grid_for(n * 32, 256), 256, 0, s>>>(toff, tlist, n, poff, pairs);
-    BM_TRY(cudaGetLastError());
-    ar.release(tlist);
-    const int lb = bits_for(L - 1);
-    unsigned long long* sorted = nullptr;
-    BM_TRY(radix_sort_u64(pairs, tmp, P, digit_shifts(lb, lb), ar, s, &sorted));
-    long long* flags;
-    BM_ALLOC(flags, long long, P);
-    long long* pos;
-    BM_ALLOC(pos, long long, P + 1);
-    note_launch();
-    unique_flags_kernel<<<grid_for(P, 256), 256, 0, s>>>(sorted, P, flags);
-    BM_TRY(cudaGetLastError());
-    BM_TRY(exclusive_scan_i64(flags, pos, P, ar, s));
-    long long E = 0;
-    BM_TRY(cudaMemcpyAsync(&E, pos + P, sizeof(long long), cudaMemcpyDeviceToHost, s));
-    BM_TRY(cudaStreamSynchronize(s));
-    if (E > 0x7fffffffLL) {
-        f.status = BM_ERR_CAPACITY;
-        f.msg = "more than 2^31-1 edges";
-        return false;
+    // 3. per chunk: count, emit, radix sort, deduplicate, append (chunks ascend in i)
+    long long* pc;
+    BM_ALLOC(pc, long long, n + 1);
+    long long* poff;
+    BM_ALLOC(poff, long long, n + 1);
+    int* edges = nullptr;
+    long long E = 0, cap = 0;
+    for (const auto& ch : chunks) {
+        const int i0 = ch.first, i1 = ch.second;
+        const long long Pc = hpre[(size_t)i1] - hpre[(size_t)i0];
+        if (Pc == 0) continue;
+        note_launch();
+        chunk_pair_counts_kernel<<<grid_for(n, 256), 256, 0, s>>>(toff, tlist, n, i0, i1, pc);
+        BM_TRY(cudaGetLastError());
+        BM_TRY(exclusive_scan_i64(pc, poff, n, ar, s));
+        unsigned long long *pairs, *tmp;
+        BM_ALLOC(pairs, unsigned long long, Pc);
+        BM_ALLOC(tmp, unsigned long long, Pc);
+        note_launch();
+        emit_chunk_pairs_kernel<<<grid_for(n * 32, 256), 256, 0, s>>>(toff, tlist, n, i0, i1, poff, pairs);
+        BM_TRY(cudaGetLastError());
+        unsigned long long* sorted = nullptr;
+        BM_TRY(radix_sort_u64(pairs, tmp, Pc, digit_shifts(bits_for(L - 1), bits_for(i1 - i0 - 1)), ar, s, &sorted));
+        long long* flags;
+        BM_ALLOC(flags, long long, Pc);
+        long long* pos;
+        BM_ALLOC(pos, long long, Pc + 1);
+        note_launch();
+        unique_flags_kernel<<<grid_for(Pc, 256), 256, 0, s>>>(sorted, Pc, flags);
+        BM_TRY(cudaGetLastError());
+        BM_TRY(exclusive_scan_i64(flags, pos, Pc, ar, s));
+        long long Ec = 0;
+        BM_TRY(cudaMemcpyAsync(&Ec, pos + Pc, sizeof(long long), cudaMemcpyDeviceToHost, s));
+        BM_TRY(cudaStreamSynchronize(s));
+        if (E + Ec > 0x7fffffffLL) {
+            f.status = BM_ERR_CAPACITY;
+            f.msg = "more than 2^31-1 edges";
+            return false;
+        }
+        if (E + Ec > cap) {   // grow the output (doubling), keeping the edges so far
+            long long ncap = std::max<long long>(E + Ec, 2 * cap);
+            int* ne;
+            BM_ALLOC(ne, int, 2 * ncap);
+            if (E) BM_TRY(cudaMemcpyAsync(ne, edges, sizeof(int) * 2 * E, cudaMemcpyDeviceToDevice, s));
+            ar.release(edges);
+            edges = ne;
+            cap = ncap;
+        }
+        note_launch();
+        unique_scatter_kernel<<<grid_for(Pc, 256), 256, 0, s>>>(sorted, Pc, pos, i0, edges + 2 * E);
+        BM_TRY(cudaGetLastError());
+        E += Ec;
+        ar.release(pos);
+        ar.release(flags);
+        ar.release(tmp);
+        ar.release(pairs);
     }
-    int* edges;
-    BM_ALLOC(edges, int, 2 * E);
-    note_launch();
-    unique_scatter_kernel<<<grid_for(P, 256), 256, 0, s>>>(sorted, P, pos, edges);
-    BM_TRY(cudaGetLastError());
-    ar.release(pos);
-    ar.release(flags);
-    ar.release(tmp);
-    ar.release(pairs);
     ar.release(poff);
+    ar.release(pc);
+    ar.release(tlist);
     ar.release(toff);
-    ar.release(cnt);
     out.edges = edges;
     out.n_edges = E;
     return true;
