@@ -132,6 +132,37 @@ BM_API bm_status bm_range_query(const float* X, int64_t n, int32_t d, const floa
 BM_API bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_options* opt,
                    bm_graph* out);
 
+/* ---- Inverted-file index: the paper's non-exhaustive approximate oracle (Sec. 5.4;
+ * nprobe cells searched per query, Sec. 6.1).  Points are grouped into nlist
+ * k-means cells; a query examines only the points of its nprobe nearest cells
+ * and decides membership exactly, so every returned point is a true member
+ * (conservative oracle, Def. 5.14: no false positives, Sec. 5.3).
+ * Cells: `iters` Lloyd iterations on `sample` points (0 = min(n, 262144))
+ * drawn by a seeded Fisher-Yates shuffle (splitmix64); the first nlist
+ * sampled points initialise the centroids; a point's cell is its nearest
+ * centroid (ties to the lowest id); centroids are FP64 means of their
+ * members in point order; an empty cell keeps its centroid.
+ * The index refers to X (device) until freed; with opt->host_io it keeps a
+ * device copy.  Its buffers come from opt's allocator. */
+typedef struct bm_ivf bm_ivf;
+
+BM_API bm_status bm_ivf_train(const float* X, int64_t n, int32_t d, int32_t nlist, int32_t iters, int64_t sample,
+                              uint64_t seed, const bm_options* opt, bm_ivf** out);
+BM_API void bm_ivf_free(bm_ivf* idx);
+/* Shape and device arrays of the index: cell of each point (n), centroids (nlist x d). */
+BM_API bm_status bm_ivf_info(const bm_ivf* idx, int64_t* n, int32_t* d, int32_t* nlist, const int32_t** cell_of,
+                             const float** centroids);
+/* out row j = { i : cell(i) among the nprobe cells nearest to Q_j, ||X_i - Q_j|| < eps }.
+ * probes: optional device int32 array (m x nprobe) receiving each query's cells. */
+BM_API bm_status bm_ivf_range_query(const bm_ivf* idx, const float* Q, int64_t m, float eps, int32_t nprobe,
+                                    const bm_options* opt, bm_csr* out, int32_t* probes, bm_stats* stats);
+/* Ball Mapper with the inverted-file oracle (Sec. 6.2 modes).  landmarks != NULL:
+ * fixed-landmark mode (their balls and nerve through the index; landmarks is
+ * device memory, or host memory with opt->host_io).  landmarks == NULL:
+ * end-to-end mode (the greedy of Sec. 2.2 driven by the index's range sets). */
+BM_API bm_status bm_build_ivf(const bm_ivf* idx, float eps, int32_t nprobe, const int32_t* landmarks,
+                              int64_t n_landmarks, const bm_options* opt, bm_graph* out);
+
 /* Release outputs (safe on zeroed structs); pass the options used to create them. */
 BM_API void bm_csr_free(bm_csr* csr, const bm_options* opt);
 BM_API void bm_graph_free(bm_graph* g, const bm_options* opt);

@@ -15,6 +15,7 @@ Functions and the passages they follow:
   edges              Sec. 2.1 nerve / Sec. 5.2 G_r(L): edge iff X_i, X_j intersect
   build              all of the above in order
   kth_nn_dist        Sec. 6.1 target-occupancy rule (self counted first)
+  masked_range_query Sec. 5.3 verified range set over a candidate set (points of probed cells)
   BallTree           Sec. 3.1 ball tree construction and pruned range query
 """
 from __future__ import annotations
@@ -80,6 +81,12 @@ def load_library(path: str):
     lib.bmo_bt_range_fill.restype = ctypes.c_int
     lib.bmo_bt_range_fill.argtypes = [ctypes.c_void_p, _f64p, ctypes.c_int64, ctypes.c_double,
                                       _i64p, _i32p]
+    lib.bmo_masked_range_count.restype = ctypes.c_int
+    lib.bmo_masked_range_count.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int, _f64p, ctypes.c_int64,
+                                           ctypes.c_double, _i32p, ctypes.c_int, _i32p, ctypes.c_int, _i64p]
+    lib.bmo_masked_range_fill.restype = ctypes.c_int
+    lib.bmo_masked_range_fill.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int, _f64p, ctypes.c_int64,
+                                          ctypes.c_double, _i32p, ctypes.c_int, _i32p, ctypes.c_int, _i64p, _i32p]
     lib.bmo_num_threads.restype = ctypes.c_int
     lib.bmo_num_threads.argtypes = []
     lib.bmo_set_num_threads.restype = None
@@ -150,6 +157,32 @@ def range_query(X, Q, eps):
     if m:
         lib.bmo_range_fill(_ptr(X, _f64p), n, d, _ptr(Q, _f64p), m, e2, _ptr(offsets, _i64p),
                            _ptr(ids, _i32p))
+    return offsets, ids[: int(offsets[-1])].copy()
+
+
+def masked_range_query(X, Q, eps, cell_of, nlist, probes):
+    """Verified range set over probed cells (Sec. 5.3): row j = {i : cell_of[i] in
+    probes[j], D(X_i, Q_j) < eps^2}, ascending.  probes: (m, nprobe) int32."""
+    X = _f64(X)
+    Q = _f64(Q)
+    n, d = X.shape
+    m = Q.shape[0]
+    cell_of = np.ascontiguousarray(cell_of, dtype=np.int32)
+    probes = np.ascontiguousarray(probes, dtype=np.int32).reshape(m, -1)
+    nprobe = probes.shape[1]
+    lib = _load()
+    counts = np.zeros(max(m, 1), dtype=np.int64)
+    e2 = eps_squared(eps)
+    if m and lib.bmo_masked_range_count(_ptr(X, _f64p), n, d, _ptr(Q, _f64p), m, e2, _ptr(cell_of, _i32p),
+                                        int(nlist), _ptr(probes, _i32p), nprobe, _ptr(counts, _i64p)):
+        raise MemoryError("masked range query")
+    offsets = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(counts[:m], out=offsets[1:])
+    ids = np.empty(max(int(offsets[-1]), 1), dtype=np.int32)
+    if m and lib.bmo_masked_range_fill(_ptr(X, _f64p), n, d, _ptr(Q, _f64p), m, e2, _ptr(cell_of, _i32p),
+                                       int(nlist), _ptr(probes, _i32p), nprobe, _ptr(offsets, _i64p),
+                                       _ptr(ids, _i32p)):
+        raise MemoryError("masked range query")
     return offsets, ids[: int(offsets[-1])].copy()
 
 

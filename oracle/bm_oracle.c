@@ -409,3 +409,67 @@ int bmo_bt_range_fill(void* h, const double* Q, int64_t m, double r, const int64
     }
     return bad ? -1 : 0;
 }
+
+/* ---------------------------------------------------------------------------
+ * Verified range set over a candidate set (Sec. 5.3): the candidates of query j
+ * are the points whose cell is one of the query's probed cells; a candidate is
+ * returned iff D(Q_j, X_i) < eps2.  cell_of[i] in [0, nlist), probes: m x nprobe.
+ * Two phases like bmo_range_count / bmo_range_fill.
+ * ------------------------------------------------------------------------- */
+static void mark_probes(unsigned char* flag, int nlist, const int32_t* probes, int nprobe, int64_t j) {
+    memset(flag, 0, (size_t)nlist);
+    for (int k = 0; k < nprobe; ++k) {
+        int32_t c = probes[(size_t)j * nprobe + k];
+        if (c >= 0 && c < nlist) flag[c] = 1;
+    }
+}
+
+int bmo_masked_range_count(const double* X, int64_t n, int d, const double* Q, int64_t m, double eps2,
+                           const int32_t* cell_of, int nlist, const int32_t* probes, int nprobe, int64_t* counts) {
+    int bad = 0;
+    #pragma omp parallel
+    {
+        unsigned char* flag = (unsigned char*)malloc((size_t)nlist);
+        if (!flag) {
+            #pragma omp atomic write
+            bad = 1;
+        }
+        #pragma omp for schedule(dynamic, 4)
+        for (int64_t j = 0; j < m; ++j) {
+            if (!flag) continue;
+            mark_probes(flag, nlist, probes, nprobe, j);
+            const double* q = Q + (size_t)j * d;
+            int64_t c = 0;
+            for (int64_t i = 0; i < n; ++i)
+                if (flag[cell_of[i]] && sqdist(q, X + (size_t)i * d, d) < eps2) ++c;
+            counts[j] = c;
+        }
+        free(flag);
+    }
+    return bad ? -1 : 0;
+}
+
+int bmo_masked_range_fill(const double* X, int64_t n, int d, const double* Q, int64_t m, double eps2,
+                          const int32_t* cell_of, int nlist, const int32_t* probes, int nprobe,
+                          const int64_t* offsets, int32_t* ids) {
+    int bad = 0;
+    #pragma omp parallel
+    {
+        unsigned char* flag = (unsigned char*)malloc((size_t)nlist);
+        if (!flag) {
+            #pragma omp atomic write
+            bad = 1;
+        }
+        #pragma omp for schedule(dynamic, 4)
+        for (int64_t j = 0; j < m; ++j) {
+            if (!flag) continue;
+            mark_probes(flag, nlist, probes, nprobe, j);
+            const double* q = Q + (size_t)j * d;
+            int64_t o = offsets[j];
+            for (int64_t i = 0; i < n; ++i)
+                if (flag[cell_of[i]] && sqdist(q, X + (size_t)i * d, d) < eps2) ids[o++] = (int32_t)i;
+        }
+        free(flag);
+    }
+    return bad ? -1 : 0;
+}

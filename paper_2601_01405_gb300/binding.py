@@ -103,6 +103,23 @@ def load(path: str = LIB_PATH):
         lib.bm_range_count_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
                                                ctypes.c_int64, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]
         lib.bm_range_count_noalloc.restype = ctypes.c_int
+        lib.bm_ivf_train.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_int64, ctypes.c_uint64, ctypes.POINTER(bm_options),
+                                     ctypes.POINTER(ctypes.c_void_p)]
+        lib.bm_ivf_train.restype = ctypes.c_int
+        lib.bm_ivf_free.argtypes = [ctypes.c_void_p]
+        lib.bm_ivf_free.restype = None
+        lib.bm_ivf_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_void_p),
+                                    ctypes.POINTER(ctypes.c_void_p)]
+        lib.bm_ivf_info.restype = ctypes.c_int
+        lib.bm_ivf_range_query.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_float,
+                                           ctypes.c_int32, ctypes.POINTER(bm_options), ctypes.POINTER(bm_csr),
+                                           ctypes.c_void_p, ctypes.POINTER(bm_stats)]
+        lib.bm_ivf_range_query.restype = ctypes.c_int
+        lib.bm_build_ivf.argtypes = [ctypes.c_void_p, ctypes.c_float, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
+                                     ctypes.POINTER(bm_options), ctypes.POINTER(bm_graph)]
+        lib.bm_build_ivf.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -137,6 +154,10 @@ class _TorchAllocator:
 
         self.alloc_cb = ALLOC_FN(_alloc)
         self.free_cb = FREE_FN(_free)
+
+    def peek(self, ptr, count, dtype):
+        """A view of a buffer the library still owns (e.g. an index's arrays)."""
+        return self.live[ptr].view(dtype)[:count]
 
     def tensor(self, ptr, count, dtype):
         """Adopt a library output as a torch tensor of `count` elements."""
@@ -289,3 +310,81 @@ def bm_range_count_noalloc(X, Q, eps: float, counts, stream=None):
     st = stream or _current_stream(kx.device)
     _check(lib, lib.bm_range_count_noalloc(px, n, d, pq, m, ctypes.c_float(eps), st, counts.data_ptr()))
     return counts
+
+
+class IvfIndex:
+    """Inverted-file index over device points X (bm_ivf_train).  The index refers to X,
+    which must stay alive and unchanged; its own buffers come from torch's allocator."""
+
+    def __init__(self, X, nlist: int = 1024, iters: int = 20, sample: int = 0, seed: int = 0):
+        import torch
+        self._lib = load()
+        if not _is_torch_cuda(X):
+            raise ValueError("X must be a CUDA tensor")
+        px, n, d, kx, _ = _as_input(X)
+        self._X = kx
+        self._alloc = _TorchAllocator(kx.device)
+        self._opt = _options(self._lib, "fp32", 0, _current_stream(kx.device), False, self._alloc)
+        h = ctypes.c_void_p()
+        _check(self._lib, self._lib.bm_ivf_train(px, n, d, int(nlist), int(iters), int(sample), int(seed),
+                                                 ctypes.byref(self._opt), ctypes.byref(h)))
+        self._h = h
+        n_ = ctypes.c_int64()
+        d_ = ctypes.c_int32()
+        nl = ctypes.c_int32()
+        co = ctypes.c_void_p()
+        ce = ctypes.c_void_p()
+        _check(self._lib, self._lib.bm_ivf_info(h, ctypes.byref(n_), ctypes.byref(d_), ctypes.byref(nl),
+                                                ctypes.byref(co), ctypes.byref(ce)))
+        self.n, self.d, self.nlist = n_.value, d_.value, nl.value
+        self.cell_of = self._alloc.peek(co.value, self.n, torch.int32)
+        self.centroids = self._alloc.peek(ce.value, self.nlist * self.d, torch.float32).view(self.nlist, self.d)
+
+    def range_query(self, Q, eps: float, nprobe: int):
+        """(offsets, ids, probes, stats): conservative range sets over the nprobe nearest cells."""
+        import torch
+        pq, m, dq, kq, _ = _as_input(Q)
+        if not _is_torch_cuda(Q):
+            raise ValueError("Q must be a CUDA tensor")
+        probes = torch.empty((m, nprobe), dtype=torch.int32, device=kq.device)
+        alloc = _TorchAllocator(kq.device)
+        opt = _options(self._lib, "fp32", 0, _current_stream(kq.device), False, alloc)
+        out = bm_csr()
+        st = bm_stats()
+        _check(self._lib, self._lib.bm_ivf_range_query(self._h, pq, m, ctypes.c_float(eps), int(nprobe),
+                                                       ctypes.byref(opt), ctypes.byref(out),
+                                                       probes.data_ptr() if m else None, ctypes.byref(st)))
+        return (alloc.tensor(out.offsets, m + 1, torch.int64), alloc.tensor(out.ids, out.nnz, torch.int32), probes,
+                st.as_dict())
+
+    def build(self, eps: float, nprobe: int, landmarks=None, batch: int = 0):
+        """Ball Mapper through the index: fixed-landmark mode (landmarks = CUDA int32 tensor)
+        or end-to-end mode (landmarks None)."""
+        import torch
+        dev = self._X.device
+        alloc = _TorchAllocator(dev)
+        opt = _options(self._lib, "fp32", batch, _current_stream(dev), False, alloc)
+        g = bm_graph()
+        lm_ptr, nl = None, 0
+        if landmarks is not None:
+            landmarks = landmarks.to(device=dev, dtype=torch.int32).contiguous()
+            lm_ptr, nl = landmarks.data_ptr() if landmarks.numel() else None, landmarks.numel()
+        _check(self._lib, self._lib.bm_build_ivf(self._h, ctypes.c_float(eps), int(nprobe), lm_ptr, nl,
+                                                 ctypes.byref(opt), ctypes.byref(g)))
+        L, nnz, E = g.n_landmarks, g.members.nnz, g.n_edges
+        return {"landmarks": alloc.tensor(g.landmarks, L, torch.int32),
+                "offsets": alloc.tensor(g.members.offsets, L + 1, torch.int64),
+                "ids": alloc.tensor(g.members.ids, nnz, torch.int32),
+                "edges": alloc.tensor(g.edges, 2 * E, torch.int32).view(E, 2),
+                "stats": g.stats.as_dict()}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.bm_ivf_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

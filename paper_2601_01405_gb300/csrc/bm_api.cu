@@ -295,8 +295,49 @@ struct SweepTimer {
 // path), FP64 recheck of the band pairs.  sd.sink must already carry the
 // greedy bookkeeping (or none) and the statistics pointers.  Hits end up in
 // o.keys with their number in *count.
+bm_status ivf_sweep(SweepDesc& sd, DeviceState* st, Arena& ar, bool greedy, cudaStream_t s) {
+    const IvfIndex& ix = *sd.ivf;
+    const long long rows_max = sd.a_rows_max;
+    int* probes = sd.ivf_probes_out;
+    if (!probes) ALLOC(probes, int, std::max<long long>(rows_max * sd.nprobe, 1));
+    long long *cnt, *cq_off, *tile_off;
+    int* cq_rows;
+    ALLOC(cnt, long long, ix.nlist + 1);
+    ALLOC(cq_off, long long, ix.nlist + 1);
+    ALLOC(tile_off, long long, ix.nlist + 1);
+    ALLOC(cq_rows, int, std::max<long long>(rows_max * sd.nprobe, 1));
+    TRY_CUDA(launch_probe_select(sd.a->x, rows_max, sd.a_rows_dev, ix, sd.nprobe, probes, s));
+    TRY_CUDA(launch_group_probes(probes, rows_max, sd.a_rows_dev, sd.nprobe, ix, cnt, cq_off, cq_rows, tile_off, ar,
+                                 s));
+    TRY_CUDA(launch_ivf_scan(sd.a->x, sd.a->phi, ix, sd.ivf_phi_perm, cq_off, cq_rows, tile_off, st, greedy, sd.sink,
+                             s));
+    ar.release(cq_rows);
+    ar.release(tile_off);
+    ar.release(cq_off);
+    ar.release(cnt);
+    if (probes != sd.ivf_probes_out) ar.release(probes);
+    return BM_OK;
+}
+
 bm_status sweep_stage(SweepDesc& sd, DeviceState* st, int path, SweepOut& o, unsigned long long* count,
-                      int overflow_bit, bool greedy, int sms, SweepTimer& stimer, cudaStream_t s) {
+                      int overflow_bit, bool greedy, int sms, SweepTimer& stimer, cudaStream_t s, Arena& ar) {
+    if (sd.ivf) {   // inverted-file scan: FP32 tiles over the probed cells, global counters
+        sd.sink.count = count;
+        sd.sink.cap = o.cap;
+        sd.sink.band_n = &st->band_n;
+        sd.sink.band_cap = o.cap;
+        sd.sink.keys = o.keys;
+        sd.sink.band_keys = o.band;
+        sd.sink.seg_counts = nullptr;
+        sd.sink.band_seg_counts = nullptr;
+        stimer.before();
+        bm_status rs = ivf_sweep(sd, st, ar, greedy, s);
+        stimer.after();
+        if (rs != BM_OK) return rs;
+        TRY_CUDA(launch_band_recheck(st, o.band, o.cap, sd.a->x, sd.ivf->X, sd.ivf->d, sd.eps2, o.keys, count, o.cap,
+                                     sd.sink, greedy, overflow_bit, greedy, s));
+        return BM_OK;
+    }
     const bool tc = path == BM_PATH_TC_SPLIT3;
     sd.sink.count = count;
     sd.sink.cap = o.cap;
@@ -342,7 +383,7 @@ bm_status read_state(const DeviceState* dst, HostState& hs, DeviceState& out, cu
 bm_status greedy_pass(const Prepared& pts, double eps2, int path, int S, Arena& ar, cudaStream_t s,
                       DeviceState* st, HostState& hs, unsigned long long& step_cap, unsigned long long& mem_cap,
                       bool* retry, int** landmarks_out, unsigned long long** mem_keys_out, DeviceState& final_state,
-                      SweepTimer& stimer) {
+                      SweepTimer& stimer, const IvfIndex* ivf, const float* phi_perm, int nprobe) {
     *retry = false;
     const long long n = pts.rows;
     const int d = pts.d;
@@ -400,6 +441,9 @@ bm_status greedy_pass(const Prepared& pts, double eps2, int path, int S, Arena& 
     sd.sink.conflict_words = words;
     sd.sink.band_count = &st->band_pairs;
     sd.sink.pair_count = &st->tile_pairs;
+    sd.ivf = ivf;
+    sd.ivf_phi_perm = phi_perm;
+    sd.nprobe = nprobe;
 
     DeviceState h;
     int chunk = 2;
@@ -408,7 +452,7 @@ bm_status greedy_pass(const Prepared& pts, double eps2, int path, int S, Arena& 
         for (int i = 0; i < chunk; ++i) {
             TRY_CUDA(launch_greedy_select(g, pts, S, tc, s));
             TRY_CUDA(launch_greedy_gather(g, pts, S, tc, s));
-            bm_status rs = sweep_stage(sd, st, path, so, &st->step_hits, kErrStepOverflow, true, sms, stimer, s);
+            bm_status rs = sweep_stage(sd, st, path, so, &st->step_hits, kErrStepOverflow, true, sms, stimer, s, ar);
             if (rs != BM_OK) return rs;
             TRY_CUDA(launch_greedy_resolve(g, S, s));
             TRY_CUDA(launch_greedy_apply(g, s));
@@ -460,78 +504,20 @@ bm_status greedy_pass(const Prepared& pts, double eps2, int path, int S, Arena& 
 
 using namespace bm;
 
-extern "C" {
+namespace bm {
+namespace {
 
-void bm_options_init(bm_options* opt) {
-    if (!opt) return;
-    std::memset(opt, 0, sizeof(*opt));
-    opt->path = BM_PATH_TC_SPLIT3;
-}
-
-const char* bm_status_string(bm_status s) {
-    switch (s) {
-        case BM_OK: return "ok";
-        case BM_ERR_ARG: return "invalid argument";
-        case BM_ERR_CUDA: return "CUDA error";
-        case BM_ERR_NOMEM: return "out of memory";
-        case BM_ERR_CAPACITY: return "capacity exceeded";
-        case BM_ERR_TIMEOUT: return "device wait timed out";
-        case BM_ERR_UNSUPPORTED: return "unsupported device";
-    }
-    return "unknown status";
-}
-
-const char* bm_last_error(void) { return g_last_error.c_str(); }
-
-int32_t bm_version(void) { return 100; }
-
-void bm_csr_free(bm_csr* csr, const bm_options* opt) {
-    if (!csr) return;
-    if (csr->on_host) {
-        std::free(csr->offsets);
-        std::free(csr->ids);
-    } else {
-        cudaStream_t s = opt ? (cudaStream_t)opt->stream : nullptr;
-        device_free(opt, s, csr->offsets);
-        device_free(opt, s, csr->ids);
-    }
-    std::memset(csr, 0, sizeof(*csr));
-}
-
-void bm_graph_free(bm_graph* g, const bm_options* opt) {
-    if (!g) return;
-    if (g->on_host) {
-        std::free(g->landmarks);
-        std::free(g->edges);
-    } else {
-        cudaStream_t s = opt ? (cudaStream_t)opt->stream : nullptr;
-        device_free(opt, s, g->landmarks);
-        device_free(opt, s, g->edges);
-    }
-    bm_csr_free(&g->members, opt);
-    std::memset(g, 0, sizeof(*g));
-}
-
-bm_status bm_range_query(const float* X, int64_t n, int32_t d, const float* Q, int64_t m, float eps,
-                         const bm_options* opt_in, bm_csr* out, bm_stats* stats) {
-    if (!out) return fail(BM_ERR_ARG, "out is NULL");
+// Range query R_eps(q) for every row q of Q over the points X (exact), or over the
+// cells an inverted-file index probes for q (conservative).  Arguments validated.
+bm_status range_core(const float* X, long long n, int d, const float* Q, long long m, float eps, const bm_options& opt,
+                     const IvfIndex* ivf, int nprobe, int* probes_out, bm_csr* out, bm_stats* stats) {
     std::memset(out, 0, sizeof(*out));
     if (stats) std::memset(stats, 0, sizeof(*stats));
-    bm_options opt;
-    bm_options_init(&opt);
-    if (opt_in) opt = *opt_in;
-    bm_status vs = validate_points(X, n, d, "X");
-    if (vs != BM_OK) return vs;
-    vs = validate_points(Q, m, d, "Q");
-    if (vs != BM_OK) return vs;
-    vs = validate_eps(eps);
-    if (vs != BM_OK) return vs;
-    vs = check_device(opt.path);
-    if (vs != BM_OK) return vs;
     cudaStream_t s = (cudaStream_t)opt.stream;
     const bool host_io = opt.host_io != 0;
     const double eps2 = (double)eps * (double)eps;
-    const bool tc = opt.path == BM_PATH_TC_SPLIT3;
+    const bool tc = opt.path == BM_PATH_TC_SPLIT3 && ivf == nullptr;
+    const int path = ivf ? (int)BM_PATH_FP32 : opt.path;
     Timer tm(s);
     tm.mark();
     SweepTimer stimer(s);
@@ -544,7 +530,7 @@ bm_status bm_range_query(const float* X, int64_t n, int32_t d, const float* Q, i
     float delta = 0.f;
     {
         Arena ar(&opt, s);
-        const float* dX = stage_input(X, n, d, host_io, ar, s, &rs);
+        const float* dX = ivf ? X : stage_input(X, n, d, host_io, ar, s, &rs);
         if (rs != BM_OK) return rs;
         const float* dQ = stage_input(Q, m, d, host_io, ar, s, &rs);
         if (rs != BM_OK) return rs;
@@ -560,11 +546,12 @@ bm_status bm_range_query(const float* X, int64_t n, int32_t d, const float* Q, i
             ALLOC(bad, int, 1);
             TRY_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
             Prepared px, pq;
-            rs = prepare(dX, n, d, eps2, false, tc, ar, &st->max_norm_bits, bad, s, px);
+            // inverted-file mode: the points enter the tiles in cell order
+            rs = prepare(ivf ? ivf->xperm : dX, n, d, eps2, false, tc, ar, &st->max_norm_bits, bad, s, px);
             if (rs != BM_OK) return rs;
             rs = prepare(dQ, m, d, eps2, true, tc, ar, &st->max_norm_q_bits, bad, s, pq);
             if (rs != BM_OK) return rs;
-            TRY_CUDA(launch_delta(st, opt.path, d, px.d_pad, eps2, false, s));
+            TRY_CUDA(launch_delta(st, path, d, px.d_pad, eps2, false, s));
             int hbad = 0;
             TRY_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
             TRY_CUDA(cudaStreamSynchronize(s));
@@ -591,7 +578,11 @@ bm_status bm_range_query(const float* X, int64_t n, int32_t d, const float* Q, i
                 sd.sink = HitSink();
                 sd.sink.band_count = &st->band_pairs;
                 sd.sink.pair_count = &st->tile_pairs;
-                rs = sweep_stage(sd, st, opt.path, so, &st->hit_count, kErrHitOverflow, false, sms, stimer, s);
+                sd.ivf = ivf;
+                sd.ivf_phi_perm = px.phi;
+                sd.nprobe = nprobe;
+                sd.ivf_probes_out = probes_out;
+                rs = sweep_stage(sd, st, path, so, &st->hit_count, kErrHitOverflow, false, sms, stimer, s, ar);
                 if (rs != BM_OK) return rs;
                 rs = read_state(st, hs, h, s);
                 if (rs != BM_OK) return rs;
@@ -650,7 +641,7 @@ bm_status bm_range_query(const float* X, int64_t n, int32_t d, const float* Q, i
         stats->band_pairs = (int64_t)band;
         stats->ms_total = tm.ms(0, 1);
         stats->band_delta = delta;
-        stats->path = opt.path;
+        stats->path = path;
         stats->ms_sweep = stimer.ms;
         stats->sweep_launches = stimer.launches;
         stats->kernel_launches = g_kernel_launches - launches0;
@@ -658,25 +649,27 @@ bm_status bm_range_query(const float* X, int64_t n, int32_t d, const float* Q, i
     return BM_OK;
 }
 
-bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_options* opt_in, bm_graph* out) {
-    if (!out) return fail(BM_ERR_ARG, "out is NULL");
+
+}  // namespace
+}  // namespace bm
+
+namespace bm {
+namespace {
+
+// Ball Mapper of the points X (n x d): greedy landmarks (or the given fixed ones),
+// full-ball memberships, nerve edges.  With an inverted-file index the balls are
+// the index's conservative range sets (Sec. 5.3-5.4); otherwise they are exact.
+bm_status build_graph(const float* X, long long n, int d, float eps, const bm_options& opt, const IvfIndex* ivf,
+                      int nprobe, const int* fixed_lm, long long nL, bm_graph* out) {
     std::memset(out, 0, sizeof(*out));
-    bm_options opt;
-    bm_options_init(&opt);
-    if (opt_in) opt = *opt_in;
-    bm_status vs = validate_points(X, n, d, "X");
-    if (vs != BM_OK) return vs;
-    vs = validate_eps(eps);
-    if (vs != BM_OK) return vs;
-    vs = check_device(opt.path);
-    if (vs != BM_OK) return vs;
     int S = opt.batch;
     if (S == 0) S = 2048;
     if (S < 32 || S > 2048 || S % 32) return fail(BM_ERR_ARG, "batch must be a multiple of 32 in [32, 2048]");
     cudaStream_t s = (cudaStream_t)opt.stream;
     const bool host_io = opt.host_io != 0;
     const double eps2 = (double)eps * (double)eps;
-    const bool tc = opt.path == BM_PATH_TC_SPLIT3;
+    const bool tc = opt.path == BM_PATH_TC_SPLIT3 && ivf == nullptr;
+    const int path = ivf ? (int)BM_PATH_FP32 : opt.path;
     Timer tm(s);
     tm.mark();  // 0
     SweepTimer stimer(s);
@@ -689,7 +682,7 @@ bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_opt
     long long edge_pairs = 0;
     {
         Arena ar(&opt, s);
-        const float* dX = stage_input(X, n, d, host_io, ar, s, &rs);
+        const float* dX = ivf ? X : stage_input(X, n, d, host_io, ar, s, &rs);
         if (rs != BM_OK) return rs;
         int* landmarks = nullptr;
         long long* offsets = nullptr;
@@ -713,7 +706,13 @@ bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_opt
             Prepared px;
             rs = prepare(dX, n, d, eps2, false, tc, ar, &st->max_norm_bits, bad, s, px);
             if (rs != BM_OK) return rs;
-            TRY_CUDA(launch_delta(st, opt.path, d, px.d_pad, eps2, true, s));
+            // inverted-file mode: phi of the cell-ordered copy of the points for the scan
+            Prepared pperm;
+            if (ivf) {
+                rs = prepare(ivf->xperm, n, d, eps2, false, false, ar, &st->max_norm_bits, bad, s, pperm);
+                if (rs != BM_OK) return rs;
+            }
+            TRY_CUDA(launch_delta(st, path, d, px.d_pad, eps2, true, s));
             int hbad = 0;
             TRY_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
             TRY_CUDA(cudaStreamSynchronize(s));
@@ -724,19 +723,69 @@ bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_opt
             unsigned long long mem_cap = (unsigned long long)std::max<long long>(4 * n, 1LL << 20);
             HostState hs;
             unsigned long long* mem_keys = nullptr;
-            for (int attempt = 0; attempt < 6; ++attempt) {
-                bool retry = false;
-                TRY_CUDA(cudaMemsetAsync(st, 0, offsetof(DeviceState, max_norm_bits), s));
-                {
-                    const int s_first = S < 256 ? S : 256;   // the batch grows while candidates survive
-                    TRY_CUDA(cudaMemcpyAsync(&st->s_next, &s_first, sizeof(int), cudaMemcpyHostToDevice, s));
-                    TRY_CUDA(cudaStreamSynchronize(s));
-                }
-                rs = greedy_pass(px, eps2, opt.path, S, ar, s, st, hs, step_cap, mem_cap, &retry, &landmarks,
-                                 &mem_keys, fin, stimer);
+            if (fixed_lm) {
+                // fixed landmarks: their balls through the index, one scan of all rows
+                ALLOC(landmarks, int, std::max<long long>(nL, 1));
+                if (nL) TRY_CUDA(cudaMemcpyAsync(landmarks, fixed_lm, sizeof(int) * nL,
+                                                 host_io ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+                float* qx;
+                ALLOC(qx, float, std::max<long long>(nL, 1) * d);
+                TRY_CUDA(launch_gather_rows(dX, landmarks, nL, d, qx, s));
+                Prepared pq;
+                rs = prepare(qx, nL, d, eps2, true, false, ar, &st->max_norm_q_bits, bad, s, pq);
                 if (rs != BM_OK) return rs;
-                if (!retry) break;
-                if (attempt == 5) return fail(BM_ERR_CAPACITY, "greedy buffers kept overflowing");
+                const int sms = device_sm_count();
+                unsigned long long cap = (unsigned long long)std::max<long long>(4 * n, 1LL << 20);
+                for (int attempt = 0; attempt < 3; ++attempt) {
+                    SweepOut so;
+                    rs = alloc_sweep_out(ar, false, cap, sms, so);
+                    if (rs != BM_OK) return rs;
+                    SweepDesc sd;
+                    sd.a = &pq;
+                    sd.b = &px;
+                    sd.a_rows_max = nL;
+                    sd.a_rows_dev = nullptr;
+                    sd.st = st;
+                    sd.check_done = false;
+                    sd.eps2 = eps2;
+                    sd.sink = HitSink();
+                    sd.sink.band_count = &st->band_pairs;
+                    sd.sink.pair_count = &st->tile_pairs;
+                    sd.ivf = ivf;
+                    sd.ivf_phi_perm = pperm.phi;
+                    sd.nprobe = nprobe;
+                    rs = sweep_stage(sd, st, path, so, &st->mem_count, kErrHitOverflow, false, sms, stimer, s, ar);
+                    if (rs != BM_OK) return rs;
+                    rs = read_state(st, hs, fin, s);
+                    if (rs != BM_OK) return rs;
+                    stimer.collect();
+                    const bool overflow = (fin.error & kErrHitOverflow) != 0 || fin.mem_count > cap || fin.band_n > cap;
+                    mem_keys = so.keys;
+                    release_sweep_out(ar, so, !overflow);
+                    if (!overflow) break;
+                    if (attempt == 2) return fail(BM_ERR_CAPACITY, "membership buffer kept overflowing");
+                    cap = std::max<unsigned long long>(2 * cap, std::max(fin.mem_count, fin.band_n) * 5 / 4 + 1024);
+                    TRY_CUDA(cudaMemsetAsync(&st->error, 0, sizeof(int), s));
+                    TRY_CUDA(cudaMemsetAsync(&st->band_n, 0, sizeof(unsigned long long), s));
+                    TRY_CUDA(cudaMemsetAsync(&st->mem_count, 0, sizeof(unsigned long long), s));
+                }
+                fin.n_landmarks = (int)nL;
+                ar.release(qx);
+            } else {
+                for (int attempt = 0; attempt < 6; ++attempt) {
+                    bool retry = false;
+                    TRY_CUDA(cudaMemsetAsync(st, 0, offsetof(DeviceState, max_norm_bits), s));
+                    {
+                        const int s_first = S < 256 ? S : 256;   // the batch grows while candidates survive
+                        TRY_CUDA(cudaMemcpyAsync(&st->s_next, &s_first, sizeof(int), cudaMemcpyHostToDevice, s));
+                        TRY_CUDA(cudaStreamSynchronize(s));
+                    }
+                    rs = greedy_pass(px, eps2, path, S, ar, s, st, hs, step_cap, mem_cap, &retry, &landmarks,
+                                     &mem_keys, fin, stimer, ivf, ivf ? pperm.phi : nullptr, nprobe);
+                    if (rs != BM_OK) return rs;
+                    if (!retry) break;
+                    if (attempt == 5) return fail(BM_ERR_CAPACITY, "greedy buffers kept overflowing");
+                }
             }
             tm.mark();  // 2: greedy (with memberships) done
             L = fin.n_landmarks;
@@ -807,12 +856,296 @@ bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_opt
     g.stats.ms_edges = tm.ms(3, 4);
     g.stats.ms_total = tm.ms(0, 5);
     g.stats.band_delta = fin.delta;
-    g.stats.path = opt.path;
+    g.stats.path = path;
     g.stats.ms_sweep = stimer.ms;
     g.stats.sweep_launches = stimer.launches;
     g.stats.kernel_launches = g_kernel_launches - launches0;
     *out = g;
     return BM_OK;
+}
+
+
+}  // namespace
+}  // namespace bm
+
+extern "C" {
+
+void bm_options_init(bm_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->path = BM_PATH_TC_SPLIT3;
+}
+
+const char* bm_status_string(bm_status s) {
+    switch (s) {
+        case BM_OK: return "ok";
+        case BM_ERR_ARG: return "invalid argument";
+        case BM_ERR_CUDA: return "CUDA error";
+        case BM_ERR_NOMEM: return "out of memory";
+        case BM_ERR_CAPACITY: return "capacity exceeded";
+        case BM_ERR_TIMEOUT: return "device wait timed out";
+        case BM_ERR_UNSUPPORTED: return "unsupported device";
+    }
+    return "unknown status";
+}
+
+const char* bm_last_error(void) { return g_last_error.c_str(); }
+
+int32_t bm_version(void) { return 100; }
+
+void bm_csr_free(bm_csr* csr, const bm_options* opt) {
+    if (!csr) return;
+    if (csr->on_host) {
+        std::free(csr->offsets);
+        std::free(csr->ids);
+    } else {
+        cudaStream_t s = opt ? (cudaStream_t)opt->stream : nullptr;
+        device_free(opt, s, csr->offsets);
+        device_free(opt, s, csr->ids);
+    }
+    std::memset(csr, 0, sizeof(*csr));
+}
+
+void bm_graph_free(bm_graph* g, const bm_options* opt) {
+    if (!g) return;
+    if (g->on_host) {
+        std::free(g->landmarks);
+        std::free(g->edges);
+    } else {
+        cudaStream_t s = opt ? (cudaStream_t)opt->stream : nullptr;
+        device_free(opt, s, g->landmarks);
+        device_free(opt, s, g->edges);
+    }
+    bm_csr_free(&g->members, opt);
+    std::memset(g, 0, sizeof(*g));
+}
+
+bm_status bm_range_query(const float* X, int64_t n, int32_t d, const float* Q, int64_t m, float eps,
+                         const bm_options* opt_in, bm_csr* out, bm_stats* stats) {
+    if (!out) return fail(BM_ERR_ARG, "out is NULL");
+    std::memset(out, 0, sizeof(*out));
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    bm_options opt;
+    bm_options_init(&opt);
+    if (opt_in) opt = *opt_in;
+    bm_status vs = validate_points(X, n, d, "X");
+    if (vs != BM_OK) return vs;
+    vs = validate_points(Q, m, d, "Q");
+    if (vs != BM_OK) return vs;
+    vs = validate_eps(eps);
+    if (vs != BM_OK) return vs;
+    vs = check_device(opt.path);
+    if (vs != BM_OK) return vs;
+    return range_core(X, n, d, Q, m, eps, opt, nullptr, 0, nullptr, out, stats);
+}
+
+bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_options* opt_in, bm_graph* out) {
+    if (!out) return fail(BM_ERR_ARG, "out is NULL");
+    std::memset(out, 0, sizeof(*out));
+    bm_options opt;
+    bm_options_init(&opt);
+    if (opt_in) opt = *opt_in;
+    bm_status vs = validate_points(X, n, d, "X");
+    if (vs != BM_OK) return vs;
+    vs = validate_eps(eps);
+    if (vs != BM_OK) return vs;
+    vs = check_device(opt.path);
+    if (vs != BM_OK) return vs;
+    return build_graph(X, n, d, eps, opt, nullptr, 0, nullptr, 0, out);
+}
+
+// ------------------------------------------------------------------ inverted file
+struct bm_ivf {
+    bm::IvfIndex ix;
+};
+
+namespace {
+
+// Buffers that live as long as the index: the caller's allocator, else cudaMallocAsync.
+void* persistent_alloc(const bm_options& opt, size_t bytes, std::vector<void*>& held) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    void* p = nullptr;
+    if (opt.alloc) p = opt.alloc(bytes, opt.stream, opt.alloc_ctx);
+    else if (cudaMallocAsync(&p, bytes, (cudaStream_t)opt.stream) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) held.push_back(p);
+    return p;
+}
+
+void free_index(bm_ivf* h) {
+    if (!h) return;
+    IvfIndex& ix = h->ix;
+    void* bufs[] = {ix.centroids, ix.cnorm, ix.cell_off, ix.cell_ids, ix.cell_of, ix.xperm, ix.xnorm, ix.owned_x};
+    for (void* b : bufs) device_free(&ix.opt, (cudaStream_t)ix.opt.stream, b);
+    delete h;
+}
+
+// splitmix64 (Steele, Lea, Flood 2014): the seeded stream of the k-means sample.
+uint64_t splitmix64(uint64_t& x) {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+}  // namespace
+
+bm_status bm_ivf_train(const float* X, int64_t n, int32_t d, int32_t nlist, int32_t iters, int64_t sample,
+                       uint64_t seed, const bm_options* opt_in, bm_ivf** out) {
+    if (!out) return fail(BM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    bm_options opt;
+    bm_options_init(&opt);
+    if (opt_in) opt = *opt_in;
+    bm_status vs = validate_points(X, n, d, "X");
+    if (vs != BM_OK) return vs;
+    if (n < 1) return fail(BM_ERR_ARG, "the index needs at least one point");
+    if (nlist < 1 || nlist > 4096 || nlist > n) return fail(BM_ERR_ARG, "nlist must be in [1, min(n, 4096)]");
+    if (iters < 0 || iters > 1000) return fail(BM_ERR_ARG, "iters must be in [0, 1000]");
+    if (sample == 0) sample = std::min<int64_t>(n, 262144);
+    if (sample < nlist || sample > n) return fail(BM_ERR_ARG, "sample must be in [nlist, n]");
+    vs = check_device(BM_PATH_FP32);
+    if (vs != BM_OK) return vs;
+    cudaStream_t s = (cudaStream_t)opt.stream;
+    bm_ivf* h = new (std::nothrow) bm_ivf;
+    if (!h) return fail(BM_ERR_NOMEM, "index handle");
+    IvfIndex& ix = h->ix;
+    ix.n = n;
+    ix.d = d;
+    ix.nlist = nlist;
+    ix.opt = opt;
+    ix.opt.host_io = 0;
+    std::vector<void*> held;
+    auto bail = [&](bm_status st, const std::string& msg) {
+        free_index(h);
+        return fail(st, msg);
+    };
+#define PALLOC(ptr, type, count)                                                                  \
+    do {                                                                                          \
+        ptr = (type*)persistent_alloc(ix.opt, sizeof(type) * (size_t)(count), held);              \
+        if (!ptr) return bail(BM_ERR_NOMEM, "allocation of the index's " #ptr " failed");          \
+    } while (0)
+#define PTRY(expr)                                                                                \
+    do {                                                                                          \
+        cudaError_t e__ = (expr);                                                                 \
+        if (e__ != cudaSuccess) {                                                                 \
+            cudaGetLastError();                                                                   \
+            return bail(BM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e__));         \
+        }                                                                                         \
+    } while (0)
+    {
+        Arena ar(&opt, s);
+        if (opt.host_io) {
+            PALLOC(ix.owned_x, float, n * d);
+            PTRY(cudaMemcpyAsync(ix.owned_x, X, sizeof(float) * n * d, cudaMemcpyHostToDevice, s));
+            ix.X = ix.owned_x;
+        } else {
+            ix.X = X;
+        }
+        // seeded sample: the first `sample` positions of a Fisher-Yates shuffle of 0..n-1;
+        // its first nlist points initialise the centroids
+        std::vector<int> perm((size_t)n);
+        for (int64_t i = 0; i < n; ++i) perm[(size_t)i] = (int)i;
+        uint64_t st64 = seed;
+        for (int64_t i = 0; i < sample; ++i) {
+            const int64_t j = i + (int64_t)(splitmix64(st64) % (uint64_t)(n - i));
+            std::swap(perm[(size_t)i], perm[(size_t)j]);
+        }
+        int* dsample = (int*)ar.get(sizeof(int) * (size_t)sample);
+        if (!dsample) return bail(BM_ERR_NOMEM, "sample ids");
+        PTRY(cudaMemcpyAsync(dsample, perm.data(), sizeof(int) * (size_t)sample, cudaMemcpyHostToDevice, s));
+        PALLOC(ix.xnorm, float, n);
+        PTRY(launch_row_norms(ix.X, n, d, ix.xnorm, s));
+        PALLOC(ix.centroids, float, (long long)nlist * d);
+        PALLOC(ix.cnorm, float, nlist);
+        PTRY(launch_gather_rows(ix.X, dsample, nlist, d, ix.centroids, s));
+        const size_t big = (size_t)std::max<int64_t>(n, sample);
+        unsigned long long* best = (unsigned long long*)ar.get(sizeof(unsigned long long) * big);
+        unsigned long long* keys = (unsigned long long*)ar.get(sizeof(unsigned long long) * big);
+        unsigned long long* tmp = (unsigned long long*)ar.get(sizeof(unsigned long long) * big);
+        long long* moff = (long long*)ar.get(sizeof(long long) * (nlist + 1));
+        int* mids = (int*)ar.get(sizeof(int) * (size_t)sample);
+        if (!best || !keys || !tmp || !moff || !mids) return bail(BM_ERR_NOMEM, "k-means scratch");
+        const std::vector<int> shifts = digit_shifts(bits_for(n - 1), bits_for(nlist - 1));
+        for (int it = 0; it < iters; ++it) {   // Lloyd iterations on the sample
+            PTRY(launch_row_norms(ix.centroids, nlist, d, ix.cnorm, s));
+            PTRY(launch_nearest_centroid(ix.X, dsample, sample, ix.xnorm, ix.centroids, ix.cnorm, nlist, d, best, s));
+            PTRY(launch_unpack_cells(best, dsample, sample, nullptr, keys, s));
+            unsigned long long* sorted = nullptr;
+            PTRY(radix_sort_u64(keys, tmp, sample, shifts, ar, s, &sorted));
+            PTRY(launch_csr_from_sorted(sorted, sample, nlist, moff, mids, s));
+            PTRY(launch_cell_means(ix.X, moff, mids, nlist, d, ix.centroids, s));
+        }
+        // every point joins its nearest centroid; cells in point order
+        PTRY(launch_row_norms(ix.centroids, nlist, d, ix.cnorm, s));
+        PTRY(launch_nearest_centroid(ix.X, nullptr, n, ix.xnorm, ix.centroids, ix.cnorm, nlist, d, best, s));
+        PALLOC(ix.cell_of, int, n);
+        PTRY(launch_unpack_cells(best, nullptr, n, ix.cell_of, keys, s));
+        unsigned long long* sorted = nullptr;
+        PTRY(radix_sort_u64(keys, tmp, n, shifts, ar, s, &sorted));
+        PALLOC(ix.cell_off, long long, nlist + 1);
+        PALLOC(ix.cell_ids, int, n);
+        PTRY(launch_csr_from_sorted(sorted, n, nlist, ix.cell_off, ix.cell_ids, s));
+        PALLOC(ix.xperm, float, n * d);
+        PTRY(launch_gather_rows(ix.X, ix.cell_ids, n, d, ix.xperm, s));
+        PTRY(cudaStreamSynchronize(s));
+    }
+#undef PALLOC
+#undef PTRY
+    *out = h;
+    return BM_OK;
+}
+
+void bm_ivf_free(bm_ivf* idx) { free_index(idx); }
+
+bm_status bm_ivf_info(const bm_ivf* idx, int64_t* n, int32_t* d, int32_t* nlist, const int32_t** cell_of,
+                      const float** centroids) {
+    if (!idx) return fail(BM_ERR_ARG, "index is NULL");
+    if (n) *n = idx->ix.n;
+    if (d) *d = idx->ix.d;
+    if (nlist) *nlist = idx->ix.nlist;
+    if (cell_of) *cell_of = idx->ix.cell_of;
+    if (centroids) *centroids = idx->ix.centroids;
+    return BM_OK;
+}
+
+bm_status bm_ivf_range_query(const bm_ivf* idx, const float* Q, int64_t m, float eps, int32_t nprobe,
+                             const bm_options* opt_in, bm_csr* out, int32_t* probes, bm_stats* stats) {
+    if (!out) return fail(BM_ERR_ARG, "out is NULL");
+    std::memset(out, 0, sizeof(*out));
+    if (!idx) return fail(BM_ERR_ARG, "index is NULL");
+    bm_options opt;
+    bm_options_init(&opt);
+    if (opt_in) opt = *opt_in;
+    const IvfIndex& ix = idx->ix;
+    bm_status vs = validate_points(Q, m, ix.d, "Q");
+    if (vs != BM_OK) return vs;
+    vs = validate_eps(eps);
+    if (vs != BM_OK) return vs;
+    if (nprobe < 1 || nprobe > ix.nlist) return fail(BM_ERR_ARG, "nprobe must be in [1, nlist]");
+    vs = check_device(BM_PATH_FP32);
+    if (vs != BM_OK) return vs;
+    return range_core(ix.X, ix.n, ix.d, Q, m, eps, opt, &ix, nprobe, probes, out, stats);
+}
+
+bm_status bm_build_ivf(const bm_ivf* idx, float eps, int32_t nprobe, const int32_t* landmarks, int64_t n_landmarks,
+                       const bm_options* opt_in, bm_graph* out) {
+    if (!out) return fail(BM_ERR_ARG, "out is NULL");
+    std::memset(out, 0, sizeof(*out));
+    if (!idx) return fail(BM_ERR_ARG, "index is NULL");
+    bm_options opt;
+    bm_options_init(&opt);
+    if (opt_in) opt = *opt_in;
+    const IvfIndex& ix = idx->ix;
+    bm_status vs = validate_eps(eps);
+    if (vs != BM_OK) return vs;
+    if (nprobe < 1 || nprobe > ix.nlist) return fail(BM_ERR_ARG, "nprobe must be in [1, nlist]");
+    if (landmarks && (n_landmarks < 0 || n_landmarks > ix.n)) return fail(BM_ERR_ARG, "n_landmarks out of range");
+    vs = check_device(BM_PATH_FP32);
+    if (vs != BM_OK) return vs;
+    return build_graph(ix.X, ix.n, ix.d, eps, opt, &ix, nprobe, landmarks, landmarks ? n_landmarks : 0, out);
 }
 
 }  // extern "C"

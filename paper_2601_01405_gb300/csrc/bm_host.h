@@ -61,6 +61,8 @@ cudaError_t launch_prep(const float* x, long long rows, int d, double eps2, bool
 cudaError_t launch_delta(DeviceState* st, int path, int d, int d_pad, double eps2, bool same_sets,
                          cudaStream_t s);
 
+struct IvfIndex;
+
 // tile_fp32.cu
 struct SweepDesc {
     const Prepared* a;           // query / candidate rows
@@ -71,6 +73,11 @@ struct SweepDesc {
     bool check_done;             // skip work when st->done
     double eps2;
     HitSink sink;
+    // inverted-file mode: scan only the nprobe cells nearest to each row
+    const IvfIndex* ivf = nullptr;
+    const float* ivf_phi_perm = nullptr;
+    int nprobe = 0;
+    int* ivf_probes_out = nullptr;   // optional: where to leave each row's probed cells
 };
 cudaError_t launch_sweep_fp32(const SweepDesc& s, cudaStream_t stream);
 
@@ -121,6 +128,46 @@ cudaError_t radix_sort_u64(unsigned long long* keys, unsigned long long* tmp, lo
                            unsigned long long** result);
 int bits_for(long long v);  // bits needed to represent v (>= 0)
 std::vector<int> digit_shifts(int lo_bits, int hi_bits);  // 8-bit digit shifts covering [0,lo) and [32,32+hi)
+
+// ivf.cu: inverted-file index (Sec. 5.4 IndexIVFFlat-style cells) and its scan.
+struct IvfIndex {
+    long long n = 0;
+    int d = 0;
+    int nlist = 0;
+    const float* X = nullptr;          // the indexed points (device, row-major), by id
+    float* centroids = nullptr;        // nlist x d
+    float* cnorm = nullptr;            // nlist: ||c||^2 (float)
+    long long* cell_off = nullptr;     // nlist + 1
+    int* cell_ids = nullptr;           // n: point ids grouped by cell, ascending within a cell
+    int* cell_of = nullptr;            // n: cell of each point
+    float* xperm = nullptr;            // n x d: rows of X in cell order
+    float* xnorm = nullptr;            // n: ||x||^2 of the rows of X (by id, float)
+    bm_options opt;                    // allocator of the index's buffers
+    float* owned_x = nullptr;          // device copy of X when the index was built from host memory
+};
+
+// Nearest centroid per row (FP32 expansion ||x||^2 + ||c||^2 - 2 x.c, ties to the
+// lowest centroid id): best[r] = (float bits of the distance << 32) | centroid.
+cudaError_t launch_nearest_centroid(const float* rows, const int* row_ids, long long nrows, const float* rnorm,
+                                    const float* cent, const float* cnorm, int nlist, int d,
+                                    unsigned long long* best, cudaStream_t s);
+cudaError_t launch_row_norms(const float* x, long long rows, int d, float* out, cudaStream_t s);
+cudaError_t launch_cell_means(const float* rows, const long long* off, const int* members, int nlist, int d,
+                              float* cent, cudaStream_t s);
+cudaError_t launch_unpack_cells(const unsigned long long* best, const int* row_ids, long long n, int* cell_of,
+                                unsigned long long* keys, cudaStream_t s);
+cudaError_t launch_gather_rows(const float* x, const int* ids, long long rows, int d, float* out, cudaStream_t s);
+// top-nprobe centroids of each query row (direct FP32 distances, ties to the lowest id)
+cudaError_t launch_probe_select(const float* A, long long rows_max, const int* rows_dev, const IvfIndex& ix,
+                                int nprobe, int* probes, cudaStream_t s);
+// group (row, probe) pairs by cell: cq_off[nlist+1], cq_rows; tile_off[nlist+1] over 64 x 64 tiles
+cudaError_t launch_group_probes(const int* probes, long long rows_max, const int* rows_dev, int nprobe,
+                                const IvfIndex& ix, long long* cnt, long long* cq_off, int* cq_rows,
+                                long long* tile_off, Arena& ar, cudaStream_t s);
+// scan the probed cells: hits -> sink (global counters), band pairs -> sink.band_keys
+cudaError_t launch_ivf_scan(const float* A, const float* phiA, const IvfIndex& ix, const float* phi_perm,
+                            const long long* cq_off, const int* cq_rows, const long long* tile_off,
+                            const DeviceState* st, bool check_done, const HitSink& sink, cudaStream_t s);
 
 // recheck.cu: FP64 re-decision of the band pairs; confirmed hits are appended
 // to keys through *count (book: the greedy's candidate-conflict bookkeeping).

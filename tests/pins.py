@@ -205,3 +205,22 @@ def pin_paper():
     out = oracle.build(X, eps)
     assert out["landmarks"].size == g["landmarks"]
     assert out["edges"].shape[0] == g["edges"]
+
+
+def pin_masked():
+    """Verified range set over probed cells (Sec. 5.3): with every cell probed it is the
+    exact range set; in general it equals the exact set filtered by cell membership."""
+    X = W.isotropic(1500, 6, 10, seed=12)
+    Q = X[:40]
+    rng = np.random.default_rng(4)
+    cell = rng.integers(0, 12, X.shape[0]).astype(np.int32)
+    allp = np.tile(np.arange(12, dtype=np.int32), (Q.shape[0], 1))
+    o1, i1 = oracle.masked_range_query(X, Q, 2.0, cell, 12, allp)
+    o2, i2 = oracle.range_query(X, Q, 2.0)
+    assert np.array_equal(o1, o2) and np.array_equal(i1, i2)
+    probes = np.stack([rng.choice(12, 3, replace=False) for _ in range(Q.shape[0])]).astype(np.int32)
+    o3, i3 = oracle.masked_range_query(X, Q, 2.0, cell, 12, probes)
+    for j in range(Q.shape[0]):
+        full = i2[o2[j]:o2[j + 1]]
+        keep = full[np.isin(cell[full], probes[j])]
+        assert i3[o3[j]:o3[j + 1]].tolist() == keep.tolist()

@@ -23,12 +23,13 @@ MUTANTS = [
     ("greedy-covers-self-only", "< eps2) covered[y] = 1;", "< eps2) covered[y] = (y == x);", 1),
     ("edge-always", "if (a[p] == b[q]) return 1;", "if (a[p] != b[q]) return 1;", 1),
     ("edge-self-loop", "for (int64_t j = i + 1; j < L; ++j) {", "for (int64_t j = i; j < L; ++j) {", 1),
-    ("transposed-range-id", "ids[o++] = (int32_t)i;", "ids[o++] = (int32_t)j;", 1),
+    ("transposed-range-id", "ids[o++] = (int32_t)i;", "ids[o++] = (int32_t)j;", 2),
     ("over-pruned-edges", "4.0 * eps2", "1.0 * eps2", 1),
     ("kth-off-by-one", "kth_smallest(row, n, k - 1)", "kth_smallest(row, n, k)", 1),
     ("balltree-prune-sign", "if (dc - nd->radius > r", "if (dc + nd->radius > r", 1),
     ("balltree-radius-min", "if (s > r2) { r2 = s; pa = p; }", "if (s < r2) { r2 = s; pa = p; }", 1),
     ("balltree-leaf-closed", "t->d) < r2) {", "t->d) <= r2) {", 1),
+    ("masked-ignores-cells", "if (flag[cell_of[i]] && sqdist", "if ((flag[cell_of[i]] || 1) && sqdist", 2),
 ]
 # A wrong node centre is not listed: any centre paired with the radius measured
 # from it still bounds the node, so the range sets stay exact.
@@ -50,6 +51,7 @@ def _all_pins():
     pins.pin_knn_scipy(W.paper_gaussian_fp64(500, 6, seed=7), 20)
     pins.pin_range_scipy(W.paper_gaussian_fp64(800, 5, seed=8), W.paper_gaussian_fp64(800, 5, seed=8)[:50], 1.3)
     pins.pin_pair_sqdist(W.isotropic(300, 16, 10, seed=9))
+    pins.pin_masked()
 
 
 def test_unmutated_oracle_passes_all_pins():

@@ -70,6 +70,10 @@ def test_range_against_scipy():
     pins.pin_range_scipy(X, X[:200], 1.3)
 
 
+def test_masked_range_query():
+    pins.pin_masked()
+
+
 def test_pair_sqdist():
     pins.pin_pair_sqdist(W.isotropic(300, 16, 10, seed=9))
 
