@@ -132,6 +132,37 @@ BM_API bm_status bm_range_query(const float* X, int64_t n, int32_t d, const floa
 BM_API bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_options* opt,
                    bm_graph* out);
 
+/* One problem of a batched build: n x d float32 points (device memory; host
+ * memory with host_io) and its own eps. */
+typedef struct {
+    const float* X;
+    int64_t n;
+    int32_t d;
+    float eps;
+} bm_instance;
+
+/* Many independent Ball Mapper builds (each exactly bm_build's result: Sec. 2.2
+ * greedy, Sec. 2.3 memberships, Sec. 5.2 nerve) in one call.  The paper builds
+ * one complex at a time; this entry point exists to fill the GPU with many
+ * small problems.  The greedy loops of all instances run inside one CUDA graph
+ * launched once: a device-side WHILE loop per instance, the loops side by side,
+ * each iteration one greedy step that decides on the device whether another is
+ * needed.  Prep runs before the graph; CSR and nerve edges after it, per
+ * instance.  An instance whose step buffers overflow inside the graph is
+ * finished by the host-driven loop with larger buffers (same result).
+ *   inst:     count instances (count >= 0); each validated like bm_build.
+ *   opt:      stream, path, host_io, skip_edges, alloc/free as for bm_build;
+ *             batch = largest candidate batch per step (0 = 1024).
+ *   outs:     count graphs, caller-owned array; each filled like bm_build's out.
+ *             stats.ms_total of every instance is the time of the whole call,
+ *             stats.ms_greedy that of the graph launch.
+ *   statuses: optional, count entries: BM_OK, or the status of the instance
+ *             that failed.
+ * On error every outs[i] is zeroed (nothing leaks) and the first failing
+ * status is returned; bm_last_error names the instance. */
+BM_API bm_status bm_build_batched(const bm_instance* inst, int32_t count, const bm_options* opt, bm_graph* outs,
+                                  int32_t* statuses);
+
 /* ---- Inverted-file index: the paper's non-exhaustive approximate oracle (Sec. 5.4;
  * nprobe cells searched per query, Sec. 6.1).  Points are grouped into nlist
  * k-means cells; a query examines only the points of its nprobe nearest cells

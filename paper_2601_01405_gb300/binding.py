@@ -58,6 +58,10 @@ class bm_graph(ctypes.Structure):
                 ("reserved0", ctypes.c_int32), ("stats", bm_stats)]
 
 
+class bm_instance(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int32), ("eps", ctypes.c_float)]
+
+
 class BallMapperError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
@@ -120,6 +124,9 @@ def load(path: str = LIB_PATH):
         lib.bm_build_ivf.argtypes = [ctypes.c_void_p, ctypes.c_float, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
                                      ctypes.POINTER(bm_options), ctypes.POINTER(bm_graph)]
         lib.bm_build_ivf.restype = ctypes.c_int
+        lib.bm_build_batched.argtypes = [ctypes.POINTER(bm_instance), ctypes.c_int32, ctypes.POINTER(bm_options),
+                                         ctypes.POINTER(bm_graph), ctypes.POINTER(ctypes.c_int32)]
+        lib.bm_build_batched.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -287,6 +294,62 @@ def bm_build(X, eps: float, path: str = "tc", batch: int = 0, stream=None, skip_
             "ids": alloc.tensor(g.members.ids, nnz, torch.int32),
             "edges": alloc.tensor(g.edges, 2 * E, torch.int32).view(E, 2),
             "stats": g.stats.as_dict()}
+
+
+def bm_build_batched(instances, path: str = "tc", batch: int = 0, stream=None, skip_edges: bool = False):
+    """Many independent exact builds in one call; the greedy loops of all instances
+    run inside one CUDA graph.  instances: sequence of (X, eps), all CUDA tensors
+    (results as torch tensors) or all host arrays (results as numpy arrays).
+    Returns a list of dicts shaped like bm_build's."""
+    lib = load()
+    ins = [_as_input(X) for X, _ in instances]
+    hosts = {h for _, _, _, _, h in ins}
+    if len(hosts) > 1:
+        raise ValueError("instances must all be device tensors or all host arrays")
+    host = hosts.pop() if hosts else False
+    count = len(ins)
+    arr_in = (bm_instance * max(count, 1))()
+    for k, ((px, n, d, _, _), (_, eps)) in enumerate(zip(ins, instances)):
+        arr_in[k].X = px
+        arr_in[k].n = n
+        arr_in[k].d = d
+        arr_in[k].eps = float(eps)
+    outs = (bm_graph * max(count, 1))()
+    statuses = (ctypes.c_int32 * max(count, 1))()
+    if host:
+        opt = _options(lib, path, batch, stream, True, None, skip_edges)
+        _check(lib, lib.bm_build_batched(arr_in, count, ctypes.byref(opt), outs, statuses))
+
+        def arr(ptr, ctype, k):
+            return np.ctypeslib.as_array((ctype * max(k, 1)).from_address(ptr))[:k].copy()
+
+        res = []
+        try:
+            for g in outs[:count]:
+                L, nnz, E = g.n_landmarks, g.members.nnz, g.n_edges
+                res.append({"landmarks": arr(g.landmarks, ctypes.c_int32, L),
+                            "offsets": arr(g.members.offsets, ctypes.c_int64, L + 1),
+                            "ids": arr(g.members.ids, ctypes.c_int32, nnz),
+                            "edges": arr(g.edges, ctypes.c_int32, 2 * E).reshape(E, 2),
+                            "stats": g.stats.as_dict()})
+        finally:
+            for k in range(count):
+                lib.bm_graph_free(ctypes.byref(outs[k]), ctypes.byref(opt))
+        return res
+    import torch
+    dev = ins[0][3].device if count else torch.device("cuda", torch.cuda.current_device())
+    alloc = _TorchAllocator(dev)
+    opt = _options(lib, path, batch, stream or _current_stream(dev), False, alloc, skip_edges)
+    _check(lib, lib.bm_build_batched(arr_in, count, ctypes.byref(opt), outs, statuses))
+    res = []
+    for g in outs[:count]:
+        L, nnz, E = g.n_landmarks, g.members.nnz, g.n_edges
+        res.append({"landmarks": alloc.tensor(g.landmarks, L, torch.int32),
+                    "offsets": alloc.tensor(g.members.offsets, L + 1, torch.int64),
+                    "ids": alloc.tensor(g.members.ids, nnz, torch.int32),
+                    "edges": alloc.tensor(g.edges, 2 * E, torch.int32).view(E, 2),
+                    "stats": g.stats.as_dict()})
+    return res
 
 
 def version() -> int:

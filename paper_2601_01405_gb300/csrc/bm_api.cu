@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -261,11 +262,13 @@ struct SweepTimer {
     double ms = 0.0;
     long long launches = 0;
     cudaStream_t s;
+    bool on = true;   // off while a stream is being captured into a graph
     explicit SweepTimer(cudaStream_t st) : s(st) {}
     ~SweepTimer() {
         for (auto e : ev) cudaEventDestroy(e);
     }
     void mark() {
+        if (!on) return;
         if (used == ev.size()) {
             cudaEvent_t e;
             if (cudaEventCreate(&e) != cudaSuccess) {
@@ -380,15 +383,25 @@ bm_status read_state(const DeviceState* dst, HostState& hs, DeviceState& out, cu
 
 // The greedy + membership part of bm_build.  Returns BM_OK with *retry set when
 // a buffer was too small (capacities are updated for the next attempt).
-bm_status greedy_pass(const Prepared& pts, double eps2, int path, int S, Arena& ar, cudaStream_t s,
-                      DeviceState* st, HostState& hs, unsigned long long& step_cap, unsigned long long& mem_cap,
-                      bool* retry, int** landmarks_out, unsigned long long** mem_keys_out, DeviceState& final_state,
-                      SweepTimer& stimer, const IvfIndex* ivf, const float* phi_perm, int nprobe) {
-    *retry = false;
+// Buffers and sweep description of one greedy build.
+struct GreedyCtx {
+    GreedyBuffers g;
+    SweepOut so;
+    SweepDesc sd;
+    int S = 0, sms = 0, path = 0;
+    bool tc = false;
+};
+
+bm_status greedy_setup(const Prepared& pts, double eps2, int path, int S, Arena& ar, cudaStream_t s, DeviceState* st,
+                       unsigned long long step_cap, unsigned long long mem_cap, const IvfIndex* ivf,
+                       const float* phi_perm, int nprobe, GreedyCtx& c) {
     const long long n = pts.rows;
     const int d = pts.d;
     const bool tc = path == BM_PATH_TC_SPLIT3;
-    GreedyBuffers g;
+    c.S = S;
+    c.path = path;
+    c.tc = tc;
+    GreedyBuffers& g = c.g;
     g.st = st;
     const long long words_n = (n + 31) / 32;
     const int words = S / 32;
@@ -418,16 +431,16 @@ bm_status greedy_pass(const Prepared& pts, double eps2, int path, int S, Arena& 
         TRY_CUDA(cudaMemsetAsync(g.cand.lo, 0, sizeof(__nv_bfloat16) * S * pts.d_pad, s));
         TRY_CUDA(cudaMemsetAsync(g.cand.aug, 0, sizeof(__nv_bfloat16) * S * 16, s));
     }
-    const int sms = device_sm_count();
-    SweepOut so;
-    bm_status ars = alloc_sweep_out(ar, tc, step_cap, sms, so);
+    c.sms = device_sm_count();
+    bm_status ars = alloc_sweep_out(ar, tc, step_cap, c.sms, c.so);
     if (ars != BM_OK) return ars;
-    g.step_keys = so.keys;
+    g.step_keys = c.so.keys;
     g.step_cap = step_cap;
     ALLOC(g.mem_keys, unsigned long long, mem_cap);
     g.mem_cap = mem_cap;
 
-    SweepDesc sd;
+    SweepDesc& sd = c.sd;
+    sd = SweepDesc();
     sd.a = &g.cand;
     sd.b = &pts;
     sd.a_rows_max = S;
@@ -444,35 +457,57 @@ bm_status greedy_pass(const Prepared& pts, double eps2, int path, int S, Arena& 
     sd.ivf = ivf;
     sd.ivf_phi_perm = phi_perm;
     sd.nprobe = nprobe;
+    return BM_OK;
+}
 
-    DeviceState h;
+// One greedy step: select, gather, sweep (+ compaction and recheck), resolve, apply.
+// Only kernel launches, so the step can also be captured into a graph body.
+bm_status greedy_enqueue_step(GreedyCtx& c, const Prepared& pts, Arena& ar, SweepTimer& stimer, cudaStream_t s) {
+    DeviceState* st = c.g.st;
+    TRY_CUDA(launch_greedy_select(c.g, pts, c.S, c.tc, s));
+    TRY_CUDA(launch_greedy_gather(c.g, pts, c.S, c.tc, s));
+    bm_status rs = sweep_stage(c.sd, st, c.path, c.so, &st->step_hits, kErrStepOverflow, true, c.sms, stimer, s, ar);
+    if (rs != BM_OK) return rs;
+    TRY_CUDA(launch_greedy_resolve(c.g, c.S, s));
+    TRY_CUDA(launch_greedy_apply(c.g, s));
+    return BM_OK;
+}
+
+// Host-driven greedy loop: enqueue steps in growing chunks, read the state, grow
+// an overflowing buffer and redo the step, until no uncovered point remains.
+// With resume set the first state read comes before any new step (the steps so
+// far ran elsewhere, e.g. in a graph).
+bm_status greedy_drive(GreedyCtx& c, const Prepared& pts, Arena& ar, cudaStream_t s, HostState& hs,
+                       unsigned long long& step_cap, unsigned long long& mem_cap, DeviceState& h,
+                       SweepTimer& stimer, bool resume) {
+    GreedyBuffers& g = c.g;
+    DeviceState* st = g.st;
     int chunk = 2;
     int regrows = 0;
+    bool enqueue = !resume;
     while (true) {
-        for (int i = 0; i < chunk; ++i) {
-            TRY_CUDA(launch_greedy_select(g, pts, S, tc, s));
-            TRY_CUDA(launch_greedy_gather(g, pts, S, tc, s));
-            bm_status rs = sweep_stage(sd, st, path, so, &st->step_hits, kErrStepOverflow, true, sms, stimer, s, ar);
+        for (int i = 0; enqueue && i < chunk; ++i) {
+            bm_status rs = greedy_enqueue_step(c, pts, ar, stimer, s);
             if (rs != BM_OK) return rs;
-            TRY_CUDA(launch_greedy_resolve(g, S, s));
-            TRY_CUDA(launch_greedy_apply(g, s));
         }
+        enqueue = true;
         bm_status rs = read_state(st, hs, h, s);
         if (rs != BM_OK) return rs;
         stimer.collect();
         if (h.error & kErrTimeout) return fail(BM_ERR_TIMEOUT, "a bounded device wait expired in the distance tiles");
+        if (h.error & kErrLoopLimit) return fail(BM_ERR_CUDA, "device-side greedy loop passed its iteration bound");
         if (h.error & (kErrStepOverflow | kErrMemberOverflow)) {
             // a step stopped before committing anything: grow the buffer and redo it
             if (++regrows > 64) return fail(BM_ERR_CAPACITY, "greedy buffers kept overflowing");
             if (h.error & kErrStepOverflow) {
                 const unsigned long long need =
-                    std::max<unsigned long long>(h.max_seg * (unsigned long long)sms, std::max(h.step_hits, h.band_n)) *
-                    3 / 2;
+                    std::max<unsigned long long>(h.max_seg * (unsigned long long)c.sms,
+                                                 std::max(h.step_hits, h.band_n)) * 3 / 2;
                 step_cap = std::max<unsigned long long>(need, 2 * step_cap);
-                release_sweep_out(ar, so, false);
-                bm_status rs2 = alloc_sweep_out(ar, tc, step_cap, sms, so);
+                release_sweep_out(ar, c.so, false);
+                bm_status rs2 = alloc_sweep_out(ar, c.tc, step_cap, c.sms, c.so);
                 if (rs2 != BM_OK) return rs2;
-                g.step_keys = so.keys;
+                g.step_keys = c.so.keys;
                 g.step_cap = step_cap;
             }
             if (h.error & kErrMemberOverflow) {
@@ -492,10 +527,22 @@ bm_status greedy_pass(const Prepared& pts, double eps2, int path, int S, Arena& 
         if (h.done) break;
         chunk = std::min(chunk * 2, 64);
     }
-    release_sweep_out(ar, so, false);
-    *landmarks_out = g.landmarks;
-    *mem_keys_out = g.mem_keys;
-    final_state = h;
+    return BM_OK;
+}
+
+bm_status greedy_pass(const Prepared& pts, double eps2, int path, int S, Arena& ar, cudaStream_t s,
+                      DeviceState* st, HostState& hs, unsigned long long& step_cap, unsigned long long& mem_cap,
+                      bool* retry, int** landmarks_out, unsigned long long** mem_keys_out, DeviceState& final_state,
+                      SweepTimer& stimer, const IvfIndex* ivf, const float* phi_perm, int nprobe) {
+    *retry = false;
+    GreedyCtx c;
+    bm_status rs = greedy_setup(pts, eps2, path, S, ar, s, st, step_cap, mem_cap, ivf, phi_perm, nprobe, c);
+    if (rs != BM_OK) return rs;
+    rs = greedy_drive(c, pts, ar, s, hs, step_cap, mem_cap, final_state, stimer, false);
+    if (rs != BM_OK) return rs;
+    release_sweep_out(ar, c.so, false);
+    *landmarks_out = c.g.landmarks;
+    *mem_keys_out = c.g.mem_keys;
     return BM_OK;
 }
 
@@ -656,6 +703,76 @@ bm_status range_core(const float* X, long long n, int d, const float* Q, long lo
 namespace bm {
 namespace {
 
+// Memberships (ordinal << 32 | point keys) to the CSR of full balls, then the
+// nerve edges (skipped with opt.skip_edges).  mem_keys is released.
+bm_status members_and_edges(Arena& ar, cudaStream_t s, const bm_options& opt, long long n, long long L,
+                            long long nnz, unsigned long long* mem_keys, Timer* tm, long long** offsets_out,
+                            int** ids_out, int** edges_out, long long* E_out, long long* edge_pairs) {
+    unsigned long long* tmp;
+    ALLOC(tmp, unsigned long long, std::max<long long>(nnz, 1));
+    unsigned long long* sorted = nullptr;
+    TRY_CUDA(radix_sort_u64(mem_keys, tmp, nnz, digit_shifts(bits_for(n - 1), bits_for(L - 1)), ar, s, &sorted));
+    long long* offsets;
+    int* ids;
+    ALLOC(offsets, long long, L + 1);
+    ALLOC(ids, int, std::max<long long>(nnz, 1));
+    TRY_CUDA(launch_csr_from_sorted(sorted, nnz, L, offsets, ids, s));
+    if (tm) tm->mark();  // CSR done
+    Failure f{BM_OK, ""};
+    EdgeResult er;
+    if (!opt.skip_edges && !build_edges(sorted, nnz, n, L, ar, s, er, f)) return fail(f.status, f.msg);
+    int* edges = er.edges;
+    if (!edges) ALLOC(edges, int, 2);
+    if (tm) tm->mark();  // edges done
+    ar.release(tmp);
+    ar.release(mem_keys);
+    *offsets_out = offsets;
+    *ids_out = ids;
+    *edges_out = edges;
+    *E_out = er.n_edges;
+    *edge_pairs = er.pairs;
+    return BM_OK;
+}
+
+// Move the result arrays into *g: copied to malloc'd host buffers (host_io) or
+// handed over as device buffers that the caller frees with bm_graph_free.
+bm_status hand_over(Arena& ar, cudaStream_t s, bool host_io, int* landmarks, long long* offsets, int* ids,
+                    int* edges, long long L, long long nnz, long long E, bm_graph& g) {
+    if (host_io) {
+        void *hl = nullptr, *ho = nullptr, *hi = nullptr, *he = nullptr;
+        bool ok = to_host(&hl, landmarks, sizeof(int) * std::max<long long>(L, 1), s) &&
+                  to_host(&ho, offsets, sizeof(long long) * (L + 1), s) &&
+                  to_host(&hi, ids, sizeof(int) * std::max<long long>(nnz, 1), s) &&
+                  to_host(&he, edges, sizeof(int) * 2 * std::max<long long>(E, 1), s);
+        if (ok && cudaStreamSynchronize(s) != cudaSuccess) ok = false;
+        if (!ok) {
+            std::free(hl); std::free(ho); std::free(hi); std::free(he);
+            cudaGetLastError();
+            return fail(BM_ERR_CUDA, "device to host copy of the result failed");
+        }
+        g.landmarks = (int*)hl;
+        g.members.offsets = (int64_t*)ho;
+        g.members.ids = (int*)hi;
+        g.edges = (int*)he;
+        g.on_host = 1;
+        g.members.on_host = 1;
+    } else {
+        ar.take(landmarks);
+        ar.take(offsets);
+        ar.take(ids);
+        ar.take(edges);
+        g.landmarks = landmarks;
+        g.members.offsets = (int64_t*)offsets;
+        g.members.ids = ids;
+        g.edges = edges;
+    }
+    g.n_landmarks = L;
+    g.members.rows = L;
+    g.members.nnz = nnz;
+    g.n_edges = E;
+    return BM_OK;
+}
+
 // Ball Mapper of the points X (n x d): greedy landmarks (or the given fixed ones),
 // full-ball memberships, nerve edges.  With an inverted-file index the balls are
 // the index's conservative range sets (Sec. 5.3-5.4); otherwise they are exact.
@@ -790,58 +907,11 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
             tm.mark();  // 2: greedy (with memberships) done
             L = fin.n_landmarks;
             nnz = (long long)fin.mem_count;
-            unsigned long long* tmp;
-            ALLOC(tmp, unsigned long long, std::max<long long>(nnz, 1));
-            unsigned long long* sorted = nullptr;
-            TRY_CUDA(radix_sort_u64(mem_keys, tmp, nnz, digit_shifts(bits_for(n - 1), bits_for(L - 1)), ar, s,
-                                    &sorted));
-            ALLOC(offsets, long long, L + 1);
-            ALLOC(ids, int, std::max<long long>(nnz, 1));
-            TRY_CUDA(launch_csr_from_sorted(sorted, nnz, L, offsets, ids, s));
-            tm.mark();  // 3: CSR done
-            Failure f{BM_OK, ""};
-            EdgeResult er;
-            if (!opt.skip_edges && !build_edges(sorted, nnz, n, L, ar, s, er, f)) return fail(f.status, f.msg);
-            edges = er.edges;
-            E = er.n_edges;
-            edge_pairs = er.pairs;
-            if (!edges) ALLOC(edges, int, 2);
-            tm.mark();  // 4: edges done
-            ar.release(tmp);
-            ar.release(mem_keys);
+            rs = members_and_edges(ar, s, opt, n, L, nnz, mem_keys, &tm, &offsets, &ids, &edges, &E, &edge_pairs);
+            if (rs != BM_OK) return rs;
         }
-        if (host_io) {
-            void *hl = nullptr, *ho = nullptr, *hi = nullptr, *he = nullptr;
-            bool ok = to_host(&hl, landmarks, sizeof(int) * std::max<long long>(L, 1), s) &&
-                      to_host(&ho, offsets, sizeof(long long) * (L + 1), s) &&
-                      to_host(&hi, ids, sizeof(int) * std::max<long long>(nnz, 1), s) &&
-                      to_host(&he, edges, sizeof(int) * 2 * std::max<long long>(E, 1), s);
-            if (ok && cudaStreamSynchronize(s) != cudaSuccess) ok = false;
-            if (!ok) {
-                std::free(hl); std::free(ho); std::free(hi); std::free(he);
-                cudaGetLastError();
-                return fail(BM_ERR_CUDA, "device to host copy of the result failed");
-            }
-            g.landmarks = (int*)hl;
-            g.members.offsets = (int64_t*)ho;
-            g.members.ids = (int*)hi;
-            g.edges = (int*)he;
-            g.on_host = 1;
-            g.members.on_host = 1;
-        } else {
-            ar.take(landmarks);
-            ar.take(offsets);
-            ar.take(ids);
-            ar.take(edges);
-            g.landmarks = landmarks;
-            g.members.offsets = (int64_t*)offsets;
-            g.members.ids = ids;
-            g.edges = edges;
-        }
-        g.n_landmarks = L;
-        g.members.rows = L;
-        g.members.nnz = nnz;
-        g.n_edges = E;
+        rs = hand_over(ar, s, host_io, landmarks, offsets, ids, edges, L, nnz, E, g);
+        if (rs != BM_OK) return rs;
     }
     tm.mark();  // 5
     g.stats.distance_evals = (int64_t)g.n_landmarks * n;
@@ -864,6 +934,229 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
     return BM_OK;
 }
 
+
+// ---- Batched builds: the greedy loops of many instances in one CUDA graph.
+
+struct BatchItem {
+    std::unique_ptr<Arena> ar;
+    long long n = 0;
+    int d = 0;
+    double eps2 = 0.0;
+    DeviceState* st = nullptr;
+    Prepared px;
+    GreedyCtx gc;
+    unsigned long long step_cap = 0, mem_cap = 0;
+    long long body_kernels = 0;
+};
+
+struct GraphGuard {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cs = nullptr;
+    ~GraphGuard() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cs) cudaStreamDestroy(cs);
+    }
+};
+
+// Stage and prepare one instance's points; its DeviceState is sts[i] (zeroed).
+bm_status batch_prep(BatchItem& it, const bm_instance& in, const bm_options& opt, bool tc, int path,
+                     DeviceState* st, int* bad, cudaStream_t s) {
+    Arena& ar = *it.ar;
+    bm_status rs = BM_OK;
+    const float* dX = stage_input(in.X, in.n, in.d, opt.host_io != 0, ar, s, &rs);
+    if (rs != BM_OK) return rs;
+    it.st = st;
+    rs = prepare(dX, in.n, in.d, it.eps2, false, tc, ar, &st->max_norm_bits, bad, s, it.px);
+    if (rs != BM_OK) return rs;
+    TRY_CUDA(launch_delta(st, path, in.d, it.px.d_pad, it.eps2, true, s));
+    return BM_OK;
+}
+
+// Capture one greedy step plus the loop condition into the body of a WHILE node.
+bm_status batch_capture(BatchItem& it, GraphGuard& gg, unsigned* iterations, SweepTimer& stimer) {
+    cudaGraphConditionalHandle h;
+    TRY_CUDA(cudaGraphConditionalHandleCreate(&h, gg.graph, 1u, cudaGraphCondAssignDefault));
+    // zero-initialised storage (the union in the struct has no default constructor)
+    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+    std::memset(cp_raw, 0, sizeof(cp_raw));
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    TRY_CUDA(cudaGraphAddNode(&node, gg.graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    TRY_CUDA(cudaStreamBeginCaptureToGraph(gg.cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    const long long k0 = g_kernel_launches;
+    bm_status rs = greedy_enqueue_step(it.gc, it.px, *it.ar, stimer, gg.cs);
+    cudaError_t le = cudaSuccess;
+    const unsigned max_iterations = (unsigned)std::min<long long>(it.n + 2, 0x7fffffffLL);
+    if (rs == BM_OK) le = launch_greedy_continue(it.gc.g, h, iterations, max_iterations, gg.cs);
+    cudaGraph_t captured = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(gg.cs, &captured);
+    it.body_kernels = g_kernel_launches - k0;
+    if (rs != BM_OK) return rs;
+    TRY_CUDA(le);
+    TRY_CUDA(ee);
+    return BM_OK;
+}
+
+bm_status build_batched(const bm_instance* inst, int count, const bm_options& opt, bm_graph* outs,
+                        int32_t* statuses, int* failed) {
+    *failed = -1;
+    int S = opt.batch;
+    if (S == 0) S = 1024;
+    if (S < 32 || S > 2048 || S % 32) return fail(BM_ERR_ARG, "batch must be a multiple of 32 in [32, 2048]");
+    cudaStream_t s = (cudaStream_t)opt.stream;
+    const bool host_io = opt.host_io != 0;
+    const bool tc = opt.path == BM_PATH_TC_SPLIT3;
+    const int path = opt.path;
+    Timer tm(s);
+    tm.mark();  // 0
+    SweepTimer stimer(s);
+    stimer.on = false;  // no event records inside graph bodies
+    Arena ar(&opt, s);  // batch-wide state
+    std::vector<BatchItem> items(count);
+    DeviceState* sts;
+    int* bads;
+    unsigned* iters;
+    ALLOC(sts, DeviceState, std::max(count, 1));
+    ALLOC(bads, int, std::max(count, 1));
+    ALLOC(iters, unsigned, std::max(count, 1));
+    TRY_CUDA(cudaMemsetAsync(sts, 0, sizeof(DeviceState) * std::max(count, 1), s));
+    TRY_CUDA(cudaMemsetAsync(bads, 0, sizeof(int) * std::max(count, 1), s));
+    TRY_CUDA(cudaMemsetAsync(iters, 0, sizeof(unsigned) * std::max(count, 1), s));
+    const int sms = device_sm_count();
+    auto tag = [&](int i, bm_status rs) {
+        *failed = i;
+        if (statuses) statuses[i] = rs;
+        g_last_error = "instance " + std::to_string(i) + ": " + g_last_error;
+        return rs;
+    };
+    // 1. prep of every instance
+    for (int i = 0; i < count; ++i) {
+        BatchItem& it = items[i];
+        it.ar.reset(new Arena(&opt, s));
+        it.n = inst[i].n;
+        it.d = inst[i].d;
+        it.eps2 = (double)inst[i].eps * (double)inst[i].eps;
+        if (it.n == 0) continue;
+        bm_status rs = batch_prep(it, inst[i], opt, tc, path, sts + i, bads + i, s);
+        if (rs != BM_OK) return tag(i, rs);
+    }
+    {
+        std::vector<int> hbad(std::max(count, 1));
+        TRY_CUDA(cudaMemcpyAsync(hbad.data(), bads, sizeof(int) * std::max(count, 1), cudaMemcpyDeviceToHost, s));
+        TRY_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < count; ++i)
+            if (hbad[i]) return tag(i, fail(BM_ERR_ARG, "input holds NaN or Inf"));
+    }
+    tm.mark();  // 1: prep done
+    // 2. greedy buffers (the state starts zeroed: the first step requests 32 candidates)
+    for (int i = 0; i < count; ++i) {
+        BatchItem& it = items[i];
+        if (it.n == 0) continue;
+        it.step_cap = (unsigned long long)std::min<long long>(std::max<long long>(32 * it.n, 1LL << 16), 1LL << 22);
+        if (tc) it.step_cap = std::max<unsigned long long>(it.step_cap, (unsigned long long)sms * 2048);
+        it.mem_cap = (unsigned long long)std::max<long long>(4 * it.n, 1LL << 16);
+        bm_status rs = greedy_setup(it.px, it.eps2, path, S, *it.ar, s, it.st, it.step_cap, it.mem_cap, nullptr,
+                                    nullptr, 0, it.gc);
+        if (rs != BM_OK) return tag(i, rs);
+    }
+    // 3. one graph: a WHILE node per instance, no edges between them
+    {
+        GraphGuard gg;
+        TRY_CUDA(cudaStreamCreateWithFlags(&gg.cs, cudaStreamNonBlocking));
+        TRY_CUDA(cudaGraphCreate(&gg.graph, 0));
+        int nodes = 0;
+        for (int i = 0; i < count; ++i) {
+            BatchItem& it = items[i];
+            if (it.n == 0) continue;
+            bm_status rs = batch_capture(it, gg, iters + i, stimer);
+            if (rs != BM_OK) return tag(i, rs);
+            ++nodes;
+        }
+        if (nodes) {
+            TRY_CUDA(cudaGraphInstantiate(&gg.exec, gg.graph, 0));
+            tm.mark();  // 2: graph built
+            TRY_CUDA(cudaGraphLaunch(gg.exec, s));
+        } else {
+            tm.mark();
+        }
+        tm.mark();  // 3: graph done
+        TRY_CUDA(cudaStreamSynchronize(s));
+    }
+    // 4. per instance: finish an interrupted greedy on the host, then CSR and edges
+    HostState hs;
+    std::vector<unsigned> hiters(std::max(count, 1));
+    TRY_CUDA(cudaMemcpyAsync(hiters.data(), iters, sizeof(unsigned) * std::max(count, 1), cudaMemcpyDeviceToHost, s));
+    for (int i = 0; i < count; ++i) {
+        BatchItem& it = items[i];
+        Arena& iar = *it.ar;
+        long long executed = 0;   // kernels run for this instance (graph iterations included)
+        bm_graph g;
+        std::memset(&g, 0, sizeof(g));
+        DeviceState fin;
+        std::memset(&fin, 0, sizeof(fin));
+        long long L = 0, nnz = 0, E = 0, edge_pairs = 0;
+        int* landmarks = nullptr;
+        long long* offsets = nullptr;
+        int* ids = nullptr;
+        int* edges = nullptr;
+        bm_status rs = BM_OK;
+        if (it.n == 0) {
+            landmarks = (int*)iar.get(sizeof(int));
+            offsets = (long long*)iar.get(sizeof(long long));
+            ids = (int*)iar.get(sizeof(int));
+            edges = (int*)iar.get(2 * sizeof(int));
+            if (!landmarks || !offsets || !ids || !edges) return tag(i, fail(BM_ERR_NOMEM, "empty result"));
+            if (cudaMemsetAsync(offsets, 0, sizeof(long long), s) != cudaSuccess) {
+                cudaGetLastError();
+                return tag(i, fail(BM_ERR_CUDA, "memset"));
+            }
+        } else {
+            executed += (long long)hiters[i] * it.body_kernels;
+            const long long k0 = g_kernel_launches;
+            rs = greedy_drive(it.gc, it.px, iar, s, hs, it.step_cap, it.mem_cap, fin, stimer, true);
+            if (rs != BM_OK) return tag(i, rs);
+            release_sweep_out(iar, it.gc.so, false);
+            executed += g_kernel_launches - k0;
+            L = fin.n_landmarks;
+            nnz = (long long)fin.mem_count;
+            landmarks = it.gc.g.landmarks;
+            const long long k1 = g_kernel_launches;
+            rs = members_and_edges(iar, s, opt, it.n, L, nnz, it.gc.g.mem_keys, nullptr, &offsets, &ids, &edges,
+                                   &E, &edge_pairs);
+            if (rs != BM_OK) return tag(i, rs);
+            executed += g_kernel_launches - k1;
+        }
+        rs = hand_over(iar, s, host_io, landmarks, offsets, ids, edges, L, nnz, E, g);
+        if (rs != BM_OK) return tag(i, rs);
+        g.stats.distance_evals = (int64_t)L * it.n;
+        g.stats.tile_pairs = (int64_t)fin.tile_pairs;
+        g.stats.band_pairs = (int64_t)fin.band_pairs;
+        g.stats.greedy_steps = (int64_t)fin.steps;
+        g.stats.candidates = (int64_t)fin.candidates;
+        g.stats.edge_pairs = edge_pairs;
+        g.stats.band_delta = fin.delta;
+        g.stats.path = path;
+        g.stats.kernel_launches = executed;
+        outs[i] = g;
+        if (statuses) statuses[i] = BM_OK;
+        it.ar.reset();  // the instance's scratch
+    }
+    tm.mark();  // 4
+    const double total = tm.ms(0, 4), prep = tm.ms(0, 1), graph = tm.ms(2, 3);
+    for (int i = 0; i < count; ++i) {
+        outs[i].stats.ms_total = total;
+        outs[i].stats.ms_prep = prep;
+        outs[i].stats.ms_greedy = graph;
+    }
+    return BM_OK;
+}
 
 }  // namespace
 }  // namespace bm
@@ -952,6 +1245,37 @@ bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_opt
     vs = check_device(opt.path);
     if (vs != BM_OK) return vs;
     return build_graph(X, n, d, eps, opt, nullptr, 0, nullptr, 0, out);
+}
+
+bm_status bm_build_batched(const bm_instance* inst, int32_t count, const bm_options* opt_in, bm_graph* outs,
+                           int32_t* statuses) {
+    if (count < 0) return fail(BM_ERR_ARG, "count < 0");
+    if (count > 0 && (!inst || !outs)) return fail(BM_ERR_ARG, "inst or outs is NULL");
+    for (int i = 0; i < count; ++i) std::memset(&outs[i], 0, sizeof(bm_graph));
+    bm_options opt;
+    bm_options_init(&opt);
+    if (opt_in) opt = *opt_in;
+    for (int i = 0; i < count; ++i) {
+        if (statuses) statuses[i] = BM_OK;
+        bm_status vs = validate_points(inst[i].X, inst[i].n, inst[i].d, "X");
+        if (vs == BM_OK) vs = validate_eps(inst[i].eps);
+        if (vs != BM_OK) {
+            if (statuses) statuses[i] = vs;
+            g_last_error = "instance " + std::to_string(i) + ": " + g_last_error;
+            return vs;
+        }
+    }
+    bm_status vs = check_device(opt.path);
+    if (vs != BM_OK) return vs;
+    if (count == 0) return BM_OK;
+    int failed = -1;
+    bm_status rs = build_batched(inst, count, opt, outs, statuses, &failed);
+    if (rs != BM_OK) {
+        const std::string msg = g_last_error;
+        for (int i = 0; i < count; ++i) bm_graph_free(&outs[i], &opt);
+        g_last_error = msg;
+    }
+    return rs;
 }
 
 // ------------------------------------------------------------------ inverted file

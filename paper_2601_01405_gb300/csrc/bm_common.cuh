@@ -15,6 +15,7 @@ enum : int {
     kErrMemberOverflow = 2,  // membership keys exceeded their buffer (recoverable)
     kErrTimeout = 4,         // a bounded wait expired
     kErrHitOverflow = 8,     // range-query hits exceeded their buffer (recoverable)
+    kErrLoopLimit = 16,      // a device-side greedy loop ran more iterations than it can need
 };
 
 // Device-resident state of one build.  Written only by the library's kernels

@@ -345,6 +345,30 @@ cudaError_t launch_greedy_resolve(const GreedyBuffers& g, int S, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Loop condition of a greedy build run as a graph WHILE node: another step while
+// points remain uncovered and no step stopped on an error (an overflowing step
+// sets done as well, and the host resumes the build with larger buffers).
+// Every step with a candidate makes at least one landmark, so n + 1 iterations
+// always suffice; past max_iterations the loop stops with kErrLoopLimit.
+__global__ void greedy_continue_kernel(DeviceState* st, cudaGraphConditionalHandle h, unsigned* iterations,
+                                       unsigned max_iterations) {
+    const unsigned it = ++*iterations;
+    unsigned go = (st->done || st->error) ? 0u : 1u;
+    if (go && it >= max_iterations) {
+        st->error |= kErrLoopLimit;
+        st->done = 1;
+        go = 0u;
+    }
+    cudaGraphSetConditional(h, go);
+}
+
+cudaError_t launch_greedy_continue(const GreedyBuffers& g, cudaGraphConditionalHandle h, unsigned* iterations,
+                                   unsigned max_iterations, cudaStream_t s) {
+    note_launch();
+    greedy_continue_kernel<<<1, 1, 0, s>>>(g.st, h, iterations, max_iterations);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_greedy_apply(const GreedyBuffers& g, cudaStream_t s) {
     note_launch();
     greedy_apply_kernel<<<152 * 8, 256, 0, s>>>(g.st, g.step_keys, g.step_cap, g.ordinal, g.covered, g.mem_keys,

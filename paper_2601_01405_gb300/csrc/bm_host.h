@@ -118,6 +118,8 @@ cudaError_t launch_greedy_select(const GreedyBuffers& g, const Prepared& pts, in
 cudaError_t launch_greedy_gather(const GreedyBuffers& g, const Prepared& pts, int S, bool want_tc, cudaStream_t s);
 cudaError_t launch_greedy_resolve(const GreedyBuffers& g, int S, cudaStream_t s);
 cudaError_t launch_greedy_apply(const GreedyBuffers& g, cudaStream_t s);
+cudaError_t launch_greedy_continue(const GreedyBuffers& g, cudaGraphConditionalHandle h, unsigned* iterations,
+                                   unsigned max_iterations, cudaStream_t s);
 cudaError_t launch_greedy_rollback(const GreedyBuffers& g, cudaStream_t s);
 
 // sort.cu
