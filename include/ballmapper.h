@@ -155,13 +155,41 @@ typedef struct {
  *             batch = largest candidate batch per step (0 = 1024).
  *   outs:     count graphs, caller-owned array; each filled like bm_build's out.
  *             stats.ms_total of every instance is the time of the whole call,
- *             stats.ms_greedy that of the graph launch.
+ *             ms_prep that of the prep of all instances, ms_greedy that of the
+ *             graph launch, ms_members that of the per-instance tails (host
+ *             resume, CSR, edges); ms_edges and ms_sweep stay 0.
  *   statuses: optional, count entries: BM_OK, or the status of the instance
  *             that failed.
  * On error every outs[i] is zeroed (nothing leaks) and the first failing
  * status is returned; bm_last_error names the instance. */
 BM_API bm_status bm_build_batched(const bm_instance* inst, int32_t count, const bm_options* opt, bm_graph* outs,
                                   int32_t* statuses);
+
+/* ---- Tensor-core tile configuration (no counterpart in the paper: it tunes how
+ * the distance tiles of Sec. 3.2 map onto the GB300's tensor cores).
+ * For a point dimension d the tiles use K extent d_pad (a multiple of ck, >= d;
+ * the operands are zero-padded to it), K chunks of ck bf16 per shared-memory
+ * stage (16, 32 or 64), point tiles of nt rows (64, 128 or 256) held in bbuf
+ * buffers, and astg stages of query chunks.  Only shapes compiled into the
+ * library are accepted (bm_tile_shapes lists them, d_pad = 0 there).  Results
+ * never depend on the configuration; speed does.  Settings are process-wide,
+ * guarded by a lock, and read when a call prepares its operands. */
+typedef struct {
+    int32_t d_pad;
+    int32_t ck;
+    int32_t nt;
+    int32_t bbuf;
+    int32_t astg;
+} bm_tile_config;
+
+/* Writes up to max compiled shapes into out (out may be NULL); returns how many exist. */
+BM_API int32_t bm_tile_shapes(bm_tile_config* out, int32_t max);
+/* The configuration used for dimension d (an override if set, else the built-in choice). */
+BM_API bm_status bm_get_tile_config(int32_t d, bm_tile_config* out);
+/* Override the configuration for dimension d; cfg = NULL restores the built-in
+ * choice.  BM_ERR_ARG (with the reason in bm_last_error) for a configuration
+ * that is not compiled, does not fit in shared memory, or pads d wrongly. */
+BM_API bm_status bm_set_tile_config(int32_t d, const bm_tile_config* cfg);
 
 /* ---- Inverted-file index: the paper's non-exhaustive approximate oracle (Sec. 5.4;
  * nprobe cells searched per query, Sec. 6.1).  Points are grouped into nlist

@@ -1,0 +1,125 @@
+"""Autotuner for the tensor-core distance tiles.
+
+For each point dimension d it times every compiled tile shape (and each valid
+padding of d for it) on the sweep of a greedy step: ``rows`` query rows against
+``n`` points with radii so small that almost no pair is a hit, which is the
+shape of the greedy's dominant work when most points end up landmarks.  The
+fastest configuration per d can be installed in the library
+(``bm_set_tile_config``) and saved to / loaded from a JSON file.
+
+Timing is the device time of the tile launches only (the library's sweep
+events), the median over ``reps`` calls after one warm-up call.
+
+    python -m paper_2601_01405_gb300.autotune --dims 8 32 64 96 128 --out tiles.json
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import statistics
+import sys
+from typing import Dict, Iterable, List
+
+
+def _paddings(d: int, ck: int) -> List[int]:
+    out = {(d + ck - 1) // ck * ck}
+    if d > 32:
+        out.add((d + 63) // 64 * 64)
+    return sorted(p for p in out if p % ck == 0 and p >= d)
+
+
+def candidates(d: int) -> List[dict]:
+    """Every (d_pad, shape) the library accepts for dimension d."""
+    from . import binding
+    found = []
+    for shp in binding.tile_shapes():
+        for d_pad in _paddings(d, shp["ck"]):
+            cfg = dict(shp, d_pad=d_pad)
+            prev = binding.get_tile_config(d)
+            try:
+                binding.set_tile_config(d, cfg)
+            except binding.BallMapperError:
+                continue
+            finally:
+                binding.set_tile_config(d, prev)
+            found.append(cfg)
+    return found
+
+
+def time_config(d: int, cfg: dict, X, Q, eps: float, reps: int) -> float:
+    """Median device time (ms) of the tile launches of one range query under cfg."""
+    from . import binding
+    import torch
+    prev = binding.get_tile_config(d)
+    binding.set_tile_config(d, cfg)
+    try:
+        binding.bm_range_query(X, Q, eps)
+        ms = []
+        for _ in range(reps):
+            _, _, st = binding.bm_range_query(X, Q, eps)
+            torch.cuda.synchronize()
+            ms.append(st["ms_sweep"])
+        return statistics.median(ms)
+    finally:
+        binding.set_tile_config(d, prev)
+
+
+def tune(dims: Iterable[int], n: int = 200_000, rows: int = 2048, reps: int = 5, seed: int = 0) -> Dict[int, dict]:
+    """{d: {"best": cfg, "builtin": cfg, "timings": [(cfg, ms), ...]}}."""
+    import torch
+    from . import binding, workloads
+    out = {}
+    for d in dims:
+        X = torch.from_numpy(workloads.isotropic(n, d, 10, seed=seed + d)).cuda()
+        Q = X[:rows].contiguous()
+        eps = 1e-3  # only the self pairs are hits
+        builtin = binding.get_tile_config(d)
+        timings = []
+        for cfg in candidates(d):
+            timings.append((cfg, time_config(d, cfg, X, Q, eps, reps)))
+        timings.sort(key=lambda t: t[1])
+        out[d] = {"best": timings[0][0], "best_ms": timings[0][1], "builtin": builtin,
+                  "builtin_ms": next(ms for c, ms in timings if c == builtin),
+                  "evals": n * rows, "timings": [{"cfg": c, "ms": ms} for c, ms in timings]}
+    return out
+
+
+def install(table: Dict) -> None:
+    """Install the best configuration of each d of a tune() result or saved file."""
+    from . import binding
+    for d, entry in table.items():
+        binding.set_tile_config(int(d), entry["best"])
+
+
+def save(table: Dict, path: str) -> None:
+    with open(path, "w") as f:
+        json.dump({str(d): v for d, v in table.items()}, f, indent=1)
+
+
+def load(path: str) -> Dict[int, dict]:
+    with open(path) as f:
+        return {int(d): v for d, v in json.load(f).items()}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--dims", type=int, nargs="+", default=[8, 32, 64, 96, 128])
+    ap.add_argument("--n", type=int, default=200_000)
+    ap.add_argument("--rows", type=int, default=2048)
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args(argv)
+    table = tune(a.dims, a.n, a.rows, a.reps)
+    if a.out:
+        save(table, a.out)
+    for d, e in table.items():
+        rate = lambda ms: e["evals"] / (ms * 1e-3)
+        print(json.dumps({"d": d, "best": e["best"], "best_evals_per_s": rate(e["best_ms"]), "builtin": e["builtin"],
+                          "builtin_evals_per_s": rate(e["builtin_ms"]),
+                          "all": [(t["cfg"]["d_pad"], t["cfg"]["ck"], t["cfg"]["nt"], t["cfg"]["bbuf"],
+                                   t["cfg"]["astg"], round(t["ms"], 4)) for t in e["timings"]]}))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -80,7 +80,8 @@ def main(argv=None):
         "batched_ms": ms_b, "single_ms": ms_s,
         "batched_instances_per_s": a.count / (best_b / 1e3), "single_instances_per_s": a.count / (best_s / 1e3),
         "speedup": best_s / best_b,
-        "graph_ms": res_b[0]["stats"]["ms_greedy"] if res_b else 0.0,
+        "batched_breakdown_ms": ({k: res_b[0]["stats"][k] for k in ("ms_total", "ms_prep", "ms_greedy", "ms_members")}
+                                 if res_b else {}),
         "kernels_batched": launches_b, "kernels_single": launches_s,
         "mismatched_instances": mismatches, "generate_s": gen_s}))
     return 0 if not mismatches else 1

@@ -62,6 +62,14 @@ class bm_instance(ctypes.Structure):
     _fields_ = [("X", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int32), ("eps", ctypes.c_float)]
 
 
+class bm_tile_config(ctypes.Structure):
+    _fields_ = [("d_pad", ctypes.c_int32), ("ck", ctypes.c_int32), ("nt", ctypes.c_int32), ("bbuf", ctypes.c_int32),
+                ("astg", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+
 class BallMapperError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
@@ -127,6 +135,12 @@ def load(path: str = LIB_PATH):
         lib.bm_build_batched.argtypes = [ctypes.POINTER(bm_instance), ctypes.c_int32, ctypes.POINTER(bm_options),
                                          ctypes.POINTER(bm_graph), ctypes.POINTER(ctypes.c_int32)]
         lib.bm_build_batched.restype = ctypes.c_int
+        lib.bm_tile_shapes.argtypes = [ctypes.POINTER(bm_tile_config), ctypes.c_int32]
+        lib.bm_tile_shapes.restype = ctypes.c_int32
+        lib.bm_get_tile_config.argtypes = [ctypes.c_int32, ctypes.POINTER(bm_tile_config)]
+        lib.bm_get_tile_config.restype = ctypes.c_int
+        lib.bm_set_tile_config.argtypes = [ctypes.c_int32, ctypes.POINTER(bm_tile_config)]
+        lib.bm_set_tile_config.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -350,6 +364,33 @@ def bm_build_batched(instances, path: str = "tc", batch: int = 0, stream=None, s
                     "edges": alloc.tensor(g.edges, 2 * E, torch.int32).view(E, 2),
                     "stats": g.stats.as_dict()})
     return res
+
+
+def tile_shapes():
+    """The compiled tensor-core tile shapes, as dicts (d_pad = 0)."""
+    lib = load()
+    n = lib.bm_tile_shapes(None, 0)
+    arr = (bm_tile_config * max(n, 1))()
+    lib.bm_tile_shapes(arr, n)
+    return [arr[i].as_dict() for i in range(n)]
+
+
+def get_tile_config(d: int) -> dict:
+    """Tile configuration used for point dimension d."""
+    lib = load()
+    c = bm_tile_config()
+    _check(lib, lib.bm_get_tile_config(int(d), ctypes.byref(c)))
+    return c.as_dict()
+
+
+def set_tile_config(d: int, cfg: Optional[dict]) -> None:
+    """Override the tile configuration for dimension d (None: the built-in choice)."""
+    lib = load()
+    if cfg is None:
+        _check(lib, lib.bm_set_tile_config(int(d), None))
+        return
+    c = bm_tile_config(**{k: int(cfg[k]) for k in ("d_pad", "ck", "nt", "bbuf", "astg")})
+    _check(lib, lib.bm_set_tile_config(int(d), ctypes.byref(c)))
 
 
 def version() -> int:

@@ -171,7 +171,12 @@ bm_status prepare(const float* x, long long rows, int d, double eps2, bool a_sid
     p.x = x;
     p.rows = rows;
     p.d = d;
-    p.d_pad = tc_pad_dim(d);
+    const TileConfig tcfg = tile_config_for(d);
+    p.d_pad = tcfg.d_pad;
+    p.ck = tcfg.ck;
+    p.nt = tcfg.nt;
+    p.bbuf = tcfg.bbuf;
+    p.astg = tcfg.astg;
     ALLOC(p.phi, float, std::max<long long>(rows, 1));
     if (want_tc) {
         ALLOC(p.hi, __nv_bfloat16, std::max<long long>(rows, 1) * p.d_pad);
@@ -422,6 +427,10 @@ bm_status greedy_setup(const Prepared& pts, double eps2, int path, int S, Arena&
     g.cand.rows = S;
     g.cand.d = d;
     g.cand.d_pad = pts.d_pad;
+    g.cand.ck = pts.ck;
+    g.cand.nt = pts.nt;
+    g.cand.bbuf = pts.bbuf;
+    g.cand.astg = pts.astg;
     ALLOC(g.cand.phi, float, S);
     if (tc) {
         ALLOC(g.cand.hi, __nv_bfloat16, (long long)S * pts.d_pad);
@@ -1149,11 +1158,12 @@ bm_status build_batched(const bm_instance* inst, int count, const bm_options& op
         it.ar.reset();  // the instance's scratch
     }
     tm.mark();  // 4
-    const double total = tm.ms(0, 4), prep = tm.ms(0, 1), graph = tm.ms(2, 3);
+    const double total = tm.ms(0, 4), prep = tm.ms(0, 1), graph = tm.ms(2, 3), tail = tm.ms(3, 4);
     for (int i = 0; i < count; ++i) {
         outs[i].stats.ms_total = total;
         outs[i].stats.ms_prep = prep;
         outs[i].stats.ms_greedy = graph;
+        outs[i].stats.ms_members = tail;
     }
     return BM_OK;
 }
@@ -1245,6 +1255,33 @@ bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_opt
     vs = check_device(opt.path);
     if (vs != BM_OK) return vs;
     return build_graph(X, n, d, eps, opt, nullptr, 0, nullptr, 0, out);
+}
+
+int32_t bm_tile_shapes(bm_tile_config* out, int32_t max) {
+    std::vector<TileConfig> v(64);
+    const int n = tile_shapes(v.data(), (int)v.size());
+    for (int i = 0; out && i < n && i < max; ++i) out[i] = {v[i].d_pad, v[i].ck, v[i].nt, v[i].bbuf, v[i].astg};
+    return n;
+}
+
+bm_status bm_get_tile_config(int32_t d, bm_tile_config* out) {
+    if (!out) return fail(BM_ERR_ARG, "out is NULL");
+    if (d < 1 || d > 65536) return fail(BM_ERR_ARG, "d out of range [1, 65536]");
+    const TileConfig c = tile_config_for(d);
+    *out = {c.d_pad, c.ck, c.nt, c.bbuf, c.astg};
+    return BM_OK;
+}
+
+bm_status bm_set_tile_config(int32_t d, const bm_tile_config* cfg) {
+    if (d < 1 || d > 65536) return fail(BM_ERR_ARG, "d out of range [1, 65536]");
+    std::string why;
+    if (cfg) {
+        const TileConfig c = {cfg->d_pad, cfg->ck, cfg->nt, cfg->bbuf, cfg->astg};
+        if (!tile_config_set(d, &c, &why)) return fail(BM_ERR_ARG, "tile configuration rejected: " + why);
+    } else {
+        tile_config_set(d, nullptr, &why);
+    }
+    return BM_OK;
 }
 
 bm_status bm_build_batched(const bm_instance* inst, int32_t count, const bm_options* opt_in, bm_graph* outs,

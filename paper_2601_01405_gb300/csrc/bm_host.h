@@ -51,9 +51,20 @@ struct Prepared {
     __nv_bfloat16* lo = nullptr;       // rows x d_pad: bf16(x - bf16(x))
     __nv_bfloat16* aug = nullptr;      // rows x 16: the -phi pieces and ones (see prep kernel)
     int d_pad = 0;
+    int ck = 0, nt = 0, bbuf = 0, astg = 0;   // tensor-core tile shape chosen for this d
 };
 
-int tc_pad_dim(int d);  // padded K extent of the tensor-core operands for dimension d
+// Tensor-core tile configuration for one point dimension d: padded K extent
+// (a multiple of ck, >= d), K chunk per shared-memory stage, point-tile width,
+// point-tile buffers and query-chunk stages.
+struct TileConfig {
+    int d_pad, ck, nt, bbuf, astg;
+};
+TileConfig tile_config_for(int d);          // the override for d if one is set, else the built-in choice
+TileConfig tile_config_builtin(int d);
+bool tile_config_check(int d, const TileConfig& c, std::string* why);
+bool tile_config_set(int d, const TileConfig* c, std::string* why);   // nullptr: back to the built-in choice
+int tile_shapes(TileConfig* out, int max);  // the compiled (ck, nt, bbuf, astg) shapes, d_pad = 0
 
 // prep.cu
 cudaError_t launch_prep(const float* x, long long rows, int d, double eps2, bool a_side, bool want_tc,

@@ -20,12 +20,6 @@
 
 namespace bm {
 
-int tc_pad_dim(int d) {
-    if (d <= 16) return 16;
-    if (d <= 32) return 32;
-    return (d + 63) / 64 * 64;
-}
-
 __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ x, long long rows, int d,
                                                    double eps2, int a_side, int want_tc,
                                                    float* __restrict__ phi_out,

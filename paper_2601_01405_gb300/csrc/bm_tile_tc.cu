@@ -25,6 +25,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <map>
+#include <mutex>
 #include <string>
 
 #include "bm_host.h"
@@ -492,6 +494,27 @@ CUtensorMapSwizzle swizzle_for(int CK) {
 
 constexpr uint32_t kMaxSmem = 232448;
 
+// The compiled tile shapes (CK, NT, BBUF, ASTG).
+#define BM_TC_SHAPES(X) \
+    X(16, 256, 2, 8)    \
+    X(32, 256, 2, 8)    \
+    X(32, 256, 1, 8)    \
+    X(32, 128, 2, 8)    \
+    X(64, 256, 2, 5)    \
+    X(64, 256, 1, 5)    \
+    X(64, 128, 2, 5)    \
+    X(64, 128, 1, 4)    \
+    X(64, 64, 1, 4)
+
+constexpr TileConfig kShapes[] = {
+#define BM_X(a, b, c, d) {0, a, b, c, d},
+    BM_TC_SHAPES(BM_X)
+#undef BM_X
+};
+
+std::mutex g_tile_mu;
+std::map<int, TileConfig> g_tile_override;
+
 template <int CK, int NT, int BBUF, int ASTG>
 cudaError_t launch_cfg(TcArgs& args, long long a_rows_max, cudaStream_t stream, std::string* why, int* grid_out) {
     const Layout L0 = make_layout(CK, NT, BBUF, ASTG, args.d_pad);
@@ -533,27 +556,76 @@ int device_sm_count() {
     return sms > 0 ? sms : 1;
 }
 
+int tile_shapes(TileConfig* out, int max) {
+    const int n = (int)(sizeof(kShapes) / sizeof(kShapes[0]));
+    for (int i = 0; out && i < n && i < max; ++i) out[i] = kShapes[i];
+    return n;
+}
+
+bool tile_config_check(int d, const TileConfig& c, std::string* why) {
+    auto bad = [&](const char* m) {
+        if (why) *why = m;
+        return false;
+    };
+    if (d < 1) return bad("d must be >= 1");
+    if (c.ck != 16 && c.ck != 32 && c.ck != 64) return bad("ck must be 16, 32 or 64");
+    if (c.d_pad < d || c.d_pad % c.ck != 0) return bad("d_pad must be a multiple of ck and >= d");
+    if (c.d_pad > 512) return bad("tensor-core tiles support d_pad <= 512");
+    bool compiled = false;
+    for (const TileConfig& k : kShapes)
+        compiled = compiled || (k.ck == c.ck && k.nt == c.nt && k.bbuf == c.bbuf && k.astg == c.astg);
+    if (!compiled) return bad("(ck, nt, bbuf, astg) is not a compiled tile shape");
+    if (make_layout(c.ck, c.nt, c.bbuf, c.astg, c.d_pad).total > kMaxSmem)
+        return bad("the tile shape does not fit in shared memory for this d_pad");
+    return true;
+}
+
+// Built-in choice: the narrowest padding for d <= 32, else a multiple of 64 with
+// 64-wide K chunks, and the widest point tile that fits, double-buffered when
+// possible.  Measured on GB300 (2048 query rows x 200k points): the 256-wide
+// point tile with one buffer beats the double-buffered 128-wide one by 1.5x at
+// d_pad = 128, while a single buffer costs only ~3% at d_pad = 64.
+TileConfig tile_config_builtin(int d) {
+    if (d <= 16) return {16, 16, 256, 2, 8};
+    if (d <= 32) return {32, 32, 256, 2, 8};
+    const int d_pad = (d + 63) / 64 * 64;
+    const TileConfig order[] = {{d_pad, 64, 256, 2, 5}, {d_pad, 64, 256, 1, 5}, {d_pad, 64, 128, 2, 5},
+                                {d_pad, 64, 128, 1, 4}};
+    for (const TileConfig& c : order)
+        if (make_layout(c.ck, c.nt, c.bbuf, c.astg, c.d_pad).total <= kMaxSmem) return c;
+    return {d_pad, 64, 64, 1, 4};
+}
+
+TileConfig tile_config_for(int d) {
+    {
+        std::lock_guard<std::mutex> lk(g_tile_mu);
+        auto it = g_tile_override.find(d);
+        if (it != g_tile_override.end()) return it->second;
+    }
+    return tile_config_builtin(d);
+}
+
+bool tile_config_set(int d, const TileConfig* c, std::string* why) {
+    if (c && !tile_config_check(d, *c, why)) return false;
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    if (c) g_tile_override[d] = *c;
+    else g_tile_override.erase(d);
+    return true;
+}
+
 cudaError_t launch_sweep_tc(const SweepDesc& s, cudaStream_t stream, std::string* why, int* grid_out) {
     *grid_out = 0;
     if (s.a_rows_max == 0 || s.b->rows == 0) return cudaSuccess;
     const int d_pad = s.b->d_pad;
-    if (d_pad > 512) {
-        if (why) *why = "tensor-core tiles support d <= 512";
-        return cudaErrorNotSupported;
+    const TileConfig cfg = {d_pad, s.b->ck, s.b->nt, s.b->bbuf, s.b->astg};
+    if (s.a->d_pad != d_pad) {
+        if (why) *why = "query and point operands were prepared with different paddings";
+        return cudaErrorInvalidValue;
     }
+    if (!tile_config_check(s.b->d, cfg, why)) return cudaErrorNotSupported;
     TcArgs args;
     memset(&args, 0, sizeof(args));
-    const int CK = d_pad <= 16 ? 16 : (d_pad <= 32 ? 32 : 64);
-    // configuration: point-tile width NT and buffering chosen to fit shared memory
-    int NT = 256, BBUF = 2;
-    if (CK == 64) {
-        const int nc = d_pad / 64;
-        if (make_layout(64, 256, 2, 5, d_pad).total <= kMaxSmem) { NT = 256; BBUF = 2; }
-        else if (make_layout(64, 128, 2, 5, d_pad).total <= kMaxSmem) { NT = 128; BBUF = 2; }
-        else if (make_layout(64, 128, 1, 4, d_pad).total <= kMaxSmem) { NT = 128; BBUF = 1; }
-        else { NT = 64; BBUF = 1; }
-        (void)nc;
-    }
+    const int CK = cfg.ck, NT = cfg.nt;
     const CUtensorMapSwizzle sw = swizzle_for(CK);
     const long long arows = s.a->rows, brows = s.b->rows;
     // The greedy sweeps the same candidate and point buffers every step: reuse the
@@ -561,13 +633,14 @@ cudaError_t launch_sweep_tc(const SweepDesc& s, cudaStream_t stream, std::string
     struct MapCache {
         const void* key[6];
         long long arows, brows;
-        int d_pad, NT;
+        int d_pad, NT, CK;
         CUtensorMap maps[6];
         bool valid;
     };
     static thread_local MapCache cache = {};
     const void* key[6] = {s.a->hi, s.a->lo, s.a->aug, s.b->hi, s.b->lo, s.b->aug};
-    bool hit = cache.valid && cache.arows == arows && cache.brows == brows && cache.d_pad == d_pad && cache.NT == NT;
+    bool hit = cache.valid && cache.arows == arows && cache.brows == brows && cache.d_pad == d_pad && cache.NT == NT &&
+               cache.CK == CK;
     for (int i = 0; hit && i < 6; ++i) hit = cache.key[i] == key[i];
     if (hit) {
         args.a_hi = cache.maps[0]; args.a_lo = cache.maps[1]; args.a_aug = cache.maps[2];
@@ -585,7 +658,7 @@ cudaError_t launch_sweep_tc(const SweepDesc& s, cudaStream_t stream, std::string
             return cudaErrorInvalidValue;
         }
         for (int i = 0; i < 6; ++i) cache.key[i] = key[i];
-        cache.arows = arows; cache.brows = brows; cache.d_pad = d_pad; cache.NT = NT;
+        cache.arows = arows; cache.brows = brows; cache.d_pad = d_pad; cache.NT = NT; cache.CK = CK;
         cache.maps[0] = args.a_hi; cache.maps[1] = args.a_lo; cache.maps[2] = args.a_aug;
         cache.maps[3] = args.b_hi; cache.maps[4] = args.b_lo; cache.maps[5] = args.b_aug;
         cache.valid = true;
@@ -601,12 +674,13 @@ cudaError_t launch_sweep_tc(const SweepDesc& s, cudaStream_t stream, std::string
     args.eps2 = s.eps2;
     args.st = const_cast<DeviceState*>(s.st);
     args.sink = s.sink;
-    if (CK == 16) return launch_cfg<16, 256, 2, 8>(args, s.a_rows_max, stream, why, grid_out);
-    if (CK == 32) return launch_cfg<32, 256, 2, 8>(args, s.a_rows_max, stream, why, grid_out);
-    if (NT == 256) return launch_cfg<64, 256, 2, 5>(args, s.a_rows_max, stream, why, grid_out);
-    if (NT == 128 && BBUF == 2) return launch_cfg<64, 128, 2, 5>(args, s.a_rows_max, stream, why, grid_out);
-    if (NT == 128) return launch_cfg<64, 128, 1, 4>(args, s.a_rows_max, stream, why, grid_out);
-    return launch_cfg<64, 64, 1, 4>(args, s.a_rows_max, stream, why, grid_out);
+#define BM_X(a, b, c, d)                                                      \
+    if (cfg.ck == a && cfg.nt == b && cfg.bbuf == c && cfg.astg == d)         \
+        return launch_cfg<a, b, c, d>(args, s.a_rows_max, stream, why, grid_out);
+    BM_TC_SHAPES(BM_X)
+#undef BM_X
+    if (why) *why = "tile shape not compiled";
+    return cudaErrorNotSupported;
 }
 
 }  // namespace bm

@@ -70,3 +70,29 @@ int main(void) {
            ctypes.sizeof(binding.bm_graph), binding.bm_graph.stats.offset,
            binding.bm_options.alloc.offset, binding.bm_stats.ms_prep.offset, binding.bm_graph.edges.offset]
     assert got == exp
+
+
+def test_tile_config_table_on_host():
+    """Tile configurations are host-side state: list, query, override, reject, reset."""
+    _build.build()
+    shapes = binding.tile_shapes()
+    assert len(shapes) >= 6 and all(s["d_pad"] == 0 for s in shapes)
+    for d in (1, 8, 16, 17, 32, 33, 64, 96, 128, 300, 512):
+        c = binding.get_tile_config(d)
+        assert c["d_pad"] >= d and c["d_pad"] % c["ck"] == 0 and c["d_pad"] % 16 == 0
+        assert {k: c[k] for k in ("ck", "nt", "bbuf", "astg")} in [{k: s[k] for k in ("ck", "nt", "bbuf", "astg")}
+                                                                   for s in shapes]
+    base = binding.get_tile_config(96)
+    try:
+        binding.set_tile_config(96, dict(d_pad=96, ck=32, nt=128, bbuf=2, astg=8))
+        assert binding.get_tile_config(96)["d_pad"] == 96
+        for bad in (dict(d_pad=96, ck=64, nt=256, bbuf=1, astg=5),    # 96 is not a multiple of 64
+                    dict(d_pad=64, ck=32, nt=128, bbuf=2, astg=8),    # pads below d
+                    dict(d_pad=96, ck=32, nt=256, bbuf=2, astg=8),    # does not fit in shared memory
+                    dict(d_pad=96, ck=32, nt=96, bbuf=2, astg=8)):    # not a compiled shape
+            with pytest.raises(binding.BallMapperError):
+                binding.set_tile_config(96, bad)
+        assert binding.get_tile_config(96)["d_pad"] == 96              # a rejected call changes nothing
+    finally:
+        binding.set_tile_config(96, None)
+    assert binding.get_tile_config(96) == base
