@@ -191,6 +191,14 @@ BM_API bm_status bm_get_tile_config(int32_t d, bm_tile_config* out);
  * that is not compiled, does not fit in shared memory, or pads d wrongly. */
 BM_API bm_status bm_set_tile_config(int32_t d, const bm_tile_config* cfg);
 
+/* Nerve-edge deduplication (Sec. 5.2): witnessed landmark pairs are made unique
+ * either in a bitmap of landmark rows (chosen when the bitmap is at most 64
+ * bytes per witnessed pair) or by sorting the pair keys.  bytes bounds the
+ * bitmap of one chunk of rows (default 1 GiB, 0 restores it; a negative value
+ * always sorts).  Process-wide; returns the previous setting.  Results do not
+ * depend on it. */
+BM_API int64_t bm_set_nerve_bitmap_bytes(int64_t bytes);
+
 /* ---- Inverted-file index: the paper's non-exhaustive approximate oracle (Sec. 5.4;
  * nprobe cells searched per query, Sec. 6.1).  Points are grouped into nlist
  * k-means cells; a query examines only the points of its nprobe nearest cells

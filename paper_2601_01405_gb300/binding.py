@@ -141,6 +141,8 @@ def load(path: str = LIB_PATH):
         lib.bm_get_tile_config.restype = ctypes.c_int
         lib.bm_set_tile_config.argtypes = [ctypes.c_int32, ctypes.POINTER(bm_tile_config)]
         lib.bm_set_tile_config.restype = ctypes.c_int
+        lib.bm_set_nerve_bitmap_bytes.argtypes = [ctypes.c_int64]
+        lib.bm_set_nerve_bitmap_bytes.restype = ctypes.c_int64
         _lib = lib
         return lib
 
@@ -391,6 +393,12 @@ def set_tile_config(d: int, cfg: Optional[dict]) -> None:
         return
     c = bm_tile_config(**{k: int(cfg[k]) for k in ("d_pad", "ck", "nt", "bbuf", "astg")})
     _check(lib, lib.bm_set_tile_config(int(d), ctypes.byref(c)))
+
+
+def set_nerve_bitmap_bytes(nbytes: int) -> int:
+    """Bitmap budget of the nerve-edge deduplication (0 = default, < 0 = always
+    sort); returns the previous setting."""
+    return int(load().bm_set_nerve_bitmap_bytes(int(nbytes)))
 
 
 def version() -> int:

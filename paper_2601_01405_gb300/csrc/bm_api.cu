@@ -26,11 +26,10 @@ void device_free(const bm_options* opt, cudaStream_t s, void* p) {
 
 Arena::~Arena() {
     for (void* p : ptrs_) device_free(opt_, stream_, p);
+    for (void* p : slabs_) device_free(opt_, stream_, p);
 }
 
-void* Arena::get(size_t bytes) {
-    bytes = (bytes + 255) & ~(size_t)255;
-    if (bytes == 0) bytes = 256;
+void* Arena::raw(size_t bytes) {
     void* p = nullptr;
     if (opt_ && opt_->alloc) {
         p = opt_->alloc(bytes, (void*)stream_, opt_->alloc_ctx);
@@ -38,6 +37,34 @@ void* Arena::get(size_t bytes) {
         cudaGetLastError();
         p = nullptr;
     }
+    return p;
+}
+
+void* Arena::get(size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (bytes == 0) bytes = 256;
+    if (slab_ && bytes <= kSlabMax) {
+        if (bytes > left_) {
+            const size_t block = std::max(bytes, next_);
+            char* b = (char*)raw(block);
+            if (!b) return nullptr;
+            slabs_.push_back(b);
+            cur_ = b;
+            left_ = block;
+            next_ = std::min<size_t>(2 * next_, 64u << 20);
+        }
+        void* p = cur_;
+        cur_ += bytes;
+        left_ -= bytes;
+        return p;
+    }
+    return get_standalone(bytes);
+}
+
+void* Arena::get_standalone(size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (bytes == 0) bytes = 256;
+    void* p = raw(bytes);
     if (p) ptrs_.push_back(p);
     return p;
 }
@@ -51,9 +78,11 @@ void Arena::release(void* p) {
     }
 }
 
-void Arena::take(void* p) {
+bool Arena::take(void* p) {
     auto it = std::find(ptrs_.begin(), ptrs_.end(), p);
-    if (it != ptrs_.end()) ptrs_.erase(it);
+    if (it == ptrs_.end()) return false;
+    ptrs_.erase(it);
+    return true;
 }
 
 namespace {
@@ -75,6 +104,16 @@ bm_status fail(bm_status s, const std::string& msg) {
             cudaGetLastError();                                                         \
             return fail(e__ == cudaErrorMemoryAllocation ? BM_ERR_NOMEM : BM_ERR_CUDA,  \
                         std::string(#expr) + ": " + cudaGetErrorString(e__));           \
+        }                                                                               \
+    } while (0)
+
+// Synchronise with the stream; a failure names the stage whose work was in flight.
+#define TRY_SYNC(stream, stage)                                                         \
+    do {                                                                                \
+        cudaError_t e__ = cudaStreamSynchronize(stream);                                \
+        if (e__ != cudaSuccess) {                                                       \
+            cudaGetLastError();                                                         \
+            return fail(BM_ERR_CUDA, std::string("after ") + (stage) + ": " + cudaGetErrorString(e__)); \
         }                                                                               \
     } while (0)
 
@@ -766,14 +805,37 @@ bm_status hand_over(Arena& ar, cudaStream_t s, bool host_io, int* landmarks, lon
         g.on_host = 1;
         g.members.on_host = 1;
     } else {
-        ar.take(landmarks);
-        ar.take(offsets);
-        ar.take(ids);
-        ar.take(edges);
-        g.landmarks = landmarks;
-        g.members.offsets = (int64_t*)offsets;
-        g.members.ids = ids;
-        g.edges = edges;
+        // buffers carved from a slab are copied into buffers of their own
+        auto own = [&](void* p, size_t bytes, bm_status* rs) -> void* {
+            if (ar.take(p)) return p;
+            void* q = ar.get_standalone(bytes);
+            if (!q || !ar.take(q)) {
+                *rs = fail(BM_ERR_NOMEM, "allocation of a result buffer failed");
+                return nullptr;
+            }
+            if (cudaMemcpyAsync(q, p, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+                cudaGetLastError();
+                device_free(ar.options(), s, q);
+                *rs = fail(BM_ERR_CUDA, "device copy of a result buffer failed");
+                return nullptr;
+            }
+            return q;
+        };
+        bm_status rs = BM_OK;
+        void* ol = own(landmarks, sizeof(int) * std::max<long long>(L, 1), &rs);
+        void* oo = rs == BM_OK ? own(offsets, sizeof(long long) * (L + 1), &rs) : nullptr;
+        void* oi = rs == BM_OK ? own(ids, sizeof(int) * std::max<long long>(nnz, 1), &rs) : nullptr;
+        void* oe = rs == BM_OK ? own(edges, sizeof(int) * 2 * std::max<long long>(E, 1), &rs) : nullptr;
+        if (rs != BM_OK) {
+            device_free(ar.options(), s, ol);
+            device_free(ar.options(), s, oo);
+            device_free(ar.options(), s, oi);
+            return rs;
+        }
+        g.landmarks = (int*)ol;
+        g.members.offsets = (int64_t*)oo;
+        g.members.ids = (int*)oi;
+        g.edges = (int*)oe;
     }
     g.n_landmarks = L;
     g.members.rows = L;
@@ -946,6 +1008,20 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
 
 // ---- Batched builds: the greedy loops of many instances in one CUDA graph.
 
+// Page-locked host array (asynchronous device-to-host copies land here).
+struct PinnedI64 {
+    long long* p = nullptr;
+    explicit PinnedI64(int count) {
+        if (cudaMallocHost(&p, sizeof(long long) * (size_t)std::max(count, 1)) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+    }
+    ~PinnedI64() {
+        if (p) cudaFreeHost(p);
+    }
+};
+
 struct BatchItem {
     std::unique_ptr<Arena> ar;
     long long n = 0;
@@ -1048,7 +1124,7 @@ bm_status build_batched(const bm_instance* inst, int count, const bm_options& op
     // 1. prep of every instance
     for (int i = 0; i < count; ++i) {
         BatchItem& it = items[i];
-        it.ar.reset(new Arena(&opt, s));
+        it.ar.reset(new Arena(&opt, s, true));
         it.n = inst[i].n;
         it.d = inst[i].d;
         it.eps2 = (double)inst[i].eps * (double)inst[i].eps;
@@ -1059,7 +1135,7 @@ bm_status build_batched(const bm_instance* inst, int count, const bm_options& op
     {
         std::vector<int> hbad(std::max(count, 1));
         TRY_CUDA(cudaMemcpyAsync(hbad.data(), bads, sizeof(int) * std::max(count, 1), cudaMemcpyDeviceToHost, s));
-        TRY_CUDA(cudaStreamSynchronize(s));
+        TRY_SYNC(s, "prep of all instances");
         for (int i = 0; i < count; ++i)
             if (hbad[i]) return tag(i, fail(BM_ERR_ARG, "input holds NaN or Inf"));
     }
@@ -1096,55 +1172,141 @@ bm_status build_batched(const bm_instance* inst, int count, const bm_options& op
             tm.mark();
         }
         tm.mark();  // 3: graph done
-        TRY_CUDA(cudaStreamSynchronize(s));
+        TRY_SYNC(s, "the graph of greedy loops");
     }
-    // 4. per instance: finish an interrupted greedy on the host, then CSR and edges
-    HostState hs;
+    // 4. tails, staged over all instances with one host synchronisation per stage:
+    //    states -> (resume) -> CSR + transpose -> pair emission -> scatter + hand-over
     std::vector<unsigned> hiters(std::max(count, 1));
+    std::vector<DeviceState> hst(std::max(count, 1));
     TRY_CUDA(cudaMemcpyAsync(hiters.data(), iters, sizeof(unsigned) * std::max(count, 1), cudaMemcpyDeviceToHost, s));
-    for (int i = 0; i < count; ++i) {
-        BatchItem& it = items[i];
-        Arena& iar = *it.ar;
-        long long executed = 0;   // kernels run for this instance (graph iterations included)
-        bm_graph g;
-        std::memset(&g, 0, sizeof(g));
+    TRY_CUDA(cudaMemcpyAsync(hst.data(), sts, sizeof(DeviceState) * std::max(count, 1), cudaMemcpyDeviceToHost, s));
+    TRY_SYNC(s, "reading the instance states");
+    PinnedI64 hP(count), hE(count), hB(count);
+    if (!hP.p || !hE.p || !hB.p) return fail(BM_ERR_NOMEM, "pinned host buffers");
+    for (int i = 0; i < count; ++i) hB.p[i] = 0;
+    struct Tail {
         DeviceState fin;
-        std::memset(&fin, 0, sizeof(fin));
-        long long L = 0, nnz = 0, E = 0, edge_pairs = 0;
-        int* landmarks = nullptr;
+        long long L = 0, nnz = 0, executed = 0;
         long long* offsets = nullptr;
         int* ids = nullptr;
         int* edges = nullptr;
-        bm_status rs = BM_OK;
+        long long E = 0, P = 0;
+        EdgeJob job;
+        bool staged = false;   // edges go through the staged pass
+        bool multi = false;    // ... but need several chunks (per-build pass)
+    };
+    std::vector<Tail> tails(count);
+    HostState hs;
+    for (int i = 0; i < count; ++i) {
+        BatchItem& it = items[i];
+        Tail& t = tails[i];
+        if (it.n == 0) continue;
+        Arena& iar = *it.ar;
+        t.executed = (long long)hiters[i] * it.body_kernels;
+        const long long k0 = g_kernel_launches;
+        t.fin = hst[i];
+        if (!t.fin.done || t.fin.error) {   // stopped inside the graph: finish on the host
+            bm_status rs = greedy_drive(it.gc, it.px, iar, s, hs, it.step_cap, it.mem_cap, t.fin, stimer, true);
+            if (rs != BM_OK) return tag(i, rs);
+        }
+        release_sweep_out(iar, it.gc.so, false);
+        t.L = t.fin.n_landmarks;
+        t.nnz = (long long)t.fin.mem_count;
+        // memberships: sort, CSR into buffers of their own (they are results)
+        unsigned long long* tmp;
+        ALLOC(tmp, unsigned long long, std::max<long long>(t.nnz, 1));
+        unsigned long long* sorted = nullptr;
+        cudaError_t ce = radix_sort_u64(it.gc.g.mem_keys, tmp, t.nnz,
+                                        digit_shifts(bits_for(it.n - 1), bits_for(t.L - 1)), iar, s, &sorted);
+        if (ce != cudaSuccess) return tag(i, fail(BM_ERR_CUDA, std::string("membership sort: ") + cudaGetErrorString(ce)));
+        t.offsets = (long long*)iar.get_standalone(sizeof(long long) * (t.L + 1));
+        t.ids = (int*)iar.get_standalone(sizeof(int) * std::max<long long>(t.nnz, 1));
+        if (!t.offsets || !t.ids) return tag(i, fail(BM_ERR_NOMEM, "membership CSR"));
+        ce = launch_csr_from_sorted(sorted, t.nnz, t.L, t.offsets, t.ids, s);
+        if (ce != cudaSuccess) return tag(i, fail(BM_ERR_CUDA, std::string("membership CSR: ") + cudaGetErrorString(ce)));
+        hP.p[i] = 0;
+        if (!opt.skip_edges && t.nnz > 0 && t.L >= 2) {
+            t.job.keys = sorted;
+            t.job.nnz = t.nnz;
+            t.job.n = it.n;
+            t.job.L = t.L;
+            Failure f{BM_OK, ""};
+            if (!edges_transpose(t.job, iar, s, f)) return tag(i, fail(f.status, f.msg));
+            ce = cudaMemcpyAsync(&hP.p[i], t.job.lpre + t.L, sizeof(long long), cudaMemcpyDeviceToHost, s);
+            if (ce != cudaSuccess) return tag(i, fail(BM_ERR_CUDA, "pair count copy"));
+            t.staged = true;
+        }
+        t.executed += g_kernel_launches - k0;
+    }
+    TRY_SYNC(s, "the membership and transpose pass");
+    for (int i = 0; i < count; ++i) {
+        Tail& t = tails[i];
+        if (!t.staged) continue;
+        t.P = hP.p[i];
+        hE.p[i] = 0;
+        if (t.P == 0) continue;
+        t.job.bitmap = edges_choose_bitmap(t.L, t.P);
+        t.multi = t.job.bitmap ? edges_bitmap_rows(t.L) < t.L : t.P > kEdgeChunkPairs;
+        if (t.multi) continue;   // several chunks: the per-build nerve pass below
+        const long long k0 = g_kernel_launches;
+        Failure f{BM_OK, ""};
+        if (!edges_emit(t.job, 0, (int)t.L, t.P, *items[i].ar, s, f)) return tag(i, fail(f.status, f.msg));
+        TRY_CUDA(cudaMemcpyAsync(&hE.p[i], t.job.count_dev, sizeof(long long), cudaMemcpyDeviceToHost, s));
+        t.executed += g_kernel_launches - k0;
+    }
+    TRY_SYNC(s, "the pair deduplication pass");
+    for (int i = 0; i < count; ++i) {
+        BatchItem& it = items[i];
+        Tail& t = tails[i];
+        Arena& iar = *it.ar;
+        bm_graph g;
+        std::memset(&g, 0, sizeof(g));
+        int* landmarks = nullptr;
+        long long edge_pairs = t.P;
+        const long long k0 = g_kernel_launches;
         if (it.n == 0) {
             landmarks = (int*)iar.get(sizeof(int));
-            offsets = (long long*)iar.get(sizeof(long long));
-            ids = (int*)iar.get(sizeof(int));
-            edges = (int*)iar.get(2 * sizeof(int));
-            if (!landmarks || !offsets || !ids || !edges) return tag(i, fail(BM_ERR_NOMEM, "empty result"));
-            if (cudaMemsetAsync(offsets, 0, sizeof(long long), s) != cudaSuccess) {
+            t.offsets = (long long*)iar.get(sizeof(long long));
+            t.ids = (int*)iar.get(sizeof(int));
+            if (!landmarks || !t.offsets || !t.ids) return tag(i, fail(BM_ERR_NOMEM, "empty result"));
+            if (cudaMemsetAsync(t.offsets, 0, sizeof(long long), s) != cudaSuccess) {
                 cudaGetLastError();
                 return tag(i, fail(BM_ERR_CUDA, "memset"));
             }
         } else {
-            executed += (long long)hiters[i] * it.body_kernels;
-            const long long k0 = g_kernel_launches;
-            rs = greedy_drive(it.gc, it.px, iar, s, hs, it.step_cap, it.mem_cap, fin, stimer, true);
-            if (rs != BM_OK) return tag(i, rs);
-            release_sweep_out(iar, it.gc.so, false);
-            executed += g_kernel_launches - k0;
-            L = fin.n_landmarks;
-            nnz = (long long)fin.mem_count;
             landmarks = it.gc.g.landmarks;
-            const long long k1 = g_kernel_launches;
-            rs = members_and_edges(iar, s, opt, it.n, L, nnz, it.gc.g.mem_keys, nullptr, &offsets, &ids, &edges,
-                                   &E, &edge_pairs);
-            if (rs != BM_OK) return tag(i, rs);
-            executed += g_kernel_launches - k1;
+            if (t.staged && t.multi) {
+                // several chunks: the per-build nerve pass
+                edges_release(t.job, iar);
+                Failure f{BM_OK, ""};
+                EdgeResult er;
+                if (!build_edges(t.job.keys, t.nnz, it.n, t.L, iar, s, er, f)) return tag(i, fail(f.status, f.msg));
+                t.edges = er.edges;
+                t.E = er.n_edges;
+                edge_pairs = er.pairs;
+            } else if (t.staged && t.P > 0) {
+                t.E = hE.p[i];
+                if (t.E > 0x7fffffffLL) return tag(i, fail(BM_ERR_CAPACITY, "more than 2^31-1 edges"));
+                t.edges = (int*)iar.get_standalone(sizeof(int) * 2 * std::max<long long>(t.E, 1));
+                if (!t.edges) return tag(i, fail(BM_ERR_NOMEM, "edge buffer"));
+                Failure f{BM_OK, ""};
+                if (!edges_scatter(t.job, 0, (int)t.L, t.P, t.edges, iar, s, f)) return tag(i, fail(f.status, f.msg));
+                if (t.job.bad) {   // checked once for all instances below
+                    hB.p[i] = 0;
+                    TRY_CUDA(cudaMemcpyAsync(&hB.p[i], t.job.bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+                }
+                edges_release(t.job, iar);
+            }
         }
-        rs = hand_over(iar, s, host_io, landmarks, offsets, ids, edges, L, nnz, E, g);
+        if (!t.edges) {
+            t.edges = (int*)iar.get(2 * sizeof(int));
+            if (!t.edges) return tag(i, fail(BM_ERR_NOMEM, "edge buffer"));
+        }
+        bm_status rs = hand_over(iar, s, host_io, landmarks, t.offsets, t.ids, t.edges, t.L, t.nnz, t.E, g);
         if (rs != BM_OK) return tag(i, rs);
-        g.stats.distance_evals = (int64_t)L * it.n;
+        t.executed += g_kernel_launches - k0;
+        const DeviceState& fin = t.fin;
+        g.stats.distance_evals = (int64_t)t.L * it.n;
         g.stats.tile_pairs = (int64_t)fin.tile_pairs;
         g.stats.band_pairs = (int64_t)fin.band_pairs;
         g.stats.greedy_steps = (int64_t)fin.steps;
@@ -1152,11 +1314,16 @@ bm_status build_batched(const bm_instance* inst, int count, const bm_options& op
         g.stats.edge_pairs = edge_pairs;
         g.stats.band_delta = fin.delta;
         g.stats.path = path;
-        g.stats.kernel_launches = executed;
+        g.stats.kernel_launches = t.executed;
         outs[i] = g;
         if (statuses) statuses[i] = BM_OK;
         it.ar.reset();  // the instance's scratch
     }
+    TRY_SYNC(s, "the edge extraction pass");
+    for (int i = 0; i < count; ++i)
+        if (hB.p[i])
+            return tag(i, fail(BM_ERR_CUDA, "nerve pass: a cover list broke its invariants (code " +
+                                                std::to_string(hB.p[i]) + ")"));
     tm.mark();  // 4
     const double total = tm.ms(0, 4), prep = tm.ms(0, 1), graph = tm.ms(2, 3), tail = tm.ms(3, 4);
     for (int i = 0; i < count; ++i) {
@@ -1256,6 +1423,8 @@ bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_opt
     if (vs != BM_OK) return vs;
     return build_graph(X, n, d, eps, opt, nullptr, 0, nullptr, 0, out);
 }
+
+int64_t bm_set_nerve_bitmap_bytes(int64_t bytes) { return edges_set_bitmap_budget(bytes); }
 
 int32_t bm_tile_shapes(bm_tile_config* out, int32_t max) {
     std::vector<TileConfig> v(64);

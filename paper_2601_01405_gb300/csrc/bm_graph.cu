@@ -8,11 +8,19 @@
 // point x covered by c_x balls witnesses the c_x (c_x - 1) / 2 pairs of its
 // covering landmarks, so the edge set is the deduplicated union of those
 // pairs.  Steps: transpose the memberships (point -> ascending covering
-// landmarks, by a radix sort of swapped keys); count the witnessed pairs per
-// smaller landmark and cut the landmark range into chunks of at most 2^28
-// pairs; per chunk emit (i << 32 | j) keys, radix sort, keep the first key of
-// every run and append.  Chunks ascend in i, so the edges come out
-// lexicographic.
+// landmarks, by a radix sort of swapped keys) and count the witnessed pairs per
+// smaller landmark.  Then one of two deduplications, chosen by size:
+//   bitmap  (dense witnesses): the landmark rows are cut into chunks whose
+//           L-bit rows fit a bitmap budget; every witnessed pair sets bit j of
+//           row i (warp-aggregated atomicOr); each row's set bits, read in
+//           order, are its edges.  Memory and work are independent of how often
+//           a pair is witnessed.
+//   sort    (sparse witnesses): chunks of at most 2^28 pairs; emit
+//           (i << 32 | j) keys, radix sort, keep the first key of every run.
+// Chunks ascend in i, so the edges come out lexicographic either way.
+#include <atomic>
+#include <string>
+
 #include "bm_host.h"
 
 namespace bm {
@@ -125,6 +133,104 @@ __global__ void unique_scatter_kernel(const unsigned long long* keys, long long 
     }
 }
 
+// Bitmap deduplication.  One warp per entry t of the transposed CSR (point x,
+// position a in its ascending cover list): i = tlist[t]; when i lies in the
+// chunk [i0, i1), every later entry j of x's cover list sets bit j of row
+// i - i0 (W 32-bit words per row).  Lanes take consecutive entries (ascending
+// j), so lanes on the same word are contiguous: a segmented OR over the run
+// leaves the union with its first lane, which issues one atomicOr.
+// Inputs that break the CSR invariants (an index outside its array) are not
+// dereferenced: the kernel records them in *bad and skips the entry.
+__global__ void nerve_bits_kernel(const unsigned long long* tkeys, const long long* toff, const int* tlist,
+                                  long long nnz, long long n, int i0, int i1, long long W, unsigned* bits, int* bad) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long t = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < nnz; t += warps) {
+        const int i = tlist[t];
+        if (i < i0 || i >= i1) continue;
+        const long long x = (long long)(tkeys[t] >> 32);
+        const long long end = x < n ? toff[x + 1] : -1;
+        if (end < t + 1 || end > nnz) {
+            if (lane == 0 && end < t + 1) atomicOr(bad, 1);
+            if (lane == 0 && end > nnz) atomicOr(bad, 2);
+            continue;
+        }
+        unsigned* row = bits + (long long)(i - i0) * W;
+        for (long long base = t + 1; base < end; base += 32) {
+            const long long b = base + lane;
+            const bool valid = b < end;
+            int j = valid ? tlist[b] : 0;
+            if (valid && (j <= i || (long long)(j >> 5) >= W)) {   // cover lists ascend and stay below L
+                atomicOr(bad, 4);
+                j = 0;
+            }
+            const bool ok = valid && j > i;
+            const int word = ok ? (j >> 5) : -1 - lane;   // skipped lanes never join a run
+            unsigned acc = ok ? (1u << (j & 31)) : 0u;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned v = __shfl_down_sync(kFull, acc, off);
+                const int w = __shfl_down_sync(kFull, word, off);
+                if (lane + off < 32 && w == word) acc |= v;
+            }
+            const int wprev = __shfl_up_sync(kFull, word, 1);
+            if (ok && (lane == 0 || wprev != word)) atomicOr(row + word, acc);
+        }
+    }
+}
+
+// Set bits per bitmap row (one warp per row).
+__global__ void bitrow_counts_kernel(const unsigned* bits, long long R, long long W, long long* cnt) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < R; r += warps) {
+        const unsigned* row = bits + r * W;
+        long long c = 0;
+        for (long long w = lane; w < W; w += 32) c += __popc(row[w]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+        if (lane == 0) cnt[r] = c;
+    }
+}
+
+// Row r's set bits, in ascending order, become edges (i0 + r, j) at
+// positions roff[r] ... (one warp per row; a warp scan orders its lanes).
+__global__ void bitrow_extract_kernel(const unsigned* bits, long long R, long long W, int i0, const long long* roff,
+                                      int* edges, int* bad) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long total = roff[R];
+    for (long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < R; r += warps) {
+        const unsigned* row = bits + r * W;
+        long long pos = roff[r];
+        const int i = i0 + (int)r;
+        for (long long w0 = 0; w0 < W; w0 += 32) {
+            unsigned word = (w0 + lane < W) ? row[w0 + lane] : 0u;
+            const int c = __popc(word);
+            int incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += y;
+            }
+            long long o = pos + (incl - c);
+            const int jbase = (int)((w0 + lane) * 32);
+            while (word) {
+                const int b = __ffs(word) - 1;
+                if (o < total) {
+                    edges[2 * o] = i;
+                    edges[2 * o + 1] = jbase + b;
+                } else {
+                    atomicOr(bad, 8);
+                }
+                ++o;
+                word &= word - 1;
+            }
+            pos += __shfl_sync(kFull, incl, 31);
+        }
+    }
+}
+
 // Gathers per-CTA segments into one contiguous array.  Blocks [0, nseg) handle
 // the hit segments, blocks [nseg, 2 nseg) the band segments of the same sweep.
 // Each block first loads all segment counts into shared memory and takes its
@@ -225,97 +331,213 @@ cudaError_t launch_compact_segments(const unsigned long long* src, const unsigne
         }                                                              \
     } while (0)
 
-bool build_edges(const unsigned long long* keys, long long nnz, long long n, long long L, Arena& ar,
-                 cudaStream_t s, EdgeResult& out, Failure& f) {
-    out = EdgeResult();
-    if (nnz == 0 || L < 2) return true;
-    // 1. point -> covering landmarks, ascending (transpose by a radix sort of swapped keys)
+// Stage 1: point -> covering landmarks (transpose by a radix sort of swapped
+// keys), pairs per smaller landmark and their exclusive scan j.lpre (L + 1).
+bool edges_transpose(EdgeJob& j, Arena& ar, cudaStream_t s, Failure& f) {
+    const long long nnz = j.nnz, n = j.n, L = j.L;
     unsigned long long *tk, *tk2;
     BM_ALLOC(tk, unsigned long long, nnz);
     BM_ALLOC(tk2, unsigned long long, nnz);
     note_launch();
-    swap_keys_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(keys, nnz, tk);
+    swap_keys_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(j.keys, nnz, tk);
     BM_TRY(cudaGetLastError());
-    unsigned long long* tsorted = nullptr;
-    BM_TRY(radix_sort_u64(tk, tk2, nnz, digit_shifts(bits_for(L - 1), bits_for(n - 1)), ar, s, &tsorted));
-    long long* toff;
-    BM_ALLOC(toff, long long, n + 1);
-    int* tlist;
-    BM_ALLOC(tlist, int, nnz);
-    BM_TRY(launch_csr_from_sorted(tsorted, nnz, n, toff, tlist, s));
-    // 2. pairs per smaller landmark -> landmark-range chunks of bounded size
+    BM_TRY(radix_sort_u64(tk, tk2, nnz, digit_shifts(bits_for(L - 1), bits_for(n - 1)), ar, s, &j.tsorted));
+    ar.release(j.tsorted == tk ? tk2 : tk);
+    BM_ALLOC(j.toff, long long, n + 1);
+    BM_ALLOC(j.tlist, int, nnz);
+    BM_TRY(launch_csr_from_sorted(j.tsorted, nnz, n, j.toff, j.tlist, s));
     unsigned long long* plc;
     BM_ALLOC(plc, unsigned long long, L + 1);
     BM_TRY(cudaMemsetAsync(plc, 0, sizeof(unsigned long long) * (L + 1), s));
     note_launch();
-    landmark_pair_counts_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(tsorted, toff, tlist, nnz, plc);
+    landmark_pair_counts_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(j.tsorted, j.toff, j.tlist, nnz, plc);
     BM_TRY(cudaGetLastError());
-    long long* lpre;
-    BM_ALLOC(lpre, long long, L + 1);
-    BM_TRY(exclusive_scan_i64((const long long*)plc, lpre, L, ar, s));
-    std::vector<long long> hpre((size_t)L + 1);
-    BM_TRY(cudaMemcpyAsync(hpre.data(), lpre, sizeof(long long) * (L + 1), cudaMemcpyDeviceToHost, s));
-    BM_TRY(cudaStreamSynchronize(s));
-    ar.release(lpre);
+    BM_ALLOC(j.lpre, long long, L + 1);
+    BM_TRY(exclusive_scan_i64((const long long*)plc, j.lpre, L, ar, s));
     ar.release(plc);
-    ar.release(tk2);
-    ar.release(tk);
+    return true;
+}
+
+namespace {
+constexpr long long kDefaultBitmapBytes = 1LL << 30;
+std::atomic<long long> g_bitmap_bytes{kDefaultBitmapBytes};
+}  // namespace
+
+long long edges_bitmap_budget() { return g_bitmap_bytes.load(); }
+
+long long edges_set_bitmap_budget(long long bytes) {
+    return g_bitmap_bytes.exchange(bytes == 0 ? kDefaultBitmapBytes : bytes);
+}
+
+long long edges_bitmap_words(long long L) { return (L + 31) / 32; }
+
+bool edges_choose_bitmap(long long L, long long P) {
+    if (edges_bitmap_budget() < 0) return false;
+    const double bytes = (double)L * (double)edges_bitmap_words(L) * 4.0;
+    return bytes <= 64.0 * (double)P;
+}
+
+long long edges_bitmap_rows(long long L) {
+    const long long row_bytes = edges_bitmap_words(L) * 4;
+    return std::max<long long>(1, std::min<long long>(L, edges_bitmap_budget() / row_bytes));
+}
+
+// Stage 2: deduplicate the Pc pairs (i, j), i in [i0, i1), witnessed by the
+// points.  Afterwards *j.count_dev (device) is the number of distinct pairs.
+bool edges_emit(EdgeJob& j, int i0, int i1, long long Pc, Arena& ar, cudaStream_t s, Failure& f) {
+    const long long n = j.n, L = j.L;
+    if (j.bitmap) {
+        const long long R = i1 - i0, W = edges_bitmap_words(L);
+        BM_ALLOC(j.bits, unsigned, R * W);
+        BM_TRY(cudaMemsetAsync(j.bits, 0, sizeof(unsigned) * R * W, s));
+        if (!j.bad) {
+            BM_ALLOC(j.bad, int, 1);
+            BM_TRY(cudaMemsetAsync(j.bad, 0, sizeof(int), s));
+        }
+        note_launch();
+        nerve_bits_kernel<<<grid_for(j.nnz * 32, 256), 256, 0, s>>>(j.tsorted, j.toff, j.tlist, j.nnz, n, i0, i1, W,
+                                                                     j.bits, j.bad);
+        BM_TRY(cudaGetLastError());
+        long long* cnt;
+        BM_ALLOC(cnt, long long, R + 1);
+        note_launch();
+        bitrow_counts_kernel<<<grid_for(R * 32, 256), 256, 0, s>>>(j.bits, R, W, cnt);
+        BM_TRY(cudaGetLastError());
+        BM_ALLOC(j.pos, long long, R + 1);
+        BM_TRY(exclusive_scan_i64(cnt, j.pos, R, ar, s));
+        ar.release(cnt);
+        j.count_dev = j.pos + R;
+        return true;
+    }
+    long long *pc, *poff;
+    BM_ALLOC(pc, long long, n + 1);
+    BM_ALLOC(poff, long long, n + 1);
+    note_launch();
+    chunk_pair_counts_kernel<<<grid_for(n, 256), 256, 0, s>>>(j.toff, j.tlist, n, i0, i1, pc);
+    BM_TRY(cudaGetLastError());
+    BM_TRY(exclusive_scan_i64(pc, poff, n, ar, s));
+    unsigned long long *pairs, *tmp;
+    BM_ALLOC(pairs, unsigned long long, Pc);
+    BM_ALLOC(tmp, unsigned long long, Pc);
+    note_launch();
+    emit_chunk_pairs_kernel<<<grid_for(n * 32, 256), 256, 0, s>>>(j.toff, j.tlist, n, i0, i1, poff, pairs);
+    BM_TRY(cudaGetLastError());
+    BM_TRY(radix_sort_u64(pairs, tmp, Pc, digit_shifts(bits_for(L - 1), bits_for(i1 - i0 - 1)), ar, s, &j.sorted));
+    long long* flags;
+    BM_ALLOC(flags, long long, Pc);
+    BM_ALLOC(j.pos, long long, Pc + 1);
+    note_launch();
+    unique_flags_kernel<<<grid_for(Pc, 256), 256, 0, s>>>(j.sorted, Pc, flags);
+    BM_TRY(cudaGetLastError());
+    BM_TRY(exclusive_scan_i64(flags, j.pos, Pc, ar, s));
+    ar.release(flags);
+    ar.release(j.sorted == pairs ? tmp : pairs);
+    ar.release(poff);
+    ar.release(pc);
+    j.count_dev = j.pos + Pc;
+    return true;
+}
+
+// Stage 3: write the distinct pairs of stage 2 (as landmark ordinals) to dst.
+bool edges_scatter(EdgeJob& j, int i0, int i1, long long Pc, int* dst, Arena& ar, cudaStream_t s, Failure& f) {
+    note_launch();
+    if (j.bitmap) {
+        const long long R = i1 - i0;
+        bitrow_extract_kernel<<<grid_for(R * 32, 256), 256, 0, s>>>(j.bits, R, edges_bitmap_words(j.L), i0, j.pos,
+                                                                    dst, j.bad);
+    } else {
+        unique_scatter_kernel<<<grid_for(Pc, 256), 256, 0, s>>>(j.sorted, Pc, j.pos, i0, dst);
+    }
+    BM_TRY(cudaGetLastError());
+    ar.release(j.pos);
+    ar.release(j.sorted);
+    ar.release(j.bits);
+    j.pos = nullptr;
+    j.sorted = nullptr;
+    j.bits = nullptr;
+    j.count_dev = nullptr;
+    return true;
+}
+
+bool edges_check(const EdgeJob& j, cudaStream_t s, Failure& f) {
+    if (!j.bad) return true;
+    int hb = 0;
+    BM_TRY(cudaMemcpyAsync(&hb, j.bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BM_TRY(cudaStreamSynchronize(s));
+    if (hb) {
+        f.status = BM_ERR_CUDA;
+        f.msg = "nerve pass: a cover list broke its invariants (code " + std::to_string(hb) + ")";
+        return false;
+    }
+    return true;
+}
+
+void edges_release(EdgeJob& j, Arena& ar) {
+    ar.release(j.tsorted);
+    ar.release(j.toff);
+    ar.release(j.tlist);
+    ar.release(j.lpre);
+    ar.release(j.bad);
+    j.tsorted = nullptr;
+    j.toff = nullptr;
+    j.tlist = nullptr;
+    j.lpre = nullptr;
+    j.bad = nullptr;
+}
+
+bool build_edges(const unsigned long long* keys, long long nnz, long long n, long long L, Arena& ar,
+                 cudaStream_t s, EdgeResult& out, Failure& f) {
+    out = EdgeResult();
+    if (nnz == 0 || L < 2) return true;
+    EdgeJob j;
+    j.keys = keys;
+    j.nnz = nnz;
+    j.n = n;
+    j.L = L;
+    if (!edges_transpose(j, ar, s, f)) return false;
+    std::vector<long long> hpre((size_t)L + 1);
+    BM_TRY(cudaMemcpyAsync(hpre.data(), j.lpre, sizeof(long long) * (L + 1), cudaMemcpyDeviceToHost, s));
+    BM_TRY(cudaStreamSynchronize(s));
     const long long P = hpre[(size_t)L];
     out.pairs = P;
-    if (P == 0) return true;
-    const long long kBudget = 1LL << 28;   // emitted pairs per chunk (32 B of scratch each)
-    std::vector<std::pair<int, int>> chunks;
-    for (long long i0 = 0; i0 < L;) {
-        long long i1 = i0 + 1;
-        // largest i1 with pairs(i0, i1) <= budget (at least one landmark)
-        long long lo = i0 + 1, hi = L;
-        while (lo < hi) {
-            const long long mid = (lo + hi + 1) / 2;
-            if (hpre[(size_t)mid] - hpre[(size_t)i0] <= kBudget) lo = mid;
-            else hi = mid - 1;
-        }
-        i1 = lo;
-        if (hpre[(size_t)i1] - hpre[(size_t)i0] >= (1LL << 32)) {
-            f.status = BM_ERR_CAPACITY;
-            f.msg = "nerve pass: one landmark witnesses more than 2^32 pairs";
-            return false;
-        }
-        chunks.emplace_back((int)i0, (int)i1);
-        i0 = i1;
+    if (P == 0) {
+        edges_release(j, ar);
+        return true;
     }
-    // 3. per chunk: count, emit, radix sort, deduplicate, append (chunks ascend in i)
-    long long* pc;
-    BM_ALLOC(pc, long long, n + 1);
-    long long* poff;
-    BM_ALLOC(poff, long long, n + 1);
+    j.bitmap = edges_choose_bitmap(L, P);
+    std::vector<std::pair<int, int>> chunks;
+    if (j.bitmap) {
+        const long long R = edges_bitmap_rows(L);
+        for (long long i0 = 0; i0 < L; i0 += R) chunks.emplace_back((int)i0, (int)std::min(L, i0 + R));
+    } else {
+        for (long long i0 = 0; i0 < L;) {
+            // largest i1 with pairs(i0, i1) <= budget (at least one landmark)
+            long long lo = i0 + 1, hi = L;
+            while (lo < hi) {
+                const long long mid = (lo + hi + 1) / 2;
+                if (hpre[(size_t)mid] - hpre[(size_t)i0] <= kEdgeChunkPairs) lo = mid;
+                else hi = mid - 1;
+            }
+            const long long i1 = lo;
+            if (hpre[(size_t)i1] - hpre[(size_t)i0] >= (1LL << 32)) {
+                f.status = BM_ERR_CAPACITY;
+                f.msg = "nerve pass: one landmark witnesses more than 2^32 pairs";
+                return false;
+            }
+            chunks.emplace_back((int)i0, (int)i1);
+            i0 = i1;
+        }
+    }
+    // per chunk: deduplicate, then append (chunks ascend in i)
     int* edges = nullptr;
     long long E = 0, cap = 0;
     for (const auto& ch : chunks) {
         const int i0 = ch.first, i1 = ch.second;
         const long long Pc = hpre[(size_t)i1] - hpre[(size_t)i0];
         if (Pc == 0) continue;
-        note_launch();
-        chunk_pair_counts_kernel<<<grid_for(n, 256), 256, 0, s>>>(toff, tlist, n, i0, i1, pc);
-        BM_TRY(cudaGetLastError());
-        BM_TRY(exclusive_scan_i64(pc, poff, n, ar, s));
-        unsigned long long *pairs, *tmp;
-        BM_ALLOC(pairs, unsigned long long, Pc);
-        BM_ALLOC(tmp, unsigned long long, Pc);
-        note_launch();
-        emit_chunk_pairs_kernel<<<grid_for(n * 32, 256), 256, 0, s>>>(toff, tlist, n, i0, i1, poff, pairs);
-        BM_TRY(cudaGetLastError());
-        unsigned long long* sorted = nullptr;
-        BM_TRY(radix_sort_u64(pairs, tmp, Pc, digit_shifts(bits_for(L - 1), bits_for(i1 - i0 - 1)), ar, s, &sorted));
-        long long* flags;
-        BM_ALLOC(flags, long long, Pc);
-        long long* pos;
-        BM_ALLOC(pos, long long, Pc + 1);
-        note_launch();
-        unique_flags_kernel<<<grid_for(Pc, 256), 256, 0, s>>>(sorted, Pc, flags);
-        BM_TRY(cudaGetLastError());
-        BM_TRY(exclusive_scan_i64(flags, pos, Pc, ar, s));
+        if (!edges_emit(j, i0, i1, Pc, ar, s, f)) return false;
         long long Ec = 0;
-        BM_TRY(cudaMemcpyAsync(&Ec, pos + Pc, sizeof(long long), cudaMemcpyDeviceToHost, s));
+        BM_TRY(cudaMemcpyAsync(&Ec, j.count_dev, sizeof(long long), cudaMemcpyDeviceToHost, s));
         BM_TRY(cudaStreamSynchronize(s));
         if (E + Ec > 0x7fffffffLL) {
             f.status = BM_ERR_CAPACITY;
@@ -331,19 +553,11 @@ bool build_edges(const unsigned long long* keys, long long nnz, long long n, lon
             edges = ne;
             cap = ncap;
         }
-        note_launch();
-        unique_scatter_kernel<<<grid_for(Pc, 256), 256, 0, s>>>(sorted, Pc, pos, i0, edges + 2 * E);
-        BM_TRY(cudaGetLastError());
+        if (!edges_scatter(j, i0, i1, Pc, edges + 2 * E, ar, s, f)) return false;
         E += Ec;
-        ar.release(pos);
-        ar.release(flags);
-        ar.release(tmp);
-        ar.release(pairs);
     }
-    ar.release(poff);
-    ar.release(pc);
-    ar.release(tlist);
-    ar.release(toff);
+    if (!edges_check(j, s, f)) return false;
+    edges_release(j, ar);
     out.edges = edges;
     out.n_edges = E;
     return true;

@@ -16,17 +16,30 @@ namespace bm {
 // Scratch/output allocator bound to one call: caller callbacks when given,
 // else stream-ordered cudaMallocAsync.  Frees whatever it still holds on
 // destruction (outputs are detached with take()).
+// Device memory of one call, freed (stream-ordered) when the Arena dies.  In
+// slab mode requests up to 16 MB are carved from a few blocks (4 MB, doubling
+// up to 64 MB): one allocator call per block instead of one per buffer;
+// release() does not return slab memory and slab buffers cannot be taken.
+// Larger requests stay buffers of their own in both modes.
 class Arena {
 public:
-    Arena(const bm_options* opt, cudaStream_t s) : opt_(opt), stream_(s) {}
+    Arena(const bm_options* opt, cudaStream_t s, bool slab = false) : opt_(opt), stream_(s), slab_(slab) {}
     ~Arena();
     void* get(size_t bytes);          // nullptr on failure; 256-byte aligned
-    void release(void* p);            // free now
-    void take(void* p);               // detach an output (caller frees it later)
+    void* get_standalone(size_t bytes);   // a buffer of its own even in slab mode
+    void release(void* p);            // free now (standalone buffers only)
+    bool take(void* p);               // detach a standalone output (caller frees it later)
+    const bm_options* options() const { return opt_; }
 private:
+    void* raw(size_t bytes);
     const bm_options* opt_;
     cudaStream_t stream_;
-    std::vector<void*> ptrs_;
+    bool slab_;
+    std::vector<void*> ptrs_;         // standalone buffers
+    std::vector<void*> slabs_;        // slab blocks
+    char* cur_ = nullptr;
+    size_t left_ = 0, next_ = 4u << 20;
+    static constexpr size_t kSlabMax = 16u << 20;
 };
 
 void device_free(const bm_options* opt, cudaStream_t s, void* p);
@@ -199,5 +212,35 @@ struct EdgeResult {
 };
 bool build_edges(const unsigned long long* sorted_keys, long long nnz, long long n_points,
                  long long n_landmarks, Arena& ar, cudaStream_t s, EdgeResult& out, Failure& f);
+
+// The stages of build_edges, for callers that run them over many builds with
+// one host synchronisation per stage: transpose (pair counts per landmark in
+// lpre), then per chunk of landmark rows emit (distinct count at *count_dev)
+// and scatter, then release.
+constexpr long long kEdgeChunkPairs = 1LL << 28;   // sort path: emitted pairs per chunk (32 B of scratch each)
+// bitmap path: bitmap bytes per chunk (process-wide; < 0 disables the bitmap path)
+long long edges_bitmap_budget();
+long long edges_set_bitmap_budget(long long bytes);   // returns the previous value; 0 = default (1 GiB)
+struct EdgeJob {
+    const unsigned long long* keys = nullptr;   // sorted membership keys (ordinal << 32 | point)
+    long long nnz = 0, n = 0, L = 0;
+    bool bitmap = false;                        // deduplicate with a row bitmap (else by sorting)
+    unsigned long long* tsorted = nullptr;     // swapped keys, sorted (point << 32 | ordinal)
+    long long* toff = nullptr;                 // point -> covering landmarks (CSR)
+    int* tlist = nullptr;
+    long long* lpre = nullptr;                 // L + 1: exclusive scan of the pairs per smaller landmark
+    unsigned long long* sorted = nullptr;      // sort path: sorted pair keys of the chunk
+    unsigned* bits = nullptr;                  // bitmap path: rows of the chunk, W words each
+    long long* pos = nullptr;                  // scan of first-of-run flags / of per-row bit counts
+    const long long* count_dev = nullptr;      // distinct pairs of the chunk (device)
+    int* bad = nullptr;                        // bitmap path: nonzero when an input broke a CSR invariant
+};
+bool edges_check(const EdgeJob& j, cudaStream_t s, Failure& f);   // synchronises; fails when *bad is set
+bool edges_transpose(EdgeJob& j, Arena& ar, cudaStream_t s, Failure& f);
+bool edges_choose_bitmap(long long L, long long P);   // bitmap when it is no larger than 64 bytes per pair
+long long edges_bitmap_rows(long long L);              // landmark rows per bitmap chunk
+bool edges_emit(EdgeJob& j, int i0, int i1, long long Pc, Arena& ar, cudaStream_t s, Failure& f);
+bool edges_scatter(EdgeJob& j, int i0, int i1, long long Pc, int* dst, Arena& ar, cudaStream_t s, Failure& f);
+void edges_release(EdgeJob& j, Arena& ar);
 
 }  // namespace bm
