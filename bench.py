@@ -28,6 +28,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Ball Mapper build s & distance evals/s (exact), TC split path vs plain FP32"
 UNIT = "evals/s"
+# DRAM bytes per tile-kernel launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# the ncu capture summarised in profiles/sweep_tc_kernel_mix32-n1M-d64_rows1024.md; a
+# step's sweep reads every point's operands once, so the figure holds for each launch of
+# this workload.  None where no capture of the current kernel exists.
+NCU_TRAFFIC = {("mix32-n1M-d64", "tc"): 292.0e6}
 
 
 def parse():
@@ -274,13 +279,14 @@ def run_ours(args):
     sweep_ms = sum(s["ms_sweep"] for s in flat)
     sweep_n = sum(s["sweep_launches"] for s in flat)
     tile_pairs = sum(s["tile_pairs"] for s in flat)
-    d_pad = 16 if d <= 16 else (32 if d <= 32 else (d + 63) // 64 * 64)
+    d_pad = binding.get_tile_config(d)["d_pad"]
     alg_flops = 2.0 * d * tile_pairs
     issued_flops = 2.0 * (3 * d_pad + 16) * tile_pairs
     achieved = alg_flops / (sweep_ms / 1000.0) / 1e12 if sweep_ms > 0 else 0.0
     peak = pk.get("bf16_tflops_sustained", 1700.0)
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if peak else None, "traffic": None,
+                "frac": achieved / peak if peak else None,
+                "traffic": NCU_TRAFFIC.get((args.workload, args.path)),
                 "kernel": "sweep_tc_kernel" if args.path == "tc" else "sweep_fp32_kernel",
                 "peak_kind": "%s bf16 sustained" % pk_kind,
                 "issued_tflops": issued_flops / (sweep_ms / 1000.0) / 1e12 if sweep_ms > 0 else 0.0,

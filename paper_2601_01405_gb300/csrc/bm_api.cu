@@ -768,7 +768,7 @@ bm_status members_and_edges(Arena& ar, cudaStream_t s, const bm_options& opt, lo
     if (tm) tm->mark();  // CSR done
     Failure f{BM_OK, ""};
     EdgeResult er;
-    if (!opt.skip_edges && !build_edges(sorted, nnz, n, L, ar, s, er, f)) return fail(f.status, f.msg);
+    if (!opt.skip_edges && !build_edges(sorted, offsets, nnz, n, L, ar, s, er, f)) return fail(f.status, f.msg);
     int* edges = er.edges;
     if (!edges) ALLOC(edges, int, 2);
     if (tm) tm->mark();  // edges done
@@ -1227,6 +1227,7 @@ bm_status build_batched(const bm_instance* inst, int count, const bm_options& op
         hP.p[i] = 0;
         if (!opt.skip_edges && t.nnz > 0 && t.L >= 2) {
             t.job.keys = sorted;
+            t.job.moff = t.offsets;
             t.job.nnz = t.nnz;
             t.job.n = it.n;
             t.job.L = t.L;
@@ -1280,7 +1281,8 @@ bm_status build_batched(const bm_instance* inst, int count, const bm_options& op
                 edges_release(t.job, iar);
                 Failure f{BM_OK, ""};
                 EdgeResult er;
-                if (!build_edges(t.job.keys, t.nnz, it.n, t.L, iar, s, er, f)) return tag(i, fail(f.status, f.msg));
+                if (!build_edges(t.job.keys, t.offsets, t.nnz, it.n, t.L, iar, s, er, f))
+                    return tag(i, fail(f.status, f.msg));
                 t.edges = er.edges;
                 t.E = er.n_edges;
                 edge_pairs = er.pairs;

@@ -133,26 +133,43 @@ __global__ void unique_scatter_kernel(const unsigned long long* keys, long long 
     }
 }
 
-// Bitmap deduplication.  One warp per entry t of the transposed CSR (point x,
-// position a in its ascending cover list): i = tlist[t]; when i lies in the
-// chunk [i0, i1), every later entry j of x's cover list sets bit j of row
-// i - i0 (W 32-bit words per row).  Lanes take consecutive entries (ascending
-// j), so lanes on the same word are contiguous: a segmented OR over the run
-// leaves the union with its first lane, which issues one atomicOr.
-// Inputs that break the CSR invariants (an index outside its array) are not
-// dereferenced: the kernel records them in *bad and skips the entry.
-__global__ void nerve_bits_kernel(const unsigned long long* tkeys, const long long* toff, const int* tlist,
-                                  long long nnz, long long n, int i0, int i1, long long W, unsigned* bits, int* bad) {
+// Bitmap deduplication.  One warp per membership (i, x) of landmark rows
+// [i0, i1), taken in row order from the sorted membership keys (entries
+// moff[i0] .. moff[i1]): the warp finds i in x's ascending cover list (binary
+// search) and every later entry j of that list sets bit j of row i - i0 (W
+// 32-bit words per row).  Walking the memberships in row order keeps the rows
+// being written few and L2-resident.  Lanes take consecutive entries
+// (ascending j), so lanes on the same word are contiguous: a segmented OR over
+// the run leaves the union with its first lane, which issues one atomicOr.
+// Inputs that break the CSR invariants (an index outside its array, i missing
+// from x's list) are not dereferenced: the kernel records them in *bad and
+// skips the entry.
+__global__ void nerve_bits_kernel(const unsigned long long* keys, const long long* moff, const long long* toff,
+                                  const int* tlist, long long nnz, long long n, int i0, int i1, long long W,
+                                  unsigned* bits, int* bad) {
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long t = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < nnz; t += warps) {
-        const int i = tlist[t];
-        if (i < i0 || i >= i1) continue;
-        const long long x = (long long)(tkeys[t] >> 32);
-        const long long end = x < n ? toff[x + 1] : -1;
-        if (end < t + 1 || end > nnz) {
-            if (lane == 0 && end < t + 1) atomicOr(bad, 1);
-            if (lane == 0 && end > nnz) atomicOr(bad, 2);
+    const long long e0 = moff[i0], e1 = moff[i1];
+    if (e0 < 0 || e1 > nnz || e0 > e1) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(bad, 16);
+        return;
+    }
+    for (long long e = e0 + (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < e1; e += warps) {
+        const unsigned long long key = keys[e];
+        const int i = (int)(key >> 32);
+        const long long x = (long long)(key & 0xffffffffull);
+        if (i < i0 || i >= i1 || x >= n) {
+            if (lane == 0) atomicOr(bad, 1);
+            continue;
+        }
+        const long long b0 = toff[x], end = toff[x + 1];
+        if (b0 < 0 || end > nnz || b0 >= end) {
+            if (lane == 0) atomicOr(bad, 2);
+            continue;
+        }
+        const long long t = lower_bound_i32(tlist, b0, end, i);
+        if (t >= end || tlist[t] != i) {
+            if (lane == 0) atomicOr(bad, 32);
             continue;
         }
         unsigned* row = bits + (long long)(i - i0) * W;
@@ -342,7 +359,6 @@ bool edges_transpose(EdgeJob& j, Arena& ar, cudaStream_t s, Failure& f) {
     swap_keys_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(j.keys, nnz, tk);
     BM_TRY(cudaGetLastError());
     BM_TRY(radix_sort_u64(tk, tk2, nnz, digit_shifts(bits_for(L - 1), bits_for(n - 1)), ar, s, &j.tsorted));
-    ar.release(j.tsorted == tk ? tk2 : tk);
     BM_ALLOC(j.toff, long long, n + 1);
     BM_ALLOC(j.tlist, int, nnz);
     BM_TRY(launch_csr_from_sorted(j.tsorted, nnz, n, j.toff, j.tlist, s));
@@ -355,6 +371,9 @@ bool edges_transpose(EdgeJob& j, Arena& ar, cudaStream_t s, Failure& f) {
     BM_ALLOC(j.lpre, long long, L + 1);
     BM_TRY(exclusive_scan_i64((const long long*)plc, j.lpre, L, ar, s));
     ar.release(plc);
+    ar.release(tk);   // the sorted swapped keys (one of the two) are not needed after this
+    ar.release(tk2);
+    j.tsorted = nullptr;
     return true;
 }
 
@@ -395,8 +414,8 @@ bool edges_emit(EdgeJob& j, int i0, int i1, long long Pc, Arena& ar, cudaStream_
             BM_TRY(cudaMemsetAsync(j.bad, 0, sizeof(int), s));
         }
         note_launch();
-        nerve_bits_kernel<<<grid_for(j.nnz * 32, 256), 256, 0, s>>>(j.tsorted, j.toff, j.tlist, j.nnz, n, i0, i1, W,
-                                                                     j.bits, j.bad);
+        nerve_bits_kernel<<<grid_for(j.nnz * 32, 256), 256, 0, s>>>(j.keys, j.moff, j.toff, j.tlist, j.nnz, n, i0, i1,
+                                                                     W, j.bits, j.bad);
         BM_TRY(cudaGetLastError());
         long long* cnt;
         BM_ALLOC(cnt, long long, R + 1);
@@ -485,12 +504,13 @@ void edges_release(EdgeJob& j, Arena& ar) {
     j.bad = nullptr;
 }
 
-bool build_edges(const unsigned long long* keys, long long nnz, long long n, long long L, Arena& ar,
-                 cudaStream_t s, EdgeResult& out, Failure& f) {
+bool build_edges(const unsigned long long* keys, const long long* moff, long long nnz, long long n, long long L,
+                 Arena& ar, cudaStream_t s, EdgeResult& out, Failure& f) {
     out = EdgeResult();
     if (nnz == 0 || L < 2) return true;
     EdgeJob j;
     j.keys = keys;
+    j.moff = moff;
     j.nnz = nnz;
     j.n = n;
     j.L = L;

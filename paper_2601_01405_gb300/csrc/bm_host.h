@@ -210,7 +210,8 @@ struct EdgeResult {
     long long n_edges = 0;
     long long pairs = 0;
 };
-bool build_edges(const unsigned long long* sorted_keys, long long nnz, long long n_points,
+// sorted_keys: memberships (ordinal << 32 | point) sorted; moff: their CSR row offsets (L + 1).
+bool build_edges(const unsigned long long* sorted_keys, const long long* moff, long long nnz, long long n_points,
                  long long n_landmarks, Arena& ar, cudaStream_t s, EdgeResult& out, Failure& f);
 
 // The stages of build_edges, for callers that run them over many builds with
@@ -223,9 +224,10 @@ long long edges_bitmap_budget();
 long long edges_set_bitmap_budget(long long bytes);   // returns the previous value; 0 = default (1 GiB)
 struct EdgeJob {
     const unsigned long long* keys = nullptr;   // sorted membership keys (ordinal << 32 | point)
+    const long long* moff = nullptr;            // their CSR row offsets (L + 1)
     long long nnz = 0, n = 0, L = 0;
     bool bitmap = false;                        // deduplicate with a row bitmap (else by sorting)
-    unsigned long long* tsorted = nullptr;     // swapped keys, sorted (point << 32 | ordinal)
+    unsigned long long* tsorted = nullptr;     // swapped keys, sorted (stage 1 only)
     long long* toff = nullptr;                 // point -> covering landmarks (CSR)
     int* tlist = nullptr;
     long long* lpre = nullptr;                 // L + 1: exclusive scan of the pairs per smaller landmark
