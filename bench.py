@@ -33,6 +33,8 @@ UNIT = "evals/s"
 # step's sweep reads every point's operands once, so the figure holds for each launch of
 # this workload.  None where no capture of the current kernel exists.
 NCU_TRAFFIC = {("mix32-n1M-d64", "tc"): 292.0e6}
+DTYPES = {"tc": "bf16x3-split/fp32-acc/fp64-recheck", "tc16": "f16-scaled/fp32-acc/fp64-recheck",
+          "fp32": "f32/fp64-recheck", "auto": "f16-scaled or bf16x3-split/fp32-acc/fp64-recheck"}
 
 
 def parse():
@@ -42,7 +44,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="mix32-n1M-d64")
-    ap.add_argument("--path", choices=["tc", "fp32"], default="tc")
+    ap.add_argument("--path", choices=["auto", "tc", "tc16", "fp32"], default="auto")
     ap.add_argument("--compare-steps", type=int, default=1, help="timed steps of the FP32 comparison path (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline sample")
@@ -281,22 +283,30 @@ def run_ours(args):
     tile_pairs = sum(s["tile_pairs"] for s in flat)
     d_pad = binding.get_tile_config(d)["d_pad"]
     alg_flops = 2.0 * d * tile_pairs
-    issued_flops = 2.0 * (3 * d_pad + 16) * tile_pairs
+    # tensor-core products per coordinate: three for the bf16 split, one for fp16 (the
+    # path each build finished on; the automatic path reports it per build)
+    issued_flops = sum(2.0 * ((1 if s["path"] == binding.BM_PATH_TC_FP16 else 3) * d_pad + 16) * s["tile_pairs"]
+                       for s in flat)
     achieved = alg_flops / (sweep_ms / 1000.0) / 1e12 if sweep_ms > 0 else 0.0
     peak = pk.get("bf16_tflops_sustained", 1700.0)
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if peak else None,
                 "traffic": NCU_TRAFFIC.get((args.workload, args.path)),
-                "kernel": "sweep_tc_kernel" if args.path == "tc" else "sweep_fp32_kernel",
+                "kernel": "sweep_fp32_kernel" if args.path == "fp32" else "sweep_tc_kernel",
                 "peak_kind": "%s bf16 sustained" % pk_kind,
                 "issued_tflops": issued_flops / (sweep_ms / 1000.0) / 1e12 if sweep_ms > 0 else 0.0,
                 "issued_frac": (issued_flops / (sweep_ms / 1000.0) / 1e12) / peak if sweep_ms > 0 and peak else None,
                 "avg_launch_ms": sweep_ms / sweep_n if sweep_n else None, "launches": sweep_n,
                 "sweep_share_of_step": sweep_ms / ms if ms else None}
 
+    # arithmetic actually used (the automatic path reports the path each build finished on)
+    used = sorted({s["path"] for s in flat})
+    by_code = {binding.BM_PATH_TC_SPLIT3: "tc", binding.BM_PATH_TC_FP16: "tc16", binding.BM_PATH_FP32: "fp32"}
+    dtype_used = " + ".join(DTYPES[by_code[u]] for u in used if u in by_code) or DTYPES[args.path]
+
     extra = {}
     # comparison: plain FP32 CUDA-core path, same workload
-    if args.compare_steps > 0 and args.path == "tc":
+    if args.compare_steps > 0 and args.path != "fp32":
         ms32, st32 = timed("fp32", 1, args.compare_steps)
         ev32 = sum(s["distance_evals"] for s in st32[0])
         f32 = [s for st in st32 for s in st]
@@ -336,7 +346,7 @@ def run_ours(args):
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16x3-split/fp32-acc/fp64-recheck" if args.path == "tc" else "f32/fp64-recheck",
+            "vs_baseline": None, "dtype": dtype_used,
             "data": "synthetic (seeded generator, same recipe and sizes as the workload)",
             "config": config_of(w, {"path": args.path, "landmarks": L_per_eps, "build_s": build_s,
                                     "evals_per_step": evals_per_step,

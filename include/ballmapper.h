@@ -57,11 +57,20 @@ typedef enum {
     BM_ERR_UNSUPPORTED = 6 /* the device is not sm_103 (GB300) or lacks a needed feature */
 } bm_status;
 
-/* Distance-tile arithmetic.  Both are exact: pairs whose approximate value
- * lies within the proven error band of eps^2 are re-decided in FP64. */
+/* Distance-tile arithmetic.  All are exact: pairs whose approximate value
+ * lies within the proven error band of eps^2 are re-decided in FP64, so the
+ * results are identical on every path; the paths differ in speed and in how
+ * many pairs fall into the band. */
 typedef enum {
-    BM_PATH_TC_SPLIT3 = 0, /* tcgen05 tensor cores: BF16 hi/lo split products, FP32 accumulation in TMEM */
-    BM_PATH_FP32 = 1       /* plain FP32 CUDA-core tiles (comparison path) */
+    BM_PATH_TC_SPLIT3 = 0, /* tcgen05 tensor cores: BF16 hi/lo split, three products, FP32 accumulation in TMEM */
+    BM_PATH_FP32 = 1,      /* plain FP32 CUDA-core tiles (comparison path) */
+    BM_PATH_TC_FP16 = 2,   /* tcgen05 tensor cores: one FP16 product on coordinates scaled by a power of two,
+                            * FP32 accumulation; about 3x fewer tensor-core operations than the split with a
+                            * band about 2^6 times wider (best when eps^2 is far from most squared distances) */
+    BM_PATH_TC_AUTO = 3    /* default.  bm_build: starts on TC_FP16 and moves to TC_SPLIT3 for the rest of the
+                            * greedy once band pairs exceed 2e-4 of the tile pairs of a chunk of steps;
+                            * bm_build_batched: TC_FP16; range queries: TC_SPLIT3.  stats.path reports the
+                            * path the build finished on. */
 } bm_path;
 
 /* Allocation callbacks: return device (or, for host outputs, ignored) memory
@@ -117,7 +126,7 @@ typedef struct {
     bm_stats stats;
 } bm_graph;
 
-/* Fill *opt with defaults (default stream, tensor-core path, device I/O). */
+/* Fill *opt with defaults (default stream, automatic tensor-core path, device I/O). */
 BM_API void bm_options_init(bm_options* opt);
 
 /* Exact range query, Sec. 5, Def. 5.1: out row j = { i : ||X_i - Q_j|| < eps }.

@@ -22,8 +22,8 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "lib", "libballmapper.so")
 
 BM_OK, BM_ERR_ARG, BM_ERR_CUDA, BM_ERR_NOMEM, BM_ERR_CAPACITY, BM_ERR_TIMEOUT, BM_ERR_UNSUPPORTED = range(7)
-BM_PATH_TC_SPLIT3, BM_PATH_FP32 = 0, 1
-PATHS = {"tc": BM_PATH_TC_SPLIT3, "fp32": BM_PATH_FP32}
+BM_PATH_TC_SPLIT3, BM_PATH_FP32, BM_PATH_TC_FP16, BM_PATH_TC_AUTO = 0, 1, 2, 3
+PATHS = {"tc": BM_PATH_TC_SPLIT3, "fp32": BM_PATH_FP32, "tc16": BM_PATH_TC_FP16, "auto": BM_PATH_TC_AUTO}
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
@@ -239,7 +239,7 @@ def _as_input(x, d_expected=None):
     return (a.ctypes.data if a.size else None), a.shape[0], a.shape[1], a, True
 
 
-def bm_range_query(X, Q, eps: float, path: str = "tc", stream=None):
+def bm_range_query(X, Q, eps: float, path: str = "auto", stream=None):
     """Exact range query R_eps(q) for every row q of Q over the points X.
 
     Device tensors in -> torch CUDA tensors out; host arrays in -> numpy out.
@@ -274,7 +274,7 @@ def bm_range_query(X, Q, eps: float, path: str = "tc", stream=None):
     return off, ids, st.as_dict()
 
 
-def bm_build(X, eps: float, path: str = "tc", batch: int = 0, stream=None, skip_edges: bool = False):
+def bm_build(X, eps: float, path: str = "auto", batch: int = 0, stream=None, skip_edges: bool = False):
     """Exact Ball Mapper: landmarks (greedy index order), CSR memberships, nerve edges.
 
     Device tensor in -> dict of torch CUDA tensors; host array in -> dict of numpy arrays.
@@ -312,7 +312,7 @@ def bm_build(X, eps: float, path: str = "tc", batch: int = 0, stream=None, skip_
             "stats": g.stats.as_dict()}
 
 
-def bm_build_batched(instances, path: str = "tc", batch: int = 0, stream=None, skip_edges: bool = False):
+def bm_build_batched(instances, path: str = "auto", batch: int = 0, stream=None, skip_edges: bool = False):
     """Many independent exact builds in one call; the greedy loops of all instances
     run inside one CUDA graph.  instances: sequence of (X, eps), all CUDA tensors
     (results as torch tensors) or all host arrays (results as numpy arrays).

@@ -137,7 +137,8 @@ bm_status check_device(int path) {
     if (major != 10 || minor != 3)
         return fail(BM_ERR_UNSUPPORTED, "libballmapper is built for sm_103 (GB300); device is sm_" +
                                             std::to_string(major) + std::to_string(minor));
-    if (path != BM_PATH_FP32 && path != BM_PATH_TC_SPLIT3) return fail(BM_ERR_ARG, "unknown path");
+    if (path != BM_PATH_FP32 && path != BM_PATH_TC_SPLIT3 && path != BM_PATH_TC_FP16 && path != BM_PATH_TC_AUTO)
+        return fail(BM_ERR_ARG, "unknown path");
     return BM_OK;
 }
 
@@ -204,25 +205,49 @@ const float* stage_input(const float* X, long long rows, int d, bool host_io, Ar
     return dX;
 }
 
-// Allocate and fill the tile operands of one point set.
-bm_status prepare(const float* x, long long rows, int d, double eps2, bool a_side, bool want_tc, Arena& ar,
+bool is_tc_path(int path) { return path == BM_PATH_TC_SPLIT3 || path == BM_PATH_TC_FP16; }
+
+int prec_for(int path) {
+    return path == BM_PATH_TC_SPLIT3 ? kPrecSplit : (path == BM_PATH_TC_FP16 ? kPrecFp16 : kPrecNone);
+}
+
+// Allocate and fill the tile operands of one point set: phi and norms always; the
+// bf16 split (kPrecSplit) here; the fp16 operands (kPrecFp16) only once the scale
+// is known (finish_fp16, after the norms have been read back).
+bm_status prepare(const float* x, long long rows, int d, double eps2, bool a_side, int prec, Arena& ar,
                   unsigned* max_norm_bits, int* bad, cudaStream_t s, Prepared& p) {
     p.x = x;
     p.rows = rows;
     p.d = d;
-    const TileConfig tcfg = tile_config_for(d);
+    p.prec = prec;
+    const TileConfig tcfg = tile_config_for(d, prec == kPrecFp16 ? 1 : 3);
     p.d_pad = tcfg.d_pad;
     p.ck = tcfg.ck;
     p.nt = tcfg.nt;
     p.bbuf = tcfg.bbuf;
     p.astg = tcfg.astg;
     ALLOC(p.phi, float, std::max<long long>(rows, 1));
-    if (want_tc) {
-        ALLOC(p.hi, __nv_bfloat16, std::max<long long>(rows, 1) * p.d_pad);
-        ALLOC(p.lo, __nv_bfloat16, std::max<long long>(rows, 1) * p.d_pad);
+    if (prec != kPrecNone) {
+        ALLOC(p.hi, __nv_bfloat16, std::max<long long>(rows, 1) * p.d_pad);   // bf16 or fp16 bits
         ALLOC(p.aug, __nv_bfloat16, std::max<long long>(rows, 1) * 16);
     }
-    TRY_CUDA(launch_prep(x, rows, d, eps2, a_side, want_tc, p, max_norm_bits, bad, s));
+    if (prec == kPrecSplit) ALLOC(p.lo, __nv_bfloat16, std::max<long long>(rows, 1) * p.d_pad);
+    TRY_CUDA(launch_prep(x, rows, d, eps2, a_side, prec == kPrecSplit, p, max_norm_bits, bad, s));
+    return BM_OK;
+}
+
+// After the norms are known on the host: fp16 operands at the chosen scale (fp16 path
+// only), then the band half-width.  Returns the scale exponent used.
+bm_status finish_prep(DeviceState* st, int path, int d, double eps2, double eps, bool same_sets, float max_norm,
+                      Prepared* a, bool a_side_a, Prepared* b, cudaStream_t s) {
+    int e = 0;
+    if (path == BM_PATH_TC_FP16) {
+        e = fp16_scale_exp((double)max_norm, eps);
+        if (a) TRY_CUDA(launch_prep16(a->x, a->rows, d, eps2, a_side_a, e, *a, s));
+        if (b) TRY_CUDA(launch_prep16(b->x, b->rows, d, eps2, true, e, *b, s));
+    }
+    const int d_pad = a ? a->d_pad : (b ? b->d_pad : d);
+    TRY_CUDA(launch_delta(st, path, d, d_pad, eps2, same_sets, s, e));
     return BM_OK;
 }
 
@@ -385,7 +410,7 @@ bm_status sweep_stage(SweepDesc& sd, DeviceState* st, int path, SweepOut& o, uns
                                      sd.sink, greedy, overflow_bit, greedy, s));
         return BM_OK;
     }
-    const bool tc = path == BM_PATH_TC_SPLIT3;
+    const bool tc = is_tc_path(path);
     sd.sink.count = count;
     sd.sink.cap = o.cap;
     sd.sink.band_n = &st->band_n;
@@ -434,17 +459,29 @@ struct GreedyCtx {
     SweepDesc sd;
     int S = 0, sms = 0, path = 0;
     bool tc = false;
+    // automatic path: start on the fp16 tiles, move to the bf16 split when the band
+    // recheck costs more than the cheaper tiles save
+    bool auto_switch = false;
+    double eps2 = 0.0;
+    int switched_at = -1;            // greedy step of the switch (-1: none)
+    unsigned long long band0 = 0, pairs0 = 0;
 };
+
+// Band pairs per tile pair above which the fp16 tiles lose to the split: a band
+// pair costs an FP64 distance (~0.35-0.7 ns at d = 64-128 on GB300), while the fp16
+// tiles save ~0.1 ps per pair.
+constexpr double kAutoBandFraction = 2e-4;
 
 bm_status greedy_setup(const Prepared& pts, double eps2, int path, int S, Arena& ar, cudaStream_t s, DeviceState* st,
                        unsigned long long step_cap, unsigned long long mem_cap, const IvfIndex* ivf,
                        const float* phi_perm, int nprobe, GreedyCtx& c) {
     const long long n = pts.rows;
     const int d = pts.d;
-    const bool tc = path == BM_PATH_TC_SPLIT3;
+    const bool tc = is_tc_path(path);
     c.S = S;
     c.path = path;
     c.tc = tc;
+    c.eps2 = eps2;
     GreedyBuffers& g = c.g;
     g.st = st;
     const long long words_n = (n + 31) / 32;
@@ -470,14 +507,18 @@ bm_status greedy_setup(const Prepared& pts, double eps2, int path, int S, Arena&
     g.cand.nt = pts.nt;
     g.cand.bbuf = pts.bbuf;
     g.cand.astg = pts.astg;
+    g.cand.prec = pts.prec;
+    g.cand.scale_exp = pts.scale_exp;
     ALLOC(g.cand.phi, float, S);
     if (tc) {
         ALLOC(g.cand.hi, __nv_bfloat16, (long long)S * pts.d_pad);
-        ALLOC(g.cand.lo, __nv_bfloat16, (long long)S * pts.d_pad);
         ALLOC(g.cand.aug, __nv_bfloat16, (long long)S * 16);
         TRY_CUDA(cudaMemsetAsync(g.cand.hi, 0, sizeof(__nv_bfloat16) * S * pts.d_pad, s));
-        TRY_CUDA(cudaMemsetAsync(g.cand.lo, 0, sizeof(__nv_bfloat16) * S * pts.d_pad, s));
         TRY_CUDA(cudaMemsetAsync(g.cand.aug, 0, sizeof(__nv_bfloat16) * S * 16, s));
+        if (pts.prec == kPrecSplit) {
+            ALLOC(g.cand.lo, __nv_bfloat16, (long long)S * pts.d_pad);
+            TRY_CUDA(cudaMemsetAsync(g.cand.lo, 0, sizeof(__nv_bfloat16) * S * pts.d_pad, s));
+        }
     }
     c.sms = device_sm_count();
     bm_status ars = alloc_sweep_out(ar, tc, step_cap, c.sms, c.so);
@@ -525,7 +566,45 @@ bm_status greedy_enqueue_step(GreedyCtx& c, const Prepared& pts, Arena& ar, Swee
 // an overflowing buffer and redo the step, until no uncovered point remains.
 // With resume set the first state read comes before any new step (the steps so
 // far ran elsewhere, e.g. in a graph).
-bm_status greedy_drive(GreedyCtx& c, const Prepared& pts, Arena& ar, cudaStream_t s, HostState& hs,
+// Move a greedy in progress from the fp16 tiles to the bf16 split: split operands of
+// the points (replacing the fp16 ones), candidate operand rows for the split, and
+// the split's band half-width.  Every step is exact on either path.
+bm_status switch_to_split(GreedyCtx& c, Prepared& pts, Arena& ar, cudaStream_t s, int step) {
+    DeviceState* st = c.g.st;
+    int* bad;
+    ALLOC(bad, int, 1);
+    TRY_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    Prepared p2;
+    bm_status rs = prepare(pts.x, pts.rows, pts.d, c.eps2, false, kPrecSplit, ar, &st->max_norm_bits, bad, s, p2);
+    if (rs != BM_OK) return rs;
+    ar.release(pts.hi);
+    ar.release(pts.aug);
+    ar.release(pts.phi);
+    pts = p2;   // c.sd.b points at pts
+    const int S = c.S;
+    Prepared& cand = c.g.cand;
+    ar.release(cand.hi);
+    ar.release(cand.aug);
+    ALLOC(cand.hi, __nv_bfloat16, (long long)S * pts.d_pad);
+    ALLOC(cand.lo, __nv_bfloat16, (long long)S * pts.d_pad);
+    ALLOC(cand.aug, __nv_bfloat16, (long long)S * 16);
+    TRY_CUDA(cudaMemsetAsync(cand.hi, 0, sizeof(__nv_bfloat16) * S * pts.d_pad, s));
+    TRY_CUDA(cudaMemsetAsync(cand.lo, 0, sizeof(__nv_bfloat16) * S * pts.d_pad, s));
+    TRY_CUDA(cudaMemsetAsync(cand.aug, 0, sizeof(__nv_bfloat16) * S * 16, s));
+    cand.d_pad = pts.d_pad;
+    cand.ck = pts.ck;
+    cand.nt = pts.nt;
+    cand.bbuf = pts.bbuf;
+    cand.astg = pts.astg;
+    cand.prec = kPrecSplit;
+    cand.scale_exp = 0;
+    TRY_CUDA(launch_delta(st, BM_PATH_TC_SPLIT3, pts.d, pts.d_pad, c.eps2, true, s, 0));
+    c.path = BM_PATH_TC_SPLIT3;
+    c.switched_at = step;
+    return BM_OK;
+}
+
+bm_status greedy_drive(GreedyCtx& c, Prepared& pts, Arena& ar, cudaStream_t s, HostState& hs,
                        unsigned long long& step_cap, unsigned long long& mem_cap, DeviceState& h,
                        SweepTimer& stimer, bool resume) {
     GreedyBuffers& g = c.g;
@@ -573,24 +652,35 @@ bm_status greedy_drive(GreedyCtx& c, const Prepared& pts, Arena& ar, cudaStream_
             continue;
         }
         if (h.done) break;
+        if (c.auto_switch && c.path == BM_PATH_TC_FP16) {
+            const unsigned long long db = h.band_pairs - c.band0, dp = h.tile_pairs - c.pairs0;
+            c.band0 = h.band_pairs;
+            c.pairs0 = h.tile_pairs;
+            if (dp > 0 && (double)db > kAutoBandFraction * (double)dp) {
+                bm_status rs2 = switch_to_split(c, pts, ar, s, (int)h.steps);
+                if (rs2 != BM_OK) return rs2;
+            }
+        }
         chunk = std::min(chunk * 2, 64);
     }
     return BM_OK;
 }
 
-bm_status greedy_pass(const Prepared& pts, double eps2, int path, int S, Arena& ar, cudaStream_t s,
+bm_status greedy_pass(Prepared& pts, double eps2, int path, bool auto_switch, int S, Arena& ar, cudaStream_t s,
                       DeviceState* st, HostState& hs, unsigned long long& step_cap, unsigned long long& mem_cap,
                       bool* retry, int** landmarks_out, unsigned long long** mem_keys_out, DeviceState& final_state,
-                      SweepTimer& stimer, const IvfIndex* ivf, const float* phi_perm, int nprobe) {
+                      SweepTimer& stimer, const IvfIndex* ivf, const float* phi_perm, int nprobe, int* path_used) {
     *retry = false;
     GreedyCtx c;
     bm_status rs = greedy_setup(pts, eps2, path, S, ar, s, st, step_cap, mem_cap, ivf, phi_perm, nprobe, c);
     if (rs != BM_OK) return rs;
+    c.auto_switch = auto_switch;
     rs = greedy_drive(c, pts, ar, s, hs, step_cap, mem_cap, final_state, stimer, false);
     if (rs != BM_OK) return rs;
     release_sweep_out(ar, c.so, false);
     *landmarks_out = c.g.landmarks;
     *mem_keys_out = c.g.mem_keys;
+    *path_used = c.path;
     return BM_OK;
 }
 
@@ -611,8 +701,10 @@ bm_status range_core(const float* X, long long n, int d, const float* Q, long lo
     cudaStream_t s = (cudaStream_t)opt.stream;
     const bool host_io = opt.host_io != 0;
     const double eps2 = (double)eps * (double)eps;
-    const bool tc = opt.path == BM_PATH_TC_SPLIT3 && ivf == nullptr;
-    const int path = ivf ? (int)BM_PATH_FP32 : opt.path;
+    // automatic path: a single sweep cannot change course, so range queries take the split
+    const int req = opt.path == BM_PATH_TC_AUTO ? (int)BM_PATH_TC_SPLIT3 : opt.path;
+    const bool tc = is_tc_path(req) && ivf == nullptr;
+    const int path = ivf ? (int)BM_PATH_FP32 : req;
     Timer tm(s);
     tm.mark();
     SweepTimer stimer(s);
@@ -642,15 +734,24 @@ bm_status range_core(const float* X, long long n, int d, const float* Q, long lo
             TRY_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
             Prepared px, pq;
             // inverted-file mode: the points enter the tiles in cell order
-            rs = prepare(ivf ? ivf->xperm : dX, n, d, eps2, false, tc, ar, &st->max_norm_bits, bad, s, px);
+            const int prec = tc ? prec_for(path) : kPrecNone;
+            rs = prepare(ivf ? ivf->xperm : dX, n, d, eps2, false, prec, ar, &st->max_norm_bits, bad, s, px);
             if (rs != BM_OK) return rs;
-            rs = prepare(dQ, m, d, eps2, true, tc, ar, &st->max_norm_q_bits, bad, s, pq);
+            rs = prepare(dQ, m, d, eps2, true, prec, ar, &st->max_norm_q_bits, bad, s, pq);
             if (rs != BM_OK) return rs;
-            TRY_CUDA(launch_delta(st, path, d, px.d_pad, eps2, false, s));
             int hbad = 0;
+            unsigned hnorm[2] = {0u, 0u};
             TRY_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+            TRY_CUDA(cudaMemcpyAsync(hnorm, &st->max_norm_bits, sizeof(hnorm), cudaMemcpyDeviceToHost, s));
             TRY_CUDA(cudaStreamSynchronize(s));
             if (hbad) return fail(BM_ERR_ARG, "input holds NaN or Inf");
+            {
+                float nx, nq;
+                std::memcpy(&nx, &hnorm[0], sizeof(float));
+                std::memcpy(&nq, &hnorm[1], sizeof(float));
+                rs = finish_prep(st, path, d, eps2, (double)eps, false, std::max(nx, nq), &px, false, &pq, s);
+                if (rs != BM_OK) return rs;
+            }
             unsigned long long cap = (unsigned long long)std::min<long long>(std::max<long long>(n, m) * 4 + (1 << 20),
                                                                               (long long)n * m);
             if (tc) cap = std::max<unsigned long long>(cap, (unsigned long long)device_sm_count() * 4096);
@@ -856,8 +957,12 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
     cudaStream_t s = (cudaStream_t)opt.stream;
     const bool host_io = opt.host_io != 0;
     const double eps2 = (double)eps * (double)eps;
-    const bool tc = opt.path == BM_PATH_TC_SPLIT3 && ivf == nullptr;
-    const int path = ivf ? (int)BM_PATH_FP32 : opt.path;
+    // automatic path: start on the fp16 tiles; the greedy moves to the split when the
+    // band gets expensive (greedy_drive)
+    const bool auto_switch = opt.path == BM_PATH_TC_AUTO && ivf == nullptr && fixed_lm == nullptr;
+    const int req = opt.path == BM_PATH_TC_AUTO ? (int)BM_PATH_TC_FP16 : opt.path;
+    const bool tc = is_tc_path(req) && ivf == nullptr;
+    int path = ivf ? (int)BM_PATH_FP32 : req;
     Timer tm(s);
     tm.mark();  // 0
     SweepTimer stimer(s);
@@ -892,19 +997,26 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
             TRY_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
             TRY_CUDA(cudaMemsetAsync(st, 0, sizeof(DeviceState), s));
             Prepared px;
-            rs = prepare(dX, n, d, eps2, false, tc, ar, &st->max_norm_bits, bad, s, px);
+            rs = prepare(dX, n, d, eps2, false, tc ? prec_for(path) : kPrecNone, ar, &st->max_norm_bits, bad, s, px);
             if (rs != BM_OK) return rs;
             // inverted-file mode: phi of the cell-ordered copy of the points for the scan
             Prepared pperm;
             if (ivf) {
-                rs = prepare(ivf->xperm, n, d, eps2, false, false, ar, &st->max_norm_bits, bad, s, pperm);
+                rs = prepare(ivf->xperm, n, d, eps2, false, kPrecNone, ar, &st->max_norm_bits, bad, s, pperm);
                 if (rs != BM_OK) return rs;
             }
-            TRY_CUDA(launch_delta(st, path, d, px.d_pad, eps2, true, s));
             int hbad = 0;
+            unsigned hnorm = 0u;
             TRY_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+            TRY_CUDA(cudaMemcpyAsync(&hnorm, &st->max_norm_bits, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
             TRY_CUDA(cudaStreamSynchronize(s));
             if (hbad) return fail(BM_ERR_ARG, "input holds NaN or Inf");
+            {
+                float nx;
+                std::memcpy(&nx, &hnorm, sizeof(float));
+                rs = finish_prep(st, path, d, eps2, (double)eps, true, nx, &px, false, nullptr, s);
+                if (rs != BM_OK) return rs;
+            }
             tm.mark();  // 1: prep done
             unsigned long long step_cap = (unsigned long long)std::min<long long>((long long)S * n, 1LL << 22);
             if (tc) step_cap = std::max<unsigned long long>(step_cap, (unsigned long long)device_sm_count() * 2048);
@@ -920,7 +1032,7 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
                 ALLOC(qx, float, std::max<long long>(nL, 1) * d);
                 TRY_CUDA(launch_gather_rows(dX, landmarks, nL, d, qx, s));
                 Prepared pq;
-                rs = prepare(qx, nL, d, eps2, true, false, ar, &st->max_norm_q_bits, bad, s, pq);
+                rs = prepare(qx, nL, d, eps2, true, kPrecNone, ar, &st->max_norm_q_bits, bad, s, pq);
                 if (rs != BM_OK) return rs;
                 const int sms = device_sm_count();
                 unsigned long long cap = (unsigned long long)std::max<long long>(4 * n, 1LL << 20);
@@ -968,9 +1080,12 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
                         TRY_CUDA(cudaMemcpyAsync(&st->s_next, &s_first, sizeof(int), cudaMemcpyHostToDevice, s));
                         TRY_CUDA(cudaStreamSynchronize(s));
                     }
-                    rs = greedy_pass(px, eps2, path, S, ar, s, st, hs, step_cap, mem_cap, &retry, &landmarks,
-                                     &mem_keys, fin, stimer, ivf, ivf ? pperm.phi : nullptr, nprobe);
+                    int path_used = path;
+                    rs = greedy_pass(px, eps2, path, auto_switch, S, ar, s, st, hs, step_cap, mem_cap, &retry,
+                                     &landmarks, &mem_keys, fin, stimer, ivf, ivf ? pperm.phi : nullptr, nprobe,
+                                     &path_used);
                     if (rs != BM_OK) return rs;
+                    path = path_used;
                     if (!retry) break;
                     if (attempt == 5) return fail(BM_ERR_CAPACITY, "greedy buffers kept overflowing");
                 }
@@ -1053,9 +1168,9 @@ bm_status batch_prep(BatchItem& it, const bm_instance& in, const bm_options& opt
     const float* dX = stage_input(in.X, in.n, in.d, opt.host_io != 0, ar, s, &rs);
     if (rs != BM_OK) return rs;
     it.st = st;
-    rs = prepare(dX, in.n, in.d, it.eps2, false, tc, ar, &st->max_norm_bits, bad, s, it.px);
+    rs = prepare(dX, in.n, in.d, it.eps2, false, tc ? prec_for(path) : kPrecNone, ar, &st->max_norm_bits, bad, s,
+                 it.px);
     if (rs != BM_OK) return rs;
-    TRY_CUDA(launch_delta(st, path, in.d, it.px.d_pad, it.eps2, true, s));
     return BM_OK;
 }
 
@@ -1097,8 +1212,10 @@ bm_status build_batched(const bm_instance* inst, int count, const bm_options& op
     if (S < 32 || S > 2048 || S % 32) return fail(BM_ERR_ARG, "batch must be a multiple of 32 in [32, 2048]");
     cudaStream_t s = (cudaStream_t)opt.stream;
     const bool host_io = opt.host_io != 0;
-    const bool tc = opt.path == BM_PATH_TC_SPLIT3;
-    const int path = opt.path;
+    // automatic path: the graph's loops cannot change course; the fp16 tiles win on
+    // typical batches (many small, well-separated instances)
+    const int path = opt.path == BM_PATH_TC_AUTO ? (int)BM_PATH_TC_FP16 : opt.path;
+    const bool tc = is_tc_path(path);
     Timer tm(s);
     tm.mark();  // 0
     SweepTimer stimer(s);
@@ -1134,10 +1251,21 @@ bm_status build_batched(const bm_instance* inst, int count, const bm_options& op
     }
     {
         std::vector<int> hbad(std::max(count, 1));
+        std::vector<DeviceState> hs0(std::max(count, 1));
         TRY_CUDA(cudaMemcpyAsync(hbad.data(), bads, sizeof(int) * std::max(count, 1), cudaMemcpyDeviceToHost, s));
+        TRY_CUDA(cudaMemcpyAsync(hs0.data(), sts, sizeof(DeviceState) * std::max(count, 1), cudaMemcpyDeviceToHost, s));
         TRY_SYNC(s, "prep of all instances");
         for (int i = 0; i < count; ++i)
             if (hbad[i]) return tag(i, fail(BM_ERR_ARG, "input holds NaN or Inf"));
+        for (int i = 0; i < count; ++i) {   // fp16 operands at each instance's scale, band half-width
+            BatchItem& it = items[i];
+            if (it.n == 0) continue;
+            float nx;
+            std::memcpy(&nx, &hs0[i].max_norm_bits, sizeof(float));
+            bm_status rs = finish_prep(it.st, path, it.d, it.eps2, (double)inst[i].eps, true, nx, &it.px, false,
+                                       nullptr, s);
+            if (rs != BM_OK) return tag(i, rs);
+        }
     }
     tm.mark();  // 1: prep done
     // 2. greedy buffers (the state starts zeroed: the first step requests 32 candidates)
@@ -1345,7 +1473,7 @@ extern "C" {
 void bm_options_init(bm_options* opt) {
     if (!opt) return;
     std::memset(opt, 0, sizeof(*opt));
-    opt->path = BM_PATH_TC_SPLIT3;
+    opt->path = BM_PATH_TC_AUTO;
 }
 
 const char* bm_status_string(bm_status s) {

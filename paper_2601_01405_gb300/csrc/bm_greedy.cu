@@ -111,8 +111,9 @@ __global__ void __launch_bounds__(kSelThreads) greedy_select_kernel(
 }
 
 // One warp per candidate: copy its float32 row, phi and, for the tensor-core
-// path, its bf16 hi/lo rows and A-side augmentation (the B-side row with the
-// halves [0,3) and [3,6) swapped) into the contiguous candidate operands.
+// paths, its 16-bit operand rows (bf16 hi and lo, or fp16 hi alone) and A-side
+// augmentation (the B-side row with the halves [0,3) and [3,6) swapped) into
+// the contiguous candidate operands.
 __global__ void __launch_bounds__(256) greedy_gather_kernel(
     const DeviceState* st, const int* __restrict__ cand_ids, const float* __restrict__ X,
     const float* __restrict__ phi, int d, float* __restrict__ cand_x, float* __restrict__ cand_phi, int want_tc,
@@ -128,7 +129,7 @@ __global__ void __launch_bounds__(256) greedy_gather_kernel(
         const int w = d_pad / 2;  // bf16 pairs per row
         for (int i = lane; i < w; i += 32) {
             cH[(long long)s * w + i] = H[id * w + i];
-            cLo[(long long)s * w + i] = Lo[id * w + i];
+            if (Lo) cLo[(long long)s * w + i] = Lo[id * w + i];   // no lo half in fp16 mode
         }
         if (lane < 16) {
             const int src = lane < 3 ? lane + 3 : (lane < 6 ? lane - 3 : lane);

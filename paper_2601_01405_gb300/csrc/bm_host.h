@@ -65,7 +65,10 @@ struct Prepared {
     __nv_bfloat16* aug = nullptr;      // rows x 16: the -phi pieces and ones (see prep kernel)
     int d_pad = 0;
     int ck = 0, nt = 0, bbuf = 0, astg = 0;   // tensor-core tile shape chosen for this d
+    int prec = 0;                      // kPrecNone / kPrecSplit (bf16 hi, lo) / kPrecFp16 (fp16 in hi, no lo)
+    int scale_exp = 0;                 // fp16: operands hold x * 2^scale_exp
 };
+constexpr int kPrecNone = 0, kPrecSplit = 1, kPrecFp16 = 2;
 
 // Tensor-core tile configuration for one point dimension d: padded K extent
 // (a multiple of ck, >= d), K chunk per shared-memory stage, point-tile width,
@@ -73,9 +76,10 @@ struct Prepared {
 struct TileConfig {
     int d_pad, ck, nt, bbuf, astg;
 };
-TileConfig tile_config_for(int d);          // the override for d if one is set, else the built-in choice
-TileConfig tile_config_builtin(int d);
-bool tile_config_check(int d, const TileConfig& c, std::string* why);
+// prod: tensor-core products per coordinate (3 for the bf16 split, 1 for fp16)
+TileConfig tile_config_for(int d, int prod = 3);   // the override for d if one is set, else the built-in choice
+TileConfig tile_config_builtin(int d, int prod = 3);
+bool tile_config_check(int d, const TileConfig& c, std::string* why, int prod = 3);
 bool tile_config_set(int d, const TileConfig* c, std::string* why);   // nullptr: back to the built-in choice
 int tile_shapes(TileConfig* out, int max);  // the compiled (ck, nt, bbuf, astg) shapes, d_pad = 0
 
@@ -83,7 +87,11 @@ int tile_shapes(TileConfig* out, int max);  // the compiled (ck, nt, bbuf, astg)
 cudaError_t launch_prep(const float* x, long long rows, int d, double eps2, bool a_side, bool want_tc,
                         Prepared& out, unsigned* max_norm_bits, int* bad_flag, cudaStream_t s);
 cudaError_t launch_delta(DeviceState* st, int path, int d, int d_pad, double eps2, bool same_sets,
-                         cudaStream_t s);
+                         cudaStream_t s, int scale_exp = 0);
+// fp16 operands of an already prepared set (hi, aug allocated as 2-byte arrays)
+cudaError_t launch_prep16(const float* x, long long rows, int d, double eps2, bool a_side, int scale_exp,
+                          Prepared& p, cudaStream_t s);
+int fp16_scale_exp(double max_norm, double eps);
 
 struct IvfIndex;
 

@@ -16,6 +16,10 @@
 //   B side (points):   aug = [1, 1, 1, -p1, -p2, -p3, 0 ...]
 //   A side (queries):  aug = [-p1, -p2, -p3, 1, 1, 1, 0 ...]
 // with phi ~ p1 + p2 + p3 (three bf16 pieces of the FP64 value).
+#include <cuda_fp16.h>
+
+#include <cmath>
+
 #include "bm_host.h"
 
 namespace bm {
@@ -81,6 +85,66 @@ __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ x, 
     }
 }
 
+// FP16 operands (BM_PATH_TC_FP16): xs = x 2^e (exact in FP64), hi = fp16(xs) rounded to
+// nearest, and the augmentation block with three fp16 pieces of
+// phi_s = ||xs||^2 / 2 - eps^2 4^e / 4 (FP64), in the same positions as the bf16 block.
+// The scale 2^e keeps every operand and phi piece inside the fp16 range.
+__global__ void __launch_bounds__(256) prep16_kernel(const float* __restrict__ x, long long rows, int d, int d_pad,
+                                                     double scale, double eps2s, int a_side,
+                                                     __half* __restrict__ hi, __half* __restrict__ aug) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long warps_total = (long long)gridDim.x * 8;
+    for (long long r = (long long)blockIdx.x * 8 + warp; r < rows; r += warps_total) {
+        const float* xr = x + r * d;
+        double s = 0.0;
+        for (int i = lane; i < d_pad; i += 32) {
+            const double v = i < d ? (double)xr[i] * scale : 0.0;
+            s += v * v;
+            hi[r * d_pad + i] = __double2half(v);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+        if (lane < 16) {
+            const double phi = 0.5 * s - 0.25 * eps2s;
+            const __half p1 = __double2half(phi);
+            const double r1 = phi - (double)__half2float(p1);
+            const __half p2 = __double2half(r1);
+            const double r2 = r1 - (double)__half2float(p2);
+            const __half p3 = __double2half(r2);
+            __half v = __float2half_rn(0.f);
+            const int pos = a_side ? lane : (lane < 3 ? lane + 3 : (lane < 6 ? lane - 3 : lane));
+            if (pos == 0) v = __hneg(p1);
+            else if (pos == 1) v = __hneg(p2);
+            else if (pos == 2) v = __hneg(p3);
+            else if (pos < 6) v = __float2half_rn(1.f);
+            aug[r * 16 + lane] = v;
+        }
+    }
+}
+
+cudaError_t launch_prep16(const float* x, long long rows, int d, double eps2, bool a_side, int scale_exp,
+                          Prepared& p, cudaStream_t s) {
+    if (rows == 0) return cudaSuccess;
+    long long blocks = (rows + 7) / 8;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    const double scale = ldexp(1.0, scale_exp);
+    p.scale_exp = scale_exp;
+    note_launch();
+    prep16_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, rows, d, p.d_pad, scale, eps2 * scale * scale, a_side ? 1 : 0,
+                                                   reinterpret_cast<__half*>(p.hi), reinterpret_cast<__half*>(p.aug));
+    return cudaGetLastError();
+}
+
+// Power-of-two scale for the fp16 operands: max(N, eps) * 2^e < 128, so that every
+// scaled coordinate and |phi_s| <= 3 * 128^2 / 4 stay far inside the fp16 range.
+int fp16_scale_exp(double max_norm, double eps) {
+    const double m = max_norm > eps ? max_norm : eps;
+    if (!(m > 0.0) || !std::isfinite(m)) return 0;
+    int k = 0;
+    std::frexp(m, &k);   // m < 2^k
+    return 7 - k;
+}
+
 cudaError_t launch_prep(const float* x, long long rows, int d, double eps2, bool a_side, bool want_tc,
                         Prepared& out, unsigned* max_norm_bits, int* bad_flag, cudaStream_t s) {
     if (rows == 0) return cudaSuccess;
@@ -111,15 +175,34 @@ cudaError_t launch_prep(const float* x, long long rows, int d, double eps2, bool
 //     delta = 2 [2 K 2^-23 (1.02 N_a N_b + 1.01 (Phi_a + Phi_b)) + 3 2^-16 N_a N_b
 //                + 2^-23 (Phi_a + Phi_b)]
 // Both bounds carry a safety factor of 2 and a tiny absolute term for underflow.
-__global__ void delta_kernel(DeviceState* st, int path, int d, int d_pad, double eps2, int same_sets) {
-    const double Nb = (double)__uint_as_float(st->max_norm_bits);
-    const double Na = same_sets ? Nb : (double)__uint_as_float(st->max_norm_q_bits);
-    const double Pa = fmax(Na * Na * 0.5 - 0.25 * eps2, 0.25 * eps2);
-    const double Pb = fmax(Nb * Nb * 0.5 - 0.25 * eps2, 0.25 * eps2);
+//
+// FP16 path (operands scaled by 2^e; N, Phi and delta in scaled units): with
+// hi = fp16(x), |x - hi| <= 2^-11 |x| + 2^-25 (normal / subnormal rounding), so
+// |q.x - hq.hx| <= 2^-10 (1 + 2^-10) N_a N_b + 2^-24 sqrt(d_pad) (N_a + N_b) + d_pad 2^-49;
+// products hq.hx are exact in FP32; K = d_pad + 6 accumulated terms charged as above;
+// three fp16 phi pieces: 2^-33 |phi| + 2^-25 each; FP64 phi: 2^-42 N^2.
+//     delta = 2 [E_rep + 2 K 2^-23 (1.002 N_a N_b + 1.001 (Phi_a + Phi_b) + 2^-24 sqrt(d_pad)(N_a + N_b))
+//                + 2^-33 (Phi_a + Phi_b) + 2^-22 + 2^-42 (N_a^2 + N_b^2)]
+__global__ void delta_kernel(DeviceState* st, int path, int d, int d_pad, double eps2, int same_sets,
+                             int scale_exp) {
+    const double sc = ldexp(1.0, scale_exp);
+    const double Nb = (double)__uint_as_float(st->max_norm_bits) * sc;
+    const double Na = same_sets ? Nb : (double)__uint_as_float(st->max_norm_q_bits) * sc;
+    const double e2 = eps2 * sc * sc;
+    const double Pa = fmax(Na * Na * 0.5 - 0.25 * e2, 0.25 * e2);
+    const double Pb = fmax(Nb * Nb * 0.5 - 0.25 * e2, 0.25 * e2);
     const double u23 = 1.0 / 8388608.0, u16 = 1.0 / 65536.0;
     double delta;
     if (path == BM_PATH_FP32) {
         delta = 2.0 * (d + 8) * u23 * (Na * Nb + Pa + Pb);
+    } else if (path == BM_PATH_TC_FP16) {
+        const double rd = sqrt((double)d_pad), K = d_pad + 6.0;
+        const double u24 = u23 * 0.5;
+        const double e_rep = ldexp(1.0 + ldexp(1.0, -10), -10) * Na * Nb + u24 * rd * (Na + Nb) + d_pad * ldexp(1.0, -49);
+        const double e_acc = 2.0 * K * u23 * (1.002 * Na * Nb + 1.001 * (Pa + Pb) + u24 * rd * (Na + Nb));
+        const double e_aug = ldexp(1.0, -33) * (Pa + Pb) + ldexp(1.0, -22);
+        const double e_phi = ldexp(1.0, -42) * (Na * Na + Nb * Nb);
+        delta = 2.0 * (e_rep + e_acc + e_aug + e_phi);
     } else {
         const double K = 3.0 * d_pad + 6.0;
         delta = 2.0 * (2.0 * K * u23 * (1.02 * Na * Nb + 1.01 * (Pa + Pb)) + 3.0 * u16 * Na * Nb +
@@ -130,9 +213,9 @@ __global__ void delta_kernel(DeviceState* st, int path, int d, int d_pad, double
 }
 
 cudaError_t launch_delta(DeviceState* st, int path, int d, int d_pad, double eps2, bool same_sets,
-                         cudaStream_t s) {
+                         cudaStream_t s, int scale_exp) {
     note_launch();
-    delta_kernel<<<1, 1, 0, s>>>(st, path, d, d_pad, eps2, same_sets ? 1 : 0);
+    delta_kernel<<<1, 1, 0, s>>>(st, path, d, d_pad, eps2, same_sets ? 1 : 0, scale_exp);
     return cudaGetLastError();
 }
 

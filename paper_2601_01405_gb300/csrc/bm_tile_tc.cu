@@ -139,9 +139,10 @@ __device__ __forceinline__ unsigned long long sdesc(uint32_t addr, uint32_t span
            ((unsigned long long)((8u * span) >> 4) << 32) | (1ull << 46) | ((unsigned long long)layout << 61);
 }
 
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16 (or both F16), both K-major.
+__host__ __device__ constexpr uint32_t idesc_f16kind(int M, int N, bool bf16) {
+    return (1u << 4) | (bf16 ? (1u << 7) | (1u << 10) : 0u) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma(uint32_t d, unsigned long long a, unsigned long long b, uint32_t idesc,
@@ -176,13 +177,14 @@ __device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32
 
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Byte sizes of the shared-memory regions for a configuration.
+// Byte sizes of the shared-memory regions for a configuration.  PROD = 3: the
+// point tile holds hi and lo chunks (bf16 split); PROD = 1: hi chunks only (fp16).
 struct Layout {
     int CK, NT, BBUF, ASTG, nc;
     uint32_t a_chunk, b_chunk, b_aug, b_bytes, b_stride, a_off, ctl_off, total;
 };
 
-__host__ __device__ inline Layout make_layout(int CK, int NT, int BBUF, int ASTG, int d_pad) {
+__host__ __device__ inline Layout make_layout(int CK, int NT, int BBUF, int ASTG, int d_pad, int PROD = 3) {
     Layout L;
     L.CK = CK;
     L.NT = NT;
@@ -192,7 +194,7 @@ __host__ __device__ inline Layout make_layout(int CK, int NT, int BBUF, int ASTG
     L.a_chunk = 128u * CK * 2u;
     L.b_chunk = (uint32_t)NT * CK * 2u;
     L.b_aug = (uint32_t)NT * 32u;
-    L.b_bytes = 2u * L.nc * L.b_chunk + L.b_aug;
+    L.b_bytes = (PROD == 3 ? 2u : 1u) * L.nc * L.b_chunk + L.b_aug;
     L.b_stride = (L.b_bytes + 1023u) & ~1023u;
     L.a_off = BBUF * L.b_stride;
     L.ctl_off = L.a_off + ASTG * L.a_chunk;
@@ -200,7 +202,7 @@ __host__ __device__ inline Layout make_layout(int CK, int NT, int BBUF, int ASTG
     return L;
 }
 
-template <int CK, int NT, int BBUF, int ASTG>
+template <int CK, int NT, int BBUF, int ASTG, int PROD>
 __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_constant__ TcArgs p) {
     const bool seg_mode = p.sink.seg_counts != nullptr;
     if (seg_mode && threadIdx.x == 0) {
@@ -213,8 +215,9 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const Layout L = make_layout(CK, NT, BBUF, ASTG, p.d_pad);
+    const Layout L = make_layout(CK, NT, BBUF, ASTG, p.d_pad, PROD);
     const int nc = L.nc;
+    const int nq = PROD == 3 ? 2 * nc : nc;   // query-tile chunks before the augmentation chunk
     Ctl* ctl = reinterpret_cast<Ctl*>(smem + L.ctl_off);
     const uint32_t sbase = su32(smem);
 
@@ -225,7 +228,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
     const long long b_tiles = (p.n + NT - 1) / NT;
     const long long items = b_tiles * n_groups;
     constexpr uint32_t kTmemCols = 2 * NT;
-    constexpr uint32_t kIdesc = idesc_bf16(128, NT);
+    constexpr uint32_t kIdesc = idesc_f16kind(128, NT, PROD == 3);
     constexpr uint32_t kSpan = CK * 2;
     int* gerr = &p.st->error;
 
@@ -280,20 +283,20 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
                 const uint32_t bb = sbase + b_buf * L.b_stride;
                 for (int c = 0; c < nc; ++c) {
                     tma_load(bb + c * L.b_chunk, &p.b_hi, &ctl->b_full[b_buf], c * CK, yb);
-                    tma_load(bb + (nc + c) * L.b_chunk, &p.b_lo, &ctl->b_full[b_buf], c * CK, yb);
+                    if (PROD == 3) tma_load(bb + (nc + c) * L.b_chunk, &p.b_lo, &ctl->b_full[b_buf], c * CK, yb);
                 }
-                tma_load(bb + 2 * nc * L.b_chunk, &p.b_aug, &ctl->b_full[b_buf], 0, yb);
+                tma_load(bb + nq * L.b_chunk, &p.b_aug, &ctl->b_full[b_buf], 0, yb);
                 b_last[b_buf] = (int)b_ph;
                 if (++b_buf == BBUF) { b_buf = 0; b_ph ^= 1; }
                 for (long long at = at0; ok && at < at1; ++at) {
                     const int ya = (int)(at * 128);
-                    for (int q = 0; q <= 2 * nc; ++q) {
+                    for (int q = 0; q <= nq; ++q) {
                         if (!bar_wait(&ctl->a_empty[a_st], a_ph ^ 1, abort_flag, gerr)) { ok = false; break; }
                         const uint32_t dst = sbase + L.a_off + a_st * L.a_chunk;
                         if (q < nc) {
                             bar_expect_tx(&ctl->a_full[a_st], L.a_chunk);
                             tma_load(dst, &p.a_hi, &ctl->a_full[a_st], q * CK, ya);
-                        } else if (q < 2 * nc) {
+                        } else if (q < nq) {
                             bar_expect_tx(&ctl->a_full[a_st], L.a_chunk);
                             tma_load(dst, &p.a_lo, &ctl->a_full[a_st], (q - nc) * CK, ya);
                         } else {
@@ -328,7 +331,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
                     fence_after();
                     const uint32_t dacc = tmem + t_buf * NT;
                     uint32_t acc = 0;
-                    for (int q = 0; q <= 2 * nc; ++q) {
+                    for (int q = 0; q <= nq; ++q) {
                         if (!bar_wait(&ctl->a_full[a_st], a_ph, abort_flag, gerr)) { ok = false; break; }
                         fence_after();
                         const uint32_t aa = sbase + L.a_off + a_st * L.a_chunk;
@@ -338,16 +341,17 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
                                 const unsigned long long ad = sdesc(aa + k * 32, kSpan);
                                 mma(dacc, ad, sdesc(bb + q * L.b_chunk + k * 32, kSpan), kIdesc, acc);
                                 acc = 1;
-                                mma(dacc, ad, sdesc(bb + (nc + q) * L.b_chunk + k * 32, kSpan), kIdesc, 1);
+                                if (PROD == 3)
+                                    mma(dacc, ad, sdesc(bb + (nc + q) * L.b_chunk + k * 32, kSpan), kIdesc, 1);
                             }
-                        } else if (q < 2 * nc) {
+                        } else if (q < nq) {
                             const int c = q - nc;
 #pragma unroll
                             for (int k = 0; k < CK / 16; ++k)
                                 mma(dacc, sdesc(aa + k * 32, kSpan), sdesc(bb + c * L.b_chunk + k * 32, kSpan),
                                     kIdesc, 1);
                         } else {
-                            mma(dacc, sdesc(aa, 32), sdesc(bb + 2 * nc * L.b_chunk, 32), kIdesc, 1);
+                            mma(dacc, sdesc(aa, 32), sdesc(bb + nq * L.b_chunk, 32), kIdesc, 1);
                         }
                         mma_commit(&ctl->a_empty[a_st]);
                         if (++a_st == ASTG) { a_st = 0; a_ph ^= 1; }
@@ -475,14 +479,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 bool make_map(CUtensorMap* m, const void* base, long long rows, int cols, int box_cols, int box_rows,
-              CUtensorMapSwizzle sw) {
+              CUtensorMapSwizzle sw, bool fp16 = false) {
     auto enc = encode_fn();
     if (!enc) return false;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)(rows > 0 ? rows : 1)};
     cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
     cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+    CUresult r = enc(m, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                     const_cast<void*>(base), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -515,13 +520,13 @@ constexpr TileConfig kShapes[] = {
 std::mutex g_tile_mu;
 std::map<int, TileConfig> g_tile_override;
 
-template <int CK, int NT, int BBUF, int ASTG>
+template <int CK, int NT, int BBUF, int ASTG, int PROD>
 cudaError_t launch_cfg(TcArgs& args, long long a_rows_max, cudaStream_t stream, std::string* why, int* grid_out) {
-    const Layout L0 = make_layout(CK, NT, BBUF, ASTG, args.d_pad);
+    const Layout L0 = make_layout(CK, NT, BBUF, ASTG, args.d_pad, PROD);
     // at least 120 KB so that two CTAs never share an SM (each holds 2*NT TMEM columns)
     Layout L = L0;
     if (L.total < 120u * 1024u) L.total = 120u * 1024u;
-    auto kern = sweep_tc_kernel<CK, NT, BBUF, ASTG>;
+    auto kern = sweep_tc_kernel<CK, NT, BBUF, ASTG, PROD>;
     static int attr_bytes = 0;
     if (attr_bytes < (int)L.total) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
@@ -562,7 +567,7 @@ int tile_shapes(TileConfig* out, int max) {
     return n;
 }
 
-bool tile_config_check(int d, const TileConfig& c, std::string* why) {
+bool tile_config_check(int d, const TileConfig& c, std::string* why, int prod) {
     auto bad = [&](const char* m) {
         if (why) *why = m;
         return false;
@@ -575,7 +580,7 @@ bool tile_config_check(int d, const TileConfig& c, std::string* why) {
     for (const TileConfig& k : kShapes)
         compiled = compiled || (k.ck == c.ck && k.nt == c.nt && k.bbuf == c.bbuf && k.astg == c.astg);
     if (!compiled) return bad("(ck, nt, bbuf, astg) is not a compiled tile shape");
-    if (make_layout(c.ck, c.nt, c.bbuf, c.astg, c.d_pad).total > kMaxSmem)
+    if (make_layout(c.ck, c.nt, c.bbuf, c.astg, c.d_pad, prod).total > kMaxSmem)
         return bad("the tile shape does not fit in shared memory for this d_pad");
     return true;
 }
@@ -585,28 +590,29 @@ bool tile_config_check(int d, const TileConfig& c, std::string* why) {
 // possible.  Measured on GB300 (2048 query rows x 200k points): the 256-wide
 // point tile with one buffer beats the double-buffered 128-wide one by 1.5x at
 // d_pad = 128, while a single buffer costs only ~3% at d_pad = 64.
-TileConfig tile_config_builtin(int d) {
+TileConfig tile_config_builtin(int d, int prod) {
     if (d <= 16) return {16, 16, 256, 2, 8};
     if (d <= 32) return {32, 32, 256, 2, 8};
     const int d_pad = (d + 63) / 64 * 64;
     const TileConfig order[] = {{d_pad, 64, 256, 2, 5}, {d_pad, 64, 256, 1, 5}, {d_pad, 64, 128, 2, 5},
                                 {d_pad, 64, 128, 1, 4}};
     for (const TileConfig& c : order)
-        if (make_layout(c.ck, c.nt, c.bbuf, c.astg, c.d_pad).total <= kMaxSmem) return c;
+        if (make_layout(c.ck, c.nt, c.bbuf, c.astg, c.d_pad, prod).total <= kMaxSmem) return c;
     return {d_pad, 64, 64, 1, 4};
 }
 
-TileConfig tile_config_for(int d) {
+TileConfig tile_config_for(int d, int prod) {
     {
         std::lock_guard<std::mutex> lk(g_tile_mu);
         auto it = g_tile_override.find(d);
         if (it != g_tile_override.end()) return it->second;
     }
-    return tile_config_builtin(d);
+    return tile_config_builtin(d, prod);
 }
 
 bool tile_config_set(int d, const TileConfig* c, std::string* why) {
-    if (c && !tile_config_check(d, *c, why)) return false;
+    // an override must fit both tensor-core representations (the split needs more room)
+    if (c && !tile_config_check(d, *c, why, 3)) return false;
     std::lock_guard<std::mutex> lk(g_tile_mu);
     if (c) g_tile_override[d] = *c;
     else g_tile_override.erase(d);
@@ -618,11 +624,17 @@ cudaError_t launch_sweep_tc(const SweepDesc& s, cudaStream_t stream, std::string
     if (s.a_rows_max == 0 || s.b->rows == 0) return cudaSuccess;
     const int d_pad = s.b->d_pad;
     const TileConfig cfg = {d_pad, s.b->ck, s.b->nt, s.b->bbuf, s.b->astg};
-    if (s.a->d_pad != d_pad) {
-        if (why) *why = "query and point operands were prepared with different paddings";
+    if (s.a->d_pad != d_pad || s.a->prec != s.b->prec) {
+        if (why) *why = "query and point operands were prepared differently";
         return cudaErrorInvalidValue;
     }
-    if (!tile_config_check(s.b->d, cfg, why)) return cudaErrorNotSupported;
+    const bool fp16 = s.b->prec == kPrecFp16;
+    if (!fp16 && s.b->prec != kPrecSplit) {
+        if (why) *why = "operands were not prepared for the tensor cores";
+        return cudaErrorInvalidValue;
+    }
+    const int prod = fp16 ? 1 : 3;
+    if (!tile_config_check(s.b->d, cfg, why, prod)) return cudaErrorNotSupported;
     TcArgs args;
     memset(&args, 0, sizeof(args));
     const int CK = cfg.ck, NT = cfg.nt;
@@ -633,25 +645,25 @@ cudaError_t launch_sweep_tc(const SweepDesc& s, cudaStream_t stream, std::string
     struct MapCache {
         const void* key[6];
         long long arows, brows;
-        int d_pad, NT, CK;
+        int d_pad, NT, CK, prod;
         CUtensorMap maps[6];
         bool valid;
     };
     static thread_local MapCache cache = {};
     const void* key[6] = {s.a->hi, s.a->lo, s.a->aug, s.b->hi, s.b->lo, s.b->aug};
     bool hit = cache.valid && cache.arows == arows && cache.brows == brows && cache.d_pad == d_pad && cache.NT == NT &&
-               cache.CK == CK;
+               cache.CK == CK && cache.prod == prod;
     for (int i = 0; hit && i < 6; ++i) hit = cache.key[i] == key[i];
     if (hit) {
         args.a_hi = cache.maps[0]; args.a_lo = cache.maps[1]; args.a_aug = cache.maps[2];
         args.b_hi = cache.maps[3]; args.b_lo = cache.maps[4]; args.b_aug = cache.maps[5];
     } else {
-        bool ok = make_map(&args.a_hi, s.a->hi, arows, d_pad, CK, 128, sw) &&
-                  make_map(&args.a_lo, s.a->lo, arows, d_pad, CK, 128, sw) &&
-                  make_map(&args.a_aug, s.a->aug, arows, 16, 16, 128, CU_TENSOR_MAP_SWIZZLE_32B) &&
-                  make_map(&args.b_hi, s.b->hi, brows, d_pad, CK, NT, sw) &&
-                  make_map(&args.b_lo, s.b->lo, brows, d_pad, CK, NT, sw) &&
-                  make_map(&args.b_aug, s.b->aug, brows, 16, 16, NT, CU_TENSOR_MAP_SWIZZLE_32B);
+        bool ok = make_map(&args.a_hi, s.a->hi, arows, d_pad, CK, 128, sw, fp16) &&
+                  (fp16 || make_map(&args.a_lo, s.a->lo, arows, d_pad, CK, 128, sw)) &&
+                  make_map(&args.a_aug, s.a->aug, arows, 16, 16, 128, CU_TENSOR_MAP_SWIZZLE_32B, fp16) &&
+                  make_map(&args.b_hi, s.b->hi, brows, d_pad, CK, NT, sw, fp16) &&
+                  (fp16 || make_map(&args.b_lo, s.b->lo, brows, d_pad, CK, NT, sw)) &&
+                  make_map(&args.b_aug, s.b->aug, brows, 16, 16, NT, CU_TENSOR_MAP_SWIZZLE_32B, fp16);
         if (!ok) {
             cache.valid = false;
             if (why) *why = "tensor map encoding failed";
@@ -659,6 +671,7 @@ cudaError_t launch_sweep_tc(const SweepDesc& s, cudaStream_t stream, std::string
         }
         for (int i = 0; i < 6; ++i) cache.key[i] = key[i];
         cache.arows = arows; cache.brows = brows; cache.d_pad = d_pad; cache.NT = NT; cache.CK = CK;
+        cache.prod = prod;
         cache.maps[0] = args.a_hi; cache.maps[1] = args.a_lo; cache.maps[2] = args.a_aug;
         cache.maps[3] = args.b_hi; cache.maps[4] = args.b_lo; cache.maps[5] = args.b_aug;
         cache.valid = true;
@@ -674,9 +687,10 @@ cudaError_t launch_sweep_tc(const SweepDesc& s, cudaStream_t stream, std::string
     args.eps2 = s.eps2;
     args.st = const_cast<DeviceState*>(s.st);
     args.sink = s.sink;
-#define BM_X(a, b, c, d)                                                      \
-    if (cfg.ck == a && cfg.nt == b && cfg.bbuf == c && cfg.astg == d)         \
-        return launch_cfg<a, b, c, d>(args, s.a_rows_max, stream, why, grid_out);
+#define BM_X(a, b, c, d)                                                                  \
+    if (cfg.ck == a && cfg.nt == b && cfg.bbuf == c && cfg.astg == d)                     \
+        return fp16 ? launch_cfg<a, b, c, d, 1>(args, s.a_rows_max, stream, why, grid_out)  \
+                    : launch_cfg<a, b, c, d, 3>(args, s.a_rows_max, stream, why, grid_out);
     BM_TC_SHAPES(BM_X)
 #undef BM_X
     if (why) *why = "tile shape not compiled";

@@ -13,7 +13,7 @@ from paper_2601_01405_gb300 import workloads as W
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-PATHS = ["tc", "fp32"]
+PATHS = ["tc", "fp32", "tc16"]
 
 
 @pytest.fixture(scope="module")

@@ -92,17 +92,18 @@ def mix():
 @pytest.mark.parametrize("eps", [2.0, 4.0, 6.0])
 def test_mix32_n1M_d64_sampled(bm, mix, eps):
     Xd = torch.from_numpy(mix).cuda()
-    out = run(bm, Xd, eps)
+    out = run(bm, Xd, eps, "tc16" if eps == 2.0 else "tc")
     sampled_checks(mix, out, eps, np.random.default_rng(int(eps)))
 
 
 def test_mix32_n1M_d64_paths_identical(bm, mix):
-    """Both distance-tile paths give the same bytes at full size (eps = 6)."""
+    """All distance-tile paths give the same bytes at full size (eps = 6)."""
     Xd = torch.from_numpy(mix).cuda()
     a = run(bm, Xd, 6.0, "tc")
-    b = run(bm, Xd, 6.0, "fp32")
-    for k in ("landmarks", "offsets", "ids", "edges"):
-        assert torch.equal(a[k], b[k]), k
+    for other in ("fp32", "tc16"):
+        b = run(bm, Xd, 6.0, other)
+        for k in ("landmarks", "offsets", "ids", "edges"):
+            assert torch.equal(a[k], b[k]), (other, k)
 
 
 @pytest.mark.parametrize("eps", [0.5, 1.0])

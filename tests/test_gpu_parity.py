@@ -1,8 +1,8 @@
 """CUDA path (through the C-ABI) against the CPU oracle, element by element.
 
 Landmarks, membership CSR and nerve edges are integer / index results and must
-be bit-identical to the oracle on the same seeded inputs, on both distance-tile
-paths."""
+be bit-identical to the oracle on the same seeded inputs, on every distance-tile
+path (bf16 split and fp16 tensor-core tiles, FP32 CUDA-core tiles)."""
 import numpy as np
 import pytest
 
@@ -12,7 +12,7 @@ from paper_2601_01405_gb300 import workloads as W
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-PATHS = ["tc", "fp32"]
+PATHS = ["tc", "fp32", "tc16", "auto"]
 
 
 @pytest.fixture(scope="module")
@@ -176,7 +176,7 @@ def test_build_host_io_and_determinism(bm, path):
 
 
 def test_paths_agree_on_paper_gaussian_fp32(bm):
-    """The paper's worked example (Sec. 6.3) cast to float32: both paths agree with
+    """The paper's worked example (Sec. 6.3) cast to float32: all paths agree with
     each other and with the oracle on the same float32 data."""
     X = W.paper_gaussian_fp64().astype(np.float32)
     eps = float(np.float32(7.553576))
@@ -229,3 +229,39 @@ def test_build_membership_buffer_regrow(bm, path):
     ref = oracle.build(X, 3.0)
     assert ref["ids"].size > 4 * X.shape[0]
     assert_same_graph(run_build(bm, X, 3.0, path), ref)
+
+
+# ------------------------------------------------------------------ magnitudes (fp16 scaling)
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("scale,offset", [(1e4, 3e5), (1e-6, 0.0), (1.0, 1e3), (2.0 ** -30, 2.0 ** -20)])
+def test_magnitudes_far_from_one(bm, path, scale, offset):
+    """Coordinates far outside [-1, 1] or tiny: the fp16 path scales them by a power
+    of two; large offsets make the norms dwarf the distances (wide bands, many
+    rechecks); every path must still match the oracle."""
+    X = (W.isotropic(3000, 12, 10, seed=31).astype(np.float64) * scale + offset).astype(np.float32)
+    D = ((X[:200, None, :].astype(np.float64) - X[None, :, :]) ** 2).sum(-1)
+    eps = float(np.sqrt(np.quantile(D[D > 0], 0.002)))
+    assert_same_graph(run_build(bm, X, eps, path), oracle.build(X, eps), (scale, offset))
+    Q = X[::13]
+    off, ids, _ = bm.bm_range_query(torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda(), eps, path=path)
+    ro, ri = oracle.range_query(X, Q, eps)
+    assert np.array_equal(off.cpu().numpy(), ro) and np.array_equal(ids.cpu().numpy(), ri)
+
+
+# ------------------------------------------------------------------ automatic path
+def test_auto_switches_to_split_on_wide_bands(bm):
+    """Swiss roll at d = 128: the fp16 band holds far more pairs than the tiles save,
+    so the automatic path moves to the bf16 split during the greedy; same result."""
+    X = W.swissroll(30000, 128, 12, seed=3)
+    got = run_build(bm, X, 0.6, "auto")
+    assert got["stats"]["path"] == bm.BM_PATH_TC_SPLIT3
+    assert_same_graph(got, oracle.build(X, 0.6))
+
+
+def test_auto_stays_fp16_on_separated_data(bm):
+    """Well-separated mixture (every ball a singleton): the band stays tiny and the
+    automatic path keeps the fp16 tiles for the whole build."""
+    X = W.mixture(20000, 64, 8, clusters=32, seed=1)
+    got = run_build(bm, X, 4.0, "auto")
+    assert got["stats"]["path"] == bm.BM_PATH_TC_FP16
+    assert_same_graph(got, oracle.build(X, 4.0))
