@@ -67,8 +67,10 @@ typedef enum {
     BM_PATH_TC_FP16 = 2,   /* tcgen05 tensor cores: one FP16 product on coordinates scaled by a power of two,
                             * FP32 accumulation; about 3x fewer tensor-core operations than the split with a
                             * band about 2^6 times wider (best when eps^2 is far from most squared distances) */
-    BM_PATH_TC_AUTO = 3    /* default.  bm_build: starts on TC_FP16 and moves to TC_SPLIT3 for the rest of the
-                            * greedy once band pairs exceed 2e-4 of the tile pairs of a chunk of steps;
+    BM_PATH_TC_AUTO = 3    /* default.  bm_build: the first greedy step runs on TC_SPLIT3; its band rate times
+                            * the ratio of the two proven band widths predicts the fp16 band, and the greedy
+                            * continues on TC_FP16 when that prediction is below 5e-5 of the tile pairs,
+                            * returning to TC_SPLIT3 (once) if the measured fp16 band exceeds 2e-4;
                             * bm_build_batched: TC_FP16; range queries: TC_SPLIT3.  stats.path reports the
                             * path the build finished on. */
 } bm_path;

@@ -207,6 +207,12 @@ const float* stage_input(const float* X, long long rows, int d, bool host_io, Ar
 
 bool is_tc_path(int path) { return path == BM_PATH_TC_SPLIT3 || path == BM_PATH_TC_FP16; }
 
+float float_from_bits(unsigned u) {
+    float f;
+    std::memcpy(&f, &u, sizeof(f));
+    return f;
+}
+
 int prec_for(int path) {
     return path == BM_PATH_TC_SPLIT3 ? kPrecSplit : (path == BM_PATH_TC_FP16 ? kPrecFp16 : kPrecNone);
 }
@@ -237,17 +243,18 @@ bm_status prepare(const float* x, long long rows, int d, double eps2, bool a_sid
 }
 
 // After the norms are known on the host: fp16 operands at the chosen scale (fp16 path
-// only), then the band half-width.  Returns the scale exponent used.
+// only), the band half-width, and +delta' in the points' augmentation (tensor-core
+// paths).  pts: the B side (points); qry: the A side (queries), or null.
 bm_status finish_prep(DeviceState* st, int path, int d, double eps2, double eps, bool same_sets, float max_norm,
-                      Prepared* a, bool a_side_a, Prepared* b, cudaStream_t s) {
+                      Prepared* pts, Prepared* qry, cudaStream_t s) {
     int e = 0;
     if (path == BM_PATH_TC_FP16) {
         e = fp16_scale_exp((double)max_norm, eps);
-        if (a) TRY_CUDA(launch_prep16(a->x, a->rows, d, eps2, a_side_a, e, *a, s));
-        if (b) TRY_CUDA(launch_prep16(b->x, b->rows, d, eps2, true, e, *b, s));
+        TRY_CUDA(launch_prep16(pts->x, pts->rows, d, eps2, false, e, *pts, s));
+        if (qry) TRY_CUDA(launch_prep16(qry->x, qry->rows, d, eps2, true, e, *qry, s));
     }
-    const int d_pad = a ? a->d_pad : (b ? b->d_pad : d);
-    TRY_CUDA(launch_delta(st, path, d, d_pad, eps2, same_sets, s, e));
+    TRY_CUDA(launch_delta(st, path, d, pts->d_pad, eps2, same_sets, s, e));
+    if (pts->prec != kPrecNone) TRY_CUDA(launch_set_aug_delta(st, *pts, s));
     return BM_OK;
 }
 
@@ -459,11 +466,14 @@ struct GreedyCtx {
     SweepDesc sd;
     int S = 0, sms = 0, path = 0;
     bool tc = false;
-    // automatic path: start on the fp16 tiles, move to the bf16 split when the band
-    // recheck costs more than the cheaper tiles save
+    // automatic path: the first step runs on the bf16 split; its band rate, scaled by
+    // the ratio of the two paths' proven band widths, predicts the fp16 band; the
+    // greedy moves to fp16 when that prediction is small and back (once) when the
+    // measured fp16 band is not
     bool auto_switch = false;
-    double eps2 = 0.0;
-    int switched_at = -1;            // greedy step of the switch (-1: none)
+    int auto_phase = 0;              // 0: deciding on the split, 1: on fp16, watching, 2: settled
+    double eps2 = 0.0, eps = 0.0;
+    std::vector<int> switches;       // greedy steps at which the path changed
     unsigned long long band0 = 0, pairs0 = 0;
 };
 
@@ -471,6 +481,7 @@ struct GreedyCtx {
 // pair costs an FP64 distance (~0.35-0.7 ns at d = 64-128 on GB300), while the fp16
 // tiles save ~0.1 ps per pair.
 constexpr double kAutoBandFraction = 2e-4;
+constexpr double kAutoPredictFraction = 5e-5;   // move to fp16 below this predicted rate
 
 bm_status greedy_setup(const Prepared& pts, double eps2, int path, int S, Arena& ar, cudaStream_t s, DeviceState* st,
                        unsigned long long step_cap, unsigned long long mem_cap, const IvfIndex* ivf,
@@ -482,6 +493,7 @@ bm_status greedy_setup(const Prepared& pts, double eps2, int path, int S, Arena&
     c.path = path;
     c.tc = tc;
     c.eps2 = eps2;
+    c.eps = std::sqrt(eps2);
     GreedyBuffers& g = c.g;
     g.st = st;
     const long long words_n = (n + 31) / 32;
@@ -566,41 +578,64 @@ bm_status greedy_enqueue_step(GreedyCtx& c, const Prepared& pts, Arena& ar, Swee
 // an overflowing buffer and redo the step, until no uncovered point remains.
 // With resume set the first state read comes before any new step (the steps so
 // far ran elsewhere, e.g. in a graph).
-// Move a greedy in progress from the fp16 tiles to the bf16 split: split operands of
-// the points (replacing the fp16 ones), candidate operand rows for the split, and
-// the split's band half-width.  Every step is exact on either path.
-bm_status switch_to_split(GreedyCtx& c, Prepared& pts, Arena& ar, cudaStream_t s, int step) {
+// Move a greedy in progress to another tensor-core representation: new operands
+// of the points (replacing the old ones), candidate operand rows to match, the new
+// band half-width and +delta'.  Every step is exact on either path.
+bm_status switch_path(GreedyCtx& c, Prepared& pts, Arena& ar, cudaStream_t s, int to, float max_norm, int step) {
     DeviceState* st = c.g.st;
-    int* bad;
-    ALLOC(bad, int, 1);
-    TRY_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
     Prepared p2;
-    bm_status rs = prepare(pts.x, pts.rows, pts.d, c.eps2, false, kPrecSplit, ar, &st->max_norm_bits, bad, s, p2);
-    if (rs != BM_OK) return rs;
+    int e = 0;
+    if (to == BM_PATH_TC_SPLIT3) {
+        int* bad;
+        ALLOC(bad, int, 1);
+        TRY_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+        bm_status rs = prepare(pts.x, pts.rows, pts.d, c.eps2, false, kPrecSplit, ar, &st->max_norm_bits, bad, s, p2);
+        if (rs != BM_OK) return rs;
+        ar.release(pts.phi);
+    } else {
+        p2 = pts;   // same rows, phi and norms
+        p2.prec = kPrecFp16;
+        const TileConfig t = tile_config_for(pts.d, 1);
+        p2.d_pad = t.d_pad;
+        p2.ck = t.ck;
+        p2.nt = t.nt;
+        p2.bbuf = t.bbuf;
+        p2.astg = t.astg;
+        p2.lo = nullptr;
+        ALLOC(p2.hi, __nv_bfloat16, std::max<long long>(pts.rows, 1) * p2.d_pad);
+        ALLOC(p2.aug, __nv_bfloat16, std::max<long long>(pts.rows, 1) * 16);
+        e = fp16_scale_exp((double)max_norm, c.eps);
+        TRY_CUDA(launch_prep16(p2.x, p2.rows, p2.d, c.eps2, false, e, p2, s));
+    }
     ar.release(pts.hi);
+    ar.release(pts.lo);
     ar.release(pts.aug);
-    ar.release(pts.phi);
     pts = p2;   // c.sd.b points at pts
     const int S = c.S;
     Prepared& cand = c.g.cand;
     ar.release(cand.hi);
+    ar.release(cand.lo);
     ar.release(cand.aug);
+    cand.lo = nullptr;
     ALLOC(cand.hi, __nv_bfloat16, (long long)S * pts.d_pad);
-    ALLOC(cand.lo, __nv_bfloat16, (long long)S * pts.d_pad);
     ALLOC(cand.aug, __nv_bfloat16, (long long)S * 16);
     TRY_CUDA(cudaMemsetAsync(cand.hi, 0, sizeof(__nv_bfloat16) * S * pts.d_pad, s));
-    TRY_CUDA(cudaMemsetAsync(cand.lo, 0, sizeof(__nv_bfloat16) * S * pts.d_pad, s));
     TRY_CUDA(cudaMemsetAsync(cand.aug, 0, sizeof(__nv_bfloat16) * S * 16, s));
+    if (to == BM_PATH_TC_SPLIT3) {
+        ALLOC(cand.lo, __nv_bfloat16, (long long)S * pts.d_pad);
+        TRY_CUDA(cudaMemsetAsync(cand.lo, 0, sizeof(__nv_bfloat16) * S * pts.d_pad, s));
+    }
     cand.d_pad = pts.d_pad;
     cand.ck = pts.ck;
     cand.nt = pts.nt;
     cand.bbuf = pts.bbuf;
     cand.astg = pts.astg;
-    cand.prec = kPrecSplit;
-    cand.scale_exp = 0;
-    TRY_CUDA(launch_delta(st, BM_PATH_TC_SPLIT3, pts.d, pts.d_pad, c.eps2, true, s, 0));
-    c.path = BM_PATH_TC_SPLIT3;
-    c.switched_at = step;
+    cand.prec = pts.prec;
+    cand.scale_exp = pts.scale_exp;
+    TRY_CUDA(launch_delta(st, to, pts.d, pts.d_pad, c.eps2, true, s, e));
+    TRY_CUDA(launch_set_aug_delta(st, pts, s));
+    c.path = to;
+    c.switches.push_back(step);
     return BM_OK;
 }
 
@@ -609,7 +644,8 @@ bm_status greedy_drive(GreedyCtx& c, Prepared& pts, Arena& ar, cudaStream_t s, H
                        SweepTimer& stimer, bool resume) {
     GreedyBuffers& g = c.g;
     DeviceState* st = g.st;
-    int chunk = 2;
+    // the automatic path looks at the band after the first step already
+    int chunk = c.auto_switch ? 1 : 2;
     int regrows = 0;
     bool enqueue = !resume;
     while (true) {
@@ -652,13 +688,30 @@ bm_status greedy_drive(GreedyCtx& c, Prepared& pts, Arena& ar, cudaStream_t s, H
             continue;
         }
         if (h.done) break;
-        if (c.auto_switch && c.path == BM_PATH_TC_FP16) {
+        if (c.auto_switch && c.auto_phase < 2) {
             const unsigned long long db = h.band_pairs - c.band0, dp = h.tile_pairs - c.pairs0;
             c.band0 = h.band_pairs;
             c.pairs0 = h.tile_pairs;
-            if (dp > 0 && (double)db > kAutoBandFraction * (double)dp) {
-                bm_status rs2 = switch_to_split(c, pts, ar, s, (int)h.steps);
-                if (rs2 != BM_OK) return rs2;
+            const float nmax = float_from_bits(h.max_norm_bits);
+            if (dp > 0 && c.auto_phase == 0) {
+                const int e = fp16_scale_exp((double)nmax, c.eps);
+                const double d16 = band_halfwidth(BM_PATH_TC_FP16, pts.d, tile_config_for(pts.d, 1).d_pad, c.eps2,
+                                                  nmax, nmax, e) * std::ldexp(1.0, -2 * e);
+                const double d3 = band_halfwidth(BM_PATH_TC_SPLIT3, pts.d, pts.d_pad, c.eps2, nmax, nmax, 0);
+                const double predicted = (double)db / (double)dp * (d16 / d3);
+                if (predicted < kAutoPredictFraction) {
+                    bm_status rs2 = switch_path(c, pts, ar, s, BM_PATH_TC_FP16, nmax, (int)h.steps);
+                    if (rs2 != BM_OK) return rs2;
+                    c.auto_phase = 1;
+                } else {
+                    c.auto_phase = 2;
+                }
+            } else if (dp > 0 && c.auto_phase == 1) {
+                if ((double)db > kAutoBandFraction * (double)dp) {
+                    bm_status rs2 = switch_path(c, pts, ar, s, BM_PATH_TC_SPLIT3, nmax, (int)h.steps);
+                    if (rs2 != BM_OK) return rs2;
+                    c.auto_phase = 2;
+                }
             }
         }
         chunk = std::min(chunk * 2, 64);
@@ -749,7 +802,7 @@ bm_status range_core(const float* X, long long n, int d, const float* Q, long lo
                 float nx, nq;
                 std::memcpy(&nx, &hnorm[0], sizeof(float));
                 std::memcpy(&nq, &hnorm[1], sizeof(float));
-                rs = finish_prep(st, path, d, eps2, (double)eps, false, std::max(nx, nq), &px, false, &pq, s);
+                rs = finish_prep(st, path, d, eps2, (double)eps, false, std::max(nx, nq), &px, &pq, s);
                 if (rs != BM_OK) return rs;
             }
             unsigned long long cap = (unsigned long long)std::min<long long>(std::max<long long>(n, m) * 4 + (1 << 20),
@@ -957,10 +1010,10 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
     cudaStream_t s = (cudaStream_t)opt.stream;
     const bool host_io = opt.host_io != 0;
     const double eps2 = (double)eps * (double)eps;
-    // automatic path: start on the fp16 tiles; the greedy moves to the split when the
-    // band gets expensive (greedy_drive)
+    // automatic path: the greedy starts on the split and picks its path after the
+    // first step (greedy_drive)
     const bool auto_switch = opt.path == BM_PATH_TC_AUTO && ivf == nullptr && fixed_lm == nullptr;
-    const int req = opt.path == BM_PATH_TC_AUTO ? (int)BM_PATH_TC_FP16 : opt.path;
+    const int req = opt.path == BM_PATH_TC_AUTO ? (int)BM_PATH_TC_SPLIT3 : opt.path;
     const bool tc = is_tc_path(req) && ivf == nullptr;
     int path = ivf ? (int)BM_PATH_FP32 : req;
     Timer tm(s);
@@ -1014,7 +1067,7 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
             {
                 float nx;
                 std::memcpy(&nx, &hnorm, sizeof(float));
-                rs = finish_prep(st, path, d, eps2, (double)eps, true, nx, &px, false, nullptr, s);
+                rs = finish_prep(st, path, d, eps2, (double)eps, true, nx, &px, nullptr, s);
                 if (rs != BM_OK) return rs;
             }
             tm.mark();  // 1: prep done
@@ -1262,8 +1315,7 @@ bm_status build_batched(const bm_instance* inst, int count, const bm_options& op
             if (it.n == 0) continue;
             float nx;
             std::memcpy(&nx, &hs0[i].max_norm_bits, sizeof(float));
-            bm_status rs = finish_prep(it.st, path, it.d, it.eps2, (double)inst[i].eps, true, nx, &it.px, false,
-                                       nullptr, s);
+            bm_status rs = finish_prep(it.st, path, it.d, it.eps2, (double)inst[i].eps, true, nx, &it.px, nullptr, s);
             if (rs != BM_OK) return tag(i, rs);
         }
     }

@@ -117,8 +117,9 @@ __global__ void __launch_bounds__(kSelThreads) greedy_select_kernel(
 __global__ void __launch_bounds__(256) greedy_gather_kernel(
     const DeviceState* st, const int* __restrict__ cand_ids, const float* __restrict__ X,
     const float* __restrict__ phi, int d, float* __restrict__ cand_x, float* __restrict__ cand_phi, int want_tc,
-    const unsigned* __restrict__ H, const unsigned* __restrict__ Lo, const __nv_bfloat16* __restrict__ Aug,
-    int d_pad, unsigned* __restrict__ cH, unsigned* __restrict__ cLo, __nv_bfloat16* __restrict__ cAug) {
+    const unsigned* __restrict__ H, const unsigned* __restrict__ Lo, const unsigned short* __restrict__ Aug,
+    int d_pad, unsigned* __restrict__ cH, unsigned* __restrict__ cLo, unsigned short* __restrict__ cAug,
+    unsigned short one_bits) {
     if (st->done) return;
     const int s = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (s >= st->cand_count) return;
@@ -133,7 +134,8 @@ __global__ void __launch_bounds__(256) greedy_gather_kernel(
         }
         if (lane < 16) {
             const int src = lane < 3 ? lane + 3 : (lane < 6 ? lane - 3 : lane);
-            cAug[(long long)s * 16 + lane] = Aug[id * 16 + src];
+            // column 6: the candidates' 1 against the points' +delta'
+            cAug[(long long)s * 16 + lane] = lane == 6 ? one_bits : Aug[id * 16 + src];
         }
     }
 }
@@ -323,8 +325,10 @@ cudaError_t launch_greedy_gather(const GreedyBuffers& g, const Prepared& pts, in
     note_launch();
     greedy_gather_kernel<<<(S + 7) / 8, 256, 0, s>>>(
         g.st, g.cand_ids, pts.x, pts.phi, pts.d, const_cast<float*>(g.cand.x), g.cand.phi, want_tc ? 1 : 0,
-        reinterpret_cast<const unsigned*>(pts.hi), reinterpret_cast<const unsigned*>(pts.lo), pts.aug, pts.d_pad,
-        reinterpret_cast<unsigned*>(g.cand.hi), reinterpret_cast<unsigned*>(g.cand.lo), g.cand.aug);
+        reinterpret_cast<const unsigned*>(pts.hi), reinterpret_cast<const unsigned*>(pts.lo),
+        reinterpret_cast<const unsigned short*>(pts.aug), pts.d_pad, reinterpret_cast<unsigned*>(g.cand.hi),
+        reinterpret_cast<unsigned*>(g.cand.lo), reinterpret_cast<unsigned short*>(g.cand.aug),
+        (unsigned short)(pts.prec == kPrecFp16 ? 0x3C00u : 0x3F80u));   // 1.0 in fp16 / bf16
     return cudaGetLastError();
 }
 

@@ -92,6 +92,11 @@ cudaError_t launch_delta(DeviceState* st, int path, int d, int d_pad, double eps
 cudaError_t launch_prep16(const float* x, long long rows, int d, double eps2, bool a_side, int scale_exp,
                           Prepared& p, cudaStream_t s);
 int fp16_scale_exp(double max_norm, double eps);
+// Proven band half-width of a path in its operand units (see bm_prep.cu)
+__host__ __device__ double band_halfwidth(int path, int d, int d_pad, double eps2, double Na, double Nb,
+                                          int scale_exp);
+// +delta' into column 6 of a B-side (points) augmentation, after launch_delta
+cudaError_t launch_set_aug_delta(const DeviceState* st, Prepared& p, cudaStream_t s);
 
 struct IvfIndex;
 

@@ -13,9 +13,12 @@
 // two bf16 values, x = hi + lo (hi = bf16(x), lo = bf16(x - hi)), and phi is
 // carried into the K dimension by a 16-wide augmentation block so that the
 // FP32 accumulator already holds v:
-//   B side (points):   aug = [1, 1, 1, -p1, -p2, -p3, 0 ...]
-//   A side (queries):  aug = [-p1, -p2, -p3, 1, 1, 1, 0 ...]
-// with phi ~ p1 + p2 + p3 (three bf16 pieces of the FP64 value).
+//   B side (points):   aug = [1, 1, 1, -p1, -p2, -p3, delta', 0 ...]
+//   A side (queries):  aug = [-p1, -p2, -p3, 1, 1, 1, 1, 0 ...]
+// with phi ~ p1 + p2 + p3 (three bf16 pieces of the FP64 value) and delta' the
+// band half-width rounded up to the operand type (written by set_aug_delta once
+// delta is known), so the accumulator holds v + delta' and the tiles classify by
+// its sign.
 #include <cuda_fp16.h>
 
 #include <cmath>
@@ -70,6 +73,7 @@ __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ x, 
             else if (pos == 1) v = __hneg(p2);
             else if (pos == 2) v = __hneg(p3);
             else if (pos < 6) v = one;
+            else if (pos == 6 && a_side) v = one;   // times the points' +delta' (set_aug_delta)
             aug[r * 16 + lane] = v;
         }
         my_max = fmaxf(my_max, __double2float_ru(sqrt(s)));
@@ -117,6 +121,7 @@ __global__ void __launch_bounds__(256) prep16_kernel(const float* __restrict__ x
             else if (pos == 1) v = __hneg(p2);
             else if (pos == 2) v = __hneg(p3);
             else if (pos < 6) v = __float2half_rn(1.f);
+            else if (pos == 6 && a_side) v = __float2half_rn(1.f);
             aug[r * 16 + lane] = v;
         }
     }
@@ -183,11 +188,14 @@ cudaError_t launch_prep(const float* x, long long rows, int d, double eps2, bool
 // three fp16 phi pieces: 2^-33 |phi| + 2^-25 each; FP64 phi: 2^-42 N^2.
 //     delta = 2 [E_rep + 2 K 2^-23 (1.002 N_a N_b + 1.001 (Phi_a + Phi_b) + 2^-24 sqrt(d_pad)(N_a + N_b))
 //                + 2^-33 (Phi_a + Phi_b) + 2^-22 + 2^-42 (N_a^2 + N_b^2)]
-__global__ void delta_kernel(DeviceState* st, int path, int d, int d_pad, double eps2, int same_sets,
-                             int scale_exp) {
+// The bound itself, in the units of the operands (scaled by 2^scale_exp on the fp16
+// path); Na, Nb are the unscaled max norms.  Used by the device (delta_kernel) and by
+// the host's choice of path.
+__host__ __device__ double band_halfwidth(int path, int d, int d_pad, double eps2, double Na, double Nb,
+                                          int scale_exp) {
     const double sc = ldexp(1.0, scale_exp);
-    const double Nb = (double)__uint_as_float(st->max_norm_bits) * sc;
-    const double Na = same_sets ? Nb : (double)__uint_as_float(st->max_norm_q_bits) * sc;
+    Na *= sc;
+    Nb *= sc;
     const double e2 = eps2 * sc * sc;
     const double Pa = fmax(Na * Na * 0.5 - 0.25 * e2, 0.25 * e2);
     const double Pb = fmax(Nb * Nb * 0.5 - 0.25 * e2, 0.25 * e2);
@@ -208,8 +216,39 @@ __global__ void delta_kernel(DeviceState* st, int path, int d, int d_pad, double
         delta = 2.0 * (2.0 * K * u23 * (1.02 * Na * Nb + 1.01 * (Pa + Pb)) + 3.0 * u16 * Na * Nb +
                        u23 * (Pa + Pb));
     }
-    delta += 1e-30;
-    st->delta = __double2float_ru(delta);
+    return delta + 1e-30;
+}
+
+__global__ void delta_kernel(DeviceState* st, int path, int d, int d_pad, double eps2, int same_sets,
+                             int scale_exp) {
+    const double Nb = (double)__uint_as_float(st->max_norm_bits);
+    const double Na = same_sets ? Nb : (double)__uint_as_float(st->max_norm_q_bits);
+    st->delta = __double2float_ru(band_halfwidth(path, d, d_pad, eps2, Na, Nb, scale_exp));
+}
+
+// Column 6 of the points' augmentation: +delta' = delta rounded up to the operand type.
+__global__ void set_aug_delta_kernel(const DeviceState* st, long long rows, int fp16, unsigned short* aug) {
+    const float delta = st->delta;
+    unsigned short bits;
+    if (fp16) {
+        const __half h = __float2half_ru(delta);
+        bits = __half_as_ushort(h);
+    } else {
+        const __nv_bfloat16 b = __float2bfloat16_ru(delta);
+        bits = __bfloat16_as_ushort(b);
+    }
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += stride) aug[r * 16 + 6] = bits;
+}
+
+cudaError_t launch_set_aug_delta(const DeviceState* st, Prepared& p, cudaStream_t s) {
+    if (p.rows == 0 || p.aug == nullptr) return cudaSuccess;
+    long long blocks = (p.rows + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    note_launch();
+    set_aug_delta_kernel<<<(unsigned)blocks, 256, 0, s>>>(st, p.rows, p.prec == kPrecFp16 ? 1 : 0,
+                                                          reinterpret_cast<unsigned short*>(p.aug));
+    return cudaGetLastError();
 }
 
 cudaError_t launch_delta(DeviceState* st, int path, int d, int d_pad, double eps2, bool same_sets,

@@ -23,6 +23,8 @@
 // Every mbarrier wait is bounded in time; on expiry the kernel records
 // kErrTimeout, drains its in-flight copies and MMAs, frees TMEM and returns.
 #include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
 #include <map>
@@ -375,7 +377,13 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
         constexpr int kChunks = NT / 64;            // 32-column loads per warp per tile
         const int quarter = warp & 3;
         const int half = (warp - 2) >> 2;
+        // The points' augmentation carries +delta' (delta rounded up to the operand type),
+        // so the accumulator holds acc = v + delta': acc < 0 (sign bit set) decides
+        // "not a member", acc > 2 delta' decides "member", the rest is the band.
         const float delta = p.st->delta;
+        const float dprime = PROD == 3 ? __bfloat162float(__float2bfloat16_ru(delta))
+                                       : __half2float(__float2half_ru(delta));
+        const float hit_thr = 2.f * dprime;
         const unsigned long long seg_off = seg_mode ? (unsigned long long)blockIdx.x * p.sink.seg_cap : 0ull;
         unsigned long long* seg_keys = p.sink.keys + seg_off;
         unsigned long long* band_keys = p.sink.band_keys + seg_off;
@@ -405,27 +413,37 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
                 __syncwarp();
                 if (lane == 0) bar_arrive(&ctl->t_empty[t_buf]);
                 if (++t_buf == 2) { t_buf = 0; t_ph ^= 1; }
+                // fast path: every value of this thread's row negative (the AND of the bit
+                // patterns keeps the sign bit) for the whole warp -> nothing to emit
+                unsigned allneg = kFull;
+#pragma unroll
+                for (int j = 0; j < kChunks; ++j)
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) allneg &= r[j][i];
+                const bool quiet = !row_ok || (allneg >> 31) != 0u;
+                if (__all_sync(kFull, quiet)) {
+                    if (threadIdx.x == 64) {
+                        const long long ra = (a_rows - at * 128) < 128 ? (a_rows - at * 128) : 128;
+                        const long long rb = (p.n - bt * NT) < NT ? (p.n - bt * NT) : NT;
+                        pairs_local += (unsigned long long)(ra * rb);
+                    }
+                    continue;
+                }
 #pragma unroll
                 for (int j = 0; j < kChunks; ++j) {
                     const long long col0 = col_base + j * 32;
-                    float m16[16];
+                    unsigned neg = kFull;
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) m16[i] = fmaxf(__uint_as_float(r[j][i]), __uint_as_float(r[j][i + 16]));
-#pragma unroll
-                    for (int w = 8; w > 0; w >>= 1)
-#pragma unroll
-                        for (int i = 0; i < w; ++i) m16[i] = fmaxf(m16[i], m16[i + w]);
-                    const float mx = m16[0];
+                    for (int i = 0; i < 32; ++i) neg &= r[j][i];
                     unsigned hit = 0, band = 0;
-                    if (row_ok && mx >= -delta) {
+                    if (row_ok && (neg >> 31) == 0u) {
                         const long long left = p.n - col0;
                         const unsigned valid = left >= 32 ? kFull : (left <= 0 ? 0u : (1u << left) - 1u);
                         unsigned near_ = 0;
 #pragma unroll
                         for (int i = 0; i < 32; ++i) {
-                            const float v = __uint_as_float(r[j][i]);
-                            hit |= (v > delta ? 1u : 0u) << i;
-                            near_ |= (v >= -delta ? 1u : 0u) << i;
+                            hit |= (__uint_as_float(r[j][i]) > hit_thr ? 1u : 0u) << i;
+                            near_ |= ((r[j][i] >> 31) ^ 1u) << i;
                         }
                         hit &= valid;
                         band = near_ & ~hit & valid;

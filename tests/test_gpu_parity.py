@@ -265,3 +265,13 @@ def test_auto_stays_fp16_on_separated_data(bm):
     got = run_build(bm, X, 4.0, "auto")
     assert got["stats"]["path"] == bm.BM_PATH_TC_FP16
     assert_same_graph(got, oracle.build(X, 4.0))
+
+
+def test_auto_returns_to_split_when_fp16_band_grows(bm):
+    """Norms far larger than eps (offset cloud, tiny eps): the split's band is empty, so
+    the automatic path moves to fp16, where every self pair falls into the wider band
+    (1/n of the pairs > 2e-4 at n = 3000) and it returns to the split; same result."""
+    X = (W.isotropic(3000, 16, 10, seed=8).astype(np.float64) + 50.0).astype(np.float32)
+    got = run_build(bm, X, 0.5, "auto")
+    assert got["stats"]["path"] == bm.BM_PATH_TC_SPLIT3
+    assert_same_graph(got, oracle.build(X, 0.5))
