@@ -46,17 +46,17 @@ def candidates(d: int) -> List[dict]:
     return found
 
 
-def time_config(d: int, cfg: dict, X, Q, eps: float, reps: int) -> float:
+def time_config(d: int, cfg: dict, X, Q, eps: float, reps: int, path: str = "tc") -> float:
     """Median device time (ms) of the tile launches of one range query under cfg."""
     from . import binding
     import torch
     prev = binding.get_tile_config(d)
     binding.set_tile_config(d, cfg)
     try:
-        binding.bm_range_query(X, Q, eps)
+        binding.bm_range_query(X, Q, eps, path=path)
         ms = []
         for _ in range(reps):
-            _, _, st = binding.bm_range_query(X, Q, eps)
+            _, _, st = binding.bm_range_query(X, Q, eps, path=path)
             torch.cuda.synchronize()
             ms.append(st["ms_sweep"])
         return statistics.median(ms)
@@ -64,7 +64,8 @@ def time_config(d: int, cfg: dict, X, Q, eps: float, reps: int) -> float:
         binding.set_tile_config(d, prev)
 
 
-def tune(dims: Iterable[int], n: int = 200_000, rows: int = 2048, reps: int = 5, seed: int = 0) -> Dict[int, dict]:
+def tune(dims: Iterable[int], n: int = 200_000, rows: int = 2048, reps: int = 5, seed: int = 0,
+         path: str = "tc") -> Dict[int, dict]:
     """{d: {"best": cfg, "builtin": cfg, "timings": [(cfg, ms), ...]}}."""
     import torch
     from . import binding, workloads
@@ -76,9 +77,9 @@ def tune(dims: Iterable[int], n: int = 200_000, rows: int = 2048, reps: int = 5,
         builtin = binding.get_tile_config(d)
         timings = []
         for cfg in candidates(d):
-            timings.append((cfg, time_config(d, cfg, X, Q, eps, reps)))
+            timings.append((cfg, time_config(d, cfg, X, Q, eps, reps, path)))
         timings.sort(key=lambda t: t[1])
-        out[d] = {"best": timings[0][0], "best_ms": timings[0][1], "builtin": builtin,
+        out[d] = {"path": path, "best": timings[0][0], "best_ms": timings[0][1], "builtin": builtin,
                   "builtin_ms": next(ms for c, ms in timings if c == builtin),
                   "evals": n * rows, "timings": [{"cfg": c, "ms": ms} for c, ms in timings]}
     return out
@@ -108,8 +109,9 @@ def main(argv=None):
     ap.add_argument("--rows", type=int, default=2048)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--path", choices=["tc", "tc16"], default="tc", help="tensor-core representation to time")
     a = ap.parse_args(argv)
-    table = tune(a.dims, a.n, a.rows, a.reps)
+    table = tune(a.dims, a.n, a.rows, a.reps, path=a.path)
     if a.out:
         save(table, a.out)
     for d, e in table.items():

@@ -43,10 +43,14 @@ __global__ void __launch_bounds__(kSelThreads) greedy_select_kernel(
     __shared__ long long s_pos;
     const int tid = threadIdx.x;
 
-    // 1. undo the previous step's bookkeeping
+    // 1. undo the previous step's bookkeeping: conflict bits live only in the rows
+    //    flagged in row_any, so only those rows are cleared
     const int prev = st->cand_count;
     for (int i = tid; i < prev; i += kSelThreads) slot_of[cand_ids[i]] = -1;
-    for (int i = tid; i < prev * words; i += kSelThreads) conflict[i] = 0;
+    for (int k = tid; k < prev; k += kSelThreads)
+        if ((row_any[k >> 5] >> (k & 31)) & 1u)
+            for (int w = 0; w < words; ++w) conflict[(size_t)k * words + w] = 0;
+    __syncthreads();
     for (int i = tid; i < words; i += kSelThreads) row_any[i] = 0;
     __shared__ int s_req;
     if (tid == 0) {
