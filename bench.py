@@ -29,10 +29,12 @@ sys.path.insert(0, ROOT)
 METRIC = "Ball Mapper build s & distance evals/s (exact), TC split path vs plain FP32"
 UNIT = "evals/s"
 # DRAM bytes per tile-kernel launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# the ncu capture summarised in profiles/sweep_tc_kernel_mix32-n1M-d64_rows1024.md; a
-# step's sweep reads every point's operands once, so the figure holds for each launch of
-# this workload.  None where no capture of the current kernel exists.
-NCU_TRAFFIC = {("mix32-n1M-d64", "tc"): 292.0e6}
+# the ncu capture of the current fp16 kernel summarised in
+# profiles/sweep_tc_kernel_fp16_mix32-n1M-d64_rows1024.md; a step's sweep reads every
+# point's operands once, so the figure holds for each launch of this workload (the
+# automatic path runs fp16 after the first step).  None where no capture of the current
+# kernel exists.
+NCU_TRAFFIC = {("mix32-n1M-d64", "auto"): 163.6e6, ("mix32-n1M-d64", "tc16"): 163.6e6}
 DTYPES = {"tc": "bf16x3-split/fp32-acc/fp64-recheck", "tc16": "f16-scaled/fp32-acc/fp64-recheck",
           "fp32": "f32/fp64-recheck", "auto": "f16-scaled or bf16x3-split/fp32-acc/fp64-recheck"}
 
