@@ -182,7 +182,8 @@ BM_API bm_status bm_build_batched(const bm_instance* inst, int32_t count, const 
  * the operands are zero-padded to it), K chunks of ck bf16 per shared-memory
  * stage (16, 32 or 64), point tiles of nt rows (64, 128 or 256) held in bbuf
  * buffers, and astg stages of query chunks.  Only shapes compiled into the
- * library are accepted (bm_tile_shapes lists them, d_pad = 0 there).  Results
+ * library are accepted (bm_tile_shapes lists them, d_pad = 0 there), and an override
+ * must fit the shared memory of both tensor-core representations.  Results
  * never depend on the configuration; speed does.  Settings are process-wide,
  * guarded by a lock, and read when a call prepares its operands. */
 typedef struct {

@@ -29,28 +29,28 @@ def _paddings(d: int, ck: int) -> List[int]:
 
 
 def candidates(d: int) -> List[dict]:
-    """Every (d_pad, shape) the library accepts for dimension d."""
+    """Every (d_pad, shape) the library accepts for dimension d.  Probing leaves d on
+    the built-in choice (any override for d is removed)."""
     from . import binding
     found = []
     for shp in binding.tile_shapes():
         for d_pad in _paddings(d, shp["ck"]):
             cfg = dict(shp, d_pad=d_pad)
-            prev = binding.get_tile_config(d)
             try:
                 binding.set_tile_config(d, cfg)
             except binding.BallMapperError:
                 continue
             finally:
-                binding.set_tile_config(d, prev)
+                binding.set_tile_config(d, None)
             found.append(cfg)
     return found
 
 
 def time_config(d: int, cfg: dict, X, Q, eps: float, reps: int, path: str = "tc") -> float:
-    """Median device time (ms) of the tile launches of one range query under cfg."""
+    """Median device time (ms) of the tile launches of one range query under cfg (d is
+    left on the built-in choice afterwards)."""
     from . import binding
     import torch
-    prev = binding.get_tile_config(d)
     binding.set_tile_config(d, cfg)
     try:
         binding.bm_range_query(X, Q, eps, path=path)
@@ -61,7 +61,7 @@ def time_config(d: int, cfg: dict, X, Q, eps: float, reps: int, path: str = "tc"
             ms.append(st["ms_sweep"])
         return statistics.median(ms)
     finally:
-        binding.set_tile_config(d, prev)
+        binding.set_tile_config(d, None)
 
 
 def tune(dims: Iterable[int], n: int = 200_000, rows: int = 2048, reps: int = 5, seed: int = 0,
@@ -80,7 +80,7 @@ def tune(dims: Iterable[int], n: int = 200_000, rows: int = 2048, reps: int = 5,
             timings.append((cfg, time_config(d, cfg, X, Q, eps, reps, path)))
         timings.sort(key=lambda t: t[1])
         out[d] = {"path": path, "best": timings[0][0], "best_ms": timings[0][1], "builtin": builtin,
-                  "builtin_ms": next(ms for c, ms in timings if c == builtin),
+                  "builtin_ms": next((ms for c, ms in timings if c == builtin), None),
                   "evals": n * rows, "timings": [{"cfg": c, "ms": ms} for c, ms in timings]}
     return out
 
@@ -115,7 +115,7 @@ def main(argv=None):
     if a.out:
         save(table, a.out)
     for d, e in table.items():
-        rate = lambda ms: e["evals"] / (ms * 1e-3)
+        rate = lambda ms: e["evals"] / (ms * 1e-3) if ms else None
         print(json.dumps({"d": d, "best": e["best"], "best_evals_per_s": rate(e["best_ms"]), "builtin": e["builtin"],
                           "builtin_evals_per_s": rate(e["builtin_ms"]),
                           "all": [(t["cfg"]["d_pad"], t["cfg"]["ck"], t["cfg"]["nt"], t["cfg"]["bbuf"],

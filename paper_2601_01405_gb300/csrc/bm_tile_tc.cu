@@ -182,8 +182,8 @@ __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.
 // Byte sizes of the shared-memory regions for a configuration.  PROD = 3: the
 // point tile holds hi and lo chunks (bf16 split); PROD = 1: hi chunks only (fp16).
 struct Layout {
-    int CK, NT, BBUF, ASTG, nc;
-    uint32_t a_chunk, b_chunk, b_aug, b_bytes, b_stride, a_off, ctl_off, total;
+    int CK, NT, BBUF, ASTG, nc, cps;
+    uint32_t a_chunk, a_stage, b_chunk, b_aug, b_bytes, b_stride, a_off, ctl_off, total;
 };
 
 __host__ __device__ inline Layout make_layout(int CK, int NT, int BBUF, int ASTG, int d_pad, int PROD = 3) {
@@ -198,13 +198,18 @@ __host__ __device__ inline Layout make_layout(int CK, int NT, int BBUF, int ASTG
     L.b_aug = (uint32_t)NT * 32u;
     L.b_bytes = (PROD == 3 ? 2u : 1u) * L.nc * L.b_chunk + L.b_aug;
     L.b_stride = (L.b_bytes + 1023u) & ~1023u;
+    // fp16: a stage holds cps K chunks of the query tile (both chunks of a d_pad = 128
+    // tile with 64-wide chunks, else one) and the last stage also its augmentation
+    // block, so a tile costs one stage hand-off where the split pays nc + 1
+    L.cps = (PROD == 1 && L.nc == 2 && CK == 64) ? 2 : 1;
+    L.a_stage = L.cps * L.a_chunk + (PROD == 1 ? 128u * 32u : 0u);
     L.a_off = BBUF * L.b_stride;
-    L.ctl_off = L.a_off + ASTG * L.a_chunk;
+    L.ctl_off = L.a_off + ASTG * L.a_stage;
     L.total = L.ctl_off + 1024u + 1024u;  // control block + alignment slack
     return L;
 }
 
-template <int CK, int NT, int BBUF, int ASTG, int PROD>
+template <int CK, int NT, int BBUF, int ASTG, int PROD, int CPS>
 __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_constant__ TcArgs p) {
     const bool seg_mode = p.sink.seg_counts != nullptr;
     if (seg_mode && threadIdx.x == 0) {
@@ -220,6 +225,8 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
     const Layout L = make_layout(CK, NT, BBUF, ASTG, p.d_pad, PROD);
     const int nc = L.nc;
     const int nq = PROD == 3 ? 2 * nc : nc;   // query-tile chunks before the augmentation chunk
+    constexpr int cps = CPS;   // = L.cps (the dispatch picks the instantiation that matches)
+    const int nstage = PROD == 3 ? nq + 1 : (nc + cps - 1) / cps;   // shared-memory stages per query tile
     Ctl* ctl = reinterpret_cast<Ctl*>(smem + L.ctl_off);
     const uint32_t sbase = su32(smem);
 
@@ -292,10 +299,17 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
                 if (++b_buf == BBUF) { b_buf = 0; b_ph ^= 1; }
                 for (long long at = at0; ok && at < at1; ++at) {
                     const int ya = (int)(at * 128);
-                    for (int q = 0; q <= nq; ++q) {
+                    for (int q = 0; q < nstage; ++q) {
                         if (!bar_wait(&ctl->a_empty[a_st], a_ph ^ 1, abort_flag, gerr)) { ok = false; break; }
-                        const uint32_t dst = sbase + L.a_off + a_st * L.a_chunk;
-                        if (q < nc) {
+                        const uint32_t dst = sbase + L.a_off + a_st * L.a_stage;
+                        if (PROD == 1) {
+                            const bool last = q == nstage - 1;
+                            const int c0 = q * cps, c1 = (c0 + cps < nc) ? c0 + cps : nc;
+                            bar_expect_tx(&ctl->a_full[a_st], (c1 - c0) * L.a_chunk + (last ? 128u * 32u : 0u));
+                            for (int c = c0; c < c1; ++c)
+                                tma_load(dst + (c - c0) * L.a_chunk, &p.a_hi, &ctl->a_full[a_st], c * CK, ya);
+                            if (last) tma_load(dst + (c1 - c0) * L.a_chunk, &p.a_aug, &ctl->a_full[a_st], 0, ya);
+                        } else if (q < nc) {
                             bar_expect_tx(&ctl->a_full[a_st], L.a_chunk);
                             tma_load(dst, &p.a_hi, &ctl->a_full[a_st], q * CK, ya);
                         } else if (q < nq) {
@@ -333,18 +347,38 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
                     fence_after();
                     const uint32_t dacc = tmem + t_buf * NT;
                     uint32_t acc = 0;
-                    for (int q = 0; q <= nq; ++q) {
+                    for (int q = 0; q < nstage; ++q) {
                         if (!bar_wait(&ctl->a_full[a_st], a_ph, abort_flag, gerr)) { ok = false; break; }
                         fence_after();
-                        const uint32_t aa = sbase + L.a_off + a_st * L.a_chunk;
-                        if (q < nc) {
+                        const uint32_t aa = sbase + L.a_off + a_st * L.a_stage;
+                        if (PROD == 1 && cps == 1) {   // one chunk per stage (the common case)
+#pragma unroll
+                            for (int k = 0; k < CK / 16; ++k) {
+                                mma(dacc, sdesc(aa + k * 32, kSpan), sdesc(bb + q * L.b_chunk + k * 32, kSpan), kIdesc,
+                                    acc);
+                                acc = 1;
+                            }
+                            if (q == nstage - 1)   // the augmentation block rides in the last stage
+                                mma(dacc, sdesc(aa + L.a_chunk, 32), sdesc(bb + nq * L.b_chunk, 32), kIdesc, 1);
+                        } else if (PROD == 1) {   // the whole query tile in one stage
+#pragma unroll
+                            for (int c = 0; c < 2; ++c) {
+                                if (c >= nc) break;
+#pragma unroll
+                                for (int k = 0; k < CK / 16; ++k) {
+                                    mma(dacc, sdesc(aa + c * L.a_chunk + k * 32, kSpan),
+                                        sdesc(bb + c * L.b_chunk + k * 32, kSpan), kIdesc, acc);
+                                    acc = 1;
+                                }
+                            }
+                            mma(dacc, sdesc(aa + nc * L.a_chunk, 32), sdesc(bb + nq * L.b_chunk, 32), kIdesc, 1);
+                        } else if (q < nc) {
 #pragma unroll
                             for (int k = 0; k < CK / 16; ++k) {
                                 const unsigned long long ad = sdesc(aa + k * 32, kSpan);
                                 mma(dacc, ad, sdesc(bb + q * L.b_chunk + k * 32, kSpan), kIdesc, acc);
                                 acc = 1;
-                                if (PROD == 3)
-                                    mma(dacc, ad, sdesc(bb + (nc + q) * L.b_chunk + k * 32, kSpan), kIdesc, 1);
+                                mma(dacc, ad, sdesc(bb + (nc + q) * L.b_chunk + k * 32, kSpan), kIdesc, 1);
                             }
                         } else if (q < nq) {
                             const int c = q - nc;
@@ -527,7 +561,9 @@ constexpr uint32_t kMaxSmem = 232448;
     X(64, 256, 1, 5)    \
     X(64, 128, 2, 5)    \
     X(64, 128, 1, 4)    \
-    X(64, 64, 1, 4)
+    X(64, 64, 1, 4)     \
+    X(64, 256, 1, 3)    \
+    X(64, 256, 2, 2)
 
 constexpr TileConfig kShapes[] = {
 #define BM_X(a, b, c, d) {0, a, b, c, d},
@@ -538,13 +574,17 @@ constexpr TileConfig kShapes[] = {
 std::mutex g_tile_mu;
 std::map<int, TileConfig> g_tile_override;
 
-template <int CK, int NT, int BBUF, int ASTG, int PROD>
+template <int CK, int NT, int BBUF, int ASTG, int PROD, int CPS>
 cudaError_t launch_cfg(TcArgs& args, long long a_rows_max, cudaStream_t stream, std::string* why, int* grid_out) {
     const Layout L0 = make_layout(CK, NT, BBUF, ASTG, args.d_pad, PROD);
+    if (L0.cps != CPS) {
+        if (why) *why = "tile instantiation does not match the stage layout";
+        return cudaErrorInvalidValue;
+    }
     // at least 120 KB so that two CTAs never share an SM (each holds 2*NT TMEM columns)
     Layout L = L0;
     if (L.total < 120u * 1024u) L.total = 120u * 1024u;
-    auto kern = sweep_tc_kernel<CK, NT, BBUF, ASTG, PROD>;
+    auto kern = sweep_tc_kernel<CK, NT, BBUF, ASTG, PROD, CPS>;
     static int attr_bytes = 0;
     if (attr_bytes < (int)L.total) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
@@ -566,6 +606,17 @@ cudaError_t launch_cfg(TcArgs& args, long long a_rows_max, cudaStream_t stream, 
     note_launch();
     kern<<<(unsigned)grid, kThreads, L.total, stream>>>(args);
     return cudaGetLastError();
+}
+
+// fp16 whole-tile stages exist for 64-wide K chunks only (d_pad = 128).
+template <int CK, int NT, int BBUF, int ASTG>
+cudaError_t launch_whole(TcArgs& args, long long a_rows_max, cudaStream_t stream, std::string* why, int* grid_out) {
+    if constexpr (CK == 64) {
+        return launch_cfg<CK, NT, BBUF, ASTG, 1, 2>(args, a_rows_max, stream, why, grid_out);
+    } else {
+        if (why) *why = "whole-tile stages need 64-wide K chunks";
+        return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
@@ -612,8 +663,8 @@ TileConfig tile_config_builtin(int d, int prod) {
     if (d <= 16) return {16, 16, 256, 2, 8};
     if (d <= 32) return {32, 32, 256, 2, 8};
     const int d_pad = (d + 63) / 64 * 64;
-    const TileConfig order[] = {{d_pad, 64, 256, 2, 5}, {d_pad, 64, 256, 1, 5}, {d_pad, 64, 128, 2, 5},
-                                {d_pad, 64, 128, 1, 4}};
+    const TileConfig order[] = {{d_pad, 64, 256, 2, 5}, {d_pad, 64, 256, 1, 5}, {d_pad, 64, 256, 1, 3},
+                                {d_pad, 64, 128, 2, 5}, {d_pad, 64, 128, 1, 4}};
     for (const TileConfig& c : order)
         if (make_layout(c.ck, c.nt, c.bbuf, c.astg, c.d_pad, prod).total <= kMaxSmem) return c;
     return {d_pad, 64, 64, 1, 4};
@@ -629,8 +680,8 @@ TileConfig tile_config_for(int d, int prod) {
 }
 
 bool tile_config_set(int d, const TileConfig* c, std::string* why) {
-    // an override must fit both tensor-core representations (the split needs more room)
-    if (c && !tile_config_check(d, *c, why, 3)) return false;
+    // an override applies to both tensor-core representations, so it must fit both
+    if (c && !(tile_config_check(d, *c, why, 3) && tile_config_check(d, *c, why, 1))) return false;
     std::lock_guard<std::mutex> lk(g_tile_mu);
     if (c) g_tile_override[d] = *c;
     else g_tile_override.erase(d);
@@ -705,10 +756,14 @@ cudaError_t launch_sweep_tc(const SweepDesc& s, cudaStream_t stream, std::string
     args.eps2 = s.eps2;
     args.st = const_cast<DeviceState*>(s.st);
     args.sink = s.sink;
-#define BM_X(a, b, c, d)                                                                  \
-    if (cfg.ck == a && cfg.nt == b && cfg.bbuf == c && cfg.astg == d)                     \
-        return fp16 ? launch_cfg<a, b, c, d, 1>(args, s.a_rows_max, stream, why, grid_out)  \
-                    : launch_cfg<a, b, c, d, 3>(args, s.a_rows_max, stream, why, grid_out);
+    // fp16 with two K chunks keeps the whole query tile in one stage (a 64-wide chunk
+    // only: d_pad = 128)
+    const bool whole = fp16 && d_pad == 2 * CK && CK == 64;
+#define BM_X(a, b, c, d)                                                                        \
+    if (cfg.ck == a && cfg.nt == b && cfg.bbuf == c && cfg.astg == d)                           \
+        return !fp16  ? launch_cfg<a, b, c, d, 3, 1>(args, s.a_rows_max, stream, why, grid_out)   \
+               : !whole ? launch_cfg<a, b, c, d, 1, 1>(args, s.a_rows_max, stream, why, grid_out) \
+                        : launch_whole<a, b, c, d>(args, s.a_rows_max, stream, why, grid_out);
     BM_TC_SHAPES(BM_X)
 #undef BM_X
     if (why) *why = "tile shape not compiled";
