@@ -158,17 +158,20 @@ typedef struct {
  * small problems.  The greedy loops of all instances run inside one CUDA graph
  * launched once: a device-side WHILE loop per instance, the loops side by side,
  * each iteration one greedy step that decides on the device whether another is
- * needed.  Prep runs before the graph; CSR and nerve edges after it, per
- * instance.  An instance whose step buffers overflow inside the graph is
- * finished by the host-driven loop with larger buffers (same result).
+ * needed.  Prep runs before the graph; CSR and nerve edges after it, for all
+ * instances at once.  An instance whose step buffers overflow inside the graph
+ * is finished by the host-driven loop with larger buffers (same result).
  *   inst:     count instances (count >= 0); each validated like bm_build.
  *   opt:      stream, path, host_io, skip_edges, alloc/free as for bm_build;
  *             batch = largest candidate batch per step (0 = 1024).
  *   outs:     count graphs, caller-owned array; each filled like bm_build's out.
  *             stats.ms_total of every instance is the time of the whole call,
  *             ms_prep that of the prep of all instances, ms_greedy that of the
- *             graph launch, ms_members that of the per-instance tails (host
- *             resume, CSR, edges); ms_edges and ms_sweep stay 0.
+ *             graph launch, ms_members that of the tails (host resume of
+ *             overflowed instances, then CSR and nerve edges of all instances as
+ *             one renumbered build); ms_edges, ms_sweep and edge_pairs stay 0.
+ *             The instances together may hold at most 2^31 - 1 points and
+ *             landmarks (BM_ERR_CAPACITY otherwise).
  *   statuses: optional, count entries: BM_OK, or the status of the instance
  *             that failed.
  * On error every outs[i] is zeroed (nothing leaks) and the first failing

@@ -25,7 +25,7 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--n-lo", type=int, default=1000)
     ap.add_argument("--n-hi", type=int, default=200000)
-    ap.add_argument("--path", default="tc")
+    ap.add_argument("--path", default="auto")
     ap.add_argument("--batch", type=int, default=0, help="largest candidate batch per step (0 = library default)")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)

@@ -16,7 +16,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="roll-n2M-d128")
     ap.add_argument("--eps", type=float, nargs="*", default=None)
-    ap.add_argument("--path", choices=["auto", "tc", "tc16", "fp32"], default="tc")
+    ap.add_argument("--path", choices=["auto", "tc", "tc16", "fp32"], default="auto")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--skip-edges", action="store_true")
     a = ap.parse_args(argv)

@@ -1354,158 +1354,133 @@ bm_status build_batched(const bm_instance* inst, int count, const bm_options& op
         tm.mark();  // 3: graph done
         TRY_SYNC(s, "the graph of greedy loops");
     }
-    // 4. tails, staged over all instances with one host synchronisation per stage:
-    //    states -> (resume) -> CSR + transpose -> pair emission -> scatter + hand-over
+    // 4. states; an instance stopped inside the graph (buffer overflow) is finished by
+    //    the host loop
     std::vector<unsigned> hiters(std::max(count, 1));
     std::vector<DeviceState> hst(std::max(count, 1));
     TRY_CUDA(cudaMemcpyAsync(hiters.data(), iters, sizeof(unsigned) * std::max(count, 1), cudaMemcpyDeviceToHost, s));
     TRY_CUDA(cudaMemcpyAsync(hst.data(), sts, sizeof(DeviceState) * std::max(count, 1), cudaMemcpyDeviceToHost, s));
     TRY_SYNC(s, "reading the instance states");
-    PinnedI64 hP(count), hE(count), hB(count);
-    if (!hP.p || !hE.p || !hB.p) return fail(BM_ERR_NOMEM, "pinned host buffers");
-    for (int i = 0; i < count; ++i) hB.p[i] = 0;
-    struct Tail {
-        DeviceState fin;
-        long long L = 0, nnz = 0, executed = 0;
-        long long* offsets = nullptr;
-        int* ids = nullptr;
-        int* edges = nullptr;
-        long long E = 0, P = 0;
-        EdgeJob job;
-        bool staged = false;   // edges go through the staged pass
-        bool multi = false;    // ... but need several chunks (per-build pass)
-    };
-    std::vector<Tail> tails(count);
-    HostState hs;
+    std::vector<long long> executed(std::max(count, 1), 0);
+    {
+        HostState hs;
+        for (int i = 0; i < count; ++i) {
+            BatchItem& it = items[i];
+            if (it.n == 0) continue;
+            executed[i] = (long long)hiters[i] * it.body_kernels;
+            if (!hst[i].done || hst[i].error) {
+                const long long k0 = g_kernel_launches;
+                bm_status rs = greedy_drive(it.gc, it.px, *it.ar, s, hs, it.step_cap, it.mem_cap, hst[i], stimer, true);
+                if (rs != BM_OK) return tag(i, rs);
+                executed[i] += g_kernel_launches - k0;
+            }
+            release_sweep_out(*it.ar, it.gc.so, false);
+        }
+    }
+    // 5. the tails as one build: memberships of all instances renumbered into global
+    //    rows and points, then one sort, one CSR and one nerve pass (bm_batch.cu)
+    std::vector<int> live;   // instances with points
+    for (int i = 0; i < count; ++i)
+        if (items[i].n > 0) live.push_back(i);
+    const int nl = (int)live.size();
+    std::vector<long long> row_base(nl + 1, 0), pt_base(nl + 1, 0), key_off(nl + 1, 0);
+    std::vector<const unsigned long long*> srcs(std::max(nl, 1), nullptr);
+    for (int k = 0; k < nl; ++k) {
+        const int i = live[k];
+        row_base[k + 1] = row_base[k] + hst[i].n_landmarks;
+        pt_base[k + 1] = pt_base[k] + items[i].n;
+        key_off[k + 1] = key_off[k] + (long long)hst[i].mem_count;
+        srcs[k] = items[i].gc.g.mem_keys;
+    }
+    const long long L_all = row_base[nl], n_all = pt_base[nl], nnz_all = key_off[nl];
+    if (n_all > 0x7fffffffLL || L_all > 0x7fffffffLL)
+        return fail(BM_ERR_CAPACITY, "a batch holds more than 2^31-1 points or landmarks in total; split it");
+    long long *d_rb, *d_pb, *d_ko, *d_bounds;
+    const unsigned long long** d_srcs;
+    ALLOC(d_rb, long long, nl + 1);
+    ALLOC(d_pb, long long, nl + 1);
+    ALLOC(d_ko, long long, nl + 1);
+    ALLOC(d_bounds, long long, nl + 1);
+    ALLOC(d_srcs, const unsigned long long*, std::max(nl, 1));
+    TRY_CUDA(cudaMemcpyAsync(d_rb, row_base.data(), sizeof(long long) * (nl + 1), cudaMemcpyHostToDevice, s));
+    TRY_CUDA(cudaMemcpyAsync(d_pb, pt_base.data(), sizeof(long long) * (nl + 1), cudaMemcpyHostToDevice, s));
+    TRY_CUDA(cudaMemcpyAsync(d_ko, key_off.data(), sizeof(long long) * (nl + 1), cudaMemcpyHostToDevice, s));
+    TRY_CUDA(cudaMemcpyAsync(d_srcs, srcs.data(), sizeof(void*) * std::max(nl, 1), cudaMemcpyHostToDevice, s));
+    unsigned long long* gkeys;
+    ALLOC(gkeys, unsigned long long, std::max<long long>(nnz_all, 1));
+    TRY_CUDA(launch_gather_batch_keys(d_srcs, d_ko, d_rb, d_pb, nl, nnz_all, gkeys, s));
+    long long* goff = nullptr;
+    int* gids = nullptr;
+    int* gedges = nullptr;
+    long long E_all = 0, pairs_all = 0;
+    if (nl > 0) {
+        bm_status rs = members_and_edges(ar, s, opt, n_all, L_all, nnz_all, gkeys, nullptr, &goff, &gids, &gedges,
+                                         &E_all, &pairs_all);
+        if (rs != BM_OK) return rs;
+        TRY_CUDA(launch_edge_bounds(gedges, E_all, d_rb, nl, d_bounds, s));
+    }
+    std::vector<long long> bounds(nl + 1, 0);
+    TRY_CUDA(cudaMemcpyAsync(bounds.data(), d_bounds, sizeof(long long) * (nl + 1), cudaMemcpyDeviceToHost, s));
+    TRY_SYNC(s, "the membership and nerve passes over all instances");
+    // 6. per-instance outputs cut from the global results
+    std::vector<BatchSplit> parts(std::max(nl, 1));
+    for (int k = 0; k < nl; ++k) {
+        const int i = live[k];
+        Arena& iar = *items[i].ar;
+        BatchSplit& p = parts[k];
+        p.row_base = row_base[k];
+        p.rows = row_base[k + 1] - row_base[k];
+        p.pt_base = pt_base[k];
+        p.nnz = key_off[k + 1] - key_off[k];
+        p.edge0 = bounds[k];
+        p.n_edges = bounds[k + 1] - bounds[k];
+        p.offsets = (long long*)iar.get_standalone(sizeof(long long) * (p.rows + 1));
+        p.ids = (int*)iar.get_standalone(sizeof(int) * std::max<long long>(p.nnz, 1));
+        p.edges = (int*)iar.get_standalone(sizeof(int) * 2 * std::max<long long>(p.n_edges, 1));
+        if (!p.offsets || !p.ids || !p.edges) return tag(i, fail(BM_ERR_NOMEM, "result buffers"));
+    }
+    BatchSplit* d_parts;
+    ALLOC(d_parts, BatchSplit, std::max(nl, 1));
+    TRY_CUDA(cudaMemcpyAsync(d_parts, parts.data(), sizeof(BatchSplit) * std::max(nl, 1), cudaMemcpyHostToDevice, s));
+    if (nl > 0) TRY_CUDA(launch_split_batch(d_parts, nl, goff, gids, gedges, s));
+    int k = 0;
     for (int i = 0; i < count; ++i) {
         BatchItem& it = items[i];
-        Tail& t = tails[i];
-        if (it.n == 0) continue;
-        Arena& iar = *it.ar;
-        t.executed = (long long)hiters[i] * it.body_kernels;
-        const long long k0 = g_kernel_launches;
-        t.fin = hst[i];
-        if (!t.fin.done || t.fin.error) {   // stopped inside the graph: finish on the host
-            bm_status rs = greedy_drive(it.gc, it.px, iar, s, hs, it.step_cap, it.mem_cap, t.fin, stimer, true);
-            if (rs != BM_OK) return tag(i, rs);
-        }
-        release_sweep_out(iar, it.gc.so, false);
-        t.L = t.fin.n_landmarks;
-        t.nnz = (long long)t.fin.mem_count;
-        // memberships: sort, CSR into buffers of their own (they are results)
-        unsigned long long* tmp;
-        ALLOC(tmp, unsigned long long, std::max<long long>(t.nnz, 1));
-        unsigned long long* sorted = nullptr;
-        cudaError_t ce = radix_sort_u64(it.gc.g.mem_keys, tmp, t.nnz,
-                                        digit_shifts(bits_for(it.n - 1), bits_for(t.L - 1)), iar, s, &sorted);
-        if (ce != cudaSuccess) return tag(i, fail(BM_ERR_CUDA, std::string("membership sort: ") + cudaGetErrorString(ce)));
-        t.offsets = (long long*)iar.get_standalone(sizeof(long long) * (t.L + 1));
-        t.ids = (int*)iar.get_standalone(sizeof(int) * std::max<long long>(t.nnz, 1));
-        if (!t.offsets || !t.ids) return tag(i, fail(BM_ERR_NOMEM, "membership CSR"));
-        ce = launch_csr_from_sorted(sorted, t.nnz, t.L, t.offsets, t.ids, s);
-        if (ce != cudaSuccess) return tag(i, fail(BM_ERR_CUDA, std::string("membership CSR: ") + cudaGetErrorString(ce)));
-        hP.p[i] = 0;
-        if (!opt.skip_edges && t.nnz > 0 && t.L >= 2) {
-            t.job.keys = sorted;
-            t.job.moff = t.offsets;
-            t.job.nnz = t.nnz;
-            t.job.n = it.n;
-            t.job.L = t.L;
-            Failure f{BM_OK, ""};
-            if (!edges_transpose(t.job, iar, s, f)) return tag(i, fail(f.status, f.msg));
-            ce = cudaMemcpyAsync(&hP.p[i], t.job.lpre + t.L, sizeof(long long), cudaMemcpyDeviceToHost, s);
-            if (ce != cudaSuccess) return tag(i, fail(BM_ERR_CUDA, "pair count copy"));
-            t.staged = true;
-        }
-        t.executed += g_kernel_launches - k0;
-    }
-    TRY_SYNC(s, "the membership and transpose pass");
-    for (int i = 0; i < count; ++i) {
-        Tail& t = tails[i];
-        if (!t.staged) continue;
-        t.P = hP.p[i];
-        hE.p[i] = 0;
-        if (t.P == 0) continue;
-        t.job.bitmap = edges_choose_bitmap(t.L, t.P);
-        t.multi = t.job.bitmap ? edges_bitmap_rows(t.L) < t.L : t.P > kEdgeChunkPairs;
-        if (t.multi) continue;   // several chunks: the per-build nerve pass below
-        const long long k0 = g_kernel_launches;
-        Failure f{BM_OK, ""};
-        if (!edges_emit(t.job, 0, (int)t.L, t.P, *items[i].ar, s, f)) return tag(i, fail(f.status, f.msg));
-        TRY_CUDA(cudaMemcpyAsync(&hE.p[i], t.job.count_dev, sizeof(long long), cudaMemcpyDeviceToHost, s));
-        t.executed += g_kernel_launches - k0;
-    }
-    TRY_SYNC(s, "the pair deduplication pass");
-    for (int i = 0; i < count; ++i) {
-        BatchItem& it = items[i];
-        Tail& t = tails[i];
         Arena& iar = *it.ar;
         bm_graph g;
         std::memset(&g, 0, sizeof(g));
-        int* landmarks = nullptr;
-        long long edge_pairs = t.P;
-        const long long k0 = g_kernel_launches;
+        bm_status rs;
         if (it.n == 0) {
-            landmarks = (int*)iar.get(sizeof(int));
-            t.offsets = (long long*)iar.get(sizeof(long long));
-            t.ids = (int*)iar.get(sizeof(int));
-            if (!landmarks || !t.offsets || !t.ids) return tag(i, fail(BM_ERR_NOMEM, "empty result"));
-            if (cudaMemsetAsync(t.offsets, 0, sizeof(long long), s) != cudaSuccess) {
+            int* lm = (int*)iar.get(sizeof(int));
+            long long* off = (long long*)iar.get(sizeof(long long));
+            int* ids = (int*)iar.get(sizeof(int));
+            int* edges = (int*)iar.get(2 * sizeof(int));
+            if (!lm || !off || !ids || !edges) return tag(i, fail(BM_ERR_NOMEM, "empty result"));
+            if (cudaMemsetAsync(off, 0, sizeof(long long), s) != cudaSuccess) {
                 cudaGetLastError();
                 return tag(i, fail(BM_ERR_CUDA, "memset"));
             }
+            rs = hand_over(iar, s, host_io, lm, off, ids, edges, 0, 0, 0, g);
         } else {
-            landmarks = it.gc.g.landmarks;
-            if (t.staged && t.multi) {
-                // several chunks: the per-build nerve pass
-                edges_release(t.job, iar);
-                Failure f{BM_OK, ""};
-                EdgeResult er;
-                if (!build_edges(t.job.keys, t.offsets, t.nnz, it.n, t.L, iar, s, er, f))
-                    return tag(i, fail(f.status, f.msg));
-                t.edges = er.edges;
-                t.E = er.n_edges;
-                edge_pairs = er.pairs;
-            } else if (t.staged && t.P > 0) {
-                t.E = hE.p[i];
-                if (t.E > 0x7fffffffLL) return tag(i, fail(BM_ERR_CAPACITY, "more than 2^31-1 edges"));
-                t.edges = (int*)iar.get_standalone(sizeof(int) * 2 * std::max<long long>(t.E, 1));
-                if (!t.edges) return tag(i, fail(BM_ERR_NOMEM, "edge buffer"));
-                Failure f{BM_OK, ""};
-                if (!edges_scatter(t.job, 0, (int)t.L, t.P, t.edges, iar, s, f)) return tag(i, fail(f.status, f.msg));
-                if (t.job.bad) {   // checked once for all instances below
-                    hB.p[i] = 0;
-                    TRY_CUDA(cudaMemcpyAsync(&hB.p[i], t.job.bad, sizeof(int), cudaMemcpyDeviceToHost, s));
-                }
-                edges_release(t.job, iar);
-            }
+            const BatchSplit& p = parts[k++];
+            rs = hand_over(iar, s, host_io, it.gc.g.landmarks, p.offsets, p.ids, p.edges, p.rows, p.nnz, p.n_edges, g);
         }
-        if (!t.edges) {
-            t.edges = (int*)iar.get(2 * sizeof(int));
-            if (!t.edges) return tag(i, fail(BM_ERR_NOMEM, "edge buffer"));
-        }
-        bm_status rs = hand_over(iar, s, host_io, landmarks, t.offsets, t.ids, t.edges, t.L, t.nnz, t.E, g);
         if (rs != BM_OK) return tag(i, rs);
-        t.executed += g_kernel_launches - k0;
-        const DeviceState& fin = t.fin;
-        g.stats.distance_evals = (int64_t)t.L * it.n;
+        const DeviceState& fin = hst[i];
+        g.stats.distance_evals = (int64_t)g.n_landmarks * it.n;
         g.stats.tile_pairs = (int64_t)fin.tile_pairs;
         g.stats.band_pairs = (int64_t)fin.band_pairs;
         g.stats.greedy_steps = (int64_t)fin.steps;
         g.stats.candidates = (int64_t)fin.candidates;
-        g.stats.edge_pairs = edge_pairs;
+        g.stats.edge_pairs = 0;   // witnessed pairs are counted for the whole batch only
         g.stats.band_delta = fin.delta;
         g.stats.path = path;
-        g.stats.kernel_launches = t.executed;
+        g.stats.kernel_launches = executed[i];
         outs[i] = g;
         if (statuses) statuses[i] = BM_OK;
-        it.ar.reset();  // the instance's scratch
     }
-    TRY_SYNC(s, "the edge extraction pass");
-    for (int i = 0; i < count; ++i)
-        if (hB.p[i])
-            return tag(i, fail(BM_ERR_CUDA, "nerve pass: a cover list broke its invariants (code " +
-                                                std::to_string(hB.p[i]) + ")"));
+    TRY_SYNC(s, "the split of the results");
+    for (int i = 0; i < count; ++i) items[i].ar.reset();   // instance scratch
     tm.mark();  // 4
     const double total = tm.ms(0, 4), prep = tm.ms(0, 1), graph = tm.ms(2, 3), tail = tm.ms(3, 4);
     for (int i = 0; i < count; ++i) {

@@ -258,4 +258,19 @@ bool edges_emit(EdgeJob& j, int i0, int i1, long long Pc, Arena& ar, cudaStream_
 bool edges_scatter(EdgeJob& j, int i0, int i1, long long Pc, int* dst, Arena& ar, cudaStream_t s, Failure& f);
 void edges_release(EdgeJob& j, Arena& ar);
 
+// batch.cu -- the tail of a batched build as one build over all instances
+struct BatchSplit {        // one instance's share of the global results
+    long long* offsets;    // rows + 1 (output)
+    int* ids;              // nnz (output)
+    int* edges;            // 2 n_edges (output)
+    long long row_base, rows, pt_base, nnz, edge0, n_edges;
+};
+cudaError_t launch_gather_batch_keys(const unsigned long long* const* srcs, const long long* key_off,
+                                     const long long* row_base, const long long* pt_base, int count,
+                                     long long total, unsigned long long* dst, cudaStream_t s);
+cudaError_t launch_edge_bounds(const int* edges, long long E, const long long* row_base, int count, long long* bounds,
+                               cudaStream_t s);
+cudaError_t launch_split_batch(const BatchSplit* parts, int count, const long long* goff, const int* gids,
+                               const int* gedges, cudaStream_t s);
+
 }  // namespace bm

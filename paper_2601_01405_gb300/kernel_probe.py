@@ -17,7 +17,7 @@ def main(argv=None):
     ap.add_argument("--workload", default="mix32-n1M-d64")
     ap.add_argument("--rows", type=int, default=1024)
     ap.add_argument("--eps", type=float, default=4.0)
-    ap.add_argument("--path", choices=["auto", "tc", "tc16", "fp32"], default="tc")
+    ap.add_argument("--path", choices=["auto", "tc", "tc16", "fp32"], default="auto")
     ap.add_argument("--repeat", type=int, default=3)
     a = ap.parse_args(argv)
 
