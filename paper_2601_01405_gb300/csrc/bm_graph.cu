@@ -196,6 +196,91 @@ __global__ void nerve_bits_kernel(const unsigned long long* keys, const long lon
     }
 }
 
+// Row-per-block bitmap emission (rows of up to 51,200 words): a block takes landmark
+// rows i from a counter and builds row i in shared memory from the memberships (i, x)
+// and the later entries j of each x's cover list (shared-memory atomicOr, one per run
+// of lanes on a word, as above), then stores the row's non-zero words.  No global
+// atomics, and a heavy row never spreads its bits over L2.  Same input checks as
+// nerve_bits_kernel.
+__global__ void __launch_bounds__(512) nerve_rows_kernel(const unsigned long long* keys, const long long* moff,
+                                                         const long long* toff, const int* tlist, long long nnz,
+                                                         long long n, int i0, int i1, long long W, unsigned* bits,
+                                                         int* bad, int* next_row) {
+    extern __shared__ unsigned srow[];
+    __shared__ int s_row;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (long long w = threadIdx.x; w < W; w += blockDim.x) srow[w] = 0u;
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_row = atomicAdd(next_row, 1);
+        __syncthreads();
+        const long long i = (long long)i0 + s_row;
+        if (i >= i1) break;
+        const long long e0 = moff[i], e1 = moff[i + 1];
+        if (e0 < 0 || e1 > nnz || e0 > e1) {
+            if (threadIdx.x == 0) atomicOr(bad, 16);
+            continue;
+        }
+        for (long long e = e0 + warp; e < e1; e += nwarps) {
+            const unsigned long long key = keys[e];
+            const long long x = (long long)(key & 0xffffffffull);
+            if ((long long)(key >> 32) != i || x >= n) {
+                if (lane == 0) atomicOr(bad, 1);
+                continue;
+            }
+            const long long b0 = toff[x], end = toff[x + 1];
+            if (b0 < 0 || end > nnz || b0 >= end) {
+                if (lane == 0) atomicOr(bad, 2);
+                continue;
+            }
+            const long long t = lower_bound_i32(tlist, b0, end, (int)i);
+            if (t >= end || tlist[t] != (int)i) {
+                if (lane == 0) atomicOr(bad, 32);
+                continue;
+            }
+            // four loads in flight per lane before the bits are combined
+            for (long long base = t + 1; base < end; base += 128) {
+                int jv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const long long b = base + u * 32 + lane;
+                    jv[u] = b < end ? tlist[b] : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (base + u * 32 >= end) break;   // warp-uniform
+                    const bool valid = base + u * 32 + lane < end;
+                    int j = jv[u];
+                    if (valid && (j <= (int)i || (long long)(j >> 5) >= W)) {
+                        atomicOr(bad, 4);
+                        j = 0;
+                    }
+                    const bool ok = valid && j > (int)i;
+                    const int word = ok ? (j >> 5) : -1 - lane;
+                    unsigned acc = ok ? (1u << (j & 31)) : 0u;
+#pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const unsigned v = __shfl_down_sync(kFull, acc, off);
+                        const int w = __shfl_down_sync(kFull, word, off);
+                        if (lane + off < 32 && w == word) acc |= v;
+                    }
+                    const int wprev = __shfl_up_sync(kFull, word, 1);
+                    if (ok && (lane == 0 || wprev != word)) atomicOr(&srow[word], acc);
+                }
+            }
+        }
+        __syncthreads();
+        unsigned* row = bits + (i - i0) * W;
+        for (long long w = ((i + 1) >> 5) + threadIdx.x; w < W; w += blockDim.x) {
+            const unsigned v = srow[w];
+            if (v) {
+                row[w] = v;
+                srow[w] = 0u;
+            }
+        }
+    }
+}
+
 // Set bits per bitmap row (one warp per row).
 __global__ void bitrow_counts_kernel(const unsigned* bits, long long R, long long W, long long* cnt) {
     const int lane = threadIdx.x & 31;
@@ -210,19 +295,40 @@ __global__ void bitrow_counts_kernel(const unsigned* bits, long long R, long lon
     }
 }
 
-// Row r's set bits, in ascending order, become edges (i0 + r, j) at
-// positions roff[r] ... (one warp per row; a warp scan orders its lanes).
+// Position of the r-th (0-based) set bit of v (popcount bisection).
+__device__ __forceinline__ int nth_set_bit(unsigned v, int r) {
+    int pos = 0;
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) {
+        const unsigned low = (1u << sh) - 1u;
+        const int c = __popc(v & low);
+        if (r >= c) {
+            r -= c;
+            v >>= sh;
+            pos += sh;
+        } else {
+            v &= low;
+        }
+    }
+    return pos;
+}
+
+// Row r's set bits, in ascending order, become edges (i0 + r, j) at positions
+// roff[r] ... (one warp per row).  Per 32 words the warp scans the popcounts and
+// writes the group's edges with consecutive lanes on consecutive slots: slot k's
+// word is found by bisection over the scanned counts, its bit by nth_set_bit.
 __global__ void bitrow_extract_kernel(const unsigned* bits, long long R, long long W, int i0, const long long* roff,
                                       int* edges, int* bad) {
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     const long long total = roff[R];
+    int2* out = reinterpret_cast<int2*>(edges);
     for (long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < R; r += warps) {
         const unsigned* row = bits + r * W;
         long long pos = roff[r];
         const int i = i0 + (int)r;
-        for (long long w0 = 0; w0 < W; w0 += 32) {
-            unsigned word = (w0 + lane < W) ? row[w0 + lane] : 0u;
+        for (long long w0 = ((long long)i + 1) >> 5 & ~31LL; w0 < W; w0 += 32) {
+            const unsigned word = (w0 + lane < W) ? row[w0 + lane] : 0u;
             const int c = __popc(word);
             int incl = c;
 #pragma unroll
@@ -230,20 +336,24 @@ __global__ void bitrow_extract_kernel(const unsigned* bits, long long R, long lo
                 const int y = __shfl_up_sync(kFull, incl, o);
                 if (lane >= o) incl += y;
             }
-            long long o = pos + (incl - c);
-            const int jbase = (int)((w0 + lane) * 32);
-            while (word) {
-                const int b = __ffs(word) - 1;
-                if (o < total) {
-                    edges[2 * o] = i;
-                    edges[2 * o + 1] = jbase + b;
-                } else {
-                    atomicOr(bad, 8);
+            const int T = __shfl_sync(kFull, incl, 31);
+            for (int kb = 0; kb < T; kb += 32) {
+                const int k = kb + lane;
+                int owner = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int v = __shfl_sync(kFull, incl, owner + step - 1);
+                    if (v <= k) owner += step;
                 }
-                ++o;
-                word &= word - 1;
+                const unsigned ow = __shfl_sync(kFull, word, owner & 31);
+                const int before = __shfl_sync(kFull, incl - c, owner & 31);
+                if (k < T) {
+                    const long long o = pos + k;
+                    if (o < total) out[o] = make_int2(i, (int)((w0 + owner) * 32) + nth_set_bit(ow, k - before));
+                    else atomicOr(bad, 8);
+                }
             }
-            pos += __shfl_sync(kFull, incl, 31);
+            pos += T;
         }
     }
 }
@@ -390,6 +500,8 @@ long long edges_set_bitmap_budget(long long bytes) {
 
 long long edges_bitmap_words(long long L) { return (L + 31) / 32; }
 
+constexpr long long kRowBlockWords = 51200;   // 200 KB of shared memory per row block
+
 bool edges_choose_bitmap(long long L, long long P) {
     if (edges_bitmap_budget() < 0) return false;
     const double bytes = (double)L * (double)edges_bitmap_words(L) * 4.0;
@@ -413,10 +525,28 @@ bool edges_emit(EdgeJob& j, int i0, int i1, long long Pc, Arena& ar, cudaStream_
             BM_ALLOC(j.bad, int, 1);
             BM_TRY(cudaMemsetAsync(j.bad, 0, sizeof(int), s));
         }
-        note_launch();
-        nerve_bits_kernel<<<grid_for(j.nnz * 32, 256), 256, 0, s>>>(j.keys, j.moff, j.toff, j.tlist, j.nnz, n, i0, i1,
-                                                                     W, j.bits, j.bad);
-        BM_TRY(cudaGetLastError());
+        if (W <= kRowBlockWords) {
+            // rows built in shared memory, one block per row at a time
+            static bool attr_set = false;
+            if (!attr_set) {
+                BM_TRY(cudaFuncSetAttribute(nerve_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(kRowBlockWords * sizeof(unsigned))));
+                attr_set = true;
+            }
+            int* next_row;
+            BM_ALLOC(next_row, int, 1);
+            BM_TRY(cudaMemsetAsync(next_row, 0, sizeof(int), s));
+            const int per_sm = W * 4 <= 48 * 1024 ? 4 : (W * 4 <= 100 * 1024 ? 2 : 1);
+            note_launch();
+            nerve_rows_kernel<<<(unsigned)(device_sm_count() * per_sm), 512, (size_t)W * sizeof(unsigned), s>>>(
+                j.keys, j.moff, j.toff, j.tlist, j.nnz, n, i0, i1, W, j.bits, j.bad, next_row);
+            BM_TRY(cudaGetLastError());
+        } else {
+            note_launch();
+            nerve_bits_kernel<<<grid_for(j.nnz * 32, 256), 256, 0, s>>>(j.keys, j.moff, j.toff, j.tlist, j.nnz, n, i0,
+                                                                         i1, W, j.bits, j.bad);
+            BM_TRY(cudaGetLastError());
+        }
         long long* cnt;
         BM_ALLOC(cnt, long long, R + 1);
         note_launch();
