@@ -84,9 +84,11 @@ typedef struct {
     void* stream;          /* cudaStream_t; NULL = legacy default stream */
     int32_t path;          /* bm_path */
     int32_t host_io;       /* 0: device pointers in and out; 1: host pointers in and out */
-    int32_t batch;         /* largest greedy batch (candidates per step), 32..2048, multiple of 32; 0 = 2048.
-                              The batch starts at min(batch, 256) and doubles / halves with the share of
-                              candidates that become landmarks. */
+    int32_t batch;         /* largest greedy batch (candidates per step), multiple of 32: 32..8192 for
+                              bm_build, 32..2048 for bm_build_batched; 0 = 8192 (bm_build).
+                              The batch starts at min(batch, 256), doubles while 90 % of the
+                              candidates become landmarks (99 % past 2048, 99.5 % past 4096) and
+                              halves below 50 % (90 % past 2048). */
     int32_t skip_edges;    /* bm_build: 1 = landmarks and memberships only (no nerve pass) */
     bm_alloc_fn alloc;     /* optional device allocator for outputs and scratch */
     bm_free_fn free;

@@ -18,6 +18,7 @@ def main(argv=None):
     ap.add_argument("--eps", type=float, nargs="*", default=None)
     ap.add_argument("--path", choices=["auto", "tc", "tc16", "fp32"], default="auto")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=0, help="largest greedy batch (0 = the library default)")
     ap.add_argument("--skip-edges", action="store_true")
     a = ap.parse_args(argv)
 
@@ -28,19 +29,19 @@ def main(argv=None):
     X = workloads.make(a.workload)
     Xd = torch.from_numpy(X).cuda()
     for eps in (a.eps or list(wl.eps)):
-        binding.bm_build(Xd, eps, path=a.path, skip_edges=a.skip_edges)
+        binding.bm_build(Xd, eps, path=a.path, batch=a.batch, skip_edges=a.skip_edges)
         torch.cuda.synchronize()
         runs = []
         out = None
         for _ in range(a.reps):
             out = None
-            out = binding.bm_build(Xd, eps, path=a.path, skip_edges=a.skip_edges)
+            out = binding.bm_build(Xd, eps, path=a.path, batch=a.batch, skip_edges=a.skip_edges)
             torch.cuda.synchronize()
             runs.append(out["stats"])
         med = {k: statistics.median(r[k] for r in runs)
                for k in ("ms_total", "ms_prep", "ms_greedy", "ms_members", "ms_edges", "ms_sweep")}
         st = runs[-1]
-        print(json.dumps({"workload": a.workload, "eps": eps, "path": a.path, "n": X.shape[0], "d": X.shape[1],
+        print(json.dumps({"workload": a.workload, "eps": eps, "path": a.path, "batch": a.batch, "n": X.shape[0], "d": X.shape[1],
                           "landmarks": int(out["landmarks"].numel()), "memberships": int(out["ids"].numel()),
                           "edges": int(out["edges"].shape[0]), "edge_pairs": st["edge_pairs"],
                           "greedy_steps": st["greedy_steps"], "band_pairs": st["band_pairs"],

@@ -1005,8 +1005,8 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
                       int nprobe, const int* fixed_lm, long long nL, bm_graph* out) {
     std::memset(out, 0, sizeof(*out));
     int S = opt.batch;
-    if (S == 0) S = 2048;
-    if (S < 32 || S > 2048 || S % 32) return fail(BM_ERR_ARG, "batch must be a multiple of 32 in [32, 2048]");
+    if (S == 0) S = 8192;
+    if (S < 32 || S > 8192 || S % 32) return fail(BM_ERR_ARG, "batch must be a multiple of 32 in [32, 8192]");
     cudaStream_t s = (cudaStream_t)opt.stream;
     const bool host_io = opt.host_io != 0;
     const double eps2 = (double)eps * (double)eps;

@@ -44,12 +44,14 @@ __global__ void __launch_bounds__(kSelThreads) greedy_select_kernel(
     const int tid = threadIdx.x;
 
     // 1. undo the previous step's bookkeeping: conflict bits live only in the rows
-    //    flagged in row_any, so only those rows are cleared
+    //    flagged in row_any and in their first ceil(prev / 32) words (columns are
+    //    candidate slots), so only those are cleared
     const int prev = st->cand_count;
+    const int prev_words = (prev + 31) >> 5;
     for (int i = tid; i < prev; i += kSelThreads) slot_of[cand_ids[i]] = -1;
     for (int k = tid; k < prev; k += kSelThreads)
         if ((row_any[k >> 5] >> (k & 31)) & 1u)
-            for (int w = 0; w < words; ++w) conflict[(size_t)k * words + w] = 0;
+            for (int w = 0; w < prev_words; ++w) conflict[(size_t)k * words + w] = 0;
     __syncthreads();
     for (int i = tid; i < words; i += kSelThreads) row_any[i] = 0;
     __shared__ int s_req;
@@ -148,17 +150,18 @@ __global__ void __launch_bounds__(256) greedy_gather_kernel(
 // the sweep; flagged rows are staged in shared memory (as many as fit; the rest
 // are read from global memory).  One warp then walks the flagged candidates in
 // index order: candidate k is a landmark iff no earlier landmark candidate
-// covers it (its bit is clear in the running 'killed' set, two words per
-// lane).  Finally every thread assigns ordinals in parallel, and the next
-// step's batch size follows the survival rate (fewer wasted candidate rows on
-// dense data, larger batches where balls are small).
-constexpr int kMaxWords = 64;   // batches of up to 2048 candidates
+// covers it (its bit is clear in the running 'killed' set, kLaneWords words per
+// lane: word lane + 32 h).  Finally every thread assigns ordinals in parallel,
+// and the next step's batch size follows the survival rate (fewer wasted
+// candidate rows on dense data, larger batches where balls are small).
+constexpr int kMaxWords = 256;   // batches of up to 8192 candidates
+constexpr int kLaneWords = kMaxWords / 32;
 
 __global__ void __launch_bounds__(256) greedy_resolve_kernel(DeviceState* st, const unsigned* conflict,
                                                              const unsigned* row_any, int words,
                                                              const int* cand_ids, int* ordinal,
                                                              int* landmarks, unsigned long long mem_cap,
-                                                             int stage_rows, int s_max) {
+                                                             int stage_words, int s_max) {
     if (st->done) return;
     // the new memberships are a subset of this step's hits: stop before anything
     // is committed if they might not fit (the host grows the buffer and redoes the step)
@@ -169,16 +172,18 @@ __global__ void __launch_bounds__(256) greedy_resolve_kernel(DeviceState* st, co
         }
         return;
     }
-    extern __shared__ unsigned s_rows[];   // staged flagged rows: min(nflag, stage_rows) x words
+    extern __shared__ unsigned s_rows[];   // staged flagged rows, cw words each (stage_words in all)
     __shared__ int s_rank_of_word[kMaxWords + 1];
     __shared__ int s_flag_row[kMaxWords * 32];
     __shared__ unsigned s_alive[kMaxWords];
     __shared__ int s_nflag;
     const int c = st->cand_count;
+    const int cw = (c + 31) >> 5;   // words of a conflict row that can hold bits (slots < c)
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid < 32) {
         int base = 0;
-        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int h = 0; h < kLaneWords; ++h) {
             const int w = lane + 32 * h;
             unsigned a = w < words ? row_any[w] : 0u;
             if (w * 32 >= c) a = 0u;
@@ -203,28 +208,37 @@ __global__ void __launch_bounds__(256) greedy_resolve_kernel(DeviceState* st, co
     }
     __syncthreads();
     const int nflag = s_nflag;
+    const int stage_rows = cw > 0 ? stage_words / cw : 0;
     const int staged = nflag < stage_rows ? nflag : stage_rows;
-    for (int e = tid; e < staged * words; e += blockDim.x) {
-        const int f = e / words, wi = e - f * words;
+    for (int e = tid; e < staged * cw; e += blockDim.x) {
+        const int f = e / cw, wi = e - f * cw;
         s_rows[e] = conflict[(size_t)s_flag_row[f] * words + wi];
     }
     __syncthreads();
     if (tid < 32) {
-        unsigned killed0 = 0, killed1 = 0;  // words lane and lane + 32 of the killed set
+        unsigned killed[kLaneWords];
+#pragma unroll
+        for (int h = 0; h < kLaneWords; ++h) killed[h] = 0u;
         for (int f = 0; f < nflag; ++f) {
             const int k = s_flag_row[f], w = k >> 5;
-            const unsigned kw = __shfl_sync(kFull, w < 32 ? killed0 : killed1, w & 31);
+            unsigned mine = 0u;   // this lane's copy of word (w mod 32) + 32 h, h = w / 32
+#pragma unroll
+            for (int h = 0; h < kLaneWords; ++h)
+                if ((w >> 5) == h) mine = killed[h];
+            const unsigned kw = __shfl_sync(kFull, mine, w & 31);
             if ((kw >> (k & 31)) & 1u) continue;
-            const unsigned* row = f < staged ? s_rows + (size_t)f * words : conflict + (size_t)k * words;
-            if (lane < words) killed0 |= row[lane];
-            if (lane + 32 < words) killed1 |= row[lane + 32];
+            const unsigned* row = f < staged ? s_rows + (size_t)f * cw : conflict + (size_t)k * words;
+#pragma unroll
+            for (int h = 0; h < kLaneWords; ++h)
+                if (lane + 32 * h < cw) killed[h] |= row[lane + 32 * h];
         }
         int base = 0;
-        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int h = 0; h < kLaneWords; ++h) {
             const int w = lane + 32 * h;
             const unsigned valid = (w * 32 + 32 <= c) ? kFull : (w * 32 >= c ? 0u : ((1u << (c - w * 32)) - 1u));
-            const unsigned alive = ~(h ? killed1 : killed0) & valid;
-            if (w < kMaxWords) s_alive[w] = alive;
+            const unsigned alive = ~killed[h] & valid;
+            s_alive[w] = alive;
             const int cnt = __popc(alive);
             int x = cnt;
             for (int o = 1; o < 32; o <<= 1) {
@@ -249,11 +263,15 @@ __global__ void __launch_bounds__(256) greedy_resolve_kernel(DeviceState* st, co
     if (tid == 0) {
         const int alive = s_rank_of_word[kMaxWords];
         st->n_landmarks = base_l + alive;
-        // next batch: double while at least 90 % of a full batch survives, halve below 50 %
+        // next batch: double while at least 90 % of a full batch survives (99 % past
+        // 2048 candidates, 99.5 % past 4096: past 2048 a wasted row costs more than
+        // the per-step work that doubling saves), halve below 50 % (90 % past 2048)
         const int cur = st->s_cur;
         int nxt = cur;
-        if (c == cur && 10 * alive >= 9 * c) nxt = cur * 2;
-        else if (2 * alive < c) nxt = cur / 2;
+        const bool grow = cur < 2048 ? 10 * alive >= 9 * c : (cur < 4096 ? 100 * alive >= 99 * c
+                                                                          : 1000 * alive >= 995 * c);
+        if (c == cur && grow) nxt = cur * 2;
+        else if (2 * alive < c || (cur > 2048 && 10 * alive < 9 * c)) nxt = cur / 2;
         nxt = nxt < 32 ? 32 : (nxt > s_max ? s_max : nxt);
         st->s_next = nxt;
     }
@@ -339,8 +357,8 @@ cudaError_t launch_greedy_gather(const GreedyBuffers& g, const Prepared& pts, in
 cudaError_t launch_greedy_resolve(const GreedyBuffers& g, int S, cudaStream_t s) {
     const int words = S / 32;
     constexpr size_t kStageBytes = 128 * 1024;
-    const int stage_rows = (int)(kStageBytes / (sizeof(unsigned) * words));
-    const size_t smem = (size_t)(stage_rows < S ? stage_rows : S) * words * sizeof(unsigned);
+    const size_t full = (size_t)S * words * sizeof(unsigned);   // every row of the largest batch
+    const size_t smem = full < kStageBytes ? full : kStageBytes;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(greedy_resolve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -350,7 +368,7 @@ cudaError_t launch_greedy_resolve(const GreedyBuffers& g, int S, cudaStream_t s)
     }
     note_launch();
     greedy_resolve_kernel<<<1, 256, smem, s>>>(g.st, g.conflict, g.row_any, words, g.cand_ids, g.ordinal,
-                                               g.landmarks, g.mem_cap, stage_rows < S ? stage_rows : S, S);
+                                               g.landmarks, g.mem_cap, (int)(smem / sizeof(unsigned)), S);
     return cudaGetLastError();
 }
 

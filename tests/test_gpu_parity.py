@@ -108,11 +108,32 @@ def test_build_iso_n10k_d16(bm, path):
 
 
 @pytest.mark.parametrize("path", PATHS)
-@pytest.mark.parametrize("batch", [32, 96, 1024, 2048])
+@pytest.mark.parametrize("batch", [32, 96, 1024, 2048, 4096, 8192])
 def test_build_batch_sizes(bm, path, batch):
     X = W.isotropic(5003, 8, 10, seed=3)
     ref = oracle.build(X, 2.0)
     assert_same_graph(run_build(bm, X, 2.0, path, batch=batch), ref, batch)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_build_batch_8192_conflicts(bm, path):
+    """Isolated points (a 2000-wide cube in 6-d, eps 1) with near copies planted
+    every 131st index, each within 8,000 positions of its original: over 99 % of
+    the candidates survive, the batch grows to 8192 (steps of 256, 512, ..., 8192,
+    8192, 8192), and the in-batch conflicts fall in every word of the candidate set
+    (the last killed slot is 8176)."""
+    rng = np.random.default_rng(5)
+    n = 26000
+    X = np.round(rng.uniform(-1000.0, 1000.0, (n, 6)) * 16.0) / 16.0
+    for i in range(40, n, 131):
+        j = i - int(rng.integers(1, min(i, 8000) + 1))
+        X[i] = X[j] + rng.integers(-4, 5, 6) / 16.0   # within sqrt(6)/4 < 1 of X[j]
+    X = X.astype(np.float32)
+    ref = oracle.build(X, 1.0)
+    assert n - ref["landmarks"].size == 199
+    got = run_build(bm, X, 1.0, path, batch=8192)
+    assert_same_graph(got, ref)
+    assert got["stats"]["greedy_steps"] < 10   # 8 steps; a batch capped at 4096 takes 10
 
 
 @pytest.mark.parametrize("path", PATHS)
