@@ -29,12 +29,12 @@ sys.path.insert(0, ROOT)
 METRIC = "Ball Mapper build s & distance evals/s (exact), TC split path vs plain FP32"
 UNIT = "evals/s"
 # DRAM bytes per tile-kernel launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# the ncu capture of the current fp16 kernel summarised in
-# profiles/sweep_tc_kernel_fp16_mix32-n1M-d64_rows1024.md; a step's sweep reads every
-# point's operands once, so the figure holds for each launch of this workload (the
-# automatic path runs fp16 after the first step).  None where no capture of the current
-# kernel exists.
-NCU_TRAFFIC = {("mix32-n1M-d64", "auto"): 164.1e6, ("mix32-n1M-d64", "tc16"): 164.1e6}
+# the ncu capture of the current fp16 kernel at the greedy's full batch (8192 candidate
+# rows x 10^6 points) summarised in profiles/sweep_tc_kernel_fp16_mix32-n1M-d64_rows8192.md;
+# a step's sweep reads every point's operands once whatever its batch, so the figure holds
+# for each launch of this workload (the automatic path runs fp16 after the first step).
+# None where no capture of the current kernel exists.
+NCU_TRAFFIC = {("mix32-n1M-d64", "auto"): 165.0e6, ("mix32-n1M-d64", "tc16"): 165.0e6}
 DTYPES = {"tc": "bf16x3-split/fp32-acc/fp64-recheck", "tc16": "f16-scaled/fp32-acc/fp64-recheck",
           "fp32": "f32/fp64-recheck", "auto": "f16-scaled or bf16x3-split/fp32-acc/fp64-recheck"}
 
@@ -70,8 +70,9 @@ def config_of(w, extra=None):
     cfg = {"workload": "%s: %s n=%d d=%d quantised 2^-%d, eps=%s, greedy in index order" %
                        (w.name, w.kind, w.n, w.d, w.k, list(w.eps)),
            "n": w.n, "d": w.d, "eps": list(w.eps), "quantisation": "2^-%d" % w.k,
-           "l2": "inputs larger than L2 (%.0f MB fp32 + %.0f MB bf16 split operands vs 129 MB)" %
-                 (w.n * w.d * 4 / 1e6, w.n * (2 * (w.d if w.d > 32 else 32) + 16) * 2 / 1e6),
+           "l2": "inputs larger than L2 (%.0f MB fp32 points; tile operands %.0f MB fp16 or %.0f MB bf16 split; "
+                 "L2 129 MB)" % (w.n * w.d * 4 / 1e6, w.n * ((w.d if w.d > 32 else 32) + 16) * 2 / 1e6,
+                                 w.n * (2 * (w.d if w.d > 32 else 32) + 16) * 2 / 1e6),
            "parallelism": "replicas"}
     if extra:
         cfg.update(extra)

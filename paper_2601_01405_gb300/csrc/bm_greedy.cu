@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(256) greedy_gather_kernel(
 constexpr int kMaxWords = 256;   // batches of up to 8192 candidates
 constexpr int kLaneWords = kMaxWords / 32;
 
-__global__ void __launch_bounds__(256) greedy_resolve_kernel(DeviceState* st, const unsigned* conflict,
+__global__ void __launch_bounds__(1024) greedy_resolve_kernel(DeviceState* st, const unsigned* conflict,
                                                              const unsigned* row_any, int words,
                                                              const int* cand_ids, int* ordinal,
                                                              int* landmarks, unsigned long long mem_cap,
@@ -367,7 +367,7 @@ cudaError_t launch_greedy_resolve(const GreedyBuffers& g, int S, cudaStream_t s)
         attr_set = true;
     }
     note_launch();
-    greedy_resolve_kernel<<<1, 256, smem, s>>>(g.st, g.conflict, g.row_any, words, g.cand_ids, g.ordinal,
+    greedy_resolve_kernel<<<1, 1024, smem, s>>>(g.st, g.conflict, g.row_any, words, g.cand_ids, g.ordinal,
                                                g.landmarks, g.mem_cap, (int)(smem / sizeof(unsigned)), S);
     return cudaGetLastError();
 }
