@@ -89,9 +89,7 @@ __device__ __forceinline__ bool bar_try(uint32_t bar, uint32_t parity) {
 }
 
 // Bounded wait.  Returns false when the CTA is aborting or the bound expired.
-__device__ __forceinline__ bool bar_wait(unsigned long long* b, uint32_t parity, volatile int* abort_flag,
-                                         int* gerr) {
-    const uint32_t bar = su32(b);
+__device__ __forceinline__ bool bar_wait_at(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* gerr) {
     if (bar_try(bar, parity)) return true;
     const unsigned long long t0 = gtimer();
     while (true) {
@@ -103,6 +101,11 @@ __device__ __forceinline__ bool bar_wait(unsigned long long* b, uint32_t parity,
             return false;
         }
     }
+}
+
+__device__ __forceinline__ bool bar_wait(unsigned long long* b, uint32_t parity, volatile int* abort_flag,
+                                         int* gerr) {
+    return bar_wait_at(su32(b), parity, abort_flag, gerr);
 }
 
 // Bounded wait used while draining; ignores the abort flag.
@@ -156,10 +159,11 @@ __device__ __forceinline__ void mma(uint32_t d, unsigned long long a, unsigned l
         : "memory");
 }
 
-__device__ __forceinline__ void mma_commit(unsigned long long* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
-                 : "memory");
+__device__ __forceinline__ void mma_commit_at(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
+
+__device__ __forceinline__ void mma_commit(unsigned long long* bar) { mma_commit_at(su32(bar)); }
 
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -335,6 +339,17 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
         if (lane == 0) {
             uint32_t a_st = 0, a_ph = 0, b_buf = 0, b_ph = 0, t_buf = 0, t_ph = 0;
             bool ok = true;
+            // One-stage, one-chunk query tiles (fp16 with d_pad = CK): a tile is five MMAs,
+            // so this thread's own instruction path per tile is on the critical path.
+            // Descriptors are formed once per stage / point tile (a descriptor's address
+            // field is the byte address / 16: offsets add to it) and barrier addresses
+            // once; one fence follows both waits.
+            const bool lean = PROD == 1 && cps == 1 && nc == 1;
+            const uint32_t a_full0 = su32(&ctl->a_full[0]), a_empty0 = su32(&ctl->a_empty[0]);
+            const uint32_t t_full0 = su32(&ctl->t_full[0]), t_empty0 = su32(&ctl->t_empty[0]);
+            const unsigned long long ad0 = sdesc(sbase + L.a_off, kSpan);
+            const unsigned long long aaug0 = sdesc(sbase + L.a_off + L.a_chunk, 32);
+            const unsigned long long astep = L.a_stage >> 4;
             for (long long item = blockIdx.x; ok && item < items; item += gridDim.x) {
                 const long long g = item % n_groups;
                 const long long at0 = g * G;
@@ -342,6 +357,30 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
                 if (!bar_wait(&ctl->b_full[b_buf], b_ph, abort_flag, gerr)) { ok = false; break; }
                 fence_after();
                 const uint32_t bb = sbase + b_buf * L.b_stride;
+                if (lean) {
+                    const unsigned long long bd = sdesc(bb, kSpan), baug = sdesc(bb + nq * L.b_chunk, 32);
+                    for (long long ia = 0; ia < at1 - at0; ++ia) {
+                        if (!bar_wait_at(t_empty0 + 8u * t_buf, t_ph ^ 1, abort_flag, gerr) ||
+                            !bar_wait_at(a_full0 + 8u * a_st, a_ph, abort_flag, gerr)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after();
+                        const uint32_t dacc = tmem + t_buf * NT;
+                        const unsigned long long ad = ad0 + a_st * astep, aaug = aaug0 + a_st * astep;
+#pragma unroll
+                        for (int k = 0; k < CK / 16; ++k) mma(dacc, ad + 2 * k, bd + 2 * k, kIdesc, k > 0);
+                        mma(dacc, aaug, baug, kIdesc, 1);
+                        mma_commit_at(a_empty0 + 8u * a_st);
+                        mma_commit_at(t_full0 + 8u * t_buf);
+                        if (++a_st == ASTG) { a_st = 0; a_ph ^= 1; }
+                        if (++t_buf == 2) { t_buf = 0; t_ph ^= 1; }
+                    }
+                    if (!ok) break;
+                    mma_commit(&ctl->b_empty[b_buf]);
+                    if (++b_buf == BBUF) { b_buf = 0; b_ph ^= 1; }
+                    continue;
+                }
                 for (long long ia = 0; ok && ia < at1 - at0; ++ia) {
                     if (!bar_wait(&ctl->t_empty[t_buf], t_ph ^ 1, abort_flag, gerr)) { ok = false; break; }
                     fence_after();
