@@ -45,6 +45,7 @@ def main(argv=None):
                           "landmarks": int(out["landmarks"].numel()), "memberships": int(out["ids"].numel()),
                           "edges": int(out["edges"].shape[0]), "edge_pairs": st["edge_pairs"],
                           "greedy_steps": st["greedy_steps"], "band_pairs": st["band_pairs"],
+                          "path_used": {v: k for k, v in binding.PATHS.items()}.get(st["path"], st["path"]),
                           "distance_evals": st["distance_evals"], "tile_pairs": st["tile_pairs"],
                           "evals_per_s": st["distance_evals"] / (med["ms_total"] / 1e3), "median_ms": med,
                           "tile": binding.get_tile_config(X.shape[1])}))

@@ -339,16 +339,17 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
         if (lane == 0) {
             uint32_t a_st = 0, a_ph = 0, b_buf = 0, b_ph = 0, t_buf = 0, t_ph = 0;
             bool ok = true;
-            // One-stage, one-chunk query tiles (fp16 with d_pad = CK): a tile is five MMAs,
-            // so this thread's own instruction path per tile is on the critical path.
-            // Descriptors are formed once per stage / point tile (a descriptor's address
-            // field is the byte address / 16: offsets add to it) and barrier addresses
-            // once; one fence follows both waits.
-            const bool lean = PROD == 1 && cps == 1 && nc == 1;
+            // One-stage query tiles (fp16: d_pad = CK, or d_pad = 2 CK in one stage): a
+            // tile is five (nine) MMAs, so this thread's own instruction path per tile is
+            // on the critical path.  Descriptors are formed once per stage / point tile (a
+            // descriptor's address field is the byte address / 16: offsets add to it) and
+            // barrier addresses once; one fence follows both waits.
+            const bool lean = PROD == 1 && nstage == 1;
             const uint32_t a_full0 = su32(&ctl->a_full[0]), a_empty0 = su32(&ctl->a_empty[0]);
             const uint32_t t_full0 = su32(&ctl->t_full[0]), t_empty0 = su32(&ctl->t_empty[0]);
             const unsigned long long ad0 = sdesc(sbase + L.a_off, kSpan);
-            const unsigned long long aaug0 = sdesc(sbase + L.a_off + L.a_chunk, 32);
+            const unsigned long long aaug0 = sdesc(sbase + L.a_off + nc * L.a_chunk, 32);
+            const unsigned long long achunk = L.a_chunk >> 4, bchunk = L.b_chunk >> 4;
             const unsigned long long astep = L.a_stage >> 4;
             for (long long item = blockIdx.x; ok && item < items; item += gridDim.x) {
                 const long long g = item % n_groups;
@@ -369,7 +370,12 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
                         const uint32_t dacc = tmem + t_buf * NT;
                         const unsigned long long ad = ad0 + a_st * astep, aaug = aaug0 + a_st * astep;
 #pragma unroll
-                        for (int k = 0; k < CK / 16; ++k) mma(dacc, ad + 2 * k, bd + 2 * k, kIdesc, k > 0);
+                        for (int c = 0; c < CPS; ++c) {
+                            if (c >= nc) break;
+#pragma unroll
+                            for (int k = 0; k < CK / 16; ++k)
+                                mma(dacc, ad + c * achunk + 2 * k, bd + c * bchunk + 2 * k, kIdesc, c > 0 || k > 0);
+                        }
                         mma(dacc, aaug, baug, kIdesc, 1);
                         mma_commit_at(a_empty0 + 8u * a_st);
                         mma_commit_at(t_full0 + 8u * t_buf);
