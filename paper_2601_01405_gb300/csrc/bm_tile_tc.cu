@@ -350,6 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
             const unsigned long long ad0 = sdesc(sbase + L.a_off, kSpan);
             const unsigned long long aaug0 = sdesc(sbase + L.a_off + nc * L.a_chunk, 32);
             const unsigned long long achunk = L.a_chunk >> 4, bchunk = L.b_chunk >> 4;
+            const unsigned long long aaug_split0 = sdesc(sbase + L.a_off, 32);   // split: aug stage
             const unsigned long long astep = L.a_stage >> 4;
             for (long long item = blockIdx.x; ok && item < items; item += gridDim.x) {
                 const long long g = item % n_groups;
@@ -387,59 +388,66 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
                     if (++b_buf == BBUF) { b_buf = 0; b_ph ^= 1; }
                     continue;
                 }
-                for (long long ia = 0; ok && ia < at1 - at0; ++ia) {
-                    if (!bar_wait(&ctl->t_empty[t_buf], t_ph ^ 1, abort_flag, gerr)) { ok = false; break; }
-                    fence_after();
-                    const uint32_t dacc = tmem + t_buf * NT;
-                    uint32_t acc = 0;
-                    for (int q = 0; q < nstage; ++q) {
-                        if (!bar_wait(&ctl->a_full[a_st], a_ph, abort_flag, gerr)) { ok = false; break; }
+                if constexpr (PROD == 3) {
+                    // bf16 split: per query tile nc hi stages (A hi x B hi and A hi x B lo),
+                    // nc lo stages (A lo x B hi) and the augmentation stage; descriptors
+                    // from per-stage / per-point-tile bases as in the lean loop
+                    const unsigned long long bd = sdesc(bb, kSpan), baug = sdesc(bb + nq * L.b_chunk, 32);
+                    for (long long ia = 0; ia < at1 - at0; ++ia) {
+                        if (!bar_wait_at(t_empty0 + 8u * t_buf, t_ph ^ 1, abort_flag, gerr)) { ok = false; break; }
+                        const uint32_t dacc = tmem + t_buf * NT;
+                        for (int q = 0; q < nstage; ++q) {
+                            if (!bar_wait_at(a_full0 + 8u * a_st, a_ph, abort_flag, gerr)) { ok = false; break; }
+                            fence_after();
+                            const unsigned long long ad = ad0 + a_st * astep;
+                            if (q < nc) {
+                                const unsigned long long bh = bd + q * bchunk, bl = bd + (nc + q) * bchunk;
+#pragma unroll
+                                for (int k = 0; k < CK / 16; ++k) {
+                                    mma(dacc, ad + 2 * k, bh + 2 * k, kIdesc, q > 0 || k > 0);
+                                    mma(dacc, ad + 2 * k, bl + 2 * k, kIdesc, 1);
+                                }
+                            } else if (q < nq) {
+                                const unsigned long long bh = bd + (q - nc) * bchunk;
+#pragma unroll
+                                for (int k = 0; k < CK / 16; ++k) mma(dacc, ad + 2 * k, bh + 2 * k, kIdesc, 1);
+                            } else {
+                                mma(dacc, aaug_split0 + a_st * astep, baug, kIdesc, 1);
+                            }
+                            mma_commit_at(a_empty0 + 8u * a_st);
+                            if (++a_st == ASTG) { a_st = 0; a_ph ^= 1; }
+                        }
+                        if (!ok) break;
+                        mma_commit_at(t_full0 + 8u * t_buf);
+                        if (++t_buf == 2) { t_buf = 0; t_ph ^= 1; }
+                    }
+                } else {
+                    // fp16 with one K chunk per stage over several stages (d_pad > CK): the
+                    // augmentation block rides in the last stage
+                    for (long long ia = 0; ok && ia < at1 - at0; ++ia) {
+                        if (!bar_wait(&ctl->t_empty[t_buf], t_ph ^ 1, abort_flag, gerr)) { ok = false; break; }
                         fence_after();
-                        const uint32_t aa = sbase + L.a_off + a_st * L.a_stage;
-                        if (PROD == 1 && cps == 1) {   // one chunk per stage (the common case)
+                        const uint32_t dacc = tmem + t_buf * NT;
+                        uint32_t acc = 0;
+                        for (int q = 0; q < nstage; ++q) {
+                            if (!bar_wait(&ctl->a_full[a_st], a_ph, abort_flag, gerr)) { ok = false; break; }
+                            fence_after();
+                            const uint32_t aa = sbase + L.a_off + a_st * L.a_stage;
 #pragma unroll
                             for (int k = 0; k < CK / 16; ++k) {
                                 mma(dacc, sdesc(aa + k * 32, kSpan), sdesc(bb + q * L.b_chunk + k * 32, kSpan), kIdesc,
                                     acc);
                                 acc = 1;
                             }
-                            if (q == nstage - 1)   // the augmentation block rides in the last stage
+                            if (q == nstage - 1)
                                 mma(dacc, sdesc(aa + L.a_chunk, 32), sdesc(bb + nq * L.b_chunk, 32), kIdesc, 1);
-                        } else if (PROD == 1) {   // the whole query tile in one stage
-#pragma unroll
-                            for (int c = 0; c < 2; ++c) {
-                                if (c >= nc) break;
-#pragma unroll
-                                for (int k = 0; k < CK / 16; ++k) {
-                                    mma(dacc, sdesc(aa + c * L.a_chunk + k * 32, kSpan),
-                                        sdesc(bb + c * L.b_chunk + k * 32, kSpan), kIdesc, acc);
-                                    acc = 1;
-                                }
-                            }
-                            mma(dacc, sdesc(aa + nc * L.a_chunk, 32), sdesc(bb + nq * L.b_chunk, 32), kIdesc, 1);
-                        } else if (q < nc) {
-#pragma unroll
-                            for (int k = 0; k < CK / 16; ++k) {
-                                const unsigned long long ad = sdesc(aa + k * 32, kSpan);
-                                mma(dacc, ad, sdesc(bb + q * L.b_chunk + k * 32, kSpan), kIdesc, acc);
-                                acc = 1;
-                                mma(dacc, ad, sdesc(bb + (nc + q) * L.b_chunk + k * 32, kSpan), kIdesc, 1);
-                            }
-                        } else if (q < nq) {
-                            const int c = q - nc;
-#pragma unroll
-                            for (int k = 0; k < CK / 16; ++k)
-                                mma(dacc, sdesc(aa + k * 32, kSpan), sdesc(bb + c * L.b_chunk + k * 32, kSpan),
-                                    kIdesc, 1);
-                        } else {
-                            mma(dacc, sdesc(aa, 32), sdesc(bb + nq * L.b_chunk, 32), kIdesc, 1);
+                            mma_commit(&ctl->a_empty[a_st]);
+                            if (++a_st == ASTG) { a_st = 0; a_ph ^= 1; }
                         }
-                        mma_commit(&ctl->a_empty[a_st]);
-                        if (++a_st == ASTG) { a_st = 0; a_ph ^= 1; }
+                        if (!ok) break;
+                        mma_commit(&ctl->t_full[t_buf]);
+                        if (++t_buf == 2) { t_buf = 0; t_ph ^= 1; }
                     }
-                    if (!ok) break;
-                    mma_commit(&ctl->t_full[t_buf]);
-                    if (++t_buf == 2) { t_buf = 0; t_ph ^= 1; }
                 }
                 if (!ok) break;
                 mma_commit(&ctl->b_empty[b_buf]);
