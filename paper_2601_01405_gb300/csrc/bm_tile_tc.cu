@@ -16,6 +16,9 @@
 //           through a ring of shared-memory stages
 //   warp 1  allocates tensor memory; lane 0 issues tcgen05.mma (M=128, N=NT,
 //           K=16 per instruction) into one of two TMEM accumulators
+//   warp 10 for one-stage query tiles (fp16), a second issuer: warps 1 and 10 take
+//           alternate tiles, each with its own accumulator, so one thread's barrier
+//           work per tile overlaps the other's MMAs
 //   warps 2-9  epilogue: tcgen05.ld of the accumulator (one TMEM lane = one
 //           query row per thread; two warps per lane quarter, each on half of
 //           the columns, all loads in flight before one wait), classification
@@ -37,7 +40,8 @@ namespace bm {
 
 namespace {
 
-constexpr int kThreads = 320;   // 2 control warps + 8 epilogue warps
+constexpr int kThreads = 352;   // producer, MMA issuer, 8 epilogue warps, second MMA issuer
+constexpr int kIssuer2 = kThreads / 32 - 1;   // the second MMA-issuing warp
 constexpr int kEpiWarps = 8;
 constexpr int kMaxGroup = 16;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
@@ -231,6 +235,10 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
     const int nq = PROD == 3 ? 2 * nc : nc;   // query-tile chunks before the augmentation chunk
     constexpr int cps = CPS;   // = L.cps (the dispatch picks the instantiation that matches)
     const int nstage = PROD == 3 ? nq + 1 : (nc + cps - 1) / cps;   // shared-memory stages per query tile
+    // One-stage query tiles (fp16: d_pad = CK, or d_pad = 2 CK in one stage) are five
+    // (nine) MMAs; the issuing thread's per-tile barrier work does not overlap its own
+    // MMAs, so two warps issue alternate tiles (tile T into accumulator T mod 2).
+    const bool dual = PROD == 1 && nstage == 1;
     Ctl* ctl = reinterpret_cast<Ctl*>(smem + L.ctl_off);
     const uint32_t sbase = su32(smem);
 
@@ -248,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
     if (threadIdx.x == 0) {
         for (int i = 0; i < BBUF; ++i) {
             bar_init(&ctl->b_full[i], 1);
-            bar_init(&ctl->b_empty[i], 1);
+            bar_init(&ctl->b_empty[i], dual ? 2 : 1);   // both issuers release the point tile
         }
         for (int i = 0; i < ASTG; ++i) {
             bar_init(&ctl->a_full[i], 1);
@@ -258,7 +266,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
             bar_init(&ctl->t_full[i], 1);
             bar_init(&ctl->t_empty[i], kEpiWarps);
         }
-        bar_init(&ctl->drain, 1);
+        bar_init(&ctl->drain, dual ? 2 : 1);
         ctl->abort_flag = 0;
         ctl->seg_used = 0;
         ctl->band_used = 0;
@@ -334,17 +342,13 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
             for (int i = 0; i < BBUF; ++i)
                 if (b_last[i] >= 0) bar_drain(&ctl->b_full[i], (uint32_t)b_last[i]);
         }
-    } else if (warp == 1) {
-        // ------------------------------------------------------------ MMA issuer
-        if (lane == 0) {
+    } else if (warp == 1 || warp == kIssuer2) {
+        // ------------------------------------------------------------ MMA issuers
+        // Descriptors are formed once per stage / point tile (a descriptor's address
+        // field is the byte address / 16: offsets add to it), barrier addresses once.
+        if (lane == 0 && (warp == 1 || dual)) {
             uint32_t a_st = 0, a_ph = 0, b_buf = 0, b_ph = 0, t_buf = 0, t_ph = 0;
             bool ok = true;
-            // One-stage query tiles (fp16: d_pad = CK, or d_pad = 2 CK in one stage): a
-            // tile is five (nine) MMAs, so this thread's own instruction path per tile is
-            // on the critical path.  Descriptors are formed once per stage / point tile (a
-            // descriptor's address field is the byte address / 16: offsets add to it) and
-            // barrier addresses once; one fence follows both waits.
-            const bool lean = PROD == 1 && nstage == 1;
             const uint32_t a_full0 = su32(&ctl->a_full[0]), a_empty0 = su32(&ctl->a_empty[0]);
             const uint32_t t_full0 = su32(&ctl->t_full[0]), t_empty0 = su32(&ctl->t_empty[0]);
             const unsigned long long ad0 = sdesc(sbase + L.a_off, kSpan);
@@ -352,6 +356,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
             const unsigned long long achunk = L.a_chunk >> 4, bchunk = L.b_chunk >> 4;
             const unsigned long long aaug_split0 = sdesc(sbase + L.a_off, 32);   // split: aug stage
             const unsigned long long astep = L.a_stage >> 4;
+            uint32_t t_seq = 0;   // dual issue: tiles of this CTA before the current item
             for (long long item = blockIdx.x; ok && item < items; item += gridDim.x) {
                 const long long g = item % n_groups;
                 const long long at0 = g * G;
@@ -359,17 +364,22 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
                 if (!bar_wait(&ctl->b_full[b_buf], b_ph, abort_flag, gerr)) { ok = false; break; }
                 fence_after();
                 const uint32_t bb = sbase + b_buf * L.b_stride;
-                if (lean) {
+                if (dual) {
+                    // tiles T of this CTA in order; this warp issues those with T mod 2 = me
+                    const uint32_t me = warp == 1 ? 0u : 1u;
                     const unsigned long long bd = sdesc(bb, kSpan), baug = sdesc(bb + nq * L.b_chunk, 32);
-                    for (long long ia = 0; ia < at1 - at0; ++ia) {
-                        if (!bar_wait_at(t_empty0 + 8u * t_buf, t_ph ^ 1, abort_flag, gerr) ||
-                            !bar_wait_at(a_full0 + 8u * a_st, a_ph, abort_flag, gerr)) {
+                    const uint32_t nt = (uint32_t)(at1 - at0);
+                    for (uint32_t i = (me ^ t_seq) & 1u; i < nt; i += 2) {
+                        const uint32_t tt = t_seq + i;
+                        const uint32_t st = tt % ASTG, sph = (tt / ASTG) & 1u, tph = (tt >> 1) & 1u;
+                        if (!bar_wait_at(t_empty0 + 8u * me, tph ^ 1u, abort_flag, gerr) ||
+                            !bar_wait_at(a_full0 + 8u * st, sph, abort_flag, gerr)) {
                             ok = false;
                             break;
                         }
                         fence_after();
-                        const uint32_t dacc = tmem + t_buf * NT;
-                        const unsigned long long ad = ad0 + a_st * astep, aaug = aaug0 + a_st * astep;
+                        const uint32_t dacc = tmem + me * NT;
+                        const unsigned long long ad = ad0 + st * astep, aaug = aaug0 + st * astep;
 #pragma unroll
                         for (int c = 0; c < CPS; ++c) {
                             if (c >= nc) break;
@@ -378,12 +388,11 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
                                 mma(dacc, ad + c * achunk + 2 * k, bd + c * bchunk + 2 * k, kIdesc, c > 0 || k > 0);
                         }
                         mma(dacc, aaug, baug, kIdesc, 1);
-                        mma_commit_at(a_empty0 + 8u * a_st);
-                        mma_commit_at(t_full0 + 8u * t_buf);
-                        if (++a_st == ASTG) { a_st = 0; a_ph ^= 1; }
-                        if (++t_buf == 2) { t_buf = 0; t_ph ^= 1; }
+                        mma_commit_at(a_empty0 + 8u * st);
+                        mma_commit_at(t_full0 + 8u * me);
                     }
                     if (!ok) break;
+                    t_seq += nt;
                     mma_commit(&ctl->b_empty[b_buf]);
                     if (++b_buf == BBUF) { b_buf = 0; b_ph ^= 1; }
                     continue;
@@ -391,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
                 if constexpr (PROD == 3) {
                     // bf16 split: per query tile nc hi stages (A hi x B hi and A hi x B lo),
                     // nc lo stages (A lo x B hi) and the augmentation stage; descriptors
-                    // from per-stage / per-point-tile bases as in the lean loop
+                    // from per-stage / per-point-tile bases
                     const unsigned long long bd = sdesc(bb, kSpan), baug = sdesc(bb + nq * L.b_chunk, 32);
                     for (long long ia = 0; ia < at1 - at0; ++ia) {
                         if (!bar_wait_at(t_empty0 + 8u * t_buf, t_ph ^ 1, abort_flag, gerr)) { ok = false; break; }
