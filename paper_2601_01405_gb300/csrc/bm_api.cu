@@ -154,6 +154,13 @@ bm_status validate_eps(float eps) {
     return BM_OK;
 }
 
+// Largest greedy batch: 0 (the default) or a multiple of 32 in [32, max].
+bm_status validate_batch(int S, int max) {
+    if (S != 0 && (S < 32 || S > max || S % 32))
+        return fail(BM_ERR_ARG, "batch must be a multiple of 32 in [32, " + std::to_string(max) + "]");
+    return BM_OK;
+}
+
 struct Timer {
     cudaEvent_t ev[8];
     int used = 0;
@@ -1576,6 +1583,8 @@ bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_opt
     if (vs != BM_OK) return vs;
     vs = validate_eps(eps);
     if (vs != BM_OK) return vs;
+    vs = validate_batch(opt.batch, 8192);   // arguments first, then the device
+    if (vs != BM_OK) return vs;
     vs = check_device(opt.path);
     if (vs != BM_OK) return vs;
     return build_graph(X, n, d, eps, opt, nullptr, 0, nullptr, 0, out);
@@ -1628,7 +1637,9 @@ bm_status bm_build_batched(const bm_instance* inst, int32_t count, const bm_opti
             return vs;
         }
     }
-    bm_status vs = check_device(opt.path);
+    bm_status vs = validate_batch(opt.batch, 2048);   // arguments first, then the device
+    if (vs != BM_OK) return vs;
+    vs = check_device(opt.path);
     if (vs != BM_OK) return vs;
     if (count == 0) return BM_OK;
     int failed = -1;
