@@ -181,6 +181,26 @@ def oracle_rate(X, eps_list, target_s, landmark_rows=None):
     return evals / dt, evals, dt, per * len(eps_list), oracle.num_threads()
 
 
+def oracle_small_build(name="iso-n10k-d16", eps=3.0):
+    """Whole oracle build (greedy, memberships, edges) of the small configuration with one
+    thread and with all threads: the oracle's own scaling, reported beside the sample rate."""
+    import oracle
+    from paper_2601_01405_gb300 import workloads as W
+    X = W.make(name)
+    threads = oracle.num_threads()
+    oracle.build(X, eps)   # first touch, untimed
+    out = {"workload": name, "eps": eps, "threads": threads}
+    try:
+        for key, th in (("s_1_thread", 1), ("s_all_threads", threads)):
+            oracle.set_num_threads(th)
+            t0 = time.perf_counter()
+            oracle.build(X, eps)
+            out[key] = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(threads)
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -345,7 +365,8 @@ def run_ours(args):
         r, ev, dt, rows, thr = oracle_rate(X, eps_list, args.cpu_seconds)
         cpu = {"value": r, "unit": UNIT, "cores": thr, "kind": "oracle",
                "sample": "%d random query rows x all %d points, full-scan FP64 membership, split over eps %s "
-                         "(%.1f s)" % (rows, n, eps_list, dt)}
+                         "(%.1f s)" % (rows, n, eps_list, dt),
+               "small_build": oracle_small_build()}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

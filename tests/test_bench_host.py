@@ -53,3 +53,16 @@ def test_reference_arm_line():
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["unit"] == "evals/s" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_oracle_small_build_timing():
+    """The oracle's whole small build with one thread and with all threads, and the
+    thread count restored afterwards."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    before = oracle.num_threads()
+    out = bench.oracle_small_build()
+    assert out["workload"] == "iso-n10k-d16" and out["threads"] == before
+    assert out["s_1_thread"] > 0 and out["s_all_threads"] > 0
+    assert oracle.num_threads() == before
