@@ -181,6 +181,14 @@ def oracle_rate(X, eps_list, target_s, landmark_rows=None):
     return evals / dt, evals, dt, per * len(eps_list), oracle.num_threads()
 
 
+def _guarded(fn):
+    """A supplementary CPU figure must never cost the benchmark its line."""
+    try:
+        return fn()
+    except Exception as e:  # noqa: BLE001
+        return {"error": "%s: %s" % (type(e).__name__, e)}
+
+
 def oracle_small_build(name="iso-n10k-d16", eps=3.0):
     """Whole oracle build (greedy, memberships, edges) of the small configuration with one
     thread and with all threads: the oracle's own scaling, reported beside the sample rate."""
@@ -366,7 +374,7 @@ def run_ours(args):
         cpu = {"value": r, "unit": UNIT, "cores": thr, "kind": "oracle",
                "sample": "%d random query rows x all %d points, full-scan FP64 membership, split over eps %s "
                          "(%.1f s)" % (rows, n, eps_list, dt),
-               "small_build": oracle_small_build()}
+               "small_build": _guarded(oracle_small_build)}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
