@@ -113,3 +113,18 @@ def test_batch_bounds_rejected_before_the_device():
         binding.bm_build_batched([(X, 1.0)], batch=4096)
     assert ei.value.status == binding.BM_ERR_ARG
     assert "[32, 2048]" in str(ei.value)
+
+
+def test_binding_enums_match_header():
+    """The binding's status and path constants equal the header's enum values, and every
+    status has a string in the library."""
+    text = open(os.path.join(ROOT, "include", "ballmapper.h")).read()
+    header = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(BM_(?:OK|ERR_\w+|PATH_\w+))\s*=\s*(\d+)", text)}
+    assert len(header) >= 11
+    for name, value in header.items():
+        assert getattr(binding, name) == value, name
+    _build.build()
+    lib = binding.load()
+    for name, value in header.items():
+        if not name.startswith("BM_PATH"):
+            assert lib.bm_status_string(value), name
