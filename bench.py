@@ -14,6 +14,12 @@ the roofline of the tensor-core distance tiles and the CPU oracle are reported
 beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Kernel-only mode, for profiling one distance-tile launch shape: one bm_range_query
+of the first ROWS points (the shape of one greedy step) against all points of the
+workload, repeated, printing the device time of the tile launches:
+
+  python bench.py --kernel-probe --workload mix32-n1M-d64 --rows 8192 --eps 4 --path tc16
 """
 import argparse
 import json
@@ -29,11 +35,10 @@ sys.path.insert(0, ROOT)
 METRIC = "Ball Mapper build s & distance evals/s (exact), TC split path vs plain FP32"
 UNIT = "evals/s"
 # DRAM bytes per tile-kernel launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# the ncu capture of the current fp16 kernel at the greedy's full batch (8192 candidate
-# rows x 10^6 points) summarised in profiles/sweep_tc_kernel_fp16_mix32-n1M-d64_rows8192.md;
-# a step's sweep reads every point's operands once whatever its batch, so the figure holds
-# for each launch of this workload (the automatic path runs fp16 after the first step).
-# None where no capture of the current kernel exists.
+# an ncu capture of the current fp16 kernel at the greedy's full batch (8192 candidate
+# rows x 10^6 points); a step's sweep reads every point's operands once whatever its
+# batch, so the figure holds for each launch of this workload (the automatic path runs
+# fp16 after the first step).  None where no capture of the current kernel exists.
 NCU_TRAFFIC = {("mix32-n1M-d64", "auto"): 164.5e6, ("mix32-n1M-d64", "tc16"): 164.5e6}
 DTYPES = {"tc": "bf16x3-split/fp32-acc/fp64-recheck", "tc16": "f16-scaled/fp32-acc/fp64-recheck",
           "fp32": "f32/fp64-recheck", "auto": "f16-scaled or bf16x3-split/fp32-acc/fp64-recheck"}
@@ -50,6 +55,11 @@ def parse():
     ap.add_argument("--compare-steps", type=int, default=1, help="timed steps of the FP32 comparison path (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--kernel-probe", action="store_true",
+                    help="time one distance-tile launch shape (a range query of --rows rows) and exit")
+    ap.add_argument("--rows", type=int, default=1024, help="query rows of the kernel probe")
+    ap.add_argument("--eps", type=float, default=4.0, help="eps of the kernel probe")
+    ap.add_argument("--repeat", type=int, default=3, help="repetitions of the kernel probe")
     return ap.parse_args()
 
 
@@ -394,8 +404,33 @@ def run_ours(args):
     return 0
 
 
+def run_kernel_probe(args):
+    """One range query of the first `rows` points against all points of the workload,
+    repeated: the distance-tile launch of one greedy step, alone (for ncu)."""
+    import torch
+    from paper_2601_01405_gb300 import binding, _build
+    _build.build()
+    w, X = workload(args.workload)
+    Xd = torch.from_numpy(X).cuda()
+    Qd = Xd[: args.rows].contiguous()
+    runs = []
+    for _ in range(args.repeat):
+        off, ids, st = binding.bm_range_query(Xd, Qd, args.eps, path=args.path)
+        torch.cuda.synchronize()
+        runs.append({"ms_sweep": st["ms_sweep"], "ms_total": st["ms_total"], "nnz": int(ids.numel()),
+                     "band_pairs": st["band_pairs"], "tile_pairs": st["tile_pairs"]})
+    best = min(r["ms_sweep"] for r in runs)
+    pairs = runs[0]["tile_pairs"]
+    print(json.dumps({"workload": args.workload, "rows": args.rows, "eps": args.eps, "path": args.path,
+                      "runs": runs, "best_ms_sweep": best,
+                      "alg_tflops": 2.0 * X.shape[1] * pairs / (best / 1e3) / 1e12 if best > 0 else None}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.kernel_probe:
+        return run_kernel_probe(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -256,18 +256,20 @@ BM_API const char* bm_last_error(void);
 
 /* Range COUNT without any allocation: counts[j] = |{ i : ||X_i - Q_j|| < eps }|.
  * The paper has no counterpart; this entry point exists for callers that
- * cannot allocate device memory when they call (inside a stream capture, in
- * allocation-free real-time code, under a fixed memory budget).  It works in
- * a 32 MiB scratch area compiled into the library (held by every GPU that
- * loads it until process exit) plus the caller's arrays:
+ * cannot allocate device memory when they call (allocation-free real-time
+ * code, code running inside another allocator's callback, a fixed memory
+ * budget).  It works in a 32 MiB scratch area compiled into the library (held
+ * by every GPU that loads it until process exit) plus the caller's arrays:
  *   X: n x d, Q: m x d float32 device arrays; counts: m int64 device array
  *   (written, previous contents ignored); stream: cudaStream_t or NULL.
  * Limits: n + m <= 4,194,304 (else BM_ERR_CAPACITY, nothing launched); at most
- * 2,097,120 pairs may fall in the error band (else BM_ERR_CAPACITY).
- * The first call on a device looks up the scratch's device address, so make
- * it before any stream capture begins.  Calls share the scratch: calls whose
- * GPU work overlaps (other streams or threads) race and must be serialised by
- * the caller.  The call synchronises `stream` before returning. */
+ * 2,097,120 pairs may fall in the error band (else BM_ERR_CAPACITY); eps <= 1e19
+ * (else BM_ERR_ARG).  NaN or Inf in X or Q: BM_ERR_ARG.
+ * The first call in a CUDA context on a device looks up the scratch's device
+ * address (again after a cudaDeviceReset), so make it before any stream
+ * capture begins.  Calls share the scratch: calls whose GPU work overlaps
+ * (other streams or threads) race and must be serialised by the caller.  The
+ * call synchronises `stream` before returning. */
 BM_API bm_status bm_range_count_noalloc(const float* X, int64_t n, int32_t d, const float* Q, int64_t m,
                                         float eps, void* stream, int64_t* counts);
 

@@ -1,25 +1,28 @@
 // bm_noalloc.cu -- bm_range_count_noalloc: an entry point that allocates nothing.
 //
 // Some callers cannot allocate device memory at the time they need an answer:
-// code running inside a CUDA stream capture (an allocation there would break
-// or be baked into the graph), real-time services that forbid allocation
-// after start-up, and callers living inside another allocator's callback or
-// behind a fixed memory budget.  For them this file offers a range COUNT,
-// |R_eps(q)| for every query row q, that works entirely in a fixed scratch
-// area compiled into the library, plus the output array the caller passes.
+// real-time services that forbid allocation after start-up, callers that live
+// inside another allocator's callback, and callers held to a fixed memory
+// budget.  For them this file offers a range COUNT, |R_eps(q)| for every query
+// row q, that works entirely in a fixed scratch area compiled into the
+// library, plus the output array the caller passes.
 //
 // The scratch is one file-scope __device__ array of kScratchBytes (32 MiB).
 // Every GPU that loads this module keeps it until the process exits.  All
 // calls share it: a call leaves its contents behind and the next call clears
 // what must start at zero, and calls whose GPU work overlaps (two streams,
 // two host threads) race on it.  The host reaches the array only through the
-// device address returned by cudaGetSymbolAddress, looked up once per device
-// by the first call on that device (so that first call should happen before
-// any stream capture begins).
+// device address returned by cudaGetSymbolAddress.  That address is looked up
+// by the first call made in a CUDA context on a device (so that call should
+// happen before any stream capture begins) and kept per context: a context
+// created after a cudaDeviceReset gets its own lookup.
 //
 // Arithmetic: the same exact decision as the other entry points -- FP32 tiles
 // with the proven error band, band pairs re-decided by the FP64 squared
 // distance in coordinate order.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <mutex>
 
 #include "bm_host.h"
@@ -113,8 +116,45 @@ __global__ void count_recheck_kernel(DeviceState* st, const unsigned long long* 
     }
 }
 
+// Largest eps accepted: eps^2 / 4 enters phi, which is stored as a float; above
+// about 3.7e19 it overflows and every pair would land in the error band.
+constexpr float kMaxEps = 1.0e19f;
+
+// Scratch address per device, valid for the CUDA context it was looked up in.
+struct ScratchSlot {
+    unsigned long long ctx_id;
+    void* addr;
+};
 std::mutex g_setup_mutex;
-void* g_scratch_dev[64] = {};
+ScratchSlot g_slot[64] = {};
+
+// Identifier of the current CUDA context (0 when the driver cannot report one).
+unsigned long long current_context_id() {
+    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (PFN_cuCtxGetCurrent_v4000)p;
+        else
+            cudaGetLastError();
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (PFN_cuCtxGetId_v12000)p;
+        else
+            cudaGetLastError();
+        looked_up = true;
+    }
+    if (!get_current || !get_id) return 0ull;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0ull;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0ull;
+    return id;
+}
 
 }  // namespace
 
@@ -137,6 +177,7 @@ extern "C" bm_status bm_range_count_noalloc(const float* X, int64_t n, int32_t d
     if (n < 0 || m < 0 || n > 0x7fffffffLL || m > 0x7fffffffLL) return fail(BM_ERR_ARG, "row counts out of range");
     if (d < 1 || d > 65536) return fail(BM_ERR_ARG, "d out of range [1, 65536]");
     if (!(eps > 0.f) || eps != eps || eps > 3.4e38f) return fail(BM_ERR_ARG, "eps must be finite and > 0");
+    if (eps > kMaxEps) return fail(BM_ERR_ARG, "bm_range_count_noalloc: eps above 1e19 is not supported");
     if (n + m > kMaxRows)
         return fail(BM_ERR_CAPACITY, "bm_range_count_noalloc: n + m exceeds its fixed scratch limit of 4194304 rows");
     if ((n > 0 && !X) || (m > 0 && (!Q || !counts))) return fail(BM_ERR_ARG, "NULL input or output");
@@ -150,7 +191,7 @@ extern "C" bm_status bm_range_count_noalloc(const float* X, int64_t n, int32_t d
         if (cudaStreamSynchronize(s) != cudaSuccess) return fail(BM_ERR_CUDA, "stream synchronisation failed");
         return BM_OK;
     }
-    // once per device: the device address of the scratch array
+    // once per device and context: the device address of the scratch array
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
         cudaGetLastError();
@@ -159,16 +200,20 @@ extern "C" bm_status bm_range_count_noalloc(const float* X, int64_t n, int32_t d
     unsigned char* base = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (!g_scratch_dev[dev]) {
+        const unsigned long long ctx = current_context_id();
+        ScratchSlot& slot = g_slot[dev];
+        if (!slot.addr || ctx == 0ull || slot.ctx_id != ctx) {
             void* p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
             if (e != cudaSuccess || !p) {
                 cudaGetLastError();
+                slot.addr = nullptr;
                 return fail(BM_ERR_CUDA, "cudaGetSymbolAddress of the no-alloc scratch failed");
             }
-            g_scratch_dev[dev] = p;
+            slot.addr = p;
+            slot.ctx_id = ctx;
         }
-        base = (unsigned char*)g_scratch_dev[dev];
+        base = (unsigned char*)slot.addr;
     }
     DeviceState* st = (DeviceState*)base;
     float* phiX = (float*)(base + kStateBytes);
@@ -183,8 +228,8 @@ extern "C" bm_status bm_range_count_noalloc(const float* X, int64_t n, int32_t d
     ok = ok && launch_prep(X, n, d, eps2, false, false, px, &st->max_norm_bits, bad, s) == cudaSuccess;
     ok = ok && launch_prep(Q, m, d, eps2, true, false, pq, &st->max_norm_q_bits, bad, s) == cudaSuccess;
     ok = ok && launch_delta(st, BM_PATH_FP32, d, d, eps2, false, s) == cudaSuccess;
+    // n + m <= 2^22 rows keeps a_tiles * b_tiles below 2^30 blocks
     const long long a_tiles = (m + BM - 1) / BM, b_tiles = (n + BN - 1) / BN;
-    if (ok && a_tiles * b_tiles > 0x7fffffffLL) return fail(BM_ERR_CAPACITY, "too many tiles for one launch");
     if (ok) {
         count_tile_kernel<<<(unsigned)(a_tiles * b_tiles), NT, 0, s>>>(Q, phiQ, m, X, phiX, n, d, a_tiles, st, band,
                                                                      kBandCap, (long long*)counts);

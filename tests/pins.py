@@ -187,14 +187,25 @@ def pin_range_scipy(X, Q, eps):
         assert ids[off[j]:off[j + 1]].tolist() == sorted(ref[j])
 
 
-def pin_pair_sqdist(X):
-    """Squared distances of listed pairs equal the direct numpy formula."""
+def pin_pair_sqdist(X, Q, k):
+    """Squared distances of listed (query row, point) pairs, with Q and X different sets
+    of different sizes, equal the exact rational values: coordinates are multiples of
+    2^-k, so D = sum_i (m_q,i - m_x,i)^2 / 4^k with integer m, and FP64 holds it
+    exactly.  Indices stay below both row counts, so a swap of the two roles reads
+    valid rows of the other set and shows as wrong values."""
+    from fractions import Fraction
+    assert X.shape[0] != Q.shape[0]
     rng = np.random.default_rng(3)
-    qrow = rng.integers(0, X.shape[0], 200)
-    xcol = rng.integers(0, X.shape[0], 200)
-    got = oracle.pair_sqdist(X, X, qrow, xcol)
-    ref = ((X[qrow].astype(np.float64) - X[xcol].astype(np.float64)) ** 2).sum(axis=1)
-    assert np.array_equal(got, ref)
+    lim = min(X.shape[0], Q.shape[0])
+    qrow = rng.integers(0, lim, 200)
+    xcol = rng.integers(0, lim, 200)
+    got = oracle.pair_sqdist(X, Q, qrow, xcol)
+    scale = 2 ** k
+    for t in range(qrow.size):
+        mq = [int(Fraction(float(v)) * scale) for v in Q[qrow[t]]]
+        mx = [int(Fraction(float(v)) * scale) for v in X[xcol[t]]]
+        exact = Fraction(sum((a - b) ** 2 for a, b in zip(mq, mx)), 4 ** k)
+        assert Fraction(float(got[t])) == exact, t
 
 
 def pin_paper():

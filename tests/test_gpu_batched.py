@@ -78,18 +78,6 @@ def test_batched_equals_single_builds(bm, path):
         assert r["stats"]["kernel_launches"] > 0
 
 
-def test_batched_overflow_resumes(bm):
-    """Balls far larger than the step buffers: the graph loop stops on the
-    overflow and the host loop finishes the instance with larger buffers."""
-    big = W.isotropic(200_000, 2, 10, seed=21)
-    inst = [(big, 50.0), (W.isotropic(2000, 8, 10, seed=22), 2.0),
-            (W.mixture(60_000, 8, 10, clusters=8, seed=23), 6.0)]
-    res = bm.bm_build_batched([(torch.from_numpy(X).cuda(), e) for X, e in inst])
-    torch.cuda.synchronize()
-    for k, ((X, e), r) in enumerate(zip(inst, res)):
-        assert_same_graph(to_np(r), oracle.build(X, e), k)
-
-
 def test_batched_host_io(bm):
     inst = mixed_instances()[:6]
     host = bm.bm_build_batched(inst)

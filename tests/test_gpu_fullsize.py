@@ -89,10 +89,12 @@ def mix():
     return W.make("mix32-n1M-d64")
 
 
-@pytest.mark.parametrize("eps", [2.0, 4.0, 6.0])
-def test_mix32_n1M_d64_sampled(bm, mix, eps):
+# the automatic path (the one bench.py times) at every eps of the workload, and the two
+# fixed tensor-core representations at one eps each
+@pytest.mark.parametrize("eps,path", [(2.0, "auto"), (4.0, "auto"), (6.0, "auto"), (2.0, "tc16"), (4.0, "tc")])
+def test_mix32_n1M_d64_sampled(bm, mix, eps, path):
     Xd = torch.from_numpy(mix).cuda()
-    out = run(bm, Xd, eps, "tc16" if eps == 2.0 else "tc")
+    out = run(bm, Xd, eps, path)
     sampled_checks(mix, out, eps, np.random.default_rng(int(eps)))
 
 
@@ -100,7 +102,7 @@ def test_mix32_n1M_d64_paths_identical(bm, mix):
     """All distance-tile paths give the same bytes at full size (eps = 6)."""
     Xd = torch.from_numpy(mix).cuda()
     a = run(bm, Xd, 6.0, "tc")
-    for other in ("fp32", "tc16"):
+    for other in ("fp32", "tc16", "auto"):
         b = run(bm, Xd, 6.0, other)
         for k in ("landmarks", "offsets", "ids", "edges"):
             assert torch.equal(a[k], b[k]), (other, k)

@@ -29,6 +29,8 @@ MUTANTS = [
     ("balltree-prune-sign", "if (dc - nd->radius > r", "if (dc + nd->radius > r", 1),
     ("balltree-radius-min", "if (s > r2) { r2 = s; pa = p; }", "if (s < r2) { r2 = s; pa = p; }", 1),
     ("balltree-leaf-closed", "t->d) < r2) {", "t->d) <= r2) {", 1),
+    ("pair-roles-swapped", "sqdist(Q + (size_t)qrow[k] * d, X + (size_t)xcol[k] * d, d)",
+     "sqdist(X + (size_t)qrow[k] * d, Q + (size_t)xcol[k] * d, d)", 1),
     ("masked-ignores-cells", "if (flag[cell_of[i]] && sqdist", "if ((flag[cell_of[i]] || 1) && sqdist", 2),
 ]
 # A wrong node centre is not listed: any centre paired with the radius measured
@@ -50,7 +52,7 @@ def _all_pins():
     pins.pin_balltree(G, 1.0, Q=G[:300])
     pins.pin_knn_scipy(W.paper_gaussian_fp64(500, 6, seed=7), 20)
     pins.pin_range_scipy(W.paper_gaussian_fp64(800, 5, seed=8), W.paper_gaussian_fp64(800, 5, seed=8)[:50], 1.3)
-    pins.pin_pair_sqdist(W.isotropic(300, 16, 10, seed=9))
+    pins.pin_pair_sqdist(W.isotropic(300, 16, 10, seed=9), W.isotropic(77, 16, 10, seed=10) * 3, 10)
     pins.pin_masked()
 
 

@@ -75,7 +75,7 @@ def test_masked_range_query():
 
 
 def test_pair_sqdist():
-    pins.pin_pair_sqdist(W.isotropic(300, 16, 10, seed=9))
+    pins.pin_pair_sqdist(W.isotropic(300, 16, 10, seed=9), W.isotropic(77, 16, 10, seed=10) * 3, 10)
 
 
 def test_iso_n10k_d16_counts():
