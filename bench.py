@@ -346,16 +346,33 @@ def run_ours(args):
     dtype_used = " + ".join(DTYPES[by_code[u]] for u in used if u in by_code) or DTYPES[args.path]
 
     extra = {}
-    # comparison: plain FP32 CUDA-core path, same workload
-    if args.compare_steps > 0 and args.path != "fp32":
-        ms32, st32 = timed("fp32", 1, args.compare_steps)
-        ev32 = sum(s["distance_evals"] for s in st32[0])
-        f32 = [s for st in st32 for s in st]
-        extra["fp32_path"] = {"value": ev32 * args.compare_steps / (ms32 / 1000.0), "unit": UNIT,
-                              "ms_per_step": ms32 / args.compare_steps, "steps": args.compare_steps,
-                              "build_s": {str(e): f32[i]["ms_total"] / 1000.0 for i, e in enumerate(eps_list)},
-                              "band_pairs": sum(s["band_pairs"] for s in f32)}
-        extra["tc_speedup_vs_fp32"] = (ms32 / args.compare_steps) / ms_step
+    # comparisons on the same workload: the bf16 hi/lo split tensor-core path (the metric's
+    # "TC split path") and the plain FP32 CUDA-core path
+    if args.compare_steps > 0:
+        for cmp_path, key in (("tc", "split_path"), ("fp32", "fp32_path")):
+            if cmp_path == args.path:
+                continue
+            msc, stc = timed(cmp_path, 1, args.compare_steps)
+            evc = sum(s["distance_evals"] for s in stc[0])
+            fc = [s for st in stc for s in st]
+            extra[key] = {"value": evc * args.compare_steps / (msc / 1000.0), "unit": UNIT,
+                          "ms_per_step": msc / args.compare_steps, "steps": args.compare_steps,
+                          "build_s": {str(e): fc[i]["ms_total"] / 1000.0 for i, e in enumerate(eps_list)},
+                          "band_pairs": sum(s["band_pairs"] for s in fc),
+                          "recheck_rate": sum(s["band_pairs"] for s in fc) / max(sum(s["tile_pairs"] for s in fc), 1)}
+            if cmp_path == "fp32":
+                extra["tc_speedup_vs_fp32"] = (msc / args.compare_steps) / ms_step
+                if "split_path" in extra:
+                    extra["split_speedup_vs_fp32"] = msc / extra["split_path"]["ms_per_step"] / args.compare_steps
+    # reported distances (opt-in output): one untimed build per eps with distances, their
+    # measured error against the FP64 distance the oracle computes
+    dist_err = []
+    for e in eps_list:
+        out = binding.bm_build(Xd, e, path=args.path, want_dists=True)
+        dist_err.append(out["stats"]["dist_max_rel_err"])
+        del out
+    extra["dists"] = {"max_rel_err_vs_fp64": max(dist_err), "tolerance": 1e-6,
+                      "note": "untimed builds with want_dists, one per eps"}
 
     # end to end through the C-ABI with host buffers: H2D of the inputs and D2H of the graph inside
     e2e = None
@@ -393,7 +410,8 @@ def run_ours(args):
             "config": config_of(w, {"path": args.path, "landmarks": L_per_eps, "build_s": build_s,
                                     "evals_per_step": evals_per_step,
                                     "band_pairs": sum(s["band_pairs"] for s in flat),
-                                    "tile_pairs": tile_pairs}),
+                                    "tile_pairs": tile_pairs,
+                                    "recheck_rate": sum(s["band_pairs"] for s in flat) / max(tile_pairs, 1)}),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches}
     line.update(extra)

@@ -93,6 +93,10 @@ typedef struct {
     bm_alloc_fn alloc;     /* optional device allocator for outputs and scratch */
     bm_free_fn free;
     void* alloc_ctx;
+    int32_t want_dists;    /* bm_build, bm_range_query, bm_build_ivf, bm_ivf_range_query: 1 = also return
+                              the distance of every stored pair (bm_csr.dists) and its measured error
+                              (bm_stats.dist_max_rel_err); bm_build_batched rejects it (BM_ERR_ARG) */
+    int32_t reserved1;
 } bm_options;
 
 typedef struct {
@@ -108,6 +112,10 @@ typedef struct {
     double ms_sweep;          /* device time of the distance-tile launches (CUDA events on the stream) */
     int64_t sweep_launches;   /* distance-tile kernel launches */
     int64_t kernel_launches;  /* all kernel launches of the call */
+    double recheck_rate;      /* band_pairs / tile_pairs: the fraction of tile decisions re-taken in FP64 */
+    double dist_max_rel_err;  /* with want_dists: max over reported distances of |dist - sqrt(D)| / sqrt(D),
+                                 D the FP64 squared distance in coordinate order (the CPU oracle's value);
+                                 the rounding of sqrt(D) to float bounds it by 2^-24; 0 otherwise */
 } bm_stats;
 
 typedef struct {
@@ -115,8 +123,11 @@ typedef struct {
     int64_t nnz;        /* number of stored ids */
     int64_t* offsets;   /* rows + 1 entries; row r is ids[offsets[r] .. offsets[r+1]) */
     int32_t* ids;       /* point ids, ascending within each row */
-    int32_t on_host;    /* 1 when offsets/ids are host memory */
+    int32_t on_host;    /* 1 when offsets/ids/dists are host memory */
     int32_t reserved0;
+    float* dists;       /* NULL unless opt->want_dists: nnz entries, dists[e] = d(q_row, X[ids[e]]) as the
+                           float nearest to the FP64 root of the FP64 squared distance summed in
+                           coordinate order (relative error <= 2^-24 against that FP64 distance) */
 } bm_csr;
 
 typedef struct {

@@ -32,7 +32,8 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void
 class bm_options(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("path", ctypes.c_int32), ("host_io", ctypes.c_int32),
                 ("batch", ctypes.c_int32), ("skip_edges", ctypes.c_int32), ("alloc", ALLOC_FN),
-                ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
+                ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("want_dists", ctypes.c_int32),
+                ("reserved1", ctypes.c_int32)]
 
 
 class bm_stats(ctypes.Structure):
@@ -41,7 +42,8 @@ class bm_stats(ctypes.Structure):
                 ("ms_prep", ctypes.c_double), ("ms_greedy", ctypes.c_double), ("ms_members", ctypes.c_double),
                 ("ms_edges", ctypes.c_double), ("ms_total", ctypes.c_double), ("band_delta", ctypes.c_float),
                 ("path", ctypes.c_int32), ("ms_sweep", ctypes.c_double), ("sweep_launches", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("recheck_rate", ctypes.c_double),
+                ("dist_max_rel_err", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -49,7 +51,8 @@ class bm_stats(ctypes.Structure):
 
 class bm_csr(ctypes.Structure):
     _fields_ = [("rows", ctypes.c_int64), ("nnz", ctypes.c_int64), ("offsets", ctypes.c_void_p),
-                ("ids", ctypes.c_void_p), ("on_host", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+                ("ids", ctypes.c_void_p), ("on_host", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("dists", ctypes.c_void_p)]
 
 
 class bm_graph(ctypes.Structure):
@@ -200,10 +203,11 @@ def _is_torch_cuda(x) -> bool:
 
 
 def _options(lib, path: str, batch: int, stream, host_io: bool, alloc: Optional[_TorchAllocator],
-             skip_edges: bool = False):
+             skip_edges: bool = False, want_dists: bool = False):
     opt = bm_options()
     lib.bm_options_init(ctypes.byref(opt))
     opt.skip_edges = 1 if skip_edges else 0
+    opt.want_dists = 1 if want_dists else 0
     opt.path = PATHS[path]
     opt.batch = int(batch)
     opt.host_io = 1 if host_io else 0
@@ -239,11 +243,12 @@ def _as_input(x, d_expected=None):
     return (a.ctypes.data if a.size else None), a.shape[0], a.shape[1], a, True
 
 
-def bm_range_query(X, Q, eps: float, path: str = "auto", stream=None):
+def bm_range_query(X, Q, eps: float, path: str = "auto", stream=None, want_dists: bool = False):
     """Exact range query R_eps(q) for every row q of Q over the points X.
 
     Device tensors in -> torch CUDA tensors out; host arrays in -> numpy out.
-    Returns (offsets int64 [m+1], ids int32 [nnz], stats dict)."""
+    Returns (offsets int64 [m+1], ids int32 [nnz], stats dict); with want_dists,
+    (offsets, ids, stats, dists float32 [nnz]) where dists[e] = d(Q_row, X[ids[e]])."""
     lib = load()
     px, n, d, kx, hx = _as_input(X)
     pq, m, dq, kq, hq = _as_input(Q)
@@ -254,36 +259,44 @@ def bm_range_query(X, Q, eps: float, path: str = "auto", stream=None):
     out = bm_csr()
     st = bm_stats()
     if hx:
-        opt = _options(lib, path, 0, stream, True, None)
+        opt = _options(lib, path, 0, stream, True, None, want_dists=want_dists)
         _check(lib, lib.bm_range_query(px, n, d, pq, m, ctypes.c_float(eps), ctypes.byref(opt), ctypes.byref(out),
                                        ctypes.byref(st)))
         try:
             off = np.ctypeslib.as_array((ctypes.c_int64 * (m + 1)).from_address(out.offsets)).copy()
             ids = np.ctypeslib.as_array((ctypes.c_int32 * max(out.nnz, 1)).from_address(out.ids))[: out.nnz].copy()
+            dists = None
+            if want_dists:
+                dists = np.ctypeslib.as_array((ctypes.c_float * max(out.nnz, 1)).from_address(out.dists))[
+                    : out.nnz].copy()
         finally:
             lib.bm_csr_free(ctypes.byref(out), ctypes.byref(opt))
-        return off, ids, st.as_dict()
+        return (off, ids, st.as_dict(), dists) if want_dists else (off, ids, st.as_dict())
     import torch
     dev = kx.device
     alloc = _TorchAllocator(dev)
-    opt = _options(lib, path, 0, stream or _current_stream(dev), False, alloc)
+    opt = _options(lib, path, 0, stream or _current_stream(dev), False, alloc, want_dists=want_dists)
     _check(lib, lib.bm_range_query(px, n, d, pq, m, ctypes.c_float(eps), ctypes.byref(opt), ctypes.byref(out),
                                    ctypes.byref(st)))
     off = alloc.tensor(out.offsets, m + 1, torch.int64)
     ids = alloc.tensor(out.ids, out.nnz, torch.int32)
+    if want_dists:
+        return off, ids, st.as_dict(), alloc.tensor(out.dists, out.nnz, torch.float32)
     return off, ids, st.as_dict()
 
 
-def bm_build(X, eps: float, path: str = "auto", batch: int = 0, stream=None, skip_edges: bool = False):
+def bm_build(X, eps: float, path: str = "auto", batch: int = 0, stream=None, skip_edges: bool = False,
+             want_dists: bool = False):
     """Exact Ball Mapper: landmarks (greedy index order), CSR memberships, nerve edges.
 
     Device tensor in -> dict of torch CUDA tensors; host array in -> dict of numpy arrays.
-    Keys: landmarks int32 [L], offsets int64 [L+1], ids int32 [nnz], edges int32 [E, 2], stats."""
+    Keys: landmarks int32 [L], offsets int64 [L+1], ids int32 [nnz], edges int32 [E, 2], stats;
+    with want_dists also dists float32 [nnz] (distance of each member to its landmark)."""
     lib = load()
     px, n, d, kx, host = _as_input(X)
     g = bm_graph()
     if host:
-        opt = _options(lib, path, batch, stream, True, None, skip_edges)
+        opt = _options(lib, path, batch, stream, True, None, skip_edges, want_dists)
         _check(lib, lib.bm_build(px, n, d, ctypes.c_float(eps), ctypes.byref(opt), ctypes.byref(g)))
         try:
             L, nnz, E = g.n_landmarks, g.members.nnz, g.n_edges
@@ -296,20 +309,31 @@ def bm_build(X, eps: float, path: str = "auto", batch: int = 0, stream=None, ski
                    "ids": arr(g.members.ids, ctypes.c_int32, nnz),
                    "edges": arr(g.edges, ctypes.c_int32, 2 * E).reshape(E, 2),
                    "stats": g.stats.as_dict()}
+            if want_dists:
+                res["dists"] = arr(g.members.dists, ctypes.c_float, nnz)
         finally:
             lib.bm_graph_free(ctypes.byref(g), ctypes.byref(opt))
         return res
     import torch
     dev = kx.device
     alloc = _TorchAllocator(dev)
-    opt = _options(lib, path, batch, stream or _current_stream(dev), False, alloc, skip_edges)
+    opt = _options(lib, path, batch, stream or _current_stream(dev), False, alloc, skip_edges, want_dists)
     _check(lib, lib.bm_build(px, n, d, ctypes.c_float(eps), ctypes.byref(opt), ctypes.byref(g)))
+    return _graph_dict(alloc, g, want_dists)
+
+
+def _graph_dict(alloc, g, want_dists=False):
+    """A device bm_graph adopted as a dict of torch tensors."""
+    import torch
     L, nnz, E = g.n_landmarks, g.members.nnz, g.n_edges
-    return {"landmarks": alloc.tensor(g.landmarks, L, torch.int32),
-            "offsets": alloc.tensor(g.members.offsets, L + 1, torch.int64),
-            "ids": alloc.tensor(g.members.ids, nnz, torch.int32),
-            "edges": alloc.tensor(g.edges, 2 * E, torch.int32).view(E, 2),
-            "stats": g.stats.as_dict()}
+    res = {"landmarks": alloc.tensor(g.landmarks, L, torch.int32),
+           "offsets": alloc.tensor(g.members.offsets, L + 1, torch.int64),
+           "ids": alloc.tensor(g.members.ids, nnz, torch.int32),
+           "edges": alloc.tensor(g.edges, 2 * E, torch.int32).view(E, 2),
+           "stats": g.stats.as_dict()}
+    if want_dists:
+        res["dists"] = alloc.tensor(g.members.dists, nnz, torch.float32)
+    return res
 
 
 def bm_build_batched(instances, path: str = "auto", batch: int = 0, stream=None, skip_edges: bool = False):
@@ -452,30 +476,34 @@ class IvfIndex:
         self.cell_of = self._alloc.peek(co.value, self.n, torch.int32)
         self.centroids = self._alloc.peek(ce.value, self.nlist * self.d, torch.float32).view(self.nlist, self.d)
 
-    def range_query(self, Q, eps: float, nprobe: int):
-        """(offsets, ids, probes, stats): conservative range sets over the nprobe nearest cells."""
+    def range_query(self, Q, eps: float, nprobe: int, want_dists: bool = False):
+        """(offsets, ids, probes, stats): conservative range sets over the nprobe nearest cells;
+        with want_dists, (offsets, ids, probes, stats, dists)."""
         import torch
         pq, m, dq, kq, _ = _as_input(Q)
         if not _is_torch_cuda(Q):
             raise ValueError("Q must be a CUDA tensor")
         probes = torch.empty((m, nprobe), dtype=torch.int32, device=kq.device)
         alloc = _TorchAllocator(kq.device)
-        opt = _options(self._lib, "fp32", 0, _current_stream(kq.device), False, alloc)
+        opt = _options(self._lib, "fp32", 0, _current_stream(kq.device), False, alloc, want_dists=want_dists)
         out = bm_csr()
         st = bm_stats()
         _check(self._lib, self._lib.bm_ivf_range_query(self._h, pq, m, ctypes.c_float(eps), int(nprobe),
                                                        ctypes.byref(opt), ctypes.byref(out),
                                                        probes.data_ptr() if m else None, ctypes.byref(st)))
-        return (alloc.tensor(out.offsets, m + 1, torch.int64), alloc.tensor(out.ids, out.nnz, torch.int32), probes,
-                st.as_dict())
+        res = (alloc.tensor(out.offsets, m + 1, torch.int64), alloc.tensor(out.ids, out.nnz, torch.int32), probes,
+               st.as_dict())
+        if want_dists:
+            res = res + (alloc.tensor(out.dists, out.nnz, torch.float32),)
+        return res
 
-    def build(self, eps: float, nprobe: int, landmarks=None, batch: int = 0):
+    def build(self, eps: float, nprobe: int, landmarks=None, batch: int = 0, want_dists: bool = False):
         """Ball Mapper through the index: fixed-landmark mode (landmarks = CUDA int32 tensor)
         or end-to-end mode (landmarks None)."""
         import torch
         dev = self._X.device
         alloc = _TorchAllocator(dev)
-        opt = _options(self._lib, "fp32", batch, _current_stream(dev), False, alloc)
+        opt = _options(self._lib, "fp32", batch, _current_stream(dev), False, alloc, want_dists=want_dists)
         g = bm_graph()
         lm_ptr, nl = None, 0
         if landmarks is not None:
@@ -483,12 +511,7 @@ class IvfIndex:
             lm_ptr, nl = landmarks.data_ptr() if landmarks.numel() else None, landmarks.numel()
         _check(self._lib, self._lib.bm_build_ivf(self._h, ctypes.c_float(eps), int(nprobe), lm_ptr, nl,
                                                  ctypes.byref(opt), ctypes.byref(g)))
-        L, nnz, E = g.n_landmarks, g.members.nnz, g.n_edges
-        return {"landmarks": alloc.tensor(g.landmarks, L, torch.int32),
-                "offsets": alloc.tensor(g.members.offsets, L + 1, torch.int64),
-                "ids": alloc.tensor(g.members.ids, nnz, torch.int32),
-                "edges": alloc.tensor(g.edges, 2 * E, torch.int32).view(E, 2),
-                "stats": g.stats.as_dict()}
+        return _graph_dict(alloc, g, want_dists)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

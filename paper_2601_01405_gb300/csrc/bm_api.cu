@@ -464,6 +464,28 @@ bm_status read_state(const DeviceState* dst, HostState& hs, DeviceState& out, cu
     return BM_OK;
 }
 
+// Reported distances of a CSR (want_dists): allocates *dists and a device error slot
+// (*err_dev, zeroed), launches the kernel; the error is read later with read_err.
+bm_status csr_dists(Arena& ar, cudaStream_t s, const float* qx, const int* qidx, const float* X, int d,
+                    const long long* offsets, long long rows, const int* ids, long long nnz, float** dists,
+                    unsigned long long** err_dev) {
+    ALLOC(*dists, float, std::max<long long>(nnz, 1));
+    ALLOC(*err_dev, unsigned long long, 1);
+    TRY_CUDA(cudaMemsetAsync(*err_dev, 0, sizeof(unsigned long long), s));
+    TRY_CUDA(launch_member_dists(qx, qidx, X, d, offsets, rows, ids, nnz, *dists, *err_dev, s));
+    return BM_OK;
+}
+
+bm_status read_err(const unsigned long long* err_dev, cudaStream_t s, double* out) {
+    *out = 0.0;
+    if (!err_dev) return BM_OK;
+    unsigned long long bits = 0;
+    TRY_CUDA(cudaMemcpyAsync(&bits, err_dev, sizeof(bits), cudaMemcpyDeviceToHost, s));
+    TRY_CUDA(cudaStreamSynchronize(s));
+    std::memcpy(out, &bits, sizeof(double));
+    return BM_OK;
+}
+
 // The greedy + membership part of bm_build.  Returns BM_OK with *retry set when
 // a buffer was too small (capacities are updated for the next attempt).
 // Buffers and sweep description of one greedy build.
@@ -775,6 +797,9 @@ bm_status range_core(const float* X, long long n, int d, const float* Q, long lo
     int* ids = nullptr;
     unsigned long long band = 0, pairs = 0;
     float delta = 0.f;
+    float* dists = nullptr;
+    unsigned long long* err_dev = nullptr;
+    double dist_err = 0.0;
     {
         Arena ar(&opt, s);
         const float* dX = ivf ? X : stage_input(X, n, d, host_io, ar, s, &rs);
@@ -869,28 +894,43 @@ bm_status range_core(const float* X, long long n, int d, const float* Q, long lo
             ALLOC(ids, int, std::max<long long>(nnz, 1));
             TRY_CUDA(launch_csr_from_sorted(sorted, nnz, m, offsets, ids, s));
         }
+        if (opt.want_dists) {
+            if (nnz == 0) {
+                ALLOC(dists, float, 1);
+            } else {
+                rs = csr_dists(ar, s, dQ, nullptr, dX, d, offsets, m, ids, nnz, &dists, &err_dev);
+                if (rs != BM_OK) return rs;
+            }
+        }
         if (host_io) {
-            void *ho = nullptr, *hi = nullptr;
+            void *ho = nullptr, *hi = nullptr, *hd = nullptr;
             if (!to_host(&ho, offsets, sizeof(long long) * (m + 1), s) ||
-                !to_host(&hi, ids, sizeof(int) * std::max<long long>(nnz, 1), s)) {
+                !to_host(&hi, ids, sizeof(int) * std::max<long long>(nnz, 1), s) ||
+                (dists && !to_host(&hd, dists, sizeof(float) * std::max<long long>(nnz, 1), s))) {
                 std::free(ho);
                 std::free(hi);
+                std::free(hd);
                 return fail(BM_ERR_CUDA, "device to host copy of the result failed");
             }
             TRY_CUDA(cudaStreamSynchronize(s));
             offsets = (long long*)ho;
             ids = (int*)hi;
+            dists = (float*)hd;
             out->on_host = 1;
         } else {
             ar.take(offsets);
             ar.take(ids);
+            if (dists && !ar.take(dists)) return fail(BM_ERR_NOMEM, "distance buffer could not be handed over");
         }
+        rs = read_err(err_dev, s, &dist_err);
+        if (rs != BM_OK) return rs;
     }
     tm.mark();
     out->rows = m;
     out->nnz = nnz;
     out->offsets = (int64_t*)offsets;
     out->ids = ids;
+    out->dists = dists;
     if (stats) {
         stats->distance_evals = (int64_t)n * m;
         stats->tile_pairs = (int64_t)pairs;
@@ -901,6 +941,8 @@ bm_status range_core(const float* X, long long n, int d, const float* Q, long lo
         stats->ms_sweep = stimer.ms;
         stats->sweep_launches = stimer.launches;
         stats->kernel_launches = g_kernel_launches - launches0;
+        stats->recheck_rate = pairs ? (double)band / (double)pairs : 0.0;
+        stats->dist_max_rel_err = dist_err;
     }
     return BM_OK;
 }
@@ -946,22 +988,24 @@ bm_status members_and_edges(Arena& ar, cudaStream_t s, const bm_options& opt, lo
 // Move the result arrays into *g: copied to malloc'd host buffers (host_io) or
 // handed over as device buffers that the caller frees with bm_graph_free.
 bm_status hand_over(Arena& ar, cudaStream_t s, bool host_io, int* landmarks, long long* offsets, int* ids,
-                    int* edges, long long L, long long nnz, long long E, bm_graph& g) {
+                    int* edges, long long L, long long nnz, long long E, bm_graph& g, float* dists = nullptr) {
     if (host_io) {
-        void *hl = nullptr, *ho = nullptr, *hi = nullptr, *he = nullptr;
+        void *hl = nullptr, *ho = nullptr, *hi = nullptr, *he = nullptr, *hd = nullptr;
         bool ok = to_host(&hl, landmarks, sizeof(int) * std::max<long long>(L, 1), s) &&
                   to_host(&ho, offsets, sizeof(long long) * (L + 1), s) &&
                   to_host(&hi, ids, sizeof(int) * std::max<long long>(nnz, 1), s) &&
-                  to_host(&he, edges, sizeof(int) * 2 * std::max<long long>(E, 1), s);
+                  to_host(&he, edges, sizeof(int) * 2 * std::max<long long>(E, 1), s) &&
+                  (!dists || to_host(&hd, dists, sizeof(float) * std::max<long long>(nnz, 1), s));
         if (ok && cudaStreamSynchronize(s) != cudaSuccess) ok = false;
         if (!ok) {
-            std::free(hl); std::free(ho); std::free(hi); std::free(he);
+            std::free(hl); std::free(ho); std::free(hi); std::free(he); std::free(hd);
             cudaGetLastError();
             return fail(BM_ERR_CUDA, "device to host copy of the result failed");
         }
         g.landmarks = (int*)hl;
         g.members.offsets = (int64_t*)ho;
         g.members.ids = (int*)hi;
+        g.members.dists = (float*)hd;
         g.edges = (int*)he;
         g.on_host = 1;
         g.members.on_host = 1;
@@ -987,15 +1031,18 @@ bm_status hand_over(Arena& ar, cudaStream_t s, bool host_io, int* landmarks, lon
         void* oo = rs == BM_OK ? own(offsets, sizeof(long long) * (L + 1), &rs) : nullptr;
         void* oi = rs == BM_OK ? own(ids, sizeof(int) * std::max<long long>(nnz, 1), &rs) : nullptr;
         void* oe = rs == BM_OK ? own(edges, sizeof(int) * 2 * std::max<long long>(E, 1), &rs) : nullptr;
+        void* od = rs == BM_OK && dists ? own(dists, sizeof(float) * std::max<long long>(nnz, 1), &rs) : nullptr;
         if (rs != BM_OK) {
             device_free(ar.options(), s, ol);
             device_free(ar.options(), s, oo);
             device_free(ar.options(), s, oi);
+            device_free(ar.options(), s, oe);
             return rs;
         }
         g.landmarks = (int*)ol;
         g.members.offsets = (int64_t*)oo;
         g.members.ids = (int*)oi;
+        g.members.dists = (float*)od;
         g.edges = (int*)oe;
     }
     g.n_landmarks = L;
@@ -1033,6 +1080,8 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
     DeviceState fin;
     std::memset(&fin, 0, sizeof(fin));
     long long edge_pairs = 0;
+    unsigned long long* err_dev = nullptr;
+    double dist_err = 0.0;
     {
         Arena ar(&opt, s);
         const float* dX = ivf ? X : stage_input(X, n, d, host_io, ar, s, &rs);
@@ -1156,7 +1205,18 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
             rs = members_and_edges(ar, s, opt, n, L, nnz, mem_keys, &tm, &offsets, &ids, &edges, &E, &edge_pairs);
             if (rs != BM_OK) return rs;
         }
-        rs = hand_over(ar, s, host_io, landmarks, offsets, ids, edges, L, nnz, E, g);
+        float* dists = nullptr;
+        if (opt.want_dists) {
+            if (n == 0) {
+                ALLOC(dists, float, 1);
+            } else {
+                rs = csr_dists(ar, s, nullptr, landmarks, dX, d, offsets, L, ids, nnz, &dists, &err_dev);
+                if (rs != BM_OK) return rs;
+            }
+        }
+        rs = hand_over(ar, s, host_io, landmarks, offsets, ids, edges, L, nnz, E, g, dists);
+        if (rs != BM_OK) return rs;
+        rs = read_err(err_dev, s, &dist_err);
         if (rs != BM_OK) return rs;
     }
     tm.mark();  // 5
@@ -1176,6 +1236,8 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
     g.stats.ms_sweep = stimer.ms;
     g.stats.sweep_launches = stimer.launches;
     g.stats.kernel_launches = g_kernel_launches - launches0;
+    g.stats.recheck_rate = fin.tile_pairs ? (double)fin.band_pairs / (double)fin.tile_pairs : 0.0;
+    g.stats.dist_max_rel_err = dist_err;
     *out = g;
     return BM_OK;
 }
@@ -1532,10 +1594,12 @@ void bm_csr_free(bm_csr* csr, const bm_options* opt) {
     if (csr->on_host) {
         std::free(csr->offsets);
         std::free(csr->ids);
+        std::free(csr->dists);
     } else {
         cudaStream_t s = opt ? (cudaStream_t)opt->stream : nullptr;
         device_free(opt, s, csr->offsets);
         device_free(opt, s, csr->ids);
+        device_free(opt, s, csr->dists);
     }
     std::memset(csr, 0, sizeof(*csr));
 }
@@ -1639,6 +1703,7 @@ bm_status bm_build_batched(const bm_instance* inst, int32_t count, const bm_opti
     }
     bm_status vs = validate_batch(opt.batch, 2048);   // arguments first, then the device
     if (vs != BM_OK) return vs;
+    if (opt.want_dists) return fail(BM_ERR_ARG, "bm_build_batched does not return distances (want_dists)");
     vs = check_device(opt.path);
     if (vs != BM_OK) return vs;
     if (count == 0) return BM_OK;

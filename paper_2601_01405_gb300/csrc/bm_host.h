@@ -215,6 +215,13 @@ cudaError_t launch_band_recheck(DeviceState* st, const unsigned long long* band,
                                 unsigned long long* count, unsigned long long cap, const HitSink& book,
                                 bool check_done, int overflow_bit, bool stop_on_overflow, cudaStream_t s);
 
+// dists.cu: dists[e] = float(sqrt(D)) for every CSR entry, D the FP64 squared distance
+// in coordinate order between the row's query (qx + r d, or X + qidx[r] d) and X[ids[e]];
+// the largest relative error against sqrt(D) is atomicMax'ed into *max_err_bits (double bits).
+cudaError_t launch_member_dists(const float* qx, const int* qidx, const float* X, int d, const long long* offsets,
+                                long long rows, const int* ids, long long nnz, float* dists,
+                                unsigned long long* max_err_bits, cudaStream_t s);
+
 // graph.cu
 cudaError_t launch_csr_from_sorted(const unsigned long long* keys, long long nnz, long long rows,
                                    long long* offsets, int* ids, cudaStream_t s);

@@ -41,9 +41,9 @@ def test_binding_loads_and_reports_version():
 
 
 def test_struct_layouts_match_header():
-    # bm_options: pointer, 4 int32, 3 pointers
-    assert ctypes.sizeof(binding.bm_options) == 8 + 16 + 24
-    assert ctypes.sizeof(binding.bm_csr) == 8 + 8 + 8 + 8 + 8
+    # bm_options: pointer, 4 int32, 3 pointers, 2 int32
+    assert ctypes.sizeof(binding.bm_options) == 8 + 16 + 24 + 8
+    assert ctypes.sizeof(binding.bm_csr) == 8 + 8 + 8 + 8 + 8 + 8
     assert binding.bm_graph.stats.offset == ctypes.sizeof(binding.bm_graph) - ctypes.sizeof(binding.bm_stats)
 
 
@@ -58,6 +58,8 @@ int main(void) {
     printf("%zu %zu %zu %zu %zu\n", sizeof(bm_options), sizeof(bm_stats), sizeof(bm_csr), sizeof(bm_graph),
            offsetof(bm_graph, stats));
     printf("%zu %zu %zu\n", offsetof(bm_options, alloc), offsetof(bm_stats, ms_prep), offsetof(bm_graph, edges));
+    printf("%zu %zu %zu\n", offsetof(bm_options, want_dists), offsetof(bm_stats, dist_max_rel_err),
+           offsetof(bm_csr, dists));
     return 0;
 }
 ''')
@@ -68,7 +70,9 @@ int main(void) {
     got = [int(v) for v in out]
     exp = [ctypes.sizeof(binding.bm_options), ctypes.sizeof(binding.bm_stats), ctypes.sizeof(binding.bm_csr),
            ctypes.sizeof(binding.bm_graph), binding.bm_graph.stats.offset,
-           binding.bm_options.alloc.offset, binding.bm_stats.ms_prep.offset, binding.bm_graph.edges.offset]
+           binding.bm_options.alloc.offset, binding.bm_stats.ms_prep.offset, binding.bm_graph.edges.offset,
+           binding.bm_options.want_dists.offset, binding.bm_stats.dist_max_rel_err.offset,
+           binding.bm_csr.dists.offset]
     assert got == exp
 
 
