@@ -156,6 +156,24 @@ BM_API bm_status bm_range_query(const float* X, int64_t n, int32_t d, const floa
 BM_API bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_options* opt,
                    bm_graph* out);
 
+/* k-th nearest-neighbour distance of every point, the point itself counted first
+ * (the target-occupancy rule of Sec. 6.1): kdist[i] = sqrt(D_(k)(i)), D_(1) <= D_(2) <= ...
+ * the FP64 squared distances (coordinate order) from X_i to all n points, X_i included.
+ * Exact: equal to the FP64 value of that definition for any finite float32 input.
+ *   X: n x d float32 (n >= 1); 1 <= k <= min(n, 1024);
+ *   kdist: n doubles (device memory; host memory with opt->host_io), written.
+ * Arithmetic: a proven upper bound of each row's k-th squared distance from a strided
+ * sample of the points (CUDA cores), a range query of every point with its own radius
+ * on the distance tiles (opt->path; automatic and fp16 run the bf16 split), then the
+ * k-th smallest FP64 squared distance of each ball.  stats may be NULL. */
+BM_API bm_status bm_knn_dist(const float* X, int64_t n, int32_t d, int32_t k, const bm_options* opt, double* kdist,
+                             bm_stats* stats);
+
+/* Target-occupancy scale (Sec. 6.1): *eps = median over the points of bm_knn_dist's
+ * values (for even n the mean of the two middle values), returned in host memory. */
+BM_API bm_status bm_occupancy_eps(const float* X, int64_t n, int32_t d, int32_t k, const bm_options* opt,
+                                  double* eps, bm_stats* stats);
+
 /* One problem of a batched build: n x d float32 points (device memory; host
  * memory with host_io) and its own eps. */
 typedef struct {

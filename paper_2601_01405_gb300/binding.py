@@ -144,6 +144,13 @@ def load(path: str = LIB_PATH):
         lib.bm_get_tile_config.restype = ctypes.c_int
         lib.bm_set_tile_config.argtypes = [ctypes.c_int32, ctypes.POINTER(bm_tile_config)]
         lib.bm_set_tile_config.restype = ctypes.c_int
+        lib.bm_knn_dist.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.POINTER(bm_options), ctypes.c_void_p, ctypes.POINTER(bm_stats)]
+        lib.bm_knn_dist.restype = ctypes.c_int
+        lib.bm_occupancy_eps.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.POINTER(bm_options), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(bm_stats)]
+        lib.bm_occupancy_eps.restype = ctypes.c_int
         lib.bm_set_nerve_bitmap_bytes.argtypes = [ctypes.c_int64]
         lib.bm_set_nerve_bitmap_bytes.restype = ctypes.c_int64
         _lib = lib
@@ -334,6 +341,42 @@ def _graph_dict(alloc, g, want_dists=False):
     if want_dists:
         res["dists"] = alloc.tensor(g.members.dists, nnz, torch.float32)
     return res
+
+
+def bm_knn_dist(X, k: int, path: str = "auto", stream=None):
+    """Distance from every point to its k-th nearest neighbour, itself counted first
+    (Sec. 6.1).  Device tensor in -> float64 CUDA tensor [n]; host array in -> numpy.
+    Returns (kdist, stats)."""
+    lib = load()
+    px, n, d, kx, host = _as_input(X)
+    st = bm_stats()
+    if host:
+        out = np.empty(max(n, 1), dtype=np.float64)
+        opt = _options(lib, path, 0, stream, True, None)
+        _check(lib, lib.bm_knn_dist(px, n, d, int(k), ctypes.byref(opt), out.ctypes.data, ctypes.byref(st)))
+        return out[:n], st.as_dict()
+    import torch
+    out = torch.empty(max(n, 1), dtype=torch.float64, device=kx.device)
+    alloc = _TorchAllocator(kx.device)
+    opt = _options(lib, path, 0, stream or _current_stream(kx.device), False, alloc)
+    _check(lib, lib.bm_knn_dist(px, n, d, int(k), ctypes.byref(opt), out.data_ptr(), ctypes.byref(st)))
+    return out[:n], st.as_dict()
+
+
+def bm_occupancy_eps(X, k: int, path: str = "auto", stream=None):
+    """Target-occupancy scale (Sec. 6.1): median over the points of the k-th NN distance.
+    Returns (eps as a Python float, stats)."""
+    lib = load()
+    px, n, d, kx, host = _as_input(X)
+    st = bm_stats()
+    eps = ctypes.c_double(0.0)
+    if host:
+        opt = _options(lib, path, 0, stream, True, None)
+    else:
+        alloc = _TorchAllocator(kx.device)
+        opt = _options(lib, path, 0, stream or _current_stream(kx.device), False, alloc)
+    _check(lib, lib.bm_occupancy_eps(px, n, d, int(k), ctypes.byref(opt), ctypes.byref(eps), ctypes.byref(st)))
+    return eps.value, st.as_dict()
 
 
 def bm_build_batched(instances, path: str = "auto", batch: int = 0, stream=None, skip_edges: bool = False):

@@ -228,7 +228,7 @@ int prec_for(int path) {
 // bf16 split (kPrecSplit) here; the fp16 operands (kPrecFp16) only once the scale
 // is known (finish_fp16, after the norms have been read back).
 bm_status prepare(const float* x, long long rows, int d, double eps2, bool a_side, int prec, Arena& ar,
-                  unsigned* max_norm_bits, int* bad, cudaStream_t s, Prepared& p) {
+                  unsigned* max_norm_bits, int* bad, cudaStream_t s, Prepared& p, const double* row_r2 = nullptr) {
     p.x = x;
     p.rows = rows;
     p.d = d;
@@ -245,7 +245,7 @@ bm_status prepare(const float* x, long long rows, int d, double eps2, bool a_sid
         ALLOC(p.aug, __nv_bfloat16, std::max<long long>(rows, 1) * 16);
     }
     if (prec == kPrecSplit) ALLOC(p.lo, __nv_bfloat16, std::max<long long>(rows, 1) * p.d_pad);
-    TRY_CUDA(launch_prep(x, rows, d, eps2, a_side, prec == kPrecSplit, p, max_norm_bits, bad, s));
+    TRY_CUDA(launch_prep(x, rows, d, eps2, a_side, prec == kPrecSplit, p, max_norm_bits, bad, s, row_r2));
     return BM_OK;
 }
 
@@ -452,7 +452,7 @@ bm_status sweep_stage(SweepDesc& sd, DeviceState* st, int path, SweepOut& o, uns
                                          o.keys, o.band, count, &st->band_n, st, overflow_bit, greedy, greedy, s));
     }
     TRY_CUDA(launch_band_recheck(st, o.band, o.cap, sd.a->x, sd.b->x, sd.b->d, sd.eps2, o.keys, count, o.cap, sd.sink,
-                                 greedy, overflow_bit, greedy, s));
+                                 greedy, overflow_bit, greedy, s, sd.row_eps2));
     return BM_OK;
 }
 
@@ -776,15 +776,19 @@ namespace {
 
 // Range query R_eps(q) for every row q of Q over the points X (exact), or over the
 // cells an inverted-file index probes for q (conservative).  Arguments validated.
+// row_r2 (device, m entries; optional): a squared radius per query row instead of eps^2
+// (k-NN sweeps; r2_max is its maximum); the tensor-core rows then use the bf16 split.
 bm_status range_core(const float* X, long long n, int d, const float* Q, long long m, float eps, const bm_options& opt,
-                     const IvfIndex* ivf, int nprobe, int* probes_out, bm_csr* out, bm_stats* stats) {
+                     const IvfIndex* ivf, int nprobe, int* probes_out, bm_csr* out, bm_stats* stats,
+                     const double* row_r2 = nullptr, double r2_max = 0.0, unsigned long long cap_hint = 0) {
     std::memset(out, 0, sizeof(*out));
     if (stats) std::memset(stats, 0, sizeof(*stats));
     cudaStream_t s = (cudaStream_t)opt.stream;
     const bool host_io = opt.host_io != 0;
-    const double eps2 = (double)eps * (double)eps;
+    const double eps2 = row_r2 ? 0.0 : (double)eps * (double)eps;
     // automatic path: a single sweep cannot change course, so range queries take the split
-    const int req = opt.path == BM_PATH_TC_AUTO ? (int)BM_PATH_TC_SPLIT3 : opt.path;
+    const int req = (opt.path == BM_PATH_TC_AUTO || (row_r2 && opt.path == BM_PATH_TC_FP16))
+                        ? (int)BM_PATH_TC_SPLIT3 : opt.path;
     const bool tc = is_tc_path(req) && ivf == nullptr;
     const int path = ivf ? (int)BM_PATH_FP32 : req;
     Timer tm(s);
@@ -822,7 +826,7 @@ bm_status range_core(const float* X, long long n, int d, const float* Q, long lo
             const int prec = tc ? prec_for(path) : kPrecNone;
             rs = prepare(ivf ? ivf->xperm : dX, n, d, eps2, false, prec, ar, &st->max_norm_bits, bad, s, px);
             if (rs != BM_OK) return rs;
-            rs = prepare(dQ, m, d, eps2, true, prec, ar, &st->max_norm_q_bits, bad, s, pq);
+            rs = prepare(dQ, m, d, eps2, true, prec, ar, &st->max_norm_q_bits, bad, s, pq, row_r2);
             if (rs != BM_OK) return rs;
             int hbad = 0;
             unsigned hnorm[2] = {0u, 0u};
@@ -834,12 +838,26 @@ bm_status range_core(const float* X, long long n, int d, const float* Q, long lo
                 float nx, nq;
                 std::memcpy(&nx, &hnorm[0], sizeof(float));
                 std::memcpy(&nq, &hnorm[1], sizeof(float));
-                rs = finish_prep(st, path, d, eps2, (double)eps, false, std::max(nx, nq), &px, &pq, s);
-                if (rs != BM_OK) return rs;
+                if (row_r2) {
+                    // |phi_q| <= max(N_q^2, r2_max) / 2 (the whole radius on the query side),
+                    // |phi_x| <= N_x^2 / 2; delta rounded up to float
+                    const double Nq = nq, Nx = nx;
+                    const double dl = band_halfwidth_core(path, d, px.d_pad, Nq, Nx, 0.5 * std::max(Nq * Nq, r2_max),
+                                                          0.5 * Nx * Nx);
+                    float df = (float)dl;
+                    if ((double)df < dl) df = std::nextafter(df, INFINITY);
+                    TRY_CUDA(cudaMemcpyAsync(&st->delta, &df, sizeof(float), cudaMemcpyHostToDevice, s));
+                    TRY_CUDA(cudaStreamSynchronize(s));
+                    if (px.prec != kPrecNone) TRY_CUDA(launch_set_aug_delta(st, px, s));
+                } else {
+                    rs = finish_prep(st, path, d, eps2, (double)eps, false, std::max(nx, nq), &px, &pq, s);
+                    if (rs != BM_OK) return rs;
+                }
             }
             unsigned long long cap = (unsigned long long)std::min<long long>(std::max<long long>(n, m) * 4 + (1 << 20),
                                                                               (long long)n * m);
             if (tc) cap = std::max<unsigned long long>(cap, (unsigned long long)device_sm_count() * 4096);
+            if (cap_hint) cap = std::max<unsigned long long>(cap, std::min<unsigned long long>(cap_hint, (unsigned long long)n * m));
             HostState hs;
             DeviceState h;
             unsigned long long* keys = nullptr;
@@ -863,6 +881,7 @@ bm_status range_core(const float* X, long long n, int d, const float* Q, long lo
                 sd.ivf_phi_perm = px.phi;
                 sd.nprobe = nprobe;
                 sd.ivf_probes_out = probes_out;
+                sd.row_eps2 = row_r2;
                 rs = sweep_stage(sd, st, path, so, &st->hit_count, kErrHitOverflow, false, sms, stimer, s, ar);
                 if (rs != BM_OK) return rs;
                 rs = read_state(st, hs, h, s);
@@ -943,6 +962,102 @@ bm_status range_core(const float* X, long long n, int d, const float* Q, long lo
         stats->kernel_launches = g_kernel_launches - launches0;
         stats->recheck_rate = pairs ? (double)band / (double)pairs : 0.0;
         stats->dist_max_rel_err = dist_err;
+    }
+    return BM_OK;
+}
+
+// k-th nearest-neighbour distance of every point, itself counted first (Sec. 6.1), and
+// optionally their median (the target-occupancy eps).  kdist: n doubles (device, or host
+// with host_io; may be NULL when only eps is wanted).  Arguments validated.
+bm_status knn_core(const float* X, long long n, int d, int k, const bm_options& opt, double* kdist, double* eps_out,
+                   bm_stats* stats) {
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    cudaStream_t s = (cudaStream_t)opt.stream;
+    const bool host_io = opt.host_io != 0;
+    Timer tm(s);
+    tm.mark();
+    const long long launches0 = g_kernel_launches;
+    bm_stats rst;
+    std::memset(&rst, 0, sizeof(rst));
+    long long nnz = 0;
+    {
+        Arena ar(&opt, s);
+        bm_status rs = BM_OK;
+        const float* dX = stage_input(X, n, d, host_io, ar, s, &rs);
+        if (rs != BM_OK) return rs;
+        // pass 1: per-row upper bounds from a strided sample of at least k points (about
+        // n / 16 of them, at least 8 k, at most 65,536): a row's ball then holds about
+        // k n / s points
+        long long target = std::max<long long>(8LL * k, n / 16);
+        target = std::max<long long>(std::min<long long>(target, 65536), k);
+        const long long stride = target >= n ? 1 : n / target;
+        const long long sN = (n + stride - 1) / stride;
+        double* rho;
+        unsigned long long* rmax;
+        int* bad;
+        ALLOC(rho, double, n);
+        ALLOC(rmax, unsigned long long, 1);
+        ALLOC(bad, int, 1);
+        TRY_CUDA(cudaMemsetAsync(rmax, 0, sizeof(unsigned long long), s));
+        TRY_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+        TRY_CUDA(launch_knn_bound(dX, n, d, stride, sN, k, rho, rmax, bad, s));
+        int hbad = 0;
+        unsigned long long hmax = 0;
+        TRY_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        TRY_CUDA(cudaMemcpyAsync(&hmax, rmax, sizeof(hmax), cudaMemcpyDeviceToHost, s));
+        TRY_CUDA(cudaStreamSynchronize(s));
+        if (hbad) return fail(BM_ERR_ARG, "input holds NaN or Inf, or squared distances that overflow float");
+        double r2_max;
+        std::memcpy(&r2_max, &hmax, sizeof(double));
+        // pass 2: range query of every point with its own squared radius (exact)
+        bm_options o2 = opt;
+        o2.host_io = 0;
+        o2.want_dists = 0;
+        bm_csr csr;
+        const double expect = 1.5 * (double)n * (double)k * ((double)n / (double)sN) + 2.0 * (double)n;
+        const unsigned long long hint = (unsigned long long)std::min(expect, (double)n * (double)n);
+        rs = range_core(dX, n, d, dX, n, 1.0f, o2, nullptr, 0, nullptr, &csr, &rst, rho, r2_max, hint);
+        if (rs != BM_OK) return rs;
+        struct CsrGuard {
+            bm_csr* c;
+            const bm_options* o;
+            ~CsrGuard() { bm_csr_free(c, o); }
+        } guard{&csr, &o2};
+        nnz = csr.nnz;
+        // pass 3: the k-th smallest FP64 squared distance of every row
+        double* D;
+        ALLOC(D, double, std::max<long long>(nnz, 1));
+        double* kd = (kdist && !host_io) ? kdist : nullptr;
+        if (!kd) ALLOC(kd, double, n);
+        TRY_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+        TRY_CUDA(launch_knn_select(dX, d, (const long long*)csr.offsets, n, csr.ids, nnz, D, k, kd, bad, s));
+        ar.release(D);
+        if (eps_out) {
+            // median: radix sort of the bit patterns (non-negative doubles order like them)
+            unsigned long long *keys, *tmp, *sorted = nullptr;
+            ALLOC(keys, unsigned long long, n);
+            ALLOC(tmp, unsigned long long, n);
+            TRY_CUDA(cudaMemcpyAsync(keys, kd, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            TRY_CUDA(radix_sort_u64(keys, tmp, n, digit_shifts(32, 32), ar, s, &sorted));
+            double mid[2] = {0.0, 0.0};
+            const long long i1 = n / 2, i0 = (n % 2) ? i1 : i1 - 1;
+            TRY_CUDA(cudaMemcpyAsync(&mid[0], sorted + i0, sizeof(double), cudaMemcpyDeviceToHost, s));
+            TRY_CUDA(cudaMemcpyAsync(&mid[1], sorted + i1, sizeof(double), cudaMemcpyDeviceToHost, s));
+            TRY_CUDA(cudaStreamSynchronize(s));
+            *eps_out = (n % 2) ? mid[1] : (mid[0] + mid[1]) * 0.5;
+        }
+        if (kdist && host_io) TRY_CUDA(cudaMemcpyAsync(kdist, kd, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        TRY_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        TRY_CUDA(cudaStreamSynchronize(s));
+        if (hbad) return fail(BM_ERR_CUDA, "k-NN select: a row's ball held fewer than k points");
+    }
+    tm.mark();
+    if (stats) {
+        *stats = rst;
+        stats->distance_evals = (int64_t)n * n;
+        stats->ms_total = tm.ms(0, 1);
+        stats->kernel_launches = g_kernel_launches - launches0;
+        stats->candidates = nnz;   // points examined by the select (the rows' balls)
     }
     return BM_OK;
 }
@@ -1652,6 +1767,39 @@ bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_opt
     vs = check_device(opt.path);
     if (vs != BM_OK) return vs;
     return build_graph(X, n, d, eps, opt, nullptr, 0, nullptr, 0, out);
+}
+
+static bm_status validate_knn(const float* X, int64_t n, int32_t d, int32_t k, const bm_options& opt) {
+    bm_status vs = validate_points(X, n, d, "X");
+    if (vs != BM_OK) return vs;
+    if (n < 1) return fail(BM_ERR_ARG, "the k-th nearest neighbour needs n >= 1");
+    if (k < 1 || k > n || k > 1024) return fail(BM_ERR_ARG, "k must be in [1, min(n, 1024)]");
+    return check_device(opt.path);
+}
+
+bm_status bm_knn_dist(const float* X, int64_t n, int32_t d, int32_t k, const bm_options* opt_in, double* kdist,
+                      bm_stats* stats) {
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (!kdist) return fail(BM_ERR_ARG, "kdist is NULL");
+    bm_options opt;
+    bm_options_init(&opt);
+    if (opt_in) opt = *opt_in;
+    bm_status vs = validate_knn(X, n, d, k, opt);
+    if (vs != BM_OK) return vs;
+    return knn_core(X, n, d, k, opt, kdist, nullptr, stats);
+}
+
+bm_status bm_occupancy_eps(const float* X, int64_t n, int32_t d, int32_t k, const bm_options* opt_in, double* eps,
+                           bm_stats* stats) {
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (!eps) return fail(BM_ERR_ARG, "eps is NULL");
+    *eps = 0.0;
+    bm_options opt;
+    bm_options_init(&opt);
+    if (opt_in) opt = *opt_in;
+    bm_status vs = validate_knn(X, n, d, k, opt);
+    if (vs != BM_OK) return vs;
+    return knn_core(X, n, d, k, opt, nullptr, eps, stats);
 }
 
 int64_t bm_set_nerve_bitmap_bytes(int64_t bytes) { return edges_set_bitmap_budget(bytes); }

@@ -84,8 +84,11 @@ bool tile_config_set(int d, const TileConfig* c, std::string* why);   // nullptr
 int tile_shapes(TileConfig* out, int max);  // the compiled (ck, nt, bbuf, astg) shapes, d_pad = 0
 
 // prep.cu
+// row_r2 (optional, query side): per-row squared radius; phi = ||x||^2/2 - row_r2[r]/2
+// (the whole radius on this side; the point side is then prepared with eps2 = 0)
 cudaError_t launch_prep(const float* x, long long rows, int d, double eps2, bool a_side, bool want_tc,
-                        Prepared& out, unsigned* max_norm_bits, int* bad_flag, cudaStream_t s);
+                        Prepared& out, unsigned* max_norm_bits, int* bad_flag, cudaStream_t s,
+                        const double* row_r2 = nullptr);
 cudaError_t launch_delta(DeviceState* st, int path, int d, int d_pad, double eps2, bool same_sets,
                          cudaStream_t s, int scale_exp = 0);
 // fp16 operands of an already prepared set (hi, aug allocated as 2-byte arrays)
@@ -95,6 +98,9 @@ int fp16_scale_exp(double max_norm, double eps);
 // Proven band half-width of a path in its operand units (see bm_prep.cu)
 __host__ __device__ double band_halfwidth(int path, int d, int d_pad, double eps2, double Na, double Nb,
                                           int scale_exp);
+// The same bound for explicit bounds Pa, Pb on |phi| of the two sides (operand units)
+__host__ __device__ double band_halfwidth_core(int path, int d, int d_pad, double Na, double Nb, double Pa,
+                                               double Pb);
 // +delta' into column 6 of a B-side (points) augmentation, after launch_delta
 cudaError_t launch_set_aug_delta(const DeviceState* st, Prepared& p, cudaStream_t s);
 
@@ -115,6 +121,8 @@ struct SweepDesc {
     const float* ivf_phi_perm = nullptr;
     int nprobe = 0;
     int* ivf_probes_out = nullptr;   // optional: where to leave each row's probed cells
+    // per-row squared radius (k-NN sweeps): the band recheck decides D < row_eps2[row]
+    const double* row_eps2 = nullptr;
 };
 cudaError_t launch_sweep_fp32(const SweepDesc& s, cudaStream_t stream);
 
@@ -213,7 +221,8 @@ cudaError_t launch_ivf_scan(const float* A, const float* phiA, const IvfIndex& i
 cudaError_t launch_band_recheck(DeviceState* st, const unsigned long long* band, unsigned long long band_cap,
                                 const float* ax, const float* bx, int d, double eps2, unsigned long long* keys,
                                 unsigned long long* count, unsigned long long cap, const HitSink& book,
-                                bool check_done, int overflow_bit, bool stop_on_overflow, cudaStream_t s);
+                                bool check_done, int overflow_bit, bool stop_on_overflow, cudaStream_t s,
+                                const double* row_eps2 = nullptr);
 
 // dists.cu: dists[e] = float(sqrt(D)) for every CSR entry, D the FP64 squared distance
 // in coordinate order between the row's query (qx + r d, or X + qidx[r] d) and X[ids[e]];
@@ -221,6 +230,18 @@ cudaError_t launch_band_recheck(DeviceState* st, const unsigned long long* band,
 cudaError_t launch_member_dists(const float* qx, const int* qidx, const float* X, int d, const long long* offsets,
                                 long long rows, const int* ids, long long nnz, float* dists,
                                 unsigned long long* max_err_bits, cudaStream_t s);
+
+// knn.cu: k-th nearest-neighbour distances (Sec. 6.1 target occupancy)
+// Pass 1: rho[q] = a squared radius strictly above the k-th smallest FP64 squared
+// distance from X[q] to the sample {X[j * stride] : j < s} (s >= k), itself a bound on
+// the k-th smallest over all points; *rho_max_bits = max rho (double bits); *bad |= 1
+// when a bound is not finite.  Shared memory: 8 k doubles per block (k <= 1024).
+cudaError_t launch_knn_bound(const float* X, long long n, int d, long long stride, long long s, int k, double* rho,
+                             unsigned long long* rho_max_bits, int* bad, cudaStream_t st);
+// Pass 3: D[e] = FP64 squared distance of CSR entry e to its row's point X[row]; kdist[r]
+// = sqrt of the k-th smallest D of row r (*bad |= 2 when a row holds fewer than k).
+cudaError_t launch_knn_select(const float* X, int d, const long long* offsets, long long rows, const int* ids,
+                              long long nnz, double* D, int k, double* kdist, int* bad, cudaStream_t st);
 
 // graph.cu
 cudaError_t launch_csr_from_sorted(const unsigned long long* keys, long long nnz, long long rows,

@@ -28,7 +28,8 @@
 namespace bm {
 
 __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ x, long long rows, int d,
-                                                   double eps2, int a_side, int want_tc,
+                                                   double eps2, const double* __restrict__ row_r2,
+                                                   int a_side, int want_tc,
                                                    float* __restrict__ phi_out,
                                                    __nv_bfloat16* __restrict__ hi,
                                                    __nv_bfloat16* __restrict__ lo,
@@ -56,7 +57,8 @@ __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ x, 
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
         if (__any_sync(kFull, bad) && lane == 0) atomicExch(bad_flag, 1);
-        const double phi = 0.5 * s - 0.25 * eps2;
+        // per-row radius (query side of a k-NN sweep): the whole r^2 on this side
+        const double phi = row_r2 ? 0.5 * s - 0.5 * row_r2[r] : 0.5 * s - 0.25 * eps2;
         if (lane == 0) phi_out[r] = (float)phi;
         if (want_tc && lane < 16) {
             const __nv_bfloat16 p1 = __double2bfloat16(phi);
@@ -151,12 +153,12 @@ int fp16_scale_exp(double max_norm, double eps) {
 }
 
 cudaError_t launch_prep(const float* x, long long rows, int d, double eps2, bool a_side, bool want_tc,
-                        Prepared& out, unsigned* max_norm_bits, int* bad_flag, cudaStream_t s) {
+                        Prepared& out, unsigned* max_norm_bits, int* bad_flag, cudaStream_t s, const double* row_r2) {
     if (rows == 0) return cudaSuccess;
     long long blocks = (rows + 7) / 8;
     if (blocks > 152 * 16) blocks = 152 * 16;
     note_launch();
-    prep_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, rows, d, eps2, a_side ? 1 : 0, want_tc ? 1 : 0,
+    prep_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, rows, d, eps2, row_r2, a_side ? 1 : 0, want_tc ? 1 : 0,
                                                  out.phi, out.hi, out.lo, out.aug, out.d_pad,
                                                  max_norm_bits, bad_flag);
     return cudaGetLastError();
@@ -191,14 +193,10 @@ cudaError_t launch_prep(const float* x, long long rows, int d, double eps2, bool
 // The bound itself, in the units of the operands (scaled by 2^scale_exp on the fp16
 // path); Na, Nb are the unscaled max norms.  Used by the device (delta_kernel) and by
 // the host's choice of path.
-__host__ __device__ double band_halfwidth(int path, int d, int d_pad, double eps2, double Na, double Nb,
-                                          int scale_exp) {
-    const double sc = ldexp(1.0, scale_exp);
-    Na *= sc;
-    Nb *= sc;
-    const double e2 = eps2 * sc * sc;
-    const double Pa = fmax(Na * Na * 0.5 - 0.25 * e2, 0.25 * e2);
-    const double Pb = fmax(Nb * Nb * 0.5 - 0.25 * e2, 0.25 * e2);
+// The bound for given (scaled) max norms Na, Nb and (scaled) bounds Pa, Pb on |phi| of
+// the two sides.
+__host__ __device__ double band_halfwidth_core(int path, int d, int d_pad, double Na, double Nb, double Pa,
+                                               double Pb) {
     const double u23 = 1.0 / 8388608.0, u16 = 1.0 / 65536.0;
     double delta;
     if (path == BM_PATH_FP32) {
@@ -217,6 +215,17 @@ __host__ __device__ double band_halfwidth(int path, int d, int d_pad, double eps
                        u23 * (Pa + Pb));
     }
     return delta + 1e-30;
+}
+
+__host__ __device__ double band_halfwidth(int path, int d, int d_pad, double eps2, double Na, double Nb,
+                                          int scale_exp) {
+    const double sc = ldexp(1.0, scale_exp);
+    Na *= sc;
+    Nb *= sc;
+    const double e2 = eps2 * sc * sc;
+    const double Pa = fmax(Na * Na * 0.5 - 0.25 * e2, 0.25 * e2);
+    const double Pb = fmax(Nb * Nb * 0.5 - 0.25 * e2, 0.25 * e2);
+    return band_halfwidth_core(path, d, d_pad, Na, Nb, Pa, Pb);
 }
 
 __global__ void delta_kernel(DeviceState* st, int path, int d, int d_pad, double eps2, int same_sets,

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(256) band_recheck_kernel(
     const float* __restrict__ ax, const float* __restrict__ bx, int d, double eps2, unsigned long long* keys,
     unsigned long long* count, unsigned long long cap, const int* slot_of, unsigned* conflict, unsigned* row_any,
     int words, int check_done, int overflow_bit, int stop_on_overflow, int vec4, double c_lo, double c_hi,
-    double abs_slack) {
+    double abs_slack, const double* __restrict__ row_eps2) {
     if (check_done && st->done) return;
     const unsigned long long nb_raw = st->band_n;
     const unsigned long long nb = nb_raw < band_cap ? nb_raw : band_cap;
@@ -73,22 +73,23 @@ __global__ void __launch_bounds__(256) band_recheck_kernel(
             const unsigned long long row = key >> 32, col = key & 0xffffffffull;
             const float* a = ax + row * (unsigned long long)d;
             const float* b = bx + col * (unsigned long long)d;
+            const double r2 = row_eps2 ? row_eps2[row] : eps2;
             // filter: decided in FP32 when eps^2 lies outside the interval that must hold
             // the FP64 value; otherwise the FP64 evaluation (the oracle's arithmetic) decides
             const float s32 = sqdist32(a, b, d, vec4);
             bool decided = false;
             if (s32 <= 3.0e38f) {
                 const double D32 = (double)s32;
-                if ((D32 + abs_slack) * c_hi < eps2) {
+                if ((D32 + abs_slack) * c_hi < r2) {
                     hit = true;
                     decided = true;
-                } else if ((D32 - abs_slack) * c_lo >= eps2) {
+                } else if ((D32 - abs_slack) * c_lo >= r2) {
                     decided = true;
                 }
             }
             if (!decided) {
                 const double D = vec4 ? exact_sqdist4(a, b, d) : exact_sqdist(a, b, d);
-                hit = D < eps2;
+                hit = D < r2;
             }
         }
         unsigned long long pos = warp_reserve(count, hit ? 1u : 0u);
@@ -116,7 +117,8 @@ __global__ void __launch_bounds__(256) band_recheck_kernel(
 cudaError_t launch_band_recheck(DeviceState* st, const unsigned long long* band, unsigned long long band_cap,
                                 const float* ax, const float* bx, int d, double eps2, unsigned long long* keys,
                                 unsigned long long* count, unsigned long long cap, const HitSink& book,
-                                bool check_done, int overflow_bit, bool stop_on_overflow, cudaStream_t s) {
+                                bool check_done, int overflow_bit, bool stop_on_overflow, cudaStream_t s,
+                                const double* row_eps2) {
     const int vec4 = (d % 4 == 0) && ((uintptr_t)ax % 16 == 0) && ((uintptr_t)bx % 16 == 0);
     // D64 (FP64, the oracle's arithmetic) lies in [(D32 - abs) c_lo, (D32 + abs) c_hi]:
     // D in [(D32 - abs)/(1 + g32), (D32 + abs)/(1 - g32)] and |D64 - D| <= g64 D, with
@@ -131,7 +133,8 @@ cudaError_t launch_band_recheck(DeviceState* st, const unsigned long long* band,
     band_recheck_kernel<<<device_sm_count() * 4, 256, 0, s>>>(st, band, band_cap, ax, bx, d, eps2, keys, count, cap,
                                                              book.slot_of, book.conflict, book.row_any,
                                                              book.conflict_words, check_done ? 1 : 0, overflow_bit,
-                                                             stop_on_overflow ? 1 : 0, vec4, c_lo, c_hi, abs_slack);
+                                                             stop_on_overflow ? 1 : 0, vec4, c_lo, c_hi, abs_slack,
+                                                             row_eps2);
     return cudaGetLastError();
 }
 

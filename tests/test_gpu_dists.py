@@ -96,7 +96,8 @@ def test_dists_extreme_magnitudes(bm, scale, offset):
 
 def test_dists_host_io_and_queries_off_the_points(bm):
     X = W.mixture(9000, 40, 8, clusters=9, seed=44)
-    Q = (W.isotropic(333, 40, 8, seed=45) * np.float32(3.0)).astype(np.float32)
+    # queries near the points but not on them
+    Q = (X[::27][:333] + W.isotropic(333, 40, 8, seed=45) * np.float32(0.5)).astype(np.float32)
     off, ids, st, dists = bm.bm_range_query(X, Q, 9.0, want_dists=True)
     assert isinstance(dists, np.ndarray)
     ro, ri = oracle.range_query(X, Q, 9.0)
