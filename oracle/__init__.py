@@ -17,6 +17,9 @@ Functions and the passages they follow:
   kth_nn_dist        Sec. 6.1 target-occupancy rule (self counted first)
   masked_range_query Sec. 5.3 verified range set over a candidate set (points of probed cells)
   BallTree           Sec. 3.1 ball tree construction and pruned range query
+  fps                Sec. 2.2 farthest point sampling epsilon-net
+  fps_build          the Ball Mapper on the farthest-point landmarks (memberships, edges)
+  color              Sec. 2.3 coloring: mean / median / min / max of f over each ball
 """
 from __future__ import annotations
 
@@ -87,6 +90,10 @@ def load_library(path: str):
     lib.bmo_masked_range_fill.restype = ctypes.c_int
     lib.bmo_masked_range_fill.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int, _f64p, ctypes.c_int64,
                                           ctypes.c_double, _i32p, ctypes.c_int, _i32p, ctypes.c_int, _i64p, _i32p]
+    lib.bmo_fps.restype = ctypes.c_int64
+    lib.bmo_fps.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int64, _i32p]
+    lib.bmo_color.restype = ctypes.c_int
+    lib.bmo_color.argtypes = [_i64p, _i32p, ctypes.c_int64, _f64p, ctypes.c_int, _f64p]
     lib.bmo_num_threads.restype = ctypes.c_int
     lib.bmo_num_threads.argtypes = []
     lib.bmo_set_num_threads.restype = None
@@ -240,6 +247,46 @@ def build(X, eps, prune: bool = True) -> dict:
     offsets, ids = memberships(X, lm, eps)
     e = edges(X, lm, offsets, ids, eps, prune=prune)
     return {"landmarks": lm, "offsets": offsets, "ids": ids, "edges": e}
+
+
+def fps(X, eps, first: int = 0) -> np.ndarray:
+    """Farthest-point landmarks in selection order (Sec. 2.2), starting at `first`."""
+    X = _f64(X)
+    n, d = X.shape
+    out = np.empty(max(n, 1), dtype=np.int32)
+    if not 0 <= first < max(n, 1):
+        raise ValueError("first out of range")
+    L = _load().bmo_fps(_ptr(X, _f64p), n, d, eps_squared(eps), int(first), _ptr(out, _i32p))
+    if L < 0:
+        raise MemoryError("oracle fps: allocation failed")
+    return out[:L].copy()
+
+
+def fps_build(X, eps, first: int = 0, prune: bool = True) -> dict:
+    """Ball Mapper on the farthest-point landmarks: full-ball memberships and nerve edges
+    in landmark selection order."""
+    lm = fps(X, eps, first)
+    offsets, ids = memberships(X, lm, eps)
+    e = edges(X, lm, offsets, ids, eps, prune=prune)
+    return {"landmarks": lm, "offsets": offsets, "ids": ids, "edges": e}
+
+
+COLOR_STATS = {"mean": 0, "median": 1, "min": 2, "max": 3}
+
+
+def color(offsets, ids, f, stat: str = "mean") -> np.ndarray:
+    """c(l_i) = stat of f over CSR row i (Sec. 2.3); NaN for an empty row."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    ids = np.ascontiguousarray(ids, dtype=np.int32)
+    if ids.size == 0:
+        ids = np.zeros(1, dtype=np.int32)
+    f = np.ascontiguousarray(np.asarray(f, dtype=np.float64).ravel())
+    rows = offsets.size - 1
+    out = np.empty(max(rows, 1), dtype=np.float64)
+    if rows and _load().bmo_color(_ptr(offsets, _i64p), _ptr(ids, _i32p), rows, _ptr(f, _f64p),
+                                  COLOR_STATS[stat], _ptr(out, _f64p)):
+        raise MemoryError("oracle color: allocation failed")
+    return out[:rows].copy()
 
 
 def kth_nn_dist(X, k: int) -> np.ndarray:

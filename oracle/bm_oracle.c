@@ -21,7 +21,12 @@
  *   - target-occupancy scale (Sec. 6.1): distance of each point to its k-th
  *     nearest neighbour, the point itself counted first;
  *   - ball tree construction and range query (Sec. 3.1), an independent
- *     exact range oracle used to cross-check the brute force one.
+ *     exact range oracle used to cross-check the brute force one;
+ *   - farthest point sampling (Sec. 2.2, the deterministic alternative to the
+ *     greedy): start from a given landmark, repeatedly take the point farthest
+ *     from the landmark set while that distance is at least eps;
+ *   - coloring (Sec. 2.3): a statistic of a per-point function f over every
+ *     ball X_i (mean, median, minimum, maximum).
  *
  * Parallelism: outer loops whose iterations are independent (one query row,
  * one landmark pair row, one k-NN row) run under OpenMP.  This does not
@@ -470,6 +475,92 @@ int bmo_masked_range_fill(const double* X, int64_t n, int d, const double* Q, in
                 if (flag[cell_of[i]] && sqdist(q, X + (size_t)i * d, d) < eps2) ids[o++] = (int32_t)i;
         }
         free(flag);
+    }
+    return bad ? -1 : 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Farthest point sampling, Sec. 2.2.  L = {first}; repeat: for every point x
+ * the distance to the set, m(x) = min_{l in L} D(x,l) (kept up to date with
+ * each new landmark); x* = argmax_x m(x), the smallest index among equal
+ * maxima; x* joins L when m(x*) >= eps^2, otherwise the procedure stops.
+ * Reading: the paper writes "> eps"; with open balls (a point at distance
+ * exactly eps is not covered) ">=" is the rule under which every point ends
+ * inside an open ball, the same cover condition as the greedy.
+ * Returns the number of landmarks (written in selection order), -1 on an
+ * allocation failure.
+ * ------------------------------------------------------------------------- */
+int64_t bmo_fps(const double* X, int64_t n, int d, double eps2, int64_t first, int32_t* landmarks) {
+    if (n <= 0) return 0;
+    double* m = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!m) return -1;
+    for (int64_t x = 0; x < n; ++x) m[x] = INFINITY;
+    int64_t L = 0;
+    int64_t cur = first;
+    landmarks[L++] = (int32_t)cur;
+    while (1) {
+        const double* c = X + (size_t)cur * d;
+        for (int64_t x = 0; x < n; ++x) {
+            const double D = sqdist(X + (size_t)x * d, c, d);
+            if (D < m[x]) m[x] = D;
+        }
+        int64_t best = 0;
+        for (int64_t x = 1; x < n; ++x)
+            if (m[x] > m[best]) best = x;
+        if (!(m[best] >= eps2)) break;
+        if (L >= n) break;   /* never reached for eps > 0: a landmark is at distance 0 */
+        cur = best;
+        landmarks[L++] = (int32_t)cur;
+    }
+    free(m);
+    return L;
+}
+
+/* ---------------------------------------------------------------------------
+ * Coloring, Sec. 2.3: c(l_i) = statistic of f over X_i, the ids of CSR row i.
+ *   stat 0: mean, (sum of f over the row, in row order, FP64) / |X_i|
+ *   stat 1: median (numpy's rule: the middle value, or for an even count the
+ *           mean of the two middle values computed as (a + b) / 2)
+ *   stat 2: minimum, stat 3: maximum
+ * An empty row gets NaN.  Returns -1 on an allocation failure.
+ * ------------------------------------------------------------------------- */
+static int cmp_f64(const void* a, const void* b) {
+    const double x = *(const double*)a, y = *(const double*)b;
+    return (x > y) - (x < y);
+}
+
+int bmo_color(const int64_t* offsets, const int32_t* ids, int64_t rows, const double* f, int stat, double* out) {
+    int bad = 0;
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t r = 0; r < rows; ++r) {
+        const int64_t b = offsets[r], e = offsets[r + 1], cnt = e - b;
+        if (cnt == 0) {
+            out[r] = NAN;
+            continue;
+        }
+        if (stat == 0) {
+            double sum = 0.0;
+            for (int64_t j = b; j < e; ++j) sum += f[ids[j]];
+            out[r] = sum / (double)cnt;
+        } else if (stat == 1) {
+            double* v = (double*)malloc(sizeof(double) * (size_t)cnt);
+            if (!v) {
+                #pragma omp atomic write
+                bad = 1;
+                continue;
+            }
+            for (int64_t j = b; j < e; ++j) v[j - b] = f[ids[j]];
+            qsort(v, (size_t)cnt, sizeof(double), cmp_f64);
+            out[r] = (cnt % 2) ? v[cnt / 2] : (v[cnt / 2 - 1] + v[cnt / 2]) / 2.0;
+            free(v);
+        } else {
+            double best = f[ids[b]];
+            for (int64_t j = b + 1; j < e; ++j) {
+                const double x = f[ids[j]];
+                if (stat == 2 ? x < best : x > best) best = x;
+            }
+            out[r] = best;
+        }
     }
     return bad ? -1 : 0;
 }

@@ -57,3 +57,25 @@ def build(X, eps, k: int) -> dict:
         if any(inside(landmarks[i], x) and inside(landmarks[j], x) for x in range(n)):
             edge_list.append((i, j))
     return {"landmarks": landmarks, "members": members, "edges": edge_list}
+
+
+def fps(X, eps, k: int, first: int = 0) -> list:
+    """Farthest point sampling (Sec. 2.2) in exact integer arithmetic: distances to the
+    landmark set as exact squared integers, the farthest point (smallest index among
+    equal maxima) joins while its squared distance is at least eps^2 * 4^k."""
+    pts = _ints(X, k)
+    n = len(pts)
+    if n == 0:
+        return []
+    lim = Fraction(float(eps)) ** 2 * (4 ** k)
+
+    def sq(a, b):
+        return sum((p - q) ** 2 for p, q in zip(pts[a], pts[b]))
+
+    chosen = [first]
+    while True:
+        far = {x: min(sq(x, l) for l in chosen) for x in range(n)}
+        top = max(far.values())
+        if top < lim:
+            return chosen
+        chosen.append(min(x for x in range(n) if far[x] == top))

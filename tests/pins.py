@@ -235,3 +235,104 @@ def pin_masked():
         full = i2[o2[j]:o2[j + 1]]
         keep = full[np.isin(cell[full], probes[j])]
         assert i3[o3[j]:o3[j + 1]].tolist() == keep.tolist()
+
+
+# ---------------------------------------------------------------- farthest point sampling
+def _fps_points(name):
+    return W.line_points(10) if name == "line" else W.grid_points(3)
+
+
+def pin_fps_golden():
+    g = golden("fps_line.json")
+    for case in g["cases"]:
+        X = _fps_points(case["points"])
+        out = oracle.fps_build(X, case["eps"], case["first"])
+        _check_case(out, case)
+
+
+def pin_fps_invariants(X, eps, first=0):
+    """Sec. 2.2 / Def. 2.1 with open balls: the landmarks start at `first`, are pairwise at
+    squared distance >= eps^2, every point lies in some open ball, and the selection
+    distances (to the landmarks before) never increase."""
+    lm = oracle.fps(X, eps, first)
+    e2 = oracle.eps_squared(eps)
+    assert lm[0] == first and np.unique(lm).size == lm.size
+    D = sqd(X[lm], X)
+    assert np.all(D.min(axis=0) < e2)                                 # cover
+    DL = sqd(X[lm], X[lm])
+    np.fill_diagonal(DL, np.inf)
+    assert np.all(DL >= e2)                                            # separation
+    sel = [DL[i, :i].min() for i in range(1, lm.size)]
+    assert all(a >= b for a, b in zip(sel, sel[1:]))                   # non-increasing
+    # the point after the last landmark would be closer than eps
+    assert D.min(axis=0).max() < e2
+
+
+def pin_fps_brute(seeds=range(12)):
+    for seed in seeds:
+        rng = np.random.default_rng(seed)
+        n = int(rng.integers(1, 12))
+        d = int(rng.integers(1, 4))
+        X = W.tiny_grid_cloud(n, d, 1, span=4, seed=seed)
+        eps = float(rng.choice([0.5, 1.0, 1.5, 2.0]))
+        first = int(rng.integers(0, n))
+        assert oracle.fps(X, eps, first).tolist() == brute.fps(X, eps, 1, first), (seed, n, d, eps)
+
+
+# ---------------------------------------------------------------- coloring
+def pin_color_golden():
+    g = golden("color_line.json")
+    X = W.line_points(10)
+    out = oracle.build(X, g["eps"])
+    f = X[:, 0].astype(np.float64) ** 2
+    for stat in ("mean", "median", "min", "max"):
+        got = oracle.color(out["offsets"], out["ids"], f, stat)
+        assert got.tolist() == g[stat], (stat, got)
+
+
+def pin_color_lipschitz(X, eps, k=2.5, seed=0):
+    """Sec. 2.3 with f = k <w, x>, |w| = 1 (k-Lipschitz) and a coloring between the
+    ball's minimum and maximum of f (mean, median, min, max):
+      |c(l_i) - f(l_i)| < k eps                 (every member is within eps of l_i)
+      max_{x in X_i} |f(x) - c(l_i)| < 2 k eps  (the ball's diameter is below 2 eps)
+      |c(l_i) - c(l_j)| < 4 k eps on every edge (a shared point links the two)
+    The paper states the second bound as k eps and the third as 2 k eps; those do not
+    follow (a lopsided ball breaks them for the mean), these do."""
+    rng = np.random.default_rng(seed)
+    w = rng.standard_normal(X.shape[1])
+    w /= np.linalg.norm(w)
+    f = k * (np.asarray(X, dtype=np.float64) @ w)
+    out = oracle.build(X, eps)
+    lm, off, ids, E = out["landmarks"], out["offsets"], out["ids"], out["edges"]
+    slack = 1e-9 * k * eps
+    for stat in ("mean", "median", "min", "max"):
+        c = oracle.color(off, ids, f, stat)
+        for i in range(lm.size):
+            row = f[ids[off[i]:off[i + 1]]]
+            assert row.min() <= c[i] <= row.max(), (stat, i)
+            assert abs(c[i] - f[lm[i]]) < k * eps + slack
+            assert np.abs(row - c[i]).max() < 2 * k * eps + slack
+        if E.size:
+            assert np.abs(c[E[:, 0]] - c[E[:, 1]]).max() < 4 * k * eps + slack
+
+
+def pin_color_values(X, eps, seed=1):
+    """Each statistic against its definition on every row: the median is a middle value of
+    the sorted row (or the mean of the two), min and max are attained, and a constant f
+    colors every ball with that constant."""
+    rng = np.random.default_rng(seed)
+    out = oracle.build(X, eps)
+    off, ids = out["offsets"], out["ids"]
+    f = rng.standard_normal(X.shape[0])
+    med = oracle.color(off, ids, f, "median")
+    mn = oracle.color(off, ids, f, "min")
+    mx = oracle.color(off, ids, f, "max")
+    mean = oracle.color(off, ids, f, "mean")
+    for i in range(off.size - 1):
+        row = np.sort(f[ids[off[i]:off[i + 1]]])
+        m = row.size
+        assert med[i] == (row[m // 2] if m % 2 else (row[m // 2 - 1] + row[m // 2]) / 2.0)
+        assert mn[i] == row[0] and mx[i] == row[-1]
+        assert abs(mean[i] - row.sum() / m) <= 1e-12 * max(1.0, np.abs(row).sum())
+    const = oracle.color(off, ids, np.full(X.shape[0], 3.25), "mean")
+    assert np.all(const == 3.25)

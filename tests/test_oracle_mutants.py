@@ -31,6 +31,12 @@ MUTANTS = [
     ("balltree-leaf-closed", "t->d) < r2) {", "t->d) <= r2) {", 1),
     ("pair-roles-swapped", "sqdist(Q + (size_t)qrow[k] * d, X + (size_t)xcol[k] * d, d)",
      "sqdist(X + (size_t)qrow[k] * d, Q + (size_t)xcol[k] * d, d)", 1),
+    ("fps-ties-to-largest", "if (m[x] > m[best]) best = x;", "if (m[x] >= m[best]) best = x;", 1),
+    ("fps-strict-eps", "if (!(m[best] >= eps2)) break;", "if (!(m[best] > eps2)) break;", 1),
+    ("fps-no-update", "if (D < m[x]) m[x] = D;", "if (D < m[x] && cur == first) m[x] = D;", 1),
+    ("color-mean-divisor", "out[r] = sum / (double)cnt;", "out[r] = sum / (double)(cnt + 1);", 1),
+    ("color-median-index", "(v[cnt / 2 - 1] + v[cnt / 2]) / 2.0", "(v[cnt / 2] + v[cnt / 2]) / 2.0", 1),
+    ("color-min-max-swapped", "if (stat == 2 ? x < best : x > best)", "if (stat == 2 ? x > best : x < best)", 1),
     ("masked-ignores-cells", "if (flag[cell_of[i]] && sqdist", "if ((flag[cell_of[i]] || 1) && sqdist", 2),
 ]
 # A wrong node centre is not listed: any centre paired with the radius measured
@@ -54,6 +60,12 @@ def _all_pins():
     pins.pin_range_scipy(W.paper_gaussian_fp64(800, 5, seed=8), W.paper_gaussian_fp64(800, 5, seed=8)[:50], 1.3)
     pins.pin_pair_sqdist(W.isotropic(300, 16, 10, seed=9), W.isotropic(77, 16, 10, seed=10) * 3, 10)
     pins.pin_masked()
+    pins.pin_fps_golden()
+    pins.pin_fps_invariants(W.isotropic(600, 5, 10, seed=61), 1.7)
+    pins.pin_fps_brute(seeds=range(6))
+    pins.pin_color_golden()
+    pins.pin_color_lipschitz(W.isotropic(800, 5, 10, seed=63), 1.2)
+    pins.pin_color_values(W.isotropic(600, 4, 10, seed=64), 0.9)
 
 
 def test_unmutated_oracle_passes_all_pins():

@@ -92,3 +92,33 @@ def test_iso_n10k_d16_counts():
 def test_paper_worked_example():
     """Sec. 6.3: Gaussian n=20000, d=50, k=50 -> eps ~ 7.5536, 6361 landmarks, 936690 edges."""
     pins.pin_paper()
+
+
+def test_fps_golden_line_and_grid():
+    pins.pin_fps_golden()
+
+
+def test_fps_invariants_and_brute_force():
+    pins.pin_fps_invariants(W.isotropic(1500, 6, 10, seed=61), 1.7)
+    pins.pin_fps_invariants(W.tiny_grid_cloud(800, 2, 1, span=6, seed=62), 1.0, first=17)
+    pins.pin_fps_brute()
+
+
+def test_color_golden_line():
+    pins.pin_color_golden()
+
+
+def test_color_lipschitz_bounds_and_values():
+    pins.pin_color_lipschitz(W.isotropic(2000, 5, 10, seed=63), 1.2)
+    pins.pin_color_values(W.isotropic(1500, 4, 10, seed=64), 0.9)
+
+
+def test_paper_coloring_bound_needs_the_diameter():
+    """Sec. 2.3, Prop. 2.4 as printed (max |f(x) - c(l_i)| <= k eps) fails for the mean on a
+    lopsided ball: f(x) = x (k = 1), landmark 0, eps = 1, members {-0.9, 0, 0.9, 0.9, 0.9}
+    give c = 0.36 and |f(-0.9) - c| = 1.26 > 1.  The bound that holds is 2 k eps."""
+    X = np.array([[0.0], [-0.875], [0.875], [0.875], [0.875]], dtype=np.float32)
+    out = oracle.build(X, 1.0)
+    assert out["landmarks"].tolist() == [0]
+    c = oracle.color(out["offsets"], out["ids"], X[:, 0], "mean")[0]
+    assert abs(-0.875 - c) > 1.0 and abs(-0.875 - c) < 2.0
