@@ -174,6 +174,30 @@ BM_API bm_status bm_knn_dist(const float* X, int64_t n, int32_t d, int32_t k, co
 BM_API bm_status bm_occupancy_eps(const float* X, int64_t n, int32_t d, int32_t k, const bm_options* opt,
                                   double* eps, bm_stats* stats);
 
+/* Ball Mapper on farthest-point landmarks (Sec. 2.2, the deterministic alternative to
+ * the greedy): L = {first}; repeatedly the point farthest from L (the smallest index
+ * among equal distances) joins L while its distance to L is at least eps (open balls:
+ * a point at exactly eps is not covered, so the paper's "> eps" is taken as ">=" here,
+ * the rule under which every point ends inside an open ball).  Landmarks are returned
+ * in selection order (out->landmarks[0] == first); memberships are the full open balls
+ * in that order and edges use those ordinals (i < j, lexicographic), as in bm_build.
+ * Distances are decided exactly (FP64 in coordinate order).  0 <= first < n (n = 0
+ * gives an empty graph).  stats.greedy_steps = selection passes, ms_greedy includes them. */
+BM_API bm_status bm_build_fps(const float* X, int64_t n, int32_t d, float eps, int64_t first, const bm_options* opt,
+                              bm_graph* out);
+
+/* Coloring (Sec. 2.3): out[i] = statistic of f over CSR row i (the ball X_i):
+ *   BM_COLOR_MEAN (FP64 sum / |X_i|; the summation order is unspecified, so the value
+ *   may differ from a sequential sum by (|X_i| - 1) 2^-53 sum |f|), BM_COLOR_MEDIAN (the
+ *   middle value, or for an even count the mean of the two middle values), BM_COLOR_MIN,
+ *   BM_COLOR_MAX.  An empty row gets NaN.
+ *   offsets (rows + 1, int64), ids (int32, in [0, n)), f (n float32, finite), out (rows
+ *   doubles): device memory, or host memory with opt->host_io.  BM_ERR_ARG for an id out
+ *   of range or a non-finite f. */
+typedef enum { BM_COLOR_MEAN = 0, BM_COLOR_MEDIAN = 1, BM_COLOR_MIN = 2, BM_COLOR_MAX = 3 } bm_color_stat;
+BM_API bm_status bm_color(const int64_t* offsets, const int32_t* ids, int64_t rows, const float* f, int64_t n,
+                          int32_t stat, const bm_options* opt, double* out);
+
 /* One problem of a batched build: n x d float32 points (device memory; host
  * memory with host_io) and its own eps. */
 typedef struct {

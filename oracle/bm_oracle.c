@@ -500,6 +500,7 @@ int64_t bmo_fps(const double* X, int64_t n, int d, double eps2, int64_t first, i
     landmarks[L++] = (int32_t)cur;
     while (1) {
         const double* c = X + (size_t)cur * d;
+        #pragma omp parallel for schedule(static)
         for (int64_t x = 0; x < n; ++x) {
             const double D = sqdist(X + (size_t)x * d, c, d);
             if (D < m[x]) m[x] = D;

@@ -144,6 +144,12 @@ def load(path: str = LIB_PATH):
         lib.bm_get_tile_config.restype = ctypes.c_int
         lib.bm_set_tile_config.argtypes = [ctypes.c_int32, ctypes.POINTER(bm_tile_config)]
         lib.bm_set_tile_config.restype = ctypes.c_int
+        lib.bm_build_fps.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_int64,
+                                     ctypes.POINTER(bm_options), ctypes.POINTER(bm_graph)]
+        lib.bm_build_fps.restype = ctypes.c_int
+        lib.bm_color.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                 ctypes.c_int32, ctypes.POINTER(bm_options), ctypes.c_void_p]
+        lib.bm_color.restype = ctypes.c_int
         lib.bm_knn_dist.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                     ctypes.POINTER(bm_options), ctypes.c_void_p, ctypes.POINTER(bm_stats)]
         lib.bm_knn_dist.restype = ctypes.c_int
@@ -341,6 +347,73 @@ def _graph_dict(alloc, g, want_dists=False):
     if want_dists:
         res["dists"] = alloc.tensor(g.members.dists, nnz, torch.float32)
     return res
+
+
+def _host_graph(lib, g, opt, want_dists):
+    """A host bm_graph copied into numpy arrays, then released."""
+    try:
+        L, nnz, E = g.n_landmarks, g.members.nnz, g.n_edges
+
+        def arr(ptr, ctype, count):
+            return np.ctypeslib.as_array((ctype * max(count, 1)).from_address(ptr))[:count].copy()
+
+        res = {"landmarks": arr(g.landmarks, ctypes.c_int32, L),
+               "offsets": arr(g.members.offsets, ctypes.c_int64, L + 1),
+               "ids": arr(g.members.ids, ctypes.c_int32, nnz),
+               "edges": arr(g.edges, ctypes.c_int32, 2 * E).reshape(E, 2),
+               "stats": g.stats.as_dict()}
+        if want_dists:
+            res["dists"] = arr(g.members.dists, ctypes.c_float, nnz)
+    finally:
+        lib.bm_graph_free(ctypes.byref(g), ctypes.byref(opt))
+    return res
+
+
+def bm_build_fps(X, eps: float, first: int = 0, path: str = "auto", stream=None, want_dists: bool = False):
+    """Ball Mapper on farthest-point landmarks (Sec. 2.2) starting at point `first`;
+    landmarks in selection order.  Same result layout as bm_build."""
+    lib = load()
+    px, n, d, kx, host = _as_input(X)
+    g = bm_graph()
+    if host:
+        opt = _options(lib, path, 0, stream, True, None, want_dists=want_dists)
+        _check(lib, lib.bm_build_fps(px, n, d, ctypes.c_float(eps), int(first), ctypes.byref(opt), ctypes.byref(g)))
+        return _host_graph(lib, g, opt, want_dists)
+    alloc = _TorchAllocator(kx.device)
+    opt = _options(lib, path, 0, stream or _current_stream(kx.device), False, alloc, want_dists=want_dists)
+    _check(lib, lib.bm_build_fps(px, n, d, ctypes.c_float(eps), int(first), ctypes.byref(opt), ctypes.byref(g)))
+    return _graph_dict(alloc, g, want_dists)
+
+
+COLOR_STATS = {"mean": 0, "median": 1, "min": 2, "max": 3}
+
+
+def bm_color(offsets, ids, f, stat: str = "mean", stream=None):
+    """Coloring (Sec. 2.3): stat of f over every CSR row.  All CUDA tensors (int64 offsets,
+    int32 ids, float32 f) -> float64 CUDA tensor; all numpy arrays -> numpy array."""
+    lib = load()
+    rows = int(offsets.shape[0]) - 1
+    n = int(f.shape[0])
+    if _is_torch_cuda(offsets):
+        import torch
+        offsets = offsets.to(torch.int64).contiguous()
+        ids = ids.to(torch.int32).contiguous()
+        f = f.to(torch.float32).contiguous()
+        out = torch.empty(max(rows, 1), dtype=torch.float64, device=offsets.device)
+        alloc = _TorchAllocator(offsets.device)
+        opt = _options(lib, "auto", 0, stream or _current_stream(offsets.device), False, alloc)
+        _check(lib, lib.bm_color(offsets.data_ptr(), ids.data_ptr() if ids.numel() else None, rows,
+                                 f.data_ptr() if n else None, n, COLOR_STATS[stat], ctypes.byref(opt),
+                                 out.data_ptr()))
+        return out[:rows]
+    o = np.ascontiguousarray(offsets, dtype=np.int64)
+    i = np.ascontiguousarray(ids, dtype=np.int32)
+    fv = np.ascontiguousarray(f, dtype=np.float32)
+    out = np.empty(max(rows, 1), dtype=np.float64)
+    opt = _options(lib, "auto", 0, stream, True, None)
+    _check(lib, lib.bm_color(o.ctypes.data, i.ctypes.data if i.size else None, rows, fv.ctypes.data if n else None,
+                             n, COLOR_STATS[stat], ctypes.byref(opt), out.ctypes.data))
+    return out[:rows]
 
 
 def bm_knn_dist(X, k: int, path: str = "auto", stream=None):

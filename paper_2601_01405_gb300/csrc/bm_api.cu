@@ -1182,7 +1182,9 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
     // automatic path: the greedy starts on the split and picks its path after the
     // first step (greedy_drive)
     const bool auto_switch = opt.path == BM_PATH_TC_AUTO && ivf == nullptr && fixed_lm == nullptr;
-    const int req = opt.path == BM_PATH_TC_AUTO ? (int)BM_PATH_TC_SPLIT3 : opt.path;
+    // fixed landmarks sweep once: the automatic path and fp16 take the bf16 split
+    const int req = (opt.path == BM_PATH_TC_AUTO || (fixed_lm && opt.path == BM_PATH_TC_FP16))
+                        ? (int)BM_PATH_TC_SPLIT3 : opt.path;
     const bool tc = is_tc_path(req) && ivf == nullptr;
     int path = ivf ? (int)BM_PATH_FP32 : req;
     Timer tm(s);
@@ -1256,13 +1258,15 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
                 ALLOC(qx, float, std::max<long long>(nL, 1) * d);
                 TRY_CUDA(launch_gather_rows(dX, landmarks, nL, d, qx, s));
                 Prepared pq;
-                rs = prepare(qx, nL, d, eps2, true, kPrecNone, ar, &st->max_norm_q_bits, bad, s, pq);
+                rs = prepare(qx, nL, d, eps2, true, tc ? prec_for(path) : kPrecNone, ar, &st->max_norm_q_bits, bad, s,
+                             pq);
                 if (rs != BM_OK) return rs;
                 const int sms = device_sm_count();
                 unsigned long long cap = (unsigned long long)std::max<long long>(4 * n, 1LL << 20);
+                if (tc) cap = std::max<unsigned long long>(cap, (unsigned long long)sms * 4096);
                 for (int attempt = 0; attempt < 3; ++attempt) {
                     SweepOut so;
-                    rs = alloc_sweep_out(ar, false, cap, sms, so);
+                    rs = alloc_sweep_out(ar, tc, cap, sms, so);
                     if (rs != BM_OK) return rs;
                     SweepDesc sd;
                     sd.a = &pq;
@@ -1288,8 +1292,11 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
                     release_sweep_out(ar, so, !overflow);
                     if (!overflow) break;
                     if (attempt == 2) return fail(BM_ERR_CAPACITY, "membership buffer kept overflowing");
-                    cap = std::max<unsigned long long>(2 * cap, std::max(fin.mem_count, fin.band_n) * 5 / 4 + 1024);
+                    cap = std::max<unsigned long long>(
+                        2 * cap, std::max(fin.max_seg * (unsigned long long)sms, std::max(fin.mem_count, fin.band_n)) *
+                                     5 / 4 + 1024);
                     TRY_CUDA(cudaMemsetAsync(&st->error, 0, sizeof(int), s));
+                    TRY_CUDA(cudaMemsetAsync(&st->max_seg, 0, sizeof(unsigned long long), s));
                     TRY_CUDA(cudaMemsetAsync(&st->band_n, 0, sizeof(unsigned long long), s));
                     TRY_CUDA(cudaMemsetAsync(&st->mem_count, 0, sizeof(unsigned long long), s));
                 }
@@ -1676,6 +1683,97 @@ bm_status build_batched(const bm_instance* inst, int count, const bm_options& op
     return BM_OK;
 }
 
+// Ball Mapper on farthest-point landmarks (Sec. 2.2): the selection loop as one graph
+// launch (a WHILE node repeating the pass kernel), then memberships and edges of those
+// landmarks through the fixed-landmark build.  Arguments validated, n >= 1.
+bm_status fps_build(const float* X, long long n, int d, float eps, long long first, const bm_options& opt,
+                    bm_graph* out) {
+    cudaStream_t s = (cudaStream_t)opt.stream;
+    const bool host_io = opt.host_io != 0;
+    const double eps2 = (double)eps * (double)eps;
+    Timer tm(s);
+    tm.mark();
+    const long long launches0 = g_kernel_launches;
+    Arena ar(&opt, s);
+    bm_status rs = BM_OK;
+    const float* dX = stage_input(X, n, d, host_io, ar, s, &rs);
+    if (rs != BM_OK) return rs;
+    int* bad;
+    ALLOC(bad, int, 1);
+    TRY_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    TRY_CUDA(launch_finite_check(dX, n * d, bad, s));
+    int hbad = 0;
+    TRY_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TRY_CUDA(cudaStreamSynchronize(s));
+    if (hbad) return fail(BM_ERR_ARG, "input holds NaN or Inf");
+    double* mind;
+    int* lm;
+    FpsState* st;
+    double* part_v;
+    int* part_i;
+    unsigned* ticket;
+    const int G = fps_grid(n);
+    ALLOC(mind, double, n);
+    ALLOC(lm, int, n);
+    ALLOC(st, FpsState, 1);
+    ALLOC(part_v, double, G);
+    ALLOC(part_i, int, G);
+    ALLOC(ticket, unsigned, 1);
+    TRY_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned), s));
+    TRY_CUDA(launch_fps_init(mind, n, lm, st, first, s));
+    tm.mark();  // 1: set-up done
+    {
+        GraphGuard gg;
+        TRY_CUDA(cudaStreamCreateWithFlags(&gg.cs, cudaStreamNonBlocking));
+        TRY_CUDA(cudaGraphCreate(&gg.graph, 0));
+        cudaGraphConditionalHandle h;
+        TRY_CUDA(cudaGraphConditionalHandleCreate(&h, gg.graph, 1u, cudaGraphCondAssignDefault));
+        alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+        std::memset(cp_raw, 0, sizeof(cp_raw));
+        cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        TRY_CUDA(cudaGraphAddNode(&node, gg.graph, nullptr, nullptr, 0, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        TRY_CUDA(cudaStreamBeginCaptureToGraph(gg.cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        const cudaError_t le = launch_fps_step(dX, n, d, eps2, mind, lm, st, part_v, part_i, ticket, h, true, gg.cs);
+        cudaGraph_t captured = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(gg.cs, &captured);
+        TRY_CUDA(le);
+        TRY_CUDA(ee);
+        TRY_CUDA(cudaGraphInstantiate(&gg.exec, gg.graph, 0));
+        TRY_CUDA(cudaGraphLaunch(gg.exec, s));
+        TRY_SYNC(s, "the farthest-point selection loop");
+    }
+    tm.mark();  // 2: selection done
+    FpsState hst;
+    TRY_CUDA(cudaMemcpyAsync(&hst, st, sizeof(FpsState), cudaMemcpyDeviceToHost, s));
+    TRY_CUDA(cudaStreamSynchronize(s));
+    if (hst.error) return fail(BM_ERR_CUDA, "farthest-point loop passed its iteration bound");
+    const long long L = hst.count;
+    std::vector<int> hl;
+    const int32_t* fixed = lm;
+    if (host_io) {   // the fixed-landmark build reads host landmarks in host I/O mode
+        hl.resize((size_t)std::max<long long>(L, 1));
+        TRY_CUDA(cudaMemcpyAsync(hl.data(), lm, sizeof(int) * L, cudaMemcpyDeviceToHost, s));
+        TRY_CUDA(cudaStreamSynchronize(s));
+        fixed = hl.data();
+    }
+    rs = build_graph(X, n, d, eps, opt, nullptr, 0, fixed, L, out);
+    if (rs != BM_OK) return rs;
+    const double ms_sel = tm.ms(1, 2), ms_setup = tm.ms(0, 1);
+    out->stats.greedy_steps = (int64_t)hst.iterations;
+    out->stats.candidates = (int64_t)hst.iterations * n;   // points examined by the passes
+    out->stats.ms_greedy += ms_sel;
+    out->stats.ms_prep += ms_setup;
+    out->stats.ms_total += ms_sel + ms_setup;
+    out->stats.kernel_launches = g_kernel_launches - launches0 + (int64_t)hst.iterations - 1;
+    return BM_OK;
+}
+
 }  // namespace
 }  // namespace bm
 
@@ -1767,6 +1865,80 @@ bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_opt
     vs = check_device(opt.path);
     if (vs != BM_OK) return vs;
     return build_graph(X, n, d, eps, opt, nullptr, 0, nullptr, 0, out);
+}
+
+bm_status bm_build_fps(const float* X, int64_t n, int32_t d, float eps, int64_t first, const bm_options* opt_in,
+                       bm_graph* out) {
+    if (!out) return fail(BM_ERR_ARG, "out is NULL");
+    std::memset(out, 0, sizeof(*out));
+    bm_options opt;
+    bm_options_init(&opt);
+    if (opt_in) opt = *opt_in;
+    bm_status vs = validate_points(X, n, d, "X");
+    if (vs != BM_OK) return vs;
+    vs = validate_eps(eps);
+    if (vs != BM_OK) return vs;
+    if (n > 0 && (first < 0 || first >= n)) return fail(BM_ERR_ARG, "first must be in [0, n)");
+    vs = check_device(opt.path);
+    if (vs != BM_OK) return vs;
+    if (n == 0) return build_graph(X, 0, d, eps, opt, nullptr, 0, nullptr, 0, out);
+    bm_status rs = fps_build(X, n, d, eps, first, opt, out);
+    if (rs != BM_OK) {
+        const std::string msg = g_last_error;
+        bm_graph_free(out, &opt);
+        g_last_error = msg;
+    }
+    return rs;
+}
+
+bm_status bm_color(const int64_t* offsets, const int32_t* ids, int64_t rows, const float* f, int64_t n, int32_t stat,
+                   const bm_options* opt_in, double* out) {
+    bm_options opt;
+    bm_options_init(&opt);
+    if (opt_in) opt = *opt_in;
+    if (rows < 0 || n < 0 || n > 0x7fffffffLL) return fail(BM_ERR_ARG, "rows or n out of range");
+    if (stat < BM_COLOR_MEAN || stat > BM_COLOR_MAX) return fail(BM_ERR_ARG, "unknown coloring statistic");
+    if (rows > 0 && (!offsets || !out)) return fail(BM_ERR_ARG, "offsets or out is NULL");
+    if (n > 0 && !f) return fail(BM_ERR_ARG, "f is NULL");
+    bm_status vs = check_device(opt.path);
+    if (vs != BM_OK) return vs;
+    if (rows == 0) return BM_OK;
+    cudaStream_t s = (cudaStream_t)opt.stream;
+    const bool host_io = opt.host_io != 0;
+    Arena ar(&opt, s);
+    const long long* doff = (const long long*)offsets;
+    const int* dids = ids;
+    const float* df = f;
+    double* dout = out;
+    if (host_io) {
+        const long long nnz = offsets[rows];
+        if (nnz < 0 || offsets[0] < 0 || offsets[0] > nnz) return fail(BM_ERR_ARG, "offsets are not a CSR");
+        if (nnz > 0 && !ids) return fail(BM_ERR_ARG, "ids is NULL");
+        long long* o;
+        int* i;
+        float* fv;
+        ALLOC(o, long long, rows + 1);
+        ALLOC(i, int, std::max<long long>(nnz, 1));
+        ALLOC(fv, float, std::max<long long>(n, 1));
+        ALLOC(dout, double, rows);
+        TRY_CUDA(cudaMemcpyAsync(o, offsets, sizeof(long long) * (rows + 1), cudaMemcpyHostToDevice, s));
+        if (nnz) TRY_CUDA(cudaMemcpyAsync(i, ids, sizeof(int) * nnz, cudaMemcpyHostToDevice, s));
+        if (n) TRY_CUDA(cudaMemcpyAsync(fv, f, sizeof(float) * n, cudaMemcpyHostToDevice, s));
+        doff = o;
+        dids = i;
+        df = fv;
+    }
+    int* bad;
+    ALLOC(bad, int, 1);
+    TRY_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    TRY_CUDA(launch_color(doff, dids, rows, df, n, stat, dout, bad, s));
+    int hbad = 0;
+    TRY_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (host_io) TRY_CUDA(cudaMemcpyAsync(out, dout, sizeof(double) * rows, cudaMemcpyDeviceToHost, s));
+    TRY_CUDA(cudaStreamSynchronize(s));
+    if (hbad & 2) return fail(BM_ERR_ARG, "f holds NaN or Inf");
+    if (hbad & 1) return fail(BM_ERR_ARG, "a membership id lies outside [0, n)");
+    return BM_OK;
 }
 
 static bm_status validate_knn(const float* X, int64_t n, int32_t d, int32_t k, const bm_options& opt) {

@@ -243,6 +243,29 @@ cudaError_t launch_knn_bound(const float* X, long long n, int d, long long strid
 cudaError_t launch_knn_select(const float* X, int d, const long long* offsets, long long rows, const int* ids,
                               long long nnz, double* D, int k, double* kdist, int* bad, cudaStream_t st);
 
+// fps.cu: farthest point sampling (Sec. 2.2), one kernel per landmark inside a graph
+// WHILE loop (the last block to finish a pass appends the landmark and sets the loop
+// condition).  mind: n doubles (the FP64 squared distance to the landmark set).
+struct FpsState {
+    long long count;                 // landmarks so far
+    long long last;                  // the newest landmark
+    int done;                        // 1 once no point is at distance >= eps
+    int error;                       // 1 when the iteration bound was passed
+    unsigned long long iterations;   // passes run
+    double last_dist2;               // squared distance of the newest landmark to the set before it
+};
+int fps_grid(long long n);           // blocks of a pass (the size of the partial arrays)
+cudaError_t launch_fps_init(double* mind, long long n, int* landmarks, FpsState* st, long long first, cudaStream_t s);
+cudaError_t launch_fps_step(const float* X, long long n, int d, double eps2, double* mind, int* landmarks, FpsState* st,
+                            double* part_v, int* part_i, unsigned* ticket, cudaGraphConditionalHandle h, bool use_graph,
+                            cudaStream_t s);
+cudaError_t launch_finite_check(const float* X, long long count, int* bad, cudaStream_t s);
+
+// color.cu: coloring (Sec. 2.3) of every CSR row; stat 0 mean, 1 median, 2 min, 3 max;
+// *bad |= 1 for an id outside [0, n), |= 2 for a non-finite f.
+cudaError_t launch_color(const long long* offsets, const int* ids, long long rows, const float* f, long long n, int stat,
+                         double* out, int* bad, cudaStream_t s);
+
 // graph.cu
 cudaError_t launch_csr_from_sorted(const unsigned long long* keys, long long nnz, long long rows,
                                    long long* offsets, int* ids, cudaStream_t s);
