@@ -514,7 +514,6 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
         const unsigned long long seg_off = seg_mode ? (unsigned long long)blockIdx.x * p.sink.seg_cap : 0ull;
         unsigned long long* seg_keys = p.sink.keys + seg_off;
         unsigned long long* band_keys = p.sink.band_keys + seg_off;
-        unsigned* band_ctr32 = seg_mode ? &ctl->band_used : nullptr;
         const unsigned long long band_cap = seg_mode ? p.sink.seg_cap : p.sink.band_cap;
         uint32_t t_buf = 0, t_ph = 0;
         unsigned long long pairs_local = 0;
@@ -554,32 +553,93 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
                     }
                     continue;
                 }
+                // classification: per 32-column chunk a hit mask (acc > 2 delta') and a band
+                // mask (0 <= acc <= 2 delta'), bit i = column col0 + i.  Sign bits are
+                // gathered with funnel shifts (bit i of the mask from register i); the sign
+                // of thr - acc is set exactly when acc > thr (a rounded difference keeps the
+                // sign of the exact one, and is +0 only when they are equal).
+                unsigned hitm[kChunks], bandm[kChunks];
+                unsigned nh = 0, nb = 0;
 #pragma unroll
                 for (int j = 0; j < kChunks; ++j) {
-                    const long long col0 = col_base + j * 32;
+                    hitm[j] = 0u;
+                    bandm[j] = 0u;
                     unsigned neg = kFull;
 #pragma unroll
                     for (int i = 0; i < 32; ++i) neg &= r[j][i];
-                    unsigned hit = 0, band = 0;
                     if (row_ok && (neg >> 31) == 0u) {
-                        const long long left = p.n - col0;
+                        const long long left = p.n - (col_base + j * 32);
                         const unsigned valid = left >= 32 ? kFull : (left <= 0 ? 0u : (1u << left) - 1u);
-                        unsigned near_ = 0;
+                        unsigned sgn = 0u;
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            hit |= (__uint_as_float(r[j][i]) > hit_thr ? 1u : 0u) << i;
-                            near_ |= ((r[j][i] >> 31) ^ 1u) << i;
+                        for (int i = 31; i >= 0; --i) sgn = __funnelshift_l(r[j][i], sgn, 1);
+                        const unsigned near_ = ~sgn & valid;
+                        unsigned gt = 0u;
+                        if (near_) {
+#pragma unroll
+                            for (int i = 31; i >= 0; --i)
+                                gt = __funnelshift_l(__float_as_uint(hit_thr - __uint_as_float(r[j][i])), gt, 1);
                         }
-                        hit &= valid;
-                        band = near_ & ~hit & valid;
+                        hitm[j] = gt & near_;
+                        bandm[j] = near_ & ~gt;
+                        nh += __popc(hitm[j]);
+                        nb += __popc(bandm[j]);
                     }
-                    // band pairs go to the FP64 recheck kernel
-                    if (__any_sync(kFull, band != 0u))
-                        emit_plain_run(band_keys, p.sink.band_n, band_ctr32, band_cap, (unsigned)row, (unsigned)col0,
-                                       band);
-                    if (__any_sync(kFull, hit != 0u)) {
-                        if (seg_mode) emit_hits_run_seg(p.sink, seg_keys, &ctl->seg_used, (unsigned)row, (unsigned)col0, hit);
-                        else emit_hits_run(p.sink, (unsigned)row, (unsigned)col0, hit);
+                }
+                // emission: one reservation per warp and tile for both kinds (counts packed
+                // as hits << 16 | band, each at most 128 per lane), then each lane writes its keys
+                const unsigned packed = (nh << 16) | nb;
+                if (__any_sync(kFull, packed != 0u)) {
+                    unsigned incl = packed;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const unsigned y = __shfl_up_sync(kFull, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    const unsigned tot = __shfl_sync(kFull, incl, 31);
+                    unsigned long long hbase = 0, bbase = 0;
+                    if (lane == 31) {
+                        if (seg_mode) {
+                            if (tot >> 16) hbase = atomicAdd(&ctl->seg_used, tot >> 16);
+                            if (tot & 0xffffu) bbase = atomicAdd(&ctl->band_used, tot & 0xffffu);
+                        } else {
+                            if (tot >> 16) hbase = atomicAdd(p.sink.count, (unsigned long long)(tot >> 16));
+                            if (tot & 0xffffu) bbase = atomicAdd(p.sink.band_n, (unsigned long long)(tot & 0xffffu));
+                        }
+                    }
+                    hbase = __shfl_sync(kFull, hbase, 31);
+                    bbase = __shfl_sync(kFull, bbase, 31);
+                    const unsigned excl = incl - packed;
+                    unsigned long long hpos = hbase + (excl >> 16), bpos = bbase + (excl & 0xffffu);
+                    unsigned long long* hkeys = seg_mode ? seg_keys : p.sink.keys;
+                    const unsigned long long hcap = seg_mode ? p.sink.seg_cap : p.sink.cap;
+                    const unsigned long long rowkey = (unsigned long long)(unsigned)row << 32;
+#pragma unroll
+                    for (int j = 0; j < kChunks; ++j) {
+                        const unsigned col0 = (unsigned)(col_base + j * 32);
+                        unsigned m = bandm[j];
+                        while (m) {
+                            const int b = __ffs(m) - 1;
+                            m &= m - 1;
+                            if (bpos < band_cap) band_keys[bpos] = rowkey | (col0 + (unsigned)b);
+                            ++bpos;
+                        }
+                        m = hitm[j];
+                        while (m) {
+                            const int b = __ffs(m) - 1;
+                            m &= m - 1;
+                            const unsigned col = col0 + (unsigned)b;
+                            if (hpos < hcap) hkeys[hpos] = rowkey | col;
+                            ++hpos;
+                            if (p.sink.slot_of) {   // greedy: a later candidate covered by this one
+                                const int sl = p.sink.slot_of[col];
+                                if (sl > (int)row) {
+                                    atomicOr(&p.sink.conflict[(size_t)row * p.sink.conflict_words + (sl >> 5)],
+                                             1u << (sl & 31));
+                                    atomicOr(&p.sink.row_any[row >> 5], 1u << (row & 31));
+                                }
+                            }
+                        }
                     }
                 }
                 if (threadIdx.x == 64) {
