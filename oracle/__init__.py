@@ -20,6 +20,9 @@ Functions and the passages they follow:
   fps                Sec. 2.2 farthest point sampling epsilon-net
   fps_build          the Ball Mapper on the farthest-point landmarks (memberships, edges)
   color              Sec. 2.3 coloring: mean / median / min / max of f over each ball
+  knn_graph          M nearest other points of every point (the proximity graph's arcs)
+  graph_index        undirected proximity graph (CSR), the graph-based index of Sec. 5.4
+  graph_range_query  Sec. 5.4 partial graph traversal + exact decision (conservative range sets)
 """
 from __future__ import annotations
 
@@ -94,6 +97,11 @@ def load_library(path: str):
     lib.bmo_fps.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int64, _i32p]
     lib.bmo_color.restype = ctypes.c_int
     lib.bmo_color.argtypes = [_i64p, _i32p, ctypes.c_int64, _f64p, ctypes.c_int, _f64p]
+    lib.bmo_knn_graph.restype = ctypes.c_int
+    lib.bmo_knn_graph.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _i32p]
+    lib.bmo_graph_range.restype = ctypes.c_int
+    lib.bmo_graph_range.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int, _i64p, _i32p, _f64p, ctypes.c_int64,
+                                    ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _i64p, _i64p, _i32p]
     lib.bmo_num_threads.restype = ctypes.c_int
     lib.bmo_num_threads.argtypes = []
     lib.bmo_set_num_threads.restype = None
@@ -287,6 +295,55 @@ def color(offsets, ids, f, stat: str = "mean") -> np.ndarray:
                                   COLOR_STATS[stat], _ptr(out, _f64p)):
         raise MemoryError("oracle color: allocation failed")
     return out[:rows].copy()
+
+
+def knn_graph(X, M: int) -> np.ndarray:
+    """(n, M) int32: the M nearest other points of every point, by (FP64 D, id)."""
+    X = _f64(X)
+    n, d = X.shape
+    out = np.empty((max(n, 1), M), dtype=np.int32)
+    if _load().bmo_knn_graph(_ptr(X, _f64p), n, d, int(M), _ptr(out, _i32p)):
+        raise ValueError("knn_graph: M out of range or allocation failure")
+    return out[:n].copy()
+
+
+def graph_index(X, M: int):
+    """Undirected proximity graph: the union of every point's M-nearest arcs and their
+    reverses, as CSR (adj_off int64 [n+1], adj int32) with ascending neighbour lists."""
+    nbr = knn_graph(X, M)
+    n = nbr.shape[0]
+    src = np.repeat(np.arange(n, dtype=np.int64), M)
+    dst = nbr.astype(np.int64).ravel()
+    keys = np.unique(np.concatenate([src * n + dst, dst * n + src]))
+    off = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(off, keys // n + 1, 1)
+    return np.cumsum(off), (keys % n).astype(np.int32)
+
+
+def graph_range_query(X, adj_off, adj, Q, eps, E: int, ef: int, max_visits: int):
+    """Conservative range sets through the proximity graph (Sec. 5.4): CSR over the rows
+    of Q of the visited points with D < eps^2 (entry, beam of ef, range expansion)."""
+    X = _f64(X)
+    Q = _f64(Q)
+    n, d = X.shape
+    m = Q.shape[0]
+    adj_off = np.ascontiguousarray(adj_off, dtype=np.int64)
+    adj = np.ascontiguousarray(adj, dtype=np.int32)
+    if adj.size == 0:
+        adj = np.zeros(1, dtype=np.int32)
+    lib = _load()
+    counts = np.zeros(max(m, 1), dtype=np.int64)
+    e2 = eps_squared(eps)
+    if m and lib.bmo_graph_range(_ptr(X, _f64p), n, d, _ptr(adj_off, _i64p), _ptr(adj, _i32p), _ptr(Q, _f64p), m, e2,
+                                 int(E), int(ef), int(max_visits), _ptr(counts, _i64p), None, None):
+        raise ValueError("graph range query failed")
+    offsets = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(counts[:m], out=offsets[1:])
+    ids = np.empty(max(int(offsets[-1]), 1), dtype=np.int32)
+    if m and lib.bmo_graph_range(_ptr(X, _f64p), n, d, _ptr(adj_off, _i64p), _ptr(adj, _i32p), _ptr(Q, _f64p), m,
+                                 e2, int(E), int(ef), int(max_visits), None, _ptr(offsets, _i64p), _ptr(ids, _i32p)):
+        raise ValueError("graph range query failed")
+    return offsets, ids[: int(offsets[-1])].copy()
 
 
 def kth_nn_dist(X, k: int) -> np.ndarray:

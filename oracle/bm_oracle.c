@@ -26,7 +26,10 @@
  *     greedy): start from a given landmark, repeatedly take the point farthest
  *     from the landmark set while that distance is at least eps;
  *   - coloring (Sec. 2.3): a statistic of a per-point function f over every
- *     ball X_i (mean, median, minimum, maximum).
+ *     ball X_i (mean, median, minimum, maximum);
+ *   - a graph-based conservative range oracle (Sec. 5.4, the proximity-graph
+ *     family of non-exhaustive indexes): a query examines only the points its
+ *     traversal of a proximity graph visits and decides membership exactly.
  *
  * Parallelism: outer loops whose iterations are independent (one query row,
  * one landmark pair row, one k-NN row) run under OpenMP.  This does not
@@ -562,6 +565,181 @@ int bmo_color(const int64_t* offsets, const int32_t* ids, int64_t rows, const do
             }
             out[r] = best;
         }
+    }
+    return bad ? -1 : 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Proximity graph and graph range query (Sec. 5.4: the candidate set C(q) of a
+ * non-exhaustive index is what a partial graph traversal visits; membership is
+ * then decided with the exact distance, so no false positives).
+ *
+ * Graph: for every point i its M nearest other points by (D, id), D the FP64
+ * squared distance; the undirected union of those arcs; each adjacency list
+ * ascending by id (CSR adj_off / adj).
+ *
+ * Query q (all distances FP64 D, candidates ordered by (D, id)):
+ *   1. entry: the nearest of the E entry points e_t = floor(t n / E), t < E;
+ *   2. beam: a list R of at most ef visited nodes, the best by (D, id), each
+ *      flagged expanded or not; repeatedly expand the best unexpanded node of R
+ *      (visit its neighbours in adjacency order: a neighbour not yet visited is
+ *      visited, and enters R when R has room or it beats R's worst, which then
+ *      leaves R); stop when every node of R is expanded;
+ *   3. range expansion: every visited node with D < eps^2 that was not expanded
+ *      is expanded in order of visit (first in, first out), visiting its
+ *      neighbours; those with D < eps^2 join the queue;
+ *   at most max_visits nodes are visited per query (visits stop at the cap).
+ * Row j = { visited v : D(q_j, v) < eps^2 }, ascending.
+ * ------------------------------------------------------------------------- */
+typedef struct { double D; int32_t id; } dkey;
+
+static int dkey_less(dkey a, dkey b) { return a.D < b.D || (a.D == b.D && a.id < b.id); }
+
+int bmo_knn_graph(const double* X, int64_t n, int d, int M, int32_t* nbr) {
+    if (M < 1 || M >= n) return -1;
+    int bad = 0;
+    #pragma omp parallel
+    {
+        dkey* best = (dkey*)malloc(sizeof(dkey) * (size_t)(M + 1));
+        if (!best) {
+            #pragma omp atomic write
+            bad = 1;
+        }
+        #pragma omp for schedule(dynamic, 16)
+        for (int64_t i = 0; i < n; ++i) {
+            if (!best) continue;
+            int cnt = 0;
+            for (int64_t j = 0; j < n; ++j) {
+                if (j == i) continue;
+                dkey c = {sqdist(X + (size_t)i * d, X + (size_t)j * d, d), (int32_t)j};
+                if (cnt == M && !dkey_less(c, best[M - 1])) continue;
+                int p = cnt < M ? cnt++ : M - 1;           /* insertion into the sorted best list */
+                while (p > 0 && dkey_less(c, best[p - 1])) { best[p] = best[p - 1]; --p; }
+                best[p] = c;
+            }
+            for (int t = 0; t < M; ++t) nbr[(size_t)i * M + t] = best[t].id;
+        }
+        free(best);
+    }
+    return bad ? -1 : 0;
+}
+
+typedef struct {
+    int32_t* mark;       /* n: visit stamp (query index + 1) */
+    int32_t* visited;    /* visit order */
+    double* vd;          /* D of the visited nodes */
+    unsigned char* expd; /* expanded flag per visited slot */
+    int32_t* slot;       /* n: visited slot of a node (valid when marked) */
+    dkey* R;             /* beam, sorted */
+    int32_t* Rslot;
+} gq_work;
+
+/* one query; writes the in-range ids (ascending) to out (when non-NULL), returns their count */
+static int64_t graph_query(const double* X, int64_t n, int d, const int64_t* adj_off, const int32_t* adj,
+                           const double* q, double eps2, int E, int ef, int64_t max_visits, int32_t stamp,
+                           gq_work* w, int32_t* out) {
+    int64_t nv = 0;
+    /* 1. entry */
+    int64_t start = 0;
+    double bd = INFINITY;
+    for (int t = 0; t < E; ++t) {
+        const int64_t e = (int64_t)t * n / E;
+        const double D = sqdist(q, X + (size_t)e * d, d);
+        if (D < bd || (D == bd && e < start)) { bd = D; start = e; }
+    }
+    w->mark[start] = stamp;
+    w->slot[start] = (int32_t)nv;
+    w->visited[nv] = (int32_t)start;
+    w->vd[nv] = bd;
+    w->expd[nv] = 0;
+    ++nv;
+    int nR = 1;
+    w->R[0].D = bd;
+    w->R[0].id = (int32_t)start;
+    w->Rslot[0] = 0;
+    /* 2. beam */
+    while (1) {
+        int pick = -1;
+        for (int r = 0; r < nR; ++r)
+            if (!w->expd[w->Rslot[r]]) { pick = r; break; }
+        if (pick < 0) break;
+        const int32_t c = w->R[pick].id;
+        w->expd[w->Rslot[pick]] = 1;
+        for (int64_t a = adj_off[c]; a < adj_off[c + 1] && nv < max_visits; ++a) {
+            const int32_t v = adj[a];
+            if (w->mark[v] == stamp) continue;
+            const double D = sqdist(q, X + (size_t)v * d, d);
+            w->mark[v] = stamp;
+            w->slot[v] = (int32_t)nv;
+            w->visited[nv] = v;
+            w->vd[nv] = D;
+            w->expd[nv] = 0;
+            dkey k = {D, v};
+            if (nR < ef || dkey_less(k, w->R[nR - 1])) {
+                int p = nR < ef ? nR++ : nR - 1;
+                while (p > 0 && dkey_less(k, w->R[p - 1])) { w->R[p] = w->R[p - 1]; w->Rslot[p] = w->Rslot[p - 1]; --p; }
+                w->R[p] = k;
+                w->Rslot[p] = (int32_t)nv;
+            }
+            ++nv;
+        }
+    }
+    /* 3. range expansion, first in first out over the visit order */
+    for (int64_t h = 0; h < nv; ++h) {
+        if (!(w->vd[h] < eps2) || w->expd[h]) continue;
+        w->expd[h] = 1;
+        const int32_t c = w->visited[h];
+        for (int64_t a = adj_off[c]; a < adj_off[c + 1] && nv < max_visits; ++a) {
+            const int32_t v = adj[a];
+            if (w->mark[v] == stamp) continue;
+            w->mark[v] = stamp;
+            w->slot[v] = (int32_t)nv;
+            w->visited[nv] = v;
+            w->vd[nv] = sqdist(q, X + (size_t)v * d, d);
+            w->expd[nv] = 0;
+            ++nv;
+        }
+    }
+    int64_t cnt = 0;
+    for (int64_t h = 0; h < nv; ++h)
+        if (w->vd[h] < eps2) {
+            if (out) out[cnt] = w->visited[h];
+            ++cnt;
+        }
+    if (out) qsort(out, (size_t)cnt, sizeof(int32_t), cmp_i32);
+    return cnt;
+}
+
+/* counts (pass offsets == NULL) or fills (ids at offsets[j]) the rows of every query */
+int bmo_graph_range(const double* X, int64_t n, int d, const int64_t* adj_off, const int32_t* adj,
+                    const double* Q, int64_t m, double eps2, int E, int ef, int64_t max_visits,
+                    int64_t* counts, const int64_t* offsets, int32_t* ids) {
+    if (n <= 0 || E < 1 || ef < 1 || max_visits < 1) return -1;
+    if (E > n) E = (int)n;
+    int bad = 0;
+    #pragma omp parallel
+    {
+        gq_work w;
+        w.mark = (int32_t*)calloc((size_t)n, sizeof(int32_t));
+        w.slot = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+        w.visited = (int32_t*)malloc(sizeof(int32_t) * (size_t)(max_visits + 1));
+        w.vd = (double*)malloc(sizeof(double) * (size_t)(max_visits + 1));
+        w.expd = (unsigned char*)malloc((size_t)(max_visits + 1));
+        w.R = (dkey*)malloc(sizeof(dkey) * (size_t)ef);
+        w.Rslot = (int32_t*)malloc(sizeof(int32_t) * (size_t)ef);
+        const int ok = w.mark && w.slot && w.visited && w.vd && w.expd && w.R && w.Rslot;
+        if (!ok) {
+            #pragma omp atomic write
+            bad = 1;
+        }
+        #pragma omp for schedule(dynamic, 4)
+        for (int64_t j = 0; j < m; ++j) {
+            if (!ok) continue;
+            const int64_t c = graph_query(X, n, d, adj_off, adj, Q + (size_t)j * d, eps2, E, ef, max_visits,
+                                          (int32_t)(j + 1), &w, offsets ? ids + offsets[j] : NULL);
+            if (counts) counts[j] = c;
+        }
+        free(w.mark); free(w.slot); free(w.visited); free(w.vd); free(w.expd); free(w.R); free(w.Rslot);
     }
     return bad ? -1 : 0;
 }

@@ -336,3 +336,42 @@ def pin_color_values(X, eps, seed=1):
         assert abs(mean[i] - row.sum() / m) <= 1e-12 * max(1.0, np.abs(row).sum())
     const = oracle.color(off, ids, np.full(X.shape[0], 3.25), "mean")
     assert np.all(const == 3.25)
+
+
+# ---------------------------------------------------------------- graph-based range oracle
+def pin_graph_golden():
+    g = golden("graph_line.json")
+    for case in g["cases"]:
+        X = np.array(case["points"], dtype=np.float32)
+        if "arcs" in case:
+            assert oracle.knn_graph(X, case["M"]).tolist() == case["arcs"]
+        off, adj = oracle.graph_index(X, case["M"])
+        assert off.tolist() == case["adj_off"] and adj.tolist() == case["adj"], case
+        Q = np.array(case["queries"], dtype=np.float32)
+        ro, ri = oracle.graph_range_query(X, off, adj, Q, case["eps"], case["E"], case["ef"], case["max_visits"])
+        assert rows(ro, ri) == case["rows"], (rows(ro, ri), case)
+
+
+def pin_knn_graph_scipy(X, M):
+    """M nearest other points on tie-free data, against scipy's k-d tree."""
+    from scipy.spatial import cKDTree
+    X64 = np.asarray(X, dtype=np.float64)
+    ref = cKDTree(X64).query(X64, k=M + 1)[1][:, 1:]
+    assert np.array_equal(oracle.knn_graph(X, M), ref)
+
+
+def pin_graph_exhaustive_and_conservative(X, Q, eps, M=6):
+    """With a beam as wide as the data and a connected graph every point is visited, so
+    the rows are the exact range sets; with a narrow beam they stay subsets of them."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import connected_components
+    off, adj = oracle.graph_index(X, M)
+    n = X.shape[0]
+    g = csr_matrix((np.ones(adj.size), adj, off), shape=(n, n))
+    assert connected_components(g, directed=False)[0] == 1
+    eo, ei = oracle.range_query(X, Q, eps)
+    go, gi = oracle.graph_range_query(X, off, adj, Q, eps, 1, n, n)
+    assert np.array_equal(go, eo) and np.array_equal(gi, ei)
+    lo, li = oracle.graph_range_query(X, off, adj, Q, eps, 4, 2, n)
+    for j in range(Q.shape[0]):
+        assert set(li[lo[j]:lo[j + 1]].tolist()) <= set(ei[eo[j]:eo[j + 1]].tolist())

@@ -37,6 +37,13 @@ MUTANTS = [
     ("color-mean-divisor", "out[r] = sum / (double)cnt;", "out[r] = sum / (double)(cnt + 1);", 1),
     ("color-median-index", "(v[cnt / 2 - 1] + v[cnt / 2]) / 2.0", "(v[cnt / 2] + v[cnt / 2]) / 2.0", 1),
     ("color-min-max-swapped", "if (stat == 2 ? x < best : x > best)", "if (stat == 2 ? x > best : x < best)", 1),
+    ("graph-ties-to-larger-id", "return a.D < b.D || (a.D == b.D && a.id < b.id);",
+     "return a.D < b.D || (a.D == b.D && a.id > b.id);", 1),
+    ("knn-graph-keeps-self", "if (j == i) continue;", "if (0) continue;", 1),
+    ("graph-no-range-expansion", "if (!(w->vd[h] < eps2) || w->expd[h]) continue;", "if (1) continue;", 1),
+    ("graph-beam-never-evicts", "if (nR < ef || dkey_less(k, w->R[nR - 1])) {", "if (nR < ef) {", 1),
+    ("graph-entry-ignores-distance", "if (D < bd || (D == bd && e < start)) { bd = D; start = e; }",
+     "if (t == 0) { bd = D; start = e; }", 1),
     ("masked-ignores-cells", "if (flag[cell_of[i]] && sqdist", "if ((flag[cell_of[i]] || 1) && sqdist", 2),
 ]
 # A wrong node centre is not listed: any centre paired with the radius measured
@@ -66,6 +73,10 @@ def _all_pins():
     pins.pin_color_golden()
     pins.pin_color_lipschitz(W.isotropic(800, 5, 10, seed=63), 1.2)
     pins.pin_color_values(W.isotropic(600, 4, 10, seed=64), 0.9)
+    pins.pin_graph_golden()
+    pins.pin_knn_graph_scipy(W.paper_gaussian_fp64(500, 5, seed=81), 7)
+    Xg = W.isotropic(1200, 6, 10, seed=82)
+    pins.pin_graph_exhaustive_and_conservative(Xg, Xg[::29], 1.6)
 
 
 def test_unmutated_oracle_passes_all_pins():

@@ -122,3 +122,16 @@ def test_paper_coloring_bound_needs_the_diameter():
     assert out["landmarks"].tolist() == [0]
     c = oracle.color(out["offsets"], out["ids"], X[:, 0], "mean")[0]
     assert abs(-0.875 - c) > 1.0 and abs(-0.875 - c) < 2.0
+
+
+def test_graph_oracle_golden():
+    pins.pin_graph_golden()
+
+
+def test_knn_graph_against_scipy():
+    pins.pin_knn_graph_scipy(W.paper_gaussian_fp64(1500, 7, seed=81), 9)
+
+
+def test_graph_oracle_exhaustive_and_conservative():
+    X = W.isotropic(2400, 6, 10, seed=82)
+    pins.pin_graph_exhaustive_and_conservative(X, X[::37], 1.6)
