@@ -116,6 +116,8 @@ typedef struct {
     double dist_max_rel_err;  /* with want_dists: max over reported distances of |dist - sqrt(D)| / sqrt(D),
                                  D the FP64 squared distance in coordinate order (the CPU oracle's value);
                                  the rounding of sqrt(D) to float bounds it by 2^-24; 0 otherwise */
+    int32_t truncated;        /* graph index: 1 when a query stopped at its visit cap */
+    int32_t reserved2;
 } bm_stats;
 
 typedef struct {
@@ -299,6 +301,39 @@ BM_API bm_status bm_ivf_range_query(const bm_ivf* idx, const float* Q, int64_t m
  * end-to-end mode (the greedy of Sec. 2.2 driven by the index's range sets). */
 BM_API bm_status bm_build_ivf(const bm_ivf* idx, float eps, int32_t nprobe, const int32_t* landmarks,
                               int64_t n_landmarks, const bm_options* opt, bm_graph* out);
+
+/* ---- Proximity-graph index: the paper's graph-based non-exhaustive oracle (Sec. 5.4:
+ * a query examines only the part of a proximity graph its traversal visits, and decides
+ * membership with the exact distance, so every returned point is a true member --
+ * false negatives only, no false positives; the breadth of the search is the efSearch
+ * of Sec. 6.1, here ef).
+ * Graph: every point's M nearest other points (by FP64 squared distance, then id),
+ * made undirected; adjacency lists ascend by id.
+ * Query (one warp per query, distances FP64 in coordinate order, candidates ordered by
+ * (distance, id)): the nearest of n_entries entry points floor(t n / n_entries); a beam
+ * of at most ef visited nodes, the best unexpanded one expanded until all are expanded;
+ * then every visited node inside the ball that was not expanded is expanded in visit
+ * order; at most max_visits visits per query (0 = 4096; stats.truncated reports a query
+ * that stopped there).  The row is the visited points strictly inside eps.
+ * The index refers to X (device) until freed; with opt->host_io it keeps a device copy.
+ *   bm_gidx_build: 1 <= M <= min(n - 1, 1023); n_entries in [1, n] (0 = min(n, 64)).
+ *   ef in [1, 256]; max_visits in [1, 2^24]. */
+typedef struct bm_gidx bm_gidx;
+
+BM_API bm_status bm_gidx_build(const float* X, int64_t n, int32_t d, int32_t M, int32_t n_entries,
+                               const bm_options* opt, bm_gidx** out);
+BM_API void bm_gidx_free(bm_gidx* idx);
+/* Shape and device arrays of the graph: adj_off (n + 1), adj (n_adj neighbour ids). */
+BM_API bm_status bm_gidx_info(const bm_gidx* idx, int64_t* n, int32_t* d, int64_t* n_adj, const int64_t** adj_off,
+                              const int32_t** adj);
+/* out row j = the points with d(X_i, Q_j) < eps among those the search for Q_j visits. */
+BM_API bm_status bm_gidx_range_query(const bm_gidx* idx, const float* Q, int64_t m, float eps, int32_t ef,
+                                     int64_t max_visits, const bm_options* opt, bm_csr* out, bm_stats* stats);
+/* Ball Mapper with the graph oracle (Sec. 6.2 modes): landmarks != NULL: fixed-landmark
+ * mode (device memory, host with opt->host_io); NULL: the greedy of Sec. 2.2 driven by
+ * the index's range sets (a point is covered when a landmark's search finds it). */
+BM_API bm_status bm_build_gidx(const bm_gidx* idx, float eps, int32_t ef, int64_t max_visits,
+                               const int32_t* landmarks, int64_t n_landmarks, const bm_options* opt, bm_graph* out);
 
 /* Release outputs (safe on zeroed structs); pass the options used to create them. */
 BM_API void bm_csr_free(bm_csr* csr, const bm_options* opt);

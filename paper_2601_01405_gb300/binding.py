@@ -43,7 +43,7 @@ class bm_stats(ctypes.Structure):
                 ("ms_edges", ctypes.c_double), ("ms_total", ctypes.c_double), ("band_delta", ctypes.c_float),
                 ("path", ctypes.c_int32), ("ms_sweep", ctypes.c_double), ("sweep_launches", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("recheck_rate", ctypes.c_double),
-                ("dist_max_rel_err", ctypes.c_double)]
+                ("dist_max_rel_err", ctypes.c_double), ("truncated", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -150,6 +150,22 @@ def load(path: str = LIB_PATH):
         lib.bm_color.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                                  ctypes.c_int32, ctypes.POINTER(bm_options), ctypes.c_void_p]
         lib.bm_color.restype = ctypes.c_int
+        lib.bm_gidx_build.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.POINTER(bm_options), ctypes.POINTER(ctypes.c_void_p)]
+        lib.bm_gidx_build.restype = ctypes.c_int
+        lib.bm_gidx_free.argtypes = [ctypes.c_void_p]
+        lib.bm_gidx_free.restype = None
+        lib.bm_gidx_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_void_p),
+                                     ctypes.POINTER(ctypes.c_void_p)]
+        lib.bm_gidx_info.restype = ctypes.c_int
+        lib.bm_gidx_range_query.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_float,
+                                            ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(bm_options),
+                                            ctypes.POINTER(bm_csr), ctypes.POINTER(bm_stats)]
+        lib.bm_gidx_range_query.restype = ctypes.c_int
+        lib.bm_build_gidx.argtypes = [ctypes.c_void_p, ctypes.c_float, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
+                                      ctypes.c_int64, ctypes.POINTER(bm_options), ctypes.POINTER(bm_graph)]
+        lib.bm_build_gidx.restype = ctypes.c_int
         lib.bm_knn_dist.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                     ctypes.POINTER(bm_options), ctypes.c_void_p, ctypes.POINTER(bm_stats)]
         lib.bm_knn_dist.restype = ctypes.c_int
@@ -632,6 +648,82 @@ class IvfIndex:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             self._lib.bm_ivf_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class GraphIndex:
+    """Proximity-graph index over device points X (bm_gidx_build): every point's M nearest
+    other points, made undirected.  The index refers to X, which must stay alive and
+    unchanged; its own buffers come from torch's allocator."""
+
+    def __init__(self, X, M: int = 16, n_entries: int = 0, path: str = "auto"):
+        import torch
+        self._lib = load()
+        if not _is_torch_cuda(X):
+            raise ValueError("X must be a CUDA tensor")
+        px, n, d, kx, _ = _as_input(X)
+        self._X = kx
+        self._alloc = _TorchAllocator(kx.device)
+        self._opt = _options(self._lib, path, 0, _current_stream(kx.device), False, self._alloc)
+        h = ctypes.c_void_p()
+        _check(self._lib, self._lib.bm_gidx_build(px, n, d, int(M), int(n_entries), ctypes.byref(self._opt),
+                                                  ctypes.byref(h)))
+        self._h = h
+        n_ = ctypes.c_int64()
+        d_ = ctypes.c_int32()
+        na = ctypes.c_int64()
+        ao = ctypes.c_void_p()
+        aj = ctypes.c_void_p()
+        _check(self._lib, self._lib.bm_gidx_info(h, ctypes.byref(n_), ctypes.byref(d_), ctypes.byref(na),
+                                                 ctypes.byref(ao), ctypes.byref(aj)))
+        self.n, self.d, self.n_adj = n_.value, d_.value, na.value
+        self.adj_off = self._alloc.peek(ao.value, self.n + 1, torch.int64)
+        self.adj = self._alloc.peek(aj.value, self.n_adj, torch.int32)
+
+    def range_query(self, Q, eps: float, ef: int, max_visits: int = 0, want_dists: bool = False):
+        """(offsets, ids, stats): conservative range sets through the graph search."""
+        import torch
+        pq, m, dq, kq, _ = _as_input(Q)
+        if not _is_torch_cuda(Q):
+            raise ValueError("Q must be a CUDA tensor")
+        alloc = _TorchAllocator(kq.device)
+        opt = _options(self._lib, "auto", 0, _current_stream(kq.device), False, alloc, want_dists=want_dists)
+        out = bm_csr()
+        st = bm_stats()
+        _check(self._lib, self._lib.bm_gidx_range_query(self._h, pq, m, ctypes.c_float(eps), int(ef), int(max_visits),
+                                                        ctypes.byref(opt), ctypes.byref(out), ctypes.byref(st)))
+        res = (alloc.tensor(out.offsets, m + 1, torch.int64), alloc.tensor(out.ids, out.nnz, torch.int32),
+               st.as_dict())
+        if want_dists:
+            res = res + (alloc.tensor(out.dists, out.nnz, torch.float32),)
+        return res
+
+    def build(self, eps: float, ef: int, max_visits: int = 0, landmarks=None, batch: int = 0,
+              want_dists: bool = False):
+        """Ball Mapper through the graph: fixed-landmark mode (landmarks = CUDA int32 tensor)
+        or end-to-end mode (landmarks None)."""
+        import torch
+        dev = self._X.device
+        alloc = _TorchAllocator(dev)
+        opt = _options(self._lib, "auto", batch, _current_stream(dev), False, alloc, want_dists=want_dists)
+        g = bm_graph()
+        lm_ptr, nl = None, 0
+        if landmarks is not None:
+            landmarks = landmarks.to(device=dev, dtype=torch.int32).contiguous()
+            lm_ptr, nl = landmarks.data_ptr() if landmarks.numel() else None, landmarks.numel()
+        _check(self._lib, self._lib.bm_build_gidx(self._h, ctypes.c_float(eps), int(ef), int(max_visits), lm_ptr, nl,
+                                                  ctypes.byref(opt), ctypes.byref(g)))
+        return _graph_dict(alloc, g, want_dists)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.bm_gidx_free(self._h)
             self._h = None
 
     def __del__(self):

@@ -407,6 +407,19 @@ bm_status ivf_sweep(SweepDesc& sd, DeviceState* st, Arena& ar, bool greedy, cuda
 
 bm_status sweep_stage(SweepDesc& sd, DeviceState* st, int path, SweepOut& o, unsigned long long* count,
                       int overflow_bit, bool greedy, int sms, SweepTimer& stimer, cudaStream_t s, Arena& ar) {
+    if (sd.gidx) {   // proximity-graph search: exact decisions on the visited points, no band
+        sd.sink.keys = o.keys;
+        sd.sink.count = count;
+        sd.sink.cap = o.cap;
+        sd.sink.seg_counts = nullptr;
+        sd.sink.band_seg_counts = nullptr;
+        stimer.before();
+        const cudaError_t e = launch_graph_search(sd, *sd.gidx, st, count, o.cap, overflow_bit, greedy, ar, s,
+                                                  &st->tile_pairs, &st->gidx_truncated);
+        stimer.after();
+        TRY_CUDA(e);
+        return BM_OK;
+    }
     if (sd.ivf) {   // inverted-file scan: FP32 tiles over the probed cells, global counters
         sd.sink.count = count;
         sd.sink.cap = o.cap;
@@ -751,11 +764,15 @@ bm_status greedy_drive(GreedyCtx& c, Prepared& pts, Arena& ar, cudaStream_t s, H
 bm_status greedy_pass(Prepared& pts, double eps2, int path, bool auto_switch, int S, Arena& ar, cudaStream_t s,
                       DeviceState* st, HostState& hs, unsigned long long& step_cap, unsigned long long& mem_cap,
                       bool* retry, int** landmarks_out, unsigned long long** mem_keys_out, DeviceState& final_state,
-                      SweepTimer& stimer, const IvfIndex* ivf, const float* phi_perm, int nprobe, int* path_used) {
+                      SweepTimer& stimer, const IvfIndex* ivf, const float* phi_perm, int nprobe, int* path_used,
+                      const GraphIndex* gidx = nullptr, int ef = 0, long long max_visits = 0) {
     *retry = false;
     GreedyCtx c;
     bm_status rs = greedy_setup(pts, eps2, path, S, ar, s, st, step_cap, mem_cap, ivf, phi_perm, nprobe, c);
     if (rs != BM_OK) return rs;
+    c.sd.gidx = gidx;
+    c.sd.gidx_ef = ef;
+    c.sd.gidx_max_visits = max_visits;
     c.auto_switch = auto_switch;
     rs = greedy_drive(c, pts, ar, s, hs, step_cap, mem_cap, final_state, stimer, false);
     if (rs != BM_OK) return rs;
@@ -780,7 +797,8 @@ namespace {
 // (k-NN sweeps; r2_max is its maximum); the tensor-core rows then use the bf16 split.
 bm_status range_core(const float* X, long long n, int d, const float* Q, long long m, float eps, const bm_options& opt,
                      const IvfIndex* ivf, int nprobe, int* probes_out, bm_csr* out, bm_stats* stats,
-                     const double* row_r2 = nullptr, double r2_max = 0.0, unsigned long long cap_hint = 0) {
+                     const double* row_r2 = nullptr, double r2_max = 0.0, unsigned long long cap_hint = 0,
+                     const GraphIndex* gidx = nullptr, int ef = 0, long long max_visits = 0) {
     std::memset(out, 0, sizeof(*out));
     if (stats) std::memset(stats, 0, sizeof(*stats));
     cudaStream_t s = (cudaStream_t)opt.stream;
@@ -789,8 +807,8 @@ bm_status range_core(const float* X, long long n, int d, const float* Q, long lo
     // automatic path: a single sweep cannot change course, so range queries take the split
     const int req = (opt.path == BM_PATH_TC_AUTO || (row_r2 && opt.path == BM_PATH_TC_FP16))
                         ? (int)BM_PATH_TC_SPLIT3 : opt.path;
-    const bool tc = is_tc_path(req) && ivf == nullptr;
-    const int path = ivf ? (int)BM_PATH_FP32 : req;
+    const bool tc = is_tc_path(req) && ivf == nullptr && gidx == nullptr;
+    const int path = (ivf || gidx) ? (int)BM_PATH_FP32 : req;
     Timer tm(s);
     tm.mark();
     SweepTimer stimer(s);
@@ -804,9 +822,10 @@ bm_status range_core(const float* X, long long n, int d, const float* Q, long lo
     float* dists = nullptr;
     unsigned long long* err_dev = nullptr;
     double dist_err = 0.0;
+    int truncated = 0;
     {
         Arena ar(&opt, s);
-        const float* dX = ivf ? X : stage_input(X, n, d, host_io, ar, s, &rs);
+        const float* dX = (ivf || gidx) ? X : stage_input(X, n, d, host_io, ar, s, &rs);
         if (rs != BM_OK) return rs;
         const float* dQ = stage_input(Q, m, d, host_io, ar, s, &rs);
         if (rs != BM_OK) return rs;
@@ -882,6 +901,9 @@ bm_status range_core(const float* X, long long n, int d, const float* Q, long lo
                 sd.nprobe = nprobe;
                 sd.ivf_probes_out = probes_out;
                 sd.row_eps2 = row_r2;
+                sd.gidx = gidx;
+                sd.gidx_ef = ef;
+                sd.gidx_max_visits = max_visits;
                 rs = sweep_stage(sd, st, path, so, &st->hit_count, kErrHitOverflow, false, sms, stimer, s, ar);
                 if (rs != BM_OK) return rs;
                 rs = read_state(st, hs, h, s);
@@ -906,6 +928,7 @@ bm_status range_core(const float* X, long long n, int d, const float* Q, long lo
             band = h.band_pairs;
             pairs = h.tile_pairs;
             delta = h.delta;
+            truncated = h.gidx_truncated;
             unsigned long long* tmp;
             ALLOC(tmp, unsigned long long, std::max<long long>(nnz, 1));
             unsigned long long* sorted = nullptr;
@@ -962,6 +985,7 @@ bm_status range_core(const float* X, long long n, int d, const float* Q, long lo
         stats->kernel_launches = g_kernel_launches - launches0;
         stats->recheck_rate = pairs ? (double)band / (double)pairs : 0.0;
         stats->dist_max_rel_err = dist_err;
+        stats->truncated = truncated;
     }
     return BM_OK;
 }
@@ -1171,7 +1195,8 @@ bm_status hand_over(Arena& ar, cudaStream_t s, bool host_io, int* landmarks, lon
 // full-ball memberships, nerve edges.  With an inverted-file index the balls are
 // the index's conservative range sets (Sec. 5.3-5.4); otherwise they are exact.
 bm_status build_graph(const float* X, long long n, int d, float eps, const bm_options& opt, const IvfIndex* ivf,
-                      int nprobe, const int* fixed_lm, long long nL, bm_graph* out) {
+                      int nprobe, const int* fixed_lm, long long nL, bm_graph* out, const GraphIndex* gidx = nullptr,
+                      int ef = 0, long long max_visits = 0) {
     std::memset(out, 0, sizeof(*out));
     int S = opt.batch;
     if (S == 0) S = 8192;
@@ -1181,12 +1206,12 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
     const double eps2 = (double)eps * (double)eps;
     // automatic path: the greedy starts on the split and picks its path after the
     // first step (greedy_drive)
-    const bool auto_switch = opt.path == BM_PATH_TC_AUTO && ivf == nullptr && fixed_lm == nullptr;
+    const bool auto_switch = opt.path == BM_PATH_TC_AUTO && ivf == nullptr && gidx == nullptr && fixed_lm == nullptr;
     // fixed landmarks sweep once: the automatic path and fp16 take the bf16 split
     const int req = (opt.path == BM_PATH_TC_AUTO || (fixed_lm && opt.path == BM_PATH_TC_FP16))
                         ? (int)BM_PATH_TC_SPLIT3 : opt.path;
-    const bool tc = is_tc_path(req) && ivf == nullptr;
-    int path = ivf ? (int)BM_PATH_FP32 : req;
+    const bool tc = is_tc_path(req) && ivf == nullptr && gidx == nullptr;
+    int path = (ivf || gidx) ? (int)BM_PATH_FP32 : req;
     Timer tm(s);
     tm.mark();  // 0
     SweepTimer stimer(s);
@@ -1201,7 +1226,7 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
     double dist_err = 0.0;
     {
         Arena ar(&opt, s);
-        const float* dX = ivf ? X : stage_input(X, n, d, host_io, ar, s, &rs);
+        const float* dX = (ivf || gidx) ? X : stage_input(X, n, d, host_io, ar, s, &rs);
         if (rs != BM_OK) return rs;
         int* landmarks = nullptr;
         long long* offsets = nullptr;
@@ -1282,6 +1307,9 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
                     sd.ivf = ivf;
                     sd.ivf_phi_perm = pperm.phi;
                     sd.nprobe = nprobe;
+                    sd.gidx = gidx;
+                    sd.gidx_ef = ef;
+                    sd.gidx_max_visits = max_visits;
                     rs = sweep_stage(sd, st, path, so, &st->mem_count, kErrHitOverflow, false, sms, stimer, s, ar);
                     if (rs != BM_OK) return rs;
                     rs = read_state(st, hs, fin, s);
@@ -1314,7 +1342,7 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
                     int path_used = path;
                     rs = greedy_pass(px, eps2, path, auto_switch, S, ar, s, st, hs, step_cap, mem_cap, &retry,
                                      &landmarks, &mem_keys, fin, stimer, ivf, ivf ? pperm.phi : nullptr, nprobe,
-                                     &path_used);
+                                     &path_used, gidx, ef, max_visits);
                     if (rs != BM_OK) return rs;
                     path = path_used;
                     if (!retry) break;
@@ -1360,6 +1388,7 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
     g.stats.kernel_launches = g_kernel_launches - launches0;
     g.stats.recheck_rate = fin.tile_pairs ? (double)fin.band_pairs / (double)fin.tile_pairs : 0.0;
     g.stats.dist_max_rel_err = dist_err;
+    g.stats.truncated = fin.gidx_truncated;
     *out = g;
     return BM_OK;
 }
@@ -2232,3 +2261,209 @@ bm_status bm_build_ivf(const bm_ivf* idx, float eps, int32_t nprobe, const int32
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ graph index
+struct bm_gidx {
+    bm::GraphIndex gx;
+};
+
+namespace {
+
+void free_gidx(bm_gidx* h) {
+    if (!h) return;
+    GraphIndex& gx = h->gx;
+    void* bufs[] = {gx.adj_off, gx.adj, gx.owned_x};
+    for (void* b : bufs) device_free(&gx.opt, (cudaStream_t)gx.opt.stream, b);
+    delete h;
+}
+
+}  // namespace
+
+bm_status bm_gidx_build(const float* X, int64_t n, int32_t d, int32_t M, int32_t n_entries, const bm_options* opt_in,
+                        bm_gidx** out) {
+    if (!out) return fail(BM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    bm_options opt;
+    bm_options_init(&opt);
+    if (opt_in) opt = *opt_in;
+    bm_status vs = validate_points(X, n, d, "X");
+    if (vs != BM_OK) return vs;
+    if (n < 2) return fail(BM_ERR_ARG, "the graph index needs at least two points");
+    if (M < 1 || M >= n || M > 1023) return fail(BM_ERR_ARG, "M must be in [1, min(n - 1, 1023)]");
+    if (n_entries == 0) n_entries = (int32_t)std::min<int64_t>(n, 64);
+    if (n_entries < 1 || n_entries > n) return fail(BM_ERR_ARG, "n_entries must be in [1, n]");
+    vs = check_device(opt.path);
+    if (vs != BM_OK) return vs;
+    cudaStream_t s = (cudaStream_t)opt.stream;
+    bm_gidx* h = new (std::nothrow) bm_gidx;
+    if (!h) return fail(BM_ERR_NOMEM, "index handle");
+    GraphIndex& gx = h->gx;
+    gx.n = n;
+    gx.d = d;
+    gx.M = M;
+    gx.E = n_entries;
+    gx.opt = opt;
+    gx.opt.host_io = 0;
+    gx.opt.want_dists = 0;
+    std::vector<void*> held;
+    auto bail = [&](bm_status st, const std::string& msg) {
+        free_gidx(h);
+        return fail(st, msg);
+    };
+#define PALLOC(ptr, type, count)                                                                  \
+    do {                                                                                          \
+        ptr = (type*)persistent_alloc(gx.opt, sizeof(type) * (size_t)(count), held);              \
+        if (!ptr) return bail(BM_ERR_NOMEM, "allocation of the index's " #ptr " failed");          \
+    } while (0)
+#define PTRY(expr)                                                                                \
+    do {                                                                                          \
+        cudaError_t e__ = (expr);                                                                 \
+        if (e__ != cudaSuccess) {                                                                 \
+            cudaGetLastError();                                                                   \
+            return bail(BM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e__));         \
+        }                                                                                         \
+    } while (0)
+    {
+        Arena ar(&opt, s);
+        if (opt.host_io) {
+            PALLOC(gx.owned_x, float, n * d);
+            PTRY(cudaMemcpyAsync(gx.owned_x, X, sizeof(float) * n * d, cudaMemcpyHostToDevice, s));
+            gx.X = gx.owned_x;
+        } else {
+            gx.X = X;
+        }
+        // the M + 1 nearest points of every row (itself included): per-row radius from the
+        // sampled bound, exact range query, then the M nearest others by (D, id)
+        const int k = M + 1;
+        long long target = std::max<long long>(8LL * k, n / 16);
+        target = std::max<long long>(std::min<long long>(target, 65536), k);
+        const long long stride = target >= n ? 1 : n / target;
+        const long long sN = (n + stride - 1) / stride;
+        double* rho = (double*)ar.get(sizeof(double) * n);
+        unsigned long long* rmax = (unsigned long long*)ar.get(sizeof(unsigned long long));
+        int* bad = (int*)ar.get(sizeof(int));
+        if (!rho || !rmax || !bad) return bail(BM_ERR_NOMEM, "graph index scratch");
+        PTRY(cudaMemsetAsync(rmax, 0, sizeof(unsigned long long), s));
+        PTRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
+        PTRY(launch_knn_bound(gx.X, n, d, stride, sN, k, rho, rmax, bad, s));
+        int hbad = 0;
+        unsigned long long hmax = 0;
+        PTRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PTRY(cudaMemcpyAsync(&hmax, rmax, sizeof(hmax), cudaMemcpyDeviceToHost, s));
+        PTRY(cudaStreamSynchronize(s));
+        if (hbad) return bail(BM_ERR_ARG, "input holds NaN or Inf, or squared distances that overflow float");
+        double r2_max;
+        std::memcpy(&r2_max, &hmax, sizeof(double));
+        bm_options o2 = gx.opt;
+        bm_csr csr;
+        const double expect = 1.5 * (double)n * (double)k * ((double)n / (double)sN) + 2.0 * (double)n;
+        const unsigned long long hint = (unsigned long long)std::min(expect, (double)n * (double)n);
+        bm_status rs = range_core(gx.X, n, d, gx.X, n, 1.0f, o2, nullptr, 0, nullptr, &csr, nullptr, rho, r2_max, hint);
+        if (rs != BM_OK) {
+            const std::string msg = g_last_error;
+            free_gidx(h);
+            return fail(rs, msg);
+        }
+        struct CsrGuard {
+            bm_csr* c;
+            const bm_options* o;
+            ~CsrGuard() { bm_csr_free(c, o); }
+        } guard{&csr, &o2};
+        const long long nnz = csr.nnz;
+        double* D = (double*)ar.get(sizeof(double) * std::max<long long>(nnz, 1));
+        double* DM = (double*)ar.get(sizeof(double) * n);
+        int* nbr = (int*)ar.get(sizeof(int) * n * M);
+        if (!D || !DM || !nbr) return bail(BM_ERR_NOMEM, "graph index scratch");
+        PTRY(launch_knn_select(gx.X, d, (const long long*)csr.offsets, n, csr.ids, nnz, D, M, nullptr, bad, s, true,
+                               DM));
+        PTRY(launch_knn_ids((const long long*)csr.offsets, csr.ids, D, DM, n, M, nbr, bad, s));
+        // undirected adjacency: arcs and their reverses, sorted, deduplicated, as CSR
+        const long long na = 2 * n * M;
+        unsigned long long* keys = (unsigned long long*)ar.get(sizeof(unsigned long long) * na);
+        unsigned long long* tmp = (unsigned long long*)ar.get(sizeof(unsigned long long) * na);
+        long long* flags = (long long*)ar.get(sizeof(long long) * na);
+        long long* pos = (long long*)ar.get(sizeof(long long) * (na + 1));
+        if (!keys || !tmp || !flags || !pos) return bail(BM_ERR_NOMEM, "graph index scratch");
+        PTRY(launch_arc_keys(nbr, n, M, keys, s));
+        unsigned long long* sorted = nullptr;
+        PTRY(radix_sort_u64(keys, tmp, na, digit_shifts(bits_for(n - 1), bits_for(n - 1)), ar, s, &sorted));
+        unsigned long long* uniq = sorted == keys ? tmp : keys;
+        PTRY(launch_unique_sorted(sorted, na, flags, pos, uniq, ar, s));
+        long long nu = 0;
+        PTRY(cudaMemcpyAsync(&nu, pos + na, sizeof(long long), cudaMemcpyDeviceToHost, s));
+        PTRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PTRY(cudaStreamSynchronize(s));
+        if (hbad) return bail(BM_ERR_CUDA, "graph index: a row's ball held fewer than M other points");
+        PALLOC(gx.adj_off, long long, n + 1);
+        PALLOC(gx.adj, int, std::max<long long>(nu, 1));
+        PTRY(launch_csr_from_sorted(uniq, nu, n, gx.adj_off, gx.adj, s));
+        gx.n_adj = nu;
+        PTRY(cudaStreamSynchronize(s));
+    }
+#undef PALLOC
+#undef PTRY
+    *out = h;
+    return BM_OK;
+}
+
+void bm_gidx_free(bm_gidx* idx) { free_gidx(idx); }
+
+bm_status bm_gidx_info(const bm_gidx* idx, int64_t* n, int32_t* d, int64_t* n_adj, const int64_t** adj_off,
+                       const int32_t** adj) {
+    if (!idx) return fail(BM_ERR_ARG, "index is NULL");
+    const GraphIndex& gx = idx->gx;
+    if (n) *n = gx.n;
+    if (d) *d = gx.d;
+    if (n_adj) *n_adj = gx.n_adj;
+    if (adj_off) *adj_off = (const int64_t*)gx.adj_off;
+    if (adj) *adj = gx.adj;
+    return BM_OK;
+}
+
+static bm_status validate_search(int32_t ef, int64_t* max_visits) {
+    if (ef < 1 || ef > 256) return fail(BM_ERR_ARG, "ef must be in [1, 256]");
+    if (*max_visits == 0) *max_visits = 4096;
+    if (*max_visits < 1 || *max_visits > (1LL << 24)) return fail(BM_ERR_ARG, "max_visits must be in [1, 2^24]");
+    return BM_OK;
+}
+
+bm_status bm_gidx_range_query(const bm_gidx* idx, const float* Q, int64_t m, float eps, int32_t ef,
+                              int64_t max_visits, const bm_options* opt_in, bm_csr* out, bm_stats* stats) {
+    if (!out) return fail(BM_ERR_ARG, "out is NULL");
+    std::memset(out, 0, sizeof(*out));
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (!idx) return fail(BM_ERR_ARG, "index is NULL");
+    bm_options opt;
+    bm_options_init(&opt);
+    if (opt_in) opt = *opt_in;
+    const GraphIndex& gx = idx->gx;
+    bm_status vs = validate_points(Q, m, gx.d, "Q");
+    if (vs == BM_OK) vs = validate_eps(eps);
+    if (vs == BM_OK) vs = validate_search(ef, &max_visits);
+    if (vs != BM_OK) return vs;
+    vs = check_device(opt.path);
+    if (vs != BM_OK) return vs;
+    return range_core(gx.X, gx.n, gx.d, Q, m, eps, opt, nullptr, 0, nullptr, out, stats, nullptr, 0.0, 0, &gx, ef,
+                      max_visits);
+}
+
+bm_status bm_build_gidx(const bm_gidx* idx, float eps, int32_t ef, int64_t max_visits, const int32_t* landmarks,
+                        int64_t n_landmarks, const bm_options* opt_in, bm_graph* out) {
+    if (!out) return fail(BM_ERR_ARG, "out is NULL");
+    std::memset(out, 0, sizeof(*out));
+    if (!idx) return fail(BM_ERR_ARG, "index is NULL");
+    bm_options opt;
+    bm_options_init(&opt);
+    if (opt_in) opt = *opt_in;
+    const GraphIndex& gx = idx->gx;
+    bm_status vs = validate_eps(eps);
+    if (vs == BM_OK) vs = validate_search(ef, &max_visits);
+    if (vs != BM_OK) return vs;
+    if (landmarks && (n_landmarks < 0 || n_landmarks > gx.n)) return fail(BM_ERR_ARG, "n_landmarks out of range");
+    vs = validate_batch(opt.batch, 8192);
+    if (vs != BM_OK) return vs;
+    vs = check_device(opt.path);
+    if (vs != BM_OK) return vs;
+    return build_graph(gx.X, gx.n, gx.d, eps, opt, nullptr, 0, landmarks, landmarks ? n_landmarks : 0, out, &gx, ef,
+                       max_visits);
+}

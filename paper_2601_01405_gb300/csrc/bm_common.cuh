@@ -42,6 +42,8 @@ struct DeviceState {
     long long step_start_pos;        // scan_pos at the start of the current greedy step
     int s_cur;                       // candidates requested by the current step
     int s_next;                      // candidates the next step requests (adapted to the survival rate)
+    int gidx_truncated;              // a graph-index search stopped at its visit cap
+    int pad1;
 };
 
 // Where a distance tile delivers its (row, point) hits.

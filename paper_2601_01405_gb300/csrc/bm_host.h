@@ -105,6 +105,7 @@ __host__ __device__ double band_halfwidth_core(int path, int d, int d_pad, doubl
 cudaError_t launch_set_aug_delta(const DeviceState* st, Prepared& p, cudaStream_t s);
 
 struct IvfIndex;
+struct GraphIndex;
 
 // tile_fp32.cu
 struct SweepDesc {
@@ -123,6 +124,10 @@ struct SweepDesc {
     int* ivf_probes_out = nullptr;   // optional: where to leave each row's probed cells
     // per-row squared radius (k-NN sweeps): the band recheck decides D < row_eps2[row]
     const double* row_eps2 = nullptr;
+    // graph-index mode: the rows' balls are searched through the proximity graph
+    const GraphIndex* gidx = nullptr;
+    int gidx_ef = 0;
+    long long gidx_max_visits = 0;
 };
 cudaError_t launch_sweep_fp32(const SweepDesc& s, cudaStream_t stream);
 
@@ -240,8 +245,11 @@ cudaError_t launch_knn_bound(const float* X, long long n, int d, long long strid
                              unsigned long long* rho_max_bits, int* bad, cudaStream_t st);
 // Pass 3: D[e] = FP64 squared distance of CSR entry e to its row's point X[row]; kdist[r]
 // = sqrt of the k-th smallest D of row r (*bad |= 2 when a row holds fewer than k).
+// exclude_self: rank among the entries other than the row's own point; kD (optional):
+// the k-th smallest squared distance itself.
 cudaError_t launch_knn_select(const float* X, int d, const long long* offsets, long long rows, const int* ids,
-                              long long nnz, double* D, int k, double* kdist, int* bad, cudaStream_t st);
+                              long long nnz, double* D, int k, double* kdist, int* bad, cudaStream_t st,
+                              bool exclude_self = false, double* kD = nullptr);
 
 // fps.cu: farthest point sampling (Sec. 2.2), one kernel per landmark inside a graph
 // WHILE loop (the last block to finish a pass appends the landmark and sets the loop
@@ -265,6 +273,32 @@ cudaError_t launch_finite_check(const float* X, long long count, int* bad, cudaS
 // *bad |= 1 for an id outside [0, n), |= 2 for a non-finite f.
 cudaError_t launch_color(const long long* offsets, const int* ids, long long rows, const float* f, long long n, int stat,
                          double* out, int* bad, cudaStream_t s);
+
+// gidx.cu: the proximity-graph index (Sec. 5.4, graph-based non-exhaustive search).
+struct GraphIndex {
+    long long n = 0;
+    int d = 0;
+    int M = 0;                        // nearest neighbours per point before symmetrisation
+    int E = 0;                        // entry points floor(t n / E), t < E
+    const float* X = nullptr;         // the indexed points (device)
+    long long* adj_off = nullptr;     // n + 1
+    int* adj = nullptr;               // undirected adjacency, ascending per node
+    long long n_adj = 0;
+    bm_options opt;                   // allocator of the index's buffers
+    float* owned_x = nullptr;         // device copy of X when built from host memory
+};
+// nbr[r M + t]: row r's M nearest other points (ball entries with D < DM, then D == DM in id order)
+cudaError_t launch_knn_ids(const long long* offsets, const int* ids, const double* D, const double* DM, long long rows,
+                           int M, int* nbr, int* bad, cudaStream_t s);
+cudaError_t launch_arc_keys(const int* nbr, long long n, int M, unsigned long long* keys, cudaStream_t s);
+// out = the distinct keys of the sorted array keys (count at pos[n] after the scan)
+cudaError_t launch_unique_sorted(const unsigned long long* keys, long long n, long long* flags, long long* pos,
+                                 unsigned long long* out, Arena& ar, cudaStream_t s);
+// rows of sd (candidates or queries) searched through gx; in-range visited points are
+// emitted as (row << 32 | point) keys (count, cap; greedy bookkeeping from sd.sink)
+cudaError_t launch_graph_search(const SweepDesc& sd, const GraphIndex& gx, DeviceState* st, unsigned long long* count,
+                                unsigned long long cap, int overflow_bit, bool greedy, Arena& ar, cudaStream_t s,
+                                unsigned long long* visits, int* truncated);
 
 // graph.cu
 cudaError_t launch_csr_from_sorted(const unsigned long long* keys, long long nnz, long long rows,

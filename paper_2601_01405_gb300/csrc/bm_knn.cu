@@ -153,19 +153,21 @@ __global__ void __launch_bounds__(256) csr_sqdist_kernel(const float* __restrict
 // Pass 3: one block per row (grid-stride), the k-th smallest of the row's FP64
 // values by an 8-bit radix select on their bit patterns (eight passes, high
 // digit first).  kdist[r] = sqrt of it.  A row with fewer than k values sets *bad.
-__global__ void __launch_bounds__(256) kth_select_kernel(const double* __restrict__ D,
+__global__ void __launch_bounds__(256) kth_select_kernel(const double* __restrict__ D, const int* __restrict__ ids,
                                                          const long long* __restrict__ offsets, long long rows, int k,
-                                                         double* __restrict__ kdist, int* bad) {
+                                                         int exclude_self, double* __restrict__ kdist,
+                                                         double* __restrict__ kD, int* bad) {
     __shared__ unsigned hist[256];
     __shared__ unsigned long long s_prefix;
     __shared__ int s_rank;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
         const long long e0 = offsets[r], e1 = offsets[r + 1];
-        if (e1 - e0 < k) {
+        if (e1 - e0 < k + exclude_self) {
             if (threadIdx.x == 0) {
                 atomicOr(bad, 2);
-                kdist[r] = -1.0;
+                if (kdist) kdist[r] = -1.0;
+                if (kD) kD[r] = -1.0;
             }
             continue;
         }
@@ -179,6 +181,7 @@ __global__ void __launch_bounds__(256) kth_select_kernel(const double* __restric
             __syncthreads();
             const unsigned long long prefix = s_prefix;
             for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+                if (exclude_self && ids[e] == (int)r) continue;
                 const unsigned long long key = (unsigned long long)__double_as_longlong(D[e]);
                 if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
             }
@@ -215,7 +218,11 @@ __global__ void __launch_bounds__(256) kth_select_kernel(const double* __restric
             mask |= 255ull << shift;
             __syncthreads();
         }
-        if (threadIdx.x == 0) kdist[r] = __dsqrt_rn(__longlong_as_double((long long)s_prefix));
+        if (threadIdx.x == 0) {
+            const double v = __longlong_as_double((long long)s_prefix);
+            if (kdist) kdist[r] = __dsqrt_rn(v);
+            if (kD) kD[r] = v;
+        }
         __syncthreads();
     }
 }
@@ -250,7 +257,8 @@ cudaError_t launch_knn_bound(const float* X, long long n, int d, long long strid
 }
 
 cudaError_t launch_knn_select(const float* X, int d, const long long* offsets, long long rows, const int* ids,
-                              long long nnz, double* D, int k, double* kdist, int* bad, cudaStream_t st) {
+                              long long nnz, double* D, int k, double* kdist, int* bad, cudaStream_t st,
+                              bool exclude_self, double* kD) {
     if (rows == 0) return cudaSuccess;
     const int vec4 = (d % 4 == 0) && ((uintptr_t)X % 16 == 0);
     long long blocks = (nnz + 255) / 256;
@@ -263,7 +271,7 @@ cudaError_t launch_knn_select(const float* X, int d, const long long* offsets, l
     if (e != cudaSuccess) return e;
     long long sb = rows < (long long)device_sm_count() * 8 ? rows : (long long)device_sm_count() * 8;
     note_launch();
-    kth_select_kernel<<<(unsigned)sb, 256, 0, st>>>(D, offsets, rows, k, kdist, bad);
+    kth_select_kernel<<<(unsigned)sb, 256, 0, st>>>(D, ids, offsets, rows, k, exclude_self ? 1 : 0, kdist, kD, bad);
     return cudaGetLastError();
 }
 
