@@ -71,8 +71,9 @@ typedef enum {
                             * the ratio of the two proven band widths predicts the fp16 band, and the greedy
                             * continues on TC_FP16 when that prediction is below 5e-5 of the tile pairs,
                             * returning to TC_SPLIT3 (once) if the measured fp16 band exceeds 2e-4;
-                            * bm_build_batched: TC_FP16; range queries: TC_SPLIT3.  stats.path reports the
-                            * path the build finished on. */
+                            * bm_build_batched: the same first-step choice per instance, made before the
+                            * graph (no return inside it); range queries: TC_SPLIT3.  stats.path reports
+                            * the path the build finished on. */
 } bm_path;
 
 /* Allocation callbacks: return device (or, for host outputs, ignored) memory
@@ -207,6 +208,9 @@ typedef struct {
     int64_t n;
     int32_t d;
     float eps;
+    int32_t batch;       /* largest greedy batch of this instance, multiple of 32 in [32, 2048];
+                            0 = opt->batch (an autotuned per-(d, n) table fills it) */
+    int32_t reserved0;
 } bm_instance;
 
 /* Many independent Ball Mapper builds (each exactly bm_build's result: Sec. 2.2
@@ -220,7 +224,12 @@ typedef struct {
  * is finished by the host-driven loop with larger buffers (same result).
  *   inst:     count instances (count >= 0); each validated like bm_build.
  *   opt:      stream, path, host_io, skip_edges, alloc/free as for bm_build;
- *             batch = largest candidate batch per step (0 = 1024).
+ *             batch = largest candidate batch per step of instances whose own
+ *             batch is 0 (0 = 1024).  With the automatic path every instance's
+ *             first greedy step runs on the bf16 split before the graph, and the
+ *             instance continues on fp16 inside the graph when its measured band
+ *             predicts a small fp16 band (the rule of bm_build's automatic path);
+ *             stats.path reports each instance's choice.
  *   outs:     count graphs, caller-owned array; each filled like bm_build's out.
  *             stats.ms_total of every instance is the time of the whole call,
  *             ms_prep that of the prep of all instances, ms_greedy that of the

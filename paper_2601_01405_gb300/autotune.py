@@ -1,4 +1,4 @@
-"""Autotuner for the tensor-core distance tiles.
+"""Autotuner for the tensor-core distance tiles and the batched greedy's batch sizes.
 
 For each point dimension d it times every compiled tile shape (and each valid
 padding of d for it) on the sweep of a greedy step: ``rows`` query rows against
@@ -11,6 +11,13 @@ Timing is the device time of the tile launches only (the library's sweep
 events), the median over ``reps`` calls after one warm-up call.
 
     python -m paper_2601_01405_gb300.autotune --dims 8 32 64 96 128 --out tiles.json
+
+Greedy batch sizes (``--batches``): for each dimension and range of n of the batched
+workload recipe, a set of instances is built with bm_build_batched at every candidate
+largest batch (candidates per greedy step), and the fastest is kept; ``batches_for``
+then gives every instance of a batched call its tuned batch from that table.
+
+    python -m paper_2601_01405_gb300.autotune --batches --out batches.json
 """
 from __future__ import annotations
 
@@ -85,6 +92,56 @@ def tune(dims: Iterable[int], n: int = 200_000, rows: int = 2048, reps: int = 5,
     return out
 
 
+BATCH_CHOICES = (128, 256, 512, 1024, 2048)
+N_BUCKETS = ((1000, 5000), (5000, 30000), (30000, 200000))
+
+
+def tune_batches(dims: Iterable[int] = (8, 32, 96), buckets=N_BUCKETS, count: int = 12,
+                 choices=BATCH_CHOICES, reps: int = 3, seed: int = 0) -> Dict[int, list]:
+    """{d: [{"n_lo", "n_hi", "best", "ms": {batch: ms}}, ...]}: per dimension and range of n,
+    the largest greedy batch with the shortest bm_build_batched time (CUDA events, median of
+    reps after one warm-up) on `count` instances of the batched recipe in that range."""
+    import torch
+    from . import binding, workloads
+    out: Dict[int, list] = {}
+    for d in dims:
+        rows = []
+        for lo, hi in buckets:
+            inst = workloads.batched_instances(count=count, seed=seed + 7 * d + lo, n_lo=lo, n_hi=hi, dims=(d,))
+            dev = [(torch.from_numpy(i.x).cuda(), i.eps) for i in inst]
+            ms = {}
+            for b in choices:
+                binding.bm_build_batched(dev, batch=b)
+                torch.cuda.synchronize()
+                t = []
+                for _ in range(reps):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    binding.bm_build_batched(dev, batch=b)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    t.append(e0.elapsed_time(e1))
+                ms[b] = statistics.median(t)
+            rows.append({"n_lo": lo, "n_hi": hi, "best": min(ms, key=ms.get), "ms": ms})
+        out[d] = rows
+    return out
+
+
+def batches_for(table: Dict, instances) -> List[int]:
+    """Per-instance largest batch from a tune_batches table: the entry of the nearest tuned
+    dimension whose range of n holds the instance (the nearest range otherwise)."""
+    dims = sorted(int(k) for k in table)
+    res = []
+    for X, _ in instances:
+        n, d = int(X.shape[0]), int(X.shape[1])
+        dd = min(dims, key=lambda v: (abs(v - d), v))
+        rows = table[dd] if dd in table else table[str(dd)]
+        row = min(rows, key=lambda r: 0 if r["n_lo"] <= n < r["n_hi"] else min(abs(n - r["n_lo"]), abs(n - r["n_hi"])))
+        res.append(int(row["best"]))
+    return res
+
+
 def install(table: Dict) -> None:
     """Install the best configuration of each d of a tune() result or saved file."""
     from . import binding
@@ -110,7 +167,16 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--out", default=None)
     ap.add_argument("--path", choices=["tc", "tc16"], default="tc", help="tensor-core representation to time")
+    ap.add_argument("--batches", action="store_true", help="tune the batched greedy's batch sizes instead")
     a = ap.parse_args(argv)
+    if a.batches:
+        table = tune_batches(a.dims if a.dims != [8, 32, 64, 96, 128] else (8, 32, 96), reps=a.reps)
+        if a.out:
+            with open(a.out, "w") as f:
+                json.dump({str(d): v for d, v in table.items()}, f, indent=1)
+        for d, rows in table.items():
+            print(json.dumps({"d": d, "rows": rows}))
+        return 0
     table = tune(a.dims, a.n, a.rows, a.reps, path=a.path)
     if a.out:
         save(table, a.out)

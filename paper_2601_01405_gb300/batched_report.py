@@ -29,6 +29,9 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=0, help="largest candidate batch per step (0 = library default)")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
+    ap.add_argument("--tune-batches", action="store_true",
+                    help="also time the batched call with per-instance batches from autotune.tune_batches")
+    ap.add_argument("--batches-table", default=None, help="a saved autotune --batches table to use instead")
     a = ap.parse_args(argv)
 
     import torch
@@ -64,6 +67,20 @@ def main(argv=None):
     res_b, ms_b = timed(batched)
     res_s, ms_s = timed(singles)
     mismatches = [k for k, (x, y) in enumerate(zip(res_b, res_s)) if not _same(x, y)]
+    tuned = None
+    if a.tune_batches or a.batches_table:
+        from paper_2601_01405_gb300 import autotune
+        t1 = time.perf_counter()
+        table = autotune.load(a.batches_table) if a.batches_table else autotune.tune_batches()
+        tune_s = time.perf_counter() - t1
+        per = autotune.batches_for(table, dev)
+        res_t, ms_t = timed(lambda: binding.bm_build_batched(dev, path=a.path, batch=a.batch, batches=per))
+        mismatches += [k for k, (x, y) in enumerate(zip(res_t, res_s)) if not _same(x, y)]
+        tuned = {"batched_ms": ms_t, "speedup_vs_single": min(ms_s) / min(ms_t),
+                 "speedup_vs_untuned": min(ms_b) / min(ms_t), "tune_s": tune_s,
+                 "batch_histogram": {str(b): per.count(b) for b in sorted(set(per))},
+                 "table": {str(d): [(r["n_lo"], r["n_hi"], r["best"]) for r in rows] for d, rows in table.items()}}
+    paths = [int(r["stats"]["path"]) for r in res_b]
     evals = sum(int(r["stats"]["distance_evals"]) for r in res_s)
     L = sum(int(r["landmarks"].numel()) for r in res_s)
     nnz = sum(int(r["ids"].numel()) for r in res_s)
@@ -83,6 +100,9 @@ def main(argv=None):
         "batched_breakdown_ms": ({k: res_b[0]["stats"][k] for k in ("ms_total", "ms_prep", "ms_greedy", "ms_members")}
                                  if res_b else {}),
         "kernels_batched": launches_b, "kernels_single": launches_s,
+        "instance_paths": {"split": paths.count(binding.BM_PATH_TC_SPLIT3), "fp16": paths.count(binding.BM_PATH_TC_FP16),
+                           "fp32": paths.count(binding.BM_PATH_FP32)},
+        "tuned_batches": tuned,
         "mismatched_instances": mismatches, "generate_s": gen_s}))
     return 0 if not mismatches else 1
 

@@ -62,7 +62,8 @@ class bm_graph(ctypes.Structure):
 
 
 class bm_instance(ctypes.Structure):
-    _fields_ = [("X", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int32), ("eps", ctypes.c_float)]
+    _fields_ = [("X", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int32), ("eps", ctypes.c_float),
+                ("batch", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
 
 class bm_tile_config(ctypes.Structure):
@@ -468,11 +469,13 @@ def bm_occupancy_eps(X, k: int, path: str = "auto", stream=None):
     return eps.value, st.as_dict()
 
 
-def bm_build_batched(instances, path: str = "auto", batch: int = 0, stream=None, skip_edges: bool = False):
+def bm_build_batched(instances, path: str = "auto", batch: int = 0, stream=None, skip_edges: bool = False,
+                     batches=None):
     """Many independent exact builds in one call; the greedy loops of all instances
     run inside one CUDA graph.  instances: sequence of (X, eps), all CUDA tensors
     (results as torch tensors) or all host arrays (results as numpy arrays).
-    Returns a list of dicts shaped like bm_build's."""
+    batches: optional per-instance largest greedy batch (0 = `batch`), e.g. from
+    autotune.batches_for.  Returns a list of dicts shaped like bm_build's."""
     lib = load()
     ins = [_as_input(X) for X, _ in instances]
     hosts = {h for _, _, _, _, h in ins}
@@ -480,12 +483,15 @@ def bm_build_batched(instances, path: str = "auto", batch: int = 0, stream=None,
         raise ValueError("instances must all be device tensors or all host arrays")
     host = hosts.pop() if hosts else False
     count = len(ins)
+    if batches is not None and len(batches) != count:
+        raise ValueError("batches needs one entry per instance")
     arr_in = (bm_instance * max(count, 1))()
     for k, ((px, n, d, _, _), (_, eps)) in enumerate(zip(ins, instances)):
         arr_in[k].X = px
         arr_in[k].n = n
         arr_in[k].d = d
         arr_in[k].eps = float(eps)
+        arr_in[k].batch = int(batches[k]) if batches is not None else 0
     outs = (bm_graph * max(count, 1))()
     statuses = (ctypes.c_int32 * max(count, 1))()
     if host:
@@ -584,8 +590,11 @@ class IvfIndex:
     """Inverted-file index over device points X (bm_ivf_train).  The index refers to X,
     which must stay alive and unchanged; its own buffers come from torch's allocator."""
 
-    def __init__(self, X, nlist: int = 1024, iters: int = 20, sample: int = 0, seed: int = 0):
+    def __init__(self, X, nlist: int = 1024, iters: int = 20, sample: int = 0, seed: int = 0, path: str = "auto"):
+        """path: the scan's arithmetic for queries and builds (auto / tc: bf16-split tensor-core
+        tiles over the cells laid out in whole tiles; fp32: CUDA-core tiles)."""
         import torch
+        self._path = path
         self._lib = load()
         if not _is_torch_cuda(X):
             raise ValueError("X must be a CUDA tensor")
@@ -608,7 +617,7 @@ class IvfIndex:
         self.cell_of = self._alloc.peek(co.value, self.n, torch.int32)
         self.centroids = self._alloc.peek(ce.value, self.nlist * self.d, torch.float32).view(self.nlist, self.d)
 
-    def range_query(self, Q, eps: float, nprobe: int, want_dists: bool = False):
+    def range_query(self, Q, eps: float, nprobe: int, want_dists: bool = False, path: Optional[str] = None):
         """(offsets, ids, probes, stats): conservative range sets over the nprobe nearest cells;
         with want_dists, (offsets, ids, probes, stats, dists)."""
         import torch
@@ -617,7 +626,8 @@ class IvfIndex:
             raise ValueError("Q must be a CUDA tensor")
         probes = torch.empty((m, nprobe), dtype=torch.int32, device=kq.device)
         alloc = _TorchAllocator(kq.device)
-        opt = _options(self._lib, "fp32", 0, _current_stream(kq.device), False, alloc, want_dists=want_dists)
+        opt = _options(self._lib, path or self._path, 0, _current_stream(kq.device), False, alloc,
+                       want_dists=want_dists)
         out = bm_csr()
         st = bm_stats()
         _check(self._lib, self._lib.bm_ivf_range_query(self._h, pq, m, ctypes.c_float(eps), int(nprobe),
@@ -629,13 +639,15 @@ class IvfIndex:
             res = res + (alloc.tensor(out.dists, out.nnz, torch.float32),)
         return res
 
-    def build(self, eps: float, nprobe: int, landmarks=None, batch: int = 0, want_dists: bool = False):
+    def build(self, eps: float, nprobe: int, landmarks=None, batch: int = 0, want_dists: bool = False,
+              path: Optional[str] = None):
         """Ball Mapper through the index: fixed-landmark mode (landmarks = CUDA int32 tensor)
         or end-to-end mode (landmarks None)."""
         import torch
         dev = self._X.device
         alloc = _TorchAllocator(dev)
-        opt = _options(self._lib, "fp32", batch, _current_stream(dev), False, alloc, want_dists=want_dists)
+        opt = _options(self._lib, path or self._path, batch, _current_stream(dev), False, alloc,
+                       want_dists=want_dists)
         g = bm_graph()
         lm_ptr, nl = None, 0
         if landmarks is not None:

@@ -405,6 +405,85 @@ bm_status ivf_sweep(SweepDesc& sd, DeviceState* st, Arena& ar, bool greedy, cuda
     return BM_OK;
 }
 
+// The inverted-file scan on the tensor-core tiles: queries grouped by probed cell, both
+// sides laid out by cell in whole tiles, the tile kernel in table mode (one item = a
+// cell's point tile against a group of its query tiles), then the usual compaction and
+// FP64 recheck of the band pairs (keys hold query and point ids).
+bm_status ivf_sweep_tc(SweepDesc& sd, DeviceState* st, int path, SweepOut& o, unsigned long long* count,
+                       int overflow_bit, bool greedy, int sms, SweepTimer& stimer, cudaStream_t s, Arena& ar) {
+    const IvfIndex& ix = *sd.ivf;
+    const Prepared& bp = *sd.ivf_b_pad;
+    const long long rows_max = sd.a_rows_max;
+    int* probes = sd.ivf_probes_out;
+    if (!probes) ALLOC(probes, int, std::max<long long>(rows_max * sd.nprobe, 1));
+    long long *cnt, *cq_off, *tile_off, *pa_off, *item_off;
+    int *cq_rows, *a_map;
+    ALLOC(cnt, long long, ix.nlist + 1);
+    ALLOC(cq_off, long long, ix.nlist + 1);
+    ALLOC(tile_off, long long, ix.nlist + 1);
+    ALLOC(pa_off, long long, ix.nlist + 1);
+    ALLOC(item_off, long long, ix.nlist + 1);
+    ALLOC(cq_rows, int, std::max<long long>(rows_max * sd.nprobe, 1));
+    TRY_CUDA(launch_probe_select(sd.a->x, rows_max, sd.a_rows_dev, ix, sd.nprobe, probes, s));
+    TRY_CUDA(launch_group_probes(probes, rows_max, sd.a_rows_dev, sd.nprobe, ix, cnt, cq_off, cq_rows, tile_off, ar,
+                                 s));
+    // padded query operands: every (query, probe) pair plus at most 127 padding rows per cell
+    Prepared apad = *sd.a;
+    apad.rows = rows_max * sd.nprobe + 127LL * ix.nlist;
+    ALLOC(apad.hi, __nv_bfloat16, apad.rows * apad.d_pad);
+    apad.lo = nullptr;
+    if (sd.a->lo) ALLOC(apad.lo, __nv_bfloat16, apad.rows * apad.d_pad);
+    ALLOC(apad.aug, __nv_bfloat16, apad.rows * 16);
+    ALLOC(a_map, int, apad.rows);
+    const int NT = bp.nt;
+    const long long bmax = ix.max_cell_tiles * (256 / NT);
+    const long long item_cap = bmax * ((rows_max * sd.nprobe / 128 + ix.nlist) / 16 + 1) + ix.npad / NT + 1;
+    TcItem* items;
+    ALLOC(items, TcItem, item_cap);
+    TRY_CUDA(launch_ivf_tc_layout(ix, NT, cq_off, cq_rows, *sd.a, apad, a_map, pa_off, cnt, items, item_off, ar, s));
+    SweepDesc sd2 = sd;
+    sd2.a = &apad;
+    sd2.b = &bp;
+    sd2.a_rows_max = apad.rows;
+    sd2.a_rows_dev = nullptr;
+    sd2.ivf = nullptr;
+    sd2.tc_items = items;
+    sd2.tc_items_count = item_off + ix.nlist;
+    sd2.tc_a_map = a_map;
+    sd2.tc_b_ids = ix.cell_ids;
+    sd2.sink.count = count;
+    sd2.sink.cap = o.cap;
+    sd2.sink.band_n = &st->band_n;
+    sd2.sink.band_cap = o.cap;
+    sd2.sink.keys = o.raw;
+    sd2.sink.band_keys = o.raw_band;
+    sd2.sink.seg_counts = o.seg_counts;
+    sd2.sink.band_seg_counts = o.band_seg_counts;
+    sd2.sink.seg_cap = o.cap / sms;
+    stimer.before();
+    int grid = 0;
+    bm_status rs = run_sweep(sd2, path, s, &grid);
+    stimer.after();
+    if (rs != BM_OK) return rs;
+    TRY_CUDA(launch_compact_segments(o.raw, o.raw_band, sd2.sink.seg_cap, o.seg_counts, o.band_seg_counts, grid, o.keys,
+                                     o.band, count, &st->band_n, st, overflow_bit, greedy, greedy, s));
+    TRY_CUDA(launch_band_recheck(st, o.band, o.cap, sd.a->x, ix.X, ix.d, sd.eps2, o.keys, count, o.cap, sd.sink,
+                                 greedy, overflow_bit, greedy, s));
+    ar.release(items);
+    ar.release(a_map);
+    ar.release(apad.aug);
+    ar.release(apad.lo);
+    ar.release(apad.hi);
+    ar.release(cq_rows);
+    ar.release(item_off);
+    ar.release(pa_off);
+    ar.release(tile_off);
+    ar.release(cq_off);
+    ar.release(cnt);
+    if (probes != sd.ivf_probes_out) ar.release(probes);
+    return BM_OK;
+}
+
 bm_status sweep_stage(SweepDesc& sd, DeviceState* st, int path, SweepOut& o, unsigned long long* count,
                       int overflow_bit, bool greedy, int sms, SweepTimer& stimer, cudaStream_t s, Arena& ar) {
     if (sd.gidx) {   // proximity-graph search: exact decisions on the visited points, no band
@@ -419,6 +498,9 @@ bm_status sweep_stage(SweepDesc& sd, DeviceState* st, int path, SweepOut& o, uns
         stimer.after();
         TRY_CUDA(e);
         return BM_OK;
+    }
+    if (sd.ivf && sd.ivf_b_pad) {   // inverted-file scan on the tensor-core tiles
+        return ivf_sweep_tc(sd, st, path, o, count, overflow_bit, greedy, sms, stimer, s, ar);
     }
     if (sd.ivf) {   // inverted-file scan: FP32 tiles over the probed cells, global counters
         sd.sink.count = count;
@@ -765,7 +847,8 @@ bm_status greedy_pass(Prepared& pts, double eps2, int path, bool auto_switch, in
                       DeviceState* st, HostState& hs, unsigned long long& step_cap, unsigned long long& mem_cap,
                       bool* retry, int** landmarks_out, unsigned long long** mem_keys_out, DeviceState& final_state,
                       SweepTimer& stimer, const IvfIndex* ivf, const float* phi_perm, int nprobe, int* path_used,
-                      const GraphIndex* gidx = nullptr, int ef = 0, long long max_visits = 0) {
+                      const GraphIndex* gidx = nullptr, int ef = 0, long long max_visits = 0,
+                      const Prepared* ivf_b_pad = nullptr) {
     *retry = false;
     GreedyCtx c;
     bm_status rs = greedy_setup(pts, eps2, path, S, ar, s, st, step_cap, mem_cap, ivf, phi_perm, nprobe, c);
@@ -773,6 +856,7 @@ bm_status greedy_pass(Prepared& pts, double eps2, int path, bool auto_switch, in
     c.sd.gidx = gidx;
     c.sd.gidx_ef = ef;
     c.sd.gidx_max_visits = max_visits;
+    c.sd.ivf_b_pad = ivf_b_pad;
     c.auto_switch = auto_switch;
     rs = greedy_drive(c, pts, ar, s, hs, step_cap, mem_cap, final_state, stimer, false);
     if (rs != BM_OK) return rs;
@@ -807,8 +891,9 @@ bm_status range_core(const float* X, long long n, int d, const float* Q, long lo
     // automatic path: a single sweep cannot change course, so range queries take the split
     const int req = (opt.path == BM_PATH_TC_AUTO || (row_r2 && opt.path == BM_PATH_TC_FP16))
                         ? (int)BM_PATH_TC_SPLIT3 : opt.path;
-    const bool tc = is_tc_path(req) && ivf == nullptr && gidx == nullptr;
-    const int path = (ivf || gidx) ? (int)BM_PATH_FP32 : req;
+    // the inverted file scans on the tensor cores unless the FP32 path is asked for
+    const bool tc = is_tc_path(req) && gidx == nullptr && !(ivf && row_r2);
+    const int path = gidx ? (int)BM_PATH_FP32 : (tc ? req : (ivf ? (int)BM_PATH_FP32 : req));
     Timer tm(s);
     tm.mark();
     SweepTimer stimer(s);
@@ -843,7 +928,9 @@ bm_status range_core(const float* X, long long n, int d, const float* Q, long lo
             Prepared px, pq;
             // inverted-file mode: the points enter the tiles in cell order
             const int prec = tc ? prec_for(path) : kPrecNone;
-            rs = prepare(ivf ? ivf->xperm : dX, n, d, eps2, false, prec, ar, &st->max_norm_bits, bad, s, px);
+            const float* bsrc = ivf ? (tc ? ivf->xpad : ivf->xperm) : dX;
+            const long long brows = (ivf && tc) ? ivf->npad : n;
+            rs = prepare(bsrc, brows, d, eps2, false, prec, ar, &st->max_norm_bits, bad, s, px);
             if (rs != BM_OK) return rs;
             rs = prepare(dQ, m, d, eps2, true, prec, ar, &st->max_norm_q_bits, bad, s, pq, row_r2);
             if (rs != BM_OK) return rs;
@@ -904,6 +991,7 @@ bm_status range_core(const float* X, long long n, int d, const float* Q, long lo
                 sd.gidx = gidx;
                 sd.gidx_ef = ef;
                 sd.gidx_max_visits = max_visits;
+                sd.ivf_b_pad = (ivf && tc) ? &px : nullptr;
                 rs = sweep_stage(sd, st, path, so, &st->hit_count, kErrHitOverflow, false, sms, stimer, s, ar);
                 if (rs != BM_OK) return rs;
                 rs = read_state(st, hs, h, s);
@@ -1210,8 +1298,8 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
     // fixed landmarks sweep once: the automatic path and fp16 take the bf16 split
     const int req = (opt.path == BM_PATH_TC_AUTO || (fixed_lm && opt.path == BM_PATH_TC_FP16))
                         ? (int)BM_PATH_TC_SPLIT3 : opt.path;
-    const bool tc = is_tc_path(req) && ivf == nullptr && gidx == nullptr;
-    int path = (ivf || gidx) ? (int)BM_PATH_FP32 : req;
+    const bool tc = is_tc_path(req) && gidx == nullptr;
+    int path = gidx ? (int)BM_PATH_FP32 : req;
     Timer tm(s);
     tm.mark();  // 0
     SweepTimer stimer(s);
@@ -1250,12 +1338,19 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
             Prepared px;
             rs = prepare(dX, n, d, eps2, false, tc ? prec_for(path) : kPrecNone, ar, &st->max_norm_bits, bad, s, px);
             if (rs != BM_OK) return rs;
-            // inverted-file mode: phi of the cell-ordered copy of the points for the scan
+            // inverted-file mode: the cell-ordered copy of the points for the scan (phi for the
+            // FP32 scan; the padded tensor-core operands otherwise)
             Prepared pperm;
-            if (ivf) {
+            if (ivf && !tc) {
                 rs = prepare(ivf->xperm, n, d, eps2, false, kPrecNone, ar, &st->max_norm_bits, bad, s, pperm);
                 if (rs != BM_OK) return rs;
             }
+            if (ivf && tc) {
+                rs = prepare(ivf->xpad, ivf->npad, d, eps2, false, prec_for(path), ar, &st->max_norm_bits, bad, s,
+                             pperm);
+                if (rs != BM_OK) return rs;
+            }
+            const Prepared* b_pad = (ivf && tc) ? &pperm : nullptr;
             int hbad = 0;
             unsigned hnorm = 0u;
             TRY_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1267,6 +1362,7 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
                 std::memcpy(&nx, &hnorm, sizeof(float));
                 rs = finish_prep(st, path, d, eps2, (double)eps, true, nx, &px, nullptr, s);
                 if (rs != BM_OK) return rs;
+                if (b_pad) TRY_CUDA(launch_set_aug_delta(st, pperm, s));
             }
             tm.mark();  // 1: prep done
             unsigned long long step_cap = (unsigned long long)std::min<long long>((long long)S * n, 1LL << 22);
@@ -1310,6 +1406,7 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
                     sd.gidx = gidx;
                     sd.gidx_ef = ef;
                     sd.gidx_max_visits = max_visits;
+                    sd.ivf_b_pad = b_pad;
                     rs = sweep_stage(sd, st, path, so, &st->mem_count, kErrHitOverflow, false, sms, stimer, s, ar);
                     if (rs != BM_OK) return rs;
                     rs = read_state(st, hs, fin, s);
@@ -1342,7 +1439,7 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
                     int path_used = path;
                     rs = greedy_pass(px, eps2, path, auto_switch, S, ar, s, st, hs, step_cap, mem_cap, &retry,
                                      &landmarks, &mem_keys, fin, stimer, ivf, ivf ? pperm.phi : nullptr, nprobe,
-                                     &path_used, gidx, ef, max_visits);
+                                     &path_used, gidx, ef, max_visits, b_pad);
                     if (rs != BM_OK) return rs;
                     path = path_used;
                     if (!retry) break;
@@ -1485,9 +1582,10 @@ bm_status build_batched(const bm_instance* inst, int count, const bm_options& op
     if (S < 32 || S > 2048 || S % 32) return fail(BM_ERR_ARG, "batch must be a multiple of 32 in [32, 2048]");
     cudaStream_t s = (cudaStream_t)opt.stream;
     const bool host_io = opt.host_io != 0;
-    // automatic path: the graph's loops cannot change course; the fp16 tiles win on
-    // typical batches (many small, well-separated instances)
-    const int path = opt.path == BM_PATH_TC_AUTO ? (int)BM_PATH_TC_FP16 : opt.path;
+    // automatic path: every instance starts on the split; its first step (run before the
+    // graph) decides whether its loop inside the graph runs on fp16
+    const bool auto_path = opt.path == BM_PATH_TC_AUTO;
+    const int path = auto_path ? (int)BM_PATH_TC_SPLIT3 : opt.path;
     const bool tc = is_tc_path(path);
     Timer tm(s);
     tm.mark();  // 0
@@ -1522,6 +1620,7 @@ bm_status build_batched(const bm_instance* inst, int count, const bm_options& op
         bm_status rs = batch_prep(it, inst[i], opt, tc, path, sts + i, bads + i, s);
         if (rs != BM_OK) return tag(i, rs);
     }
+    std::vector<float> norms(std::max(count, 1), 0.f);
     {
         std::vector<int> hbad(std::max(count, 1));
         std::vector<DeviceState> hs0(std::max(count, 1));
@@ -1535,21 +1634,51 @@ bm_status build_batched(const bm_instance* inst, int count, const bm_options& op
             if (it.n == 0) continue;
             float nx;
             std::memcpy(&nx, &hs0[i].max_norm_bits, sizeof(float));
+            norms[i] = nx;
             bm_status rs = finish_prep(it.st, path, it.d, it.eps2, (double)inst[i].eps, true, nx, &it.px, nullptr, s);
             if (rs != BM_OK) return tag(i, rs);
         }
     }
     tm.mark();  // 1: prep done
-    // 2. greedy buffers (the state starts zeroed: the first step requests 32 candidates)
+    // 2. greedy buffers (the state starts zeroed: the first step requests 32 candidates);
+    //    each instance's largest batch is its own (an autotuned table) or opt.batch
     for (int i = 0; i < count; ++i) {
         BatchItem& it = items[i];
         if (it.n == 0) continue;
+        const int Si = inst[i].batch ? inst[i].batch : S;
         it.step_cap = (unsigned long long)std::min<long long>(std::max<long long>(32 * it.n, 1LL << 16), 1LL << 22);
         if (tc) it.step_cap = std::max<unsigned long long>(it.step_cap, (unsigned long long)sms * 2048);
         it.mem_cap = (unsigned long long)std::max<long long>(4 * it.n, 1LL << 16);
-        bm_status rs = greedy_setup(it.px, it.eps2, path, S, *it.ar, s, it.st, it.step_cap, it.mem_cap, nullptr,
+        bm_status rs = greedy_setup(it.px, it.eps2, path, Si, *it.ar, s, it.st, it.step_cap, it.mem_cap, nullptr,
                                     nullptr, 0, it.gc);
         if (rs != BM_OK) return tag(i, rs);
+    }
+    // 2b. automatic path: the first step of every instance on the split, then each instance
+    //     picks its representation for the graph from its band (as greedy_drive's first step)
+    if (auto_path) {
+        for (int i = 0; i < count; ++i) {
+            BatchItem& it = items[i];
+            if (it.n == 0) continue;
+            bm_status rs = greedy_enqueue_step(it.gc, it.px, *it.ar, stimer, s);
+            if (rs != BM_OK) return tag(i, rs);
+        }
+        std::vector<DeviceState> h1(std::max(count, 1));
+        TRY_CUDA(cudaMemcpyAsync(h1.data(), sts, sizeof(DeviceState) * std::max(count, 1), cudaMemcpyDeviceToHost, s));
+        TRY_SYNC(s, "the first greedy step of all instances");
+        for (int i = 0; i < count; ++i) {
+            BatchItem& it = items[i];
+            if (it.n == 0 || h1[i].done || h1[i].error || h1[i].tile_pairs == 0) continue;
+            const double eps = std::sqrt(it.eps2);
+            const int e = fp16_scale_exp((double)norms[i], eps);
+            const double d16 = band_halfwidth(BM_PATH_TC_FP16, it.d, tile_config_for(it.d, 1).d_pad, it.eps2, norms[i],
+                                              norms[i], e) * std::ldexp(1.0, -2 * e);
+            const double d3 = band_halfwidth(BM_PATH_TC_SPLIT3, it.d, it.px.d_pad, it.eps2, norms[i], norms[i], 0);
+            const double predicted = (double)h1[i].band_pairs / (double)h1[i].tile_pairs * (d16 / d3);
+            if (predicted < kAutoPredictFraction) {
+                bm_status rs = switch_path(it.gc, it.px, *it.ar, s, BM_PATH_TC_FP16, norms[i], 1);
+                if (rs != BM_OK) return tag(i, rs);
+            }
+        }
     }
     // 3. one graph: a WHILE node per instance, no edges between them
     {
@@ -1694,7 +1823,7 @@ bm_status build_batched(const bm_instance* inst, int count, const bm_options& op
         g.stats.candidates = (int64_t)fin.candidates;
         g.stats.edge_pairs = 0;   // witnessed pairs are counted for the whole batch only
         g.stats.band_delta = fin.delta;
-        g.stats.path = path;
+        g.stats.path = it.n ? it.gc.path : path;
         g.stats.kernel_launches = executed[i];
         outs[i] = g;
         if (statuses) statuses[i] = BM_OK;
@@ -2044,6 +2173,7 @@ bm_status bm_build_batched(const bm_instance* inst, int32_t count, const bm_opti
         if (statuses) statuses[i] = BM_OK;
         bm_status vs = validate_points(inst[i].X, inst[i].n, inst[i].d, "X");
         if (vs == BM_OK) vs = validate_eps(inst[i].eps);
+        if (vs == BM_OK) vs = validate_batch(inst[i].batch, 2048);
         if (vs != BM_OK) {
             if (statuses) statuses[i] = vs;
             g_last_error = "instance " + std::to_string(i) + ": " + g_last_error;
@@ -2089,7 +2219,8 @@ void* persistent_alloc(const bm_options& opt, size_t bytes, std::vector<void*>& 
 void free_index(bm_ivf* h) {
     if (!h) return;
     IvfIndex& ix = h->ix;
-    void* bufs[] = {ix.centroids, ix.cnorm, ix.cell_off, ix.cell_ids, ix.cell_of, ix.xperm, ix.xnorm, ix.owned_x};
+    void* bufs[] = {ix.centroids, ix.cnorm, ix.cell_off, ix.cell_ids, ix.cell_of, ix.xperm, ix.xnorm, ix.owned_x,
+                    ix.pad_off, ix.xpad};
     for (void* b : bufs) device_free(&ix.opt, (cudaStream_t)ix.opt.stream, b);
     delete h;
 }
@@ -2202,6 +2333,19 @@ bm_status bm_ivf_train(const float* X, int64_t n, int32_t d, int32_t nlist, int3
         PTRY(launch_csr_from_sorted(sorted, n, nlist, ix.cell_off, ix.cell_ids, s));
         PALLOC(ix.xperm, float, n * d);
         PTRY(launch_gather_rows(ix.X, ix.cell_ids, n, d, ix.xperm, s));
+        // the tensor-core scan's layout: every cell padded to a multiple of 256 rows
+        PALLOC(ix.pad_off, long long, nlist + 1);
+        long long* pcnt = (long long*)ar.get(sizeof(long long) * (nlist + 1));
+        if (!pcnt) return bail(BM_ERR_NOMEM, "padding scratch");
+        PTRY(launch_cell_pad_offsets(ix.cell_off, nlist, 256, pcnt, ix.pad_off, ar, s));
+        std::vector<long long> hpo((size_t)nlist + 1);
+        PTRY(cudaMemcpyAsync(hpo.data(), ix.pad_off, sizeof(long long) * (nlist + 1), cudaMemcpyDeviceToHost, s));
+        PTRY(cudaStreamSynchronize(s));
+        ix.npad = hpo[(size_t)nlist];
+        for (int c = 0; c < nlist; ++c)
+            ix.max_cell_tiles = std::max<long long>(ix.max_cell_tiles, (hpo[(size_t)c + 1] - hpo[(size_t)c]) / 256);
+        PALLOC(ix.xpad, float, std::max<long long>(ix.npad, 1) * d);
+        PTRY(launch_pad_rows(ix.xperm, ix.cell_off, ix.pad_off, nlist, ix.npad, d, ix.xpad, s));
         PTRY(cudaStreamSynchronize(s));
     }
 #undef PALLOC

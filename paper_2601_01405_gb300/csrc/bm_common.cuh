@@ -46,6 +46,21 @@ struct DeviceState {
     int pad1;
 };
 
+// One work item of the tensor-core tiles in table mode (the inverted-file scan): the
+// point tile b_tile (NT rows of the padded cell-ordered operands) against query tiles
+// a_tile0 .. a_tile0 + a_count - 1 (128 rows each of the padded query operands).
+// Rows below a_end hold queries; columns below col_end hold points, column c being
+// source row src0 + (c - b_col0) of the cell order.
+struct TcItem {
+    long long b_tile;
+    int a_tile0;
+    int a_count;
+    long long a_end;
+    long long col_end;
+    long long b_col0;
+    long long src0;
+};
+
 // Where a distance tile delivers its (row, point) hits.
 //   key = (uint64 row << 32) | point
 // In greedy mode (slot_of != nullptr) a hit whose point is itself a candidate

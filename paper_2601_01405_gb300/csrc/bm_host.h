@@ -128,6 +128,13 @@ struct SweepDesc {
     const GraphIndex* gidx = nullptr;
     int gidx_ef = 0;
     long long gidx_max_visits = 0;
+    // inverted-file scan on the tensor cores: the padded cell-ordered point operands
+    const Prepared* ivf_b_pad = nullptr;
+    // table mode of the tensor-core tiles (work items, A row -> query, source row -> point)
+    const TcItem* tc_items = nullptr;
+    const long long* tc_items_count = nullptr;
+    const int* tc_a_map = nullptr;
+    const int* tc_b_ids = nullptr;
 };
 cudaError_t launch_sweep_fp32(const SweepDesc& s, cudaStream_t stream);
 
@@ -196,7 +203,26 @@ struct IvfIndex {
     float* xnorm = nullptr;            // n: ||x||^2 of the rows of X (by id, float)
     bm_options opt;                    // allocator of the index's buffers
     float* owned_x = nullptr;          // device copy of X when the index was built from host memory
+    // tensor-core scan: the cell-ordered points with every cell padded to a multiple of 256
+    // rows (zero rows after its points), so that point tiles never straddle two cells
+    long long* pad_off = nullptr;      // nlist + 1: first padded row of each cell
+    float* xpad = nullptr;             // npad x d
+    long long npad = 0;
+    long long max_cell_tiles = 0;      // largest padded cell / 256
 };
+// pad_off = exclusive scan of the cell sizes (off[c+1] - off[c]) rounded up to `unit`
+cudaError_t launch_cell_pad_offsets(const long long* off, int nlist, int unit, long long* counts, long long* pad_off,
+                                    Arena& ar, cudaStream_t s);
+// xpad row pad_off[c] + j = xperm row cell_off[c] + j for j < the cell's size, zeros after
+cudaError_t launch_pad_rows(const float* xperm, const long long* cell_off, const long long* pad_off, int nlist,
+                            long long npad, int d, float* xpad, cudaStream_t s);
+// The tensor-core scan's layout for one sweep (queries grouped by probed cell, cq_off /
+// cq_rows): the padded query operands (A hi / lo / aug rows copied from `a`, zero rows
+// for padding; a_map = query of each padded row or -1) and the work items (per cell:
+// its point tiles x groups of up to 16 query tiles).  items_count (device) = items made.
+cudaError_t launch_ivf_tc_layout(const IvfIndex& ix, int NT, const long long* cq_off, const int* cq_rows,
+                                 const Prepared& a, Prepared& apad, int* a_map, long long* pa_off, long long* cnt,
+                                 TcItem* items, long long* item_off, Arena& ar, cudaStream_t s);
 
 // Nearest centroid per row (FP32 expansion ||x||^2 + ||c||^2 - 2 x.c, ties to the
 // lowest centroid id): best[r] = (float bits of the distance << 32) | centroid.

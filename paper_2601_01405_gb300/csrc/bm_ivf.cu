@@ -403,3 +403,151 @@ cudaError_t launch_ivf_scan(const float* A, const float* phiA, const IvfIndex& i
 }
 
 }  // namespace bm
+
+// ---------------------------------------------------------------- tensor-core scan layout
+//
+// The tensor-core tiles stream a point tile of NT rows against up to 16 query tiles of
+// 128 rows.  For the inverted file the points of a cell and the queries that probe it
+// must meet in the same tiles, so both sides are laid out by cell with every cell padded
+// to whole tiles: points (once per index) to multiples of 256 rows, the (query, probe)
+// pairs of a sweep to multiples of 128 rows.  A work item is one point tile of a cell
+// against a group of that cell's query tiles; the kernel maps padded A rows to queries
+// (a_map) and padded columns back to point ids through the cell order.
+
+namespace bm {
+
+namespace {
+
+__global__ void pad_counts_kernel(const long long* off, int nlist, int unit, long long* counts) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nlist) return;
+    const long long sz = off[c + 1] - off[c];
+    counts[c] = (sz + unit - 1) / unit * unit;
+}
+
+__device__ __forceinline__ int cell_of_row(const long long* off, int nlist, long long r) {
+    int lo = 0, hi = nlist - 1;   // largest c with off[c] <= r
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= r) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void pad_rows_kernel(const float* __restrict__ xperm, const long long* __restrict__ cell_off,
+                                const long long* __restrict__ pad_off, int nlist, long long npad, int d,
+                                float* __restrict__ xpad) {
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const int lane = threadIdx.x & 31;
+    for (long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < npad; r += warps) {
+        const int c = cell_of_row(pad_off, nlist, r);
+        const long long j = r - pad_off[c], nx = cell_off[c + 1] - cell_off[c];
+        const float* src = j < nx ? xperm + (cell_off[c] + j) * d : nullptr;
+        for (int i = lane; i < d; i += 32) xpad[r * d + i] = src ? src[i] : 0.f;
+    }
+}
+
+// One warp per padded query row: its query (or -1) and its operand rows.
+__global__ void gather_query_pad_kernel(const long long* __restrict__ pa_off, const long long* __restrict__ cq_off,
+                                        const int* __restrict__ cq_rows, int nlist,
+                                        const unsigned* __restrict__ hi, const unsigned* __restrict__ lo,
+                                        const unsigned* __restrict__ aug, int words, unsigned* __restrict__ ohi,
+                                        unsigned* __restrict__ olo, unsigned* __restrict__ oaug, int* __restrict__ a_map) {
+    const long long total = pa_off[nlist];
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const int lane = threadIdx.x & 31;
+    for (long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < total; r += warps) {
+        const int c = cell_of_row(pa_off, nlist, r);
+        const long long j = r - pa_off[c], nq = cq_off[c + 1] - cq_off[c];
+        const int q = j < nq ? cq_rows[cq_off[c] + j] : -1;
+        if (lane == 0) a_map[r] = q;
+        for (int i = lane; i < words; i += 32) {
+            ohi[r * words + i] = q >= 0 ? hi[(long long)q * words + i] : 0u;
+            if (olo) olo[r * words + i] = q >= 0 ? lo[(long long)q * words + i] : 0u;
+        }
+        if (lane < 8) oaug[r * 8 + lane] = q >= 0 ? aug[(long long)q * 8 + lane] : 0u;
+    }
+}
+
+__global__ void item_counts_kernel(const long long* cq_off, const long long* cell_off, const long long* pad_off,
+                                   int nlist, int NT, long long* counts) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nlist) return;
+    const long long nq = cq_off[c + 1] - cq_off[c], nx = cell_off[c + 1] - cell_off[c];
+    const long long b_tiles = (pad_off[c + 1] - pad_off[c]) / NT, a_tiles = (nq + 127) / 128;
+    counts[c] = (nq > 0 && nx > 0) ? b_tiles * ((a_tiles + 15) / 16) : 0;
+}
+
+__global__ void item_fill_kernel(const long long* cq_off, const long long* cell_off, const long long* pad_off,
+                                 const long long* pa_off, const long long* item_off, int nlist, int NT, TcItem* items) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nlist) return;
+    const long long nq = cq_off[c + 1] - cq_off[c], nx = cell_off[c + 1] - cell_off[c];
+    const long long k0 = item_off[c], k1 = item_off[c + 1];
+    if (k1 == k0) return;
+    const long long b_tiles = (pad_off[c + 1] - pad_off[c]) / NT, a_tiles = (nq + 127) / 128;
+    const long long groups = (a_tiles + 15) / 16;
+    for (long long k = k0; k < k1; ++k) {
+        const long long local = k - k0, u = local / groups, g = local % groups;
+        TcItem it;
+        it.b_tile = pad_off[c] / NT + u;
+        it.a_tile0 = (int)(pa_off[c] / 128 + g * 16);
+        it.a_count = (int)((a_tiles - g * 16) < 16 ? (a_tiles - g * 16) : 16);
+        it.a_end = pa_off[c] + nq;
+        it.col_end = pad_off[c] + nx;
+        it.b_col0 = pad_off[c];
+        it.src0 = cell_off[c];
+        items[k] = it;
+    }
+}
+
+unsigned grid_rows(long long n, int per_block) {
+    long long b = (n + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > 152 * 32) b = 152 * 32;
+    return (unsigned)b;
+}
+
+}  // namespace
+
+cudaError_t launch_cell_pad_offsets(const long long* off, int nlist, int unit, long long* counts, long long* pad_off,
+                                    Arena& ar, cudaStream_t s) {
+    note_launch();
+    pad_counts_kernel<<<(nlist + 255) / 256, 256, 0, s>>>(off, nlist, unit, counts);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return exclusive_scan_i64(counts, pad_off, nlist, ar, s);
+}
+
+cudaError_t launch_pad_rows(const float* xperm, const long long* cell_off, const long long* pad_off, int nlist,
+                            long long npad, int d, float* xpad, cudaStream_t s) {
+    if (npad == 0) return cudaSuccess;
+    note_launch();
+    pad_rows_kernel<<<grid_rows(npad, 8), 256, 0, s>>>(xperm, cell_off, pad_off, nlist, npad, d, xpad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ivf_tc_layout(const IvfIndex& ix, int NT, const long long* cq_off, const int* cq_rows,
+                                 const Prepared& a, Prepared& apad, int* a_map, long long* pa_off, long long* cnt,
+                                 TcItem* items, long long* item_off, Arena& ar, cudaStream_t s) {
+    cudaError_t e = launch_cell_pad_offsets(cq_off, ix.nlist, 128, cnt, pa_off, ar, s);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    gather_query_pad_kernel<<<grid_rows(apad.rows, 8), 256, 0, s>>>(
+        pa_off, cq_off, cq_rows, ix.nlist, reinterpret_cast<const unsigned*>(a.hi),
+        reinterpret_cast<const unsigned*>(a.lo), reinterpret_cast<const unsigned*>(a.aug), a.d_pad / 2,
+        reinterpret_cast<unsigned*>(apad.hi), reinterpret_cast<unsigned*>(apad.lo),
+        reinterpret_cast<unsigned*>(apad.aug), a_map);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    note_launch();
+    item_counts_kernel<<<(ix.nlist + 255) / 256, 256, 0, s>>>(cq_off, ix.cell_off, ix.pad_off, ix.nlist, NT, cnt);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = exclusive_scan_i64(cnt, item_off, ix.nlist, ar, s)) != cudaSuccess) return e;
+    note_launch();
+    item_fill_kernel<<<(ix.nlist + 255) / 256, 256, 0, s>>>(cq_off, ix.cell_off, ix.pad_off, pa_off, item_off, ix.nlist,
+                                                            NT, items);
+    return cudaGetLastError();
+}
+
+}  // namespace bm

@@ -61,6 +61,12 @@ struct TcArgs {
     double eps2;
     DeviceState* st;
     HitSink sink;
+    // table mode (inverted-file scan): work items from a device table; A row r holds the
+    // query a_map[r], B column c of an item is point b_ids[src0 + c - b_col0]
+    const TcItem* items;
+    const long long* items_count;
+    const int* a_map;
+    const int* b_ids;
 };
 
 struct Ctl {
@@ -278,7 +284,8 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
     const int G = (int)(a_tiles < kMaxGroup ? a_tiles : kMaxGroup);
     const long long n_groups = (a_tiles + G - 1) / G;
     const long long b_tiles = (p.n + NT - 1) / NT;
-    const long long items = b_tiles * n_groups;
+    const bool table = p.items != nullptr;
+    const long long items = table ? *p.items_count : b_tiles * n_groups;
     constexpr uint32_t kTmemCols = 2 * NT;
     constexpr uint32_t kIdesc = idesc_f16kind(128, NT, PROD == 3);
     constexpr uint32_t kSpan = CK * 2;
@@ -326,9 +333,18 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
             for (int i = 0; i < ASTG; ++i) a_last[i] = -1;
             for (int i = 0; i < BBUF; ++i) b_last[i] = -1;
             for (long long item = blockIdx.x; ok && item < items; item += gridDim.x) {
-                const long long bt = item / n_groups, g = item % n_groups;
-                const long long at0 = g * G;
-                const long long at1 = (at0 + G < a_tiles) ? at0 + G : a_tiles;
+                long long bt, at0, at1;
+                if (table) {
+                    const TcItem& it = p.items[item];
+                    bt = it.b_tile;
+                    at0 = it.a_tile0;
+                    at1 = at0 + it.a_count;
+                } else {
+                    const long long g = item % n_groups;
+                    bt = item / n_groups;
+                    at0 = g * G;
+                    at1 = (at0 + G < a_tiles) ? at0 + G : a_tiles;
+                }
                 const int yb = (int)(bt * NT);
                 if (!bar_wait(&ctl->b_empty[b_buf], b_ph ^ 1, abort_flag, gerr)) { ok = false; break; }
                 bar_expect_tx(&ctl->b_full[b_buf], L.b_bytes);
@@ -389,9 +405,15 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
             const unsigned long long astep = L.a_stage >> 4;
             uint32_t t_seq = 0;   // dual issue: tiles of this CTA before the current item
             for (long long item = blockIdx.x; ok && item < items; item += gridDim.x) {
-                const long long g = item % n_groups;
-                const long long at0 = g * G;
-                const long long at1 = (at0 + G < a_tiles) ? at0 + G : a_tiles;
+                long long at0, at1;
+                if (table) {
+                    at0 = p.items[item].a_tile0;
+                    at1 = at0 + p.items[item].a_count;
+                } else {
+                    const long long g = item % n_groups;
+                    at0 = g * G;
+                    at1 = (at0 + G < a_tiles) ? at0 + G : a_tiles;
+                }
                 if (!bar_wait(&ctl->b_full[b_buf], b_ph, abort_flag, gerr)) { ok = false; break; }
                 fence_after();
                 const uint32_t bb = sbase + b_buf * L.b_stride;
@@ -519,16 +541,31 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
         unsigned long long pairs_local = 0;
         bool ok = true;
         for (long long item = blockIdx.x; ok && item < items; item += gridDim.x) {
-            const long long bt = item / n_groups, g = item % n_groups;
-            const long long at0 = g * G;
-            const long long at1 = (at0 + G < a_tiles) ? at0 + G : a_tiles;
+            long long bt, at0, at1, a_end = a_rows, col_end = p.n, b_col0 = 0, src0 = 0;
+            if (table) {
+                const TcItem it = p.items[item];
+                bt = it.b_tile;
+                at0 = it.a_tile0;
+                at1 = at0 + it.a_count;
+                a_end = it.a_end;
+                col_end = it.col_end;
+                b_col0 = it.b_col0;
+                src0 = it.src0;
+            } else {
+                const long long g = item % n_groups;
+                bt = item / n_groups;
+                at0 = g * G;
+                at1 = (at0 + G < a_tiles) ? at0 + G : a_tiles;
+            }
             const long long col_base = bt * NT + half * (NT / 2);
             for (long long at = at0; at < at1; ++at) {
                 const bool w = __all_sync(kFull, bar_wait(&ctl->t_full[t_buf], t_ph, abort_flag, gerr));
                 if (!w) { ok = false; break; }
                 fence_after();
                 const long long row = at * 128 + quarter * 32 + lane;
-                const bool row_ok = row < a_rows;
+                const bool row_ok = row < a_end;
+                // the query this A row holds (table mode) and the key's row part
+                const long long qid = table ? (row_ok ? (long long)p.a_map[row] : -1) : row;
                 const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + t_buf * NT + half * (NT / 2);
                 uint32_t r[kChunks][32];
                 tmem_ld_all<kChunks>(taddr, r);
@@ -547,9 +584,9 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
                 const bool quiet = !row_ok || (allneg >> 31) != 0u;
                 if (__all_sync(kFull, quiet)) {
                     if (threadIdx.x == 64) {
-                        const long long ra = (a_rows - at * 128) < 128 ? (a_rows - at * 128) : 128;
-                        const long long rb = (p.n - bt * NT) < NT ? (p.n - bt * NT) : NT;
-                        pairs_local += (unsigned long long)(ra * rb);
+                        const long long ra = (a_end - at * 128) < 128 ? (a_end - at * 128) : 128;
+                        const long long rb = (col_end - bt * NT) < NT ? (col_end - bt * NT) : NT;
+                        if (ra > 0 && rb > 0) pairs_local += (unsigned long long)(ra * rb);
                     }
                     continue;
                 }
@@ -568,7 +605,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
 #pragma unroll
                     for (int i = 0; i < 32; ++i) neg &= r[j][i];
                     if (row_ok && (neg >> 31) == 0u) {
-                        const long long left = p.n - (col_base + j * 32);
+                        const long long left = col_end - (col_base + j * 32);
                         const unsigned valid = left >= 32 ? kFull : (left <= 0 ? 0u : (1u << left) - 1u);
                         unsigned sgn = 0u;
 #pragma unroll
@@ -613,7 +650,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
                     unsigned long long hpos = hbase + (excl >> 16), bpos = bbase + (excl & 0xffffu);
                     unsigned long long* hkeys = seg_mode ? seg_keys : p.sink.keys;
                     const unsigned long long hcap = seg_mode ? p.sink.seg_cap : p.sink.cap;
-                    const unsigned long long rowkey = (unsigned long long)(unsigned)row << 32;
+                    const unsigned long long rowkey = (unsigned long long)(unsigned)qid << 32;
 #pragma unroll
                     for (int j = 0; j < kChunks; ++j) {
                         const unsigned col0 = (unsigned)(col_base + j * 32);
@@ -621,31 +658,35 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
                         while (m) {
                             const int b = __ffs(m) - 1;
                             m &= m - 1;
-                            if (bpos < band_cap) band_keys[bpos] = rowkey | (col0 + (unsigned)b);
+                            unsigned col = col0 + (unsigned)b;
+                            if (table) col = (unsigned)p.b_ids[src0 + ((long long)col - b_col0)];
+                            if (bpos < band_cap) band_keys[bpos] = rowkey | col;
                             ++bpos;
                         }
                         m = hitm[j];
                         while (m) {
                             const int b = __ffs(m) - 1;
                             m &= m - 1;
-                            const unsigned col = col0 + (unsigned)b;
+                            unsigned col = col0 + (unsigned)b;
+                            if (table) col = (unsigned)p.b_ids[src0 + ((long long)col - b_col0)];
                             if (hpos < hcap) hkeys[hpos] = rowkey | col;
                             ++hpos;
                             if (p.sink.slot_of) {   // greedy: a later candidate covered by this one
                                 const int sl = p.sink.slot_of[col];
-                                if (sl > (int)row) {
-                                    atomicOr(&p.sink.conflict[(size_t)row * p.sink.conflict_words + (sl >> 5)],
+                                const int qr = (int)qid;
+                                if (sl > qr) {
+                                    atomicOr(&p.sink.conflict[(size_t)qr * p.sink.conflict_words + (sl >> 5)],
                                              1u << (sl & 31));
-                                    atomicOr(&p.sink.row_any[row >> 5], 1u << (row & 31));
+                                    atomicOr(&p.sink.row_any[qr >> 5], 1u << (qr & 31));
                                 }
                             }
                         }
                     }
                 }
                 if (threadIdx.x == 64) {
-                    const long long ra = (a_rows - at * 128) < 128 ? (a_rows - at * 128) : 128;
-                    const long long rb = (p.n - bt * NT) < NT ? (p.n - bt * NT) : NT;
-                    pairs_local += (unsigned long long)(ra * rb);
+                    const long long ra = (a_end - at * 128) < 128 ? (a_end - at * 128) : 128;
+                    const long long rb = (col_end - bt * NT) < NT ? (col_end - bt * NT) : NT;
+                    if (ra > 0 && rb > 0) pairs_local += (unsigned long long)(ra * rb);
                 }
             }
         }
@@ -751,7 +792,8 @@ cudaError_t launch_cfg(TcArgs& args, long long a_rows_max, cudaStream_t stream, 
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long grid = items < sms ? items : sms;
+    // table mode: the item count is on the device; every SM takes part
+    const long long grid = args.items ? sms : (items < sms ? items : sms);
     *grid_out = (int)(grid > 0 ? grid : 0);
     if (grid <= 0) return cudaSuccess;
     note_launch();
@@ -907,6 +949,10 @@ cudaError_t launch_sweep_tc(const SweepDesc& s, cudaStream_t stream, std::string
     args.eps2 = s.eps2;
     args.st = const_cast<DeviceState*>(s.st);
     args.sink = s.sink;
+    args.items = s.tc_items;
+    args.items_count = s.tc_items_count;
+    args.a_map = s.tc_a_map;
+    args.b_ids = s.tc_b_ids;
     // fp16 with two K chunks keeps the whole query tile in one stage (a 64-wide chunk
     // only: d_pad = 128)
     const bool whole = fp16 && d_pad == 2 * CK && CK == 64;

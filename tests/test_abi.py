@@ -45,6 +45,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(binding.bm_options) == 8 + 16 + 24 + 8
     assert ctypes.sizeof(binding.bm_csr) == 8 + 8 + 8 + 8 + 8 + 8
     assert binding.bm_graph.stats.offset == ctypes.sizeof(binding.bm_graph) - ctypes.sizeof(binding.bm_stats)
+    assert ctypes.sizeof(binding.bm_instance) == 32
 
 
 def test_struct_layouts_match_c_compiler(tmp_path):

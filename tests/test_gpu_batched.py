@@ -113,3 +113,37 @@ def test_batched_rejects_nan_instance(bm):
 
 def test_batched_empty_list(bm):
     assert bm.bm_build_batched([]) == []
+
+
+def test_batched_auto_picks_a_path_per_instance(bm):
+    """The automatic path's first step runs every instance on the split and moves the
+    well-separated ones to fp16 before the graph; a Swiss roll (wide fp16 band) stays on
+    the split.  Every result equals the oracle's."""
+    inst = [(W.mixture(6000, 64, 8, clusters=8, seed=51), 2.0),
+            (W.swissroll(8000, 128, 12, seed=52), 0.5),
+            (W.isotropic(3000, 32, 10, seed=53), 1.0)]
+    res = bm.bm_build_batched([(torch.from_numpy(X).cuda(), e) for X, e in inst])
+    torch.cuda.synchronize()
+    paths = [r["stats"]["path"] for r in res]
+    assert paths[0] == bm.BM_PATH_TC_FP16
+    assert paths[1] == bm.BM_PATH_TC_SPLIT3
+    for k, ((X, e), r) in enumerate(zip(inst, res)):
+        assert_same_graph(to_np(r), oracle.build(X, e), k)
+
+
+def test_batched_per_instance_batches(bm):
+    """Per-instance largest batches (what the autotuned table supplies) change the schedule,
+    never the result."""
+    from paper_2601_01405_gb300 import autotune
+    inst = W.batched_instances(count=9, seed=61, n_hi=20000)
+    dev = [(torch.from_numpy(i.x).cuda(), i.eps) for i in inst]
+    table = {8: [{"n_lo": 1000, "n_hi": 5000, "best": 128}, {"n_lo": 5000, "n_hi": 200000, "best": 2048}],
+             32: [{"n_lo": 1000, "n_hi": 200000, "best": 256}], 96: [{"n_lo": 1000, "n_hi": 200000, "best": 512}]}
+    per = autotune.batches_for(table, dev)
+    assert set(per) <= {128, 256, 512, 2048}
+    a = bm.bm_build_batched(dev, batches=per)
+    b = bm.bm_build_batched(dev)
+    for k, (x, y) in enumerate(zip(a, b)):
+        assert_same_graph(to_np(x), to_np(y), k)
+    with pytest.raises(bm.BallMapperError):
+        bm.bm_build_batched(dev, batches=[48] * len(dev))

@@ -47,10 +47,13 @@ def test_cells_are_nearest_centroids(index, data):
     assert np.bincount(cell, minlength=64).min() >= 1
 
 
+@pytest.mark.parametrize("path", ["tc", "fp32"])
 @pytest.mark.parametrize("nprobe", [1, 4, 17, 64])
-def test_range_query_matches_masked_oracle(index, data, nprobe):
+def test_range_query_matches_masked_oracle(index, data, nprobe, path):
+    """Both scans (the tensor-core tiles over cells laid out in whole tiles, and the FP32
+    CUDA-core tiles) give the verified range set over the probed cells."""
     Q = data[::37]
-    off, ids, probes, st = index.range_query(torch.from_numpy(Q).cuda(), 4.0, nprobe)
+    off, ids, probes, st = index.range_query(torch.from_numpy(Q).cuda(), 4.0, nprobe, path=path)
     p = probes.cpu().numpy()
     # probes: nprobe distinct cells, the nearest ones (up to float32 ties)
     D = sqd(Q, index.centroids.cpu().numpy())
@@ -65,12 +68,13 @@ def test_range_query_matches_masked_oracle(index, data, nprobe):
         assert np.array_equal(ro, eo) and np.array_equal(ri, ei)
 
 
-def test_fixed_landmark_build(bm, index, data):
+@pytest.mark.parametrize("path", ["tc", "fp32"])
+def test_fixed_landmark_build(bm, index, data, path):
     """Fixed-landmark mode (Sec. 6.2): balls through the index, nerve of those balls;
     conservative, so every membership and edge is also exact (Prop. 5.15)."""
     Xd = torch.from_numpy(data).cuda()
     exact = bm.bm_build(Xd, 4.0)
-    approx = index.build(4.0, 8, landmarks=exact["landmarks"])
+    approx = index.build(4.0, 8, landmarks=exact["landmarks"], path=path)
     lm = exact["landmarks"].cpu().numpy()
     _, _, probes, _ = index.range_query(torch.from_numpy(data[lm]).cuda(), 4.0, 8)
     ro, ri = oracle.masked_range_query(data, data[lm], 4.0, index.cell_of.cpu().numpy(), 64, probes.cpu().numpy())
@@ -82,10 +86,11 @@ def test_fixed_landmark_build(bm, index, data):
     assert len(e_ref) < len(exact_edges)          # the index loses some edges at nprobe = 8
 
 
-def test_end_to_end_build(index, data):
+@pytest.mark.parametrize("path", ["tc", "fp32"])
+def test_end_to_end_build(index, data, path):
     """End-to-end mode: the greedy driven by the index's range sets.  x is a landmark
     iff no earlier landmark's approximate ball holds x; the exact balls still cover X."""
-    out = index.build(4.0, 4)
+    out = index.build(4.0, 4, path=path)
     lm = out["landmarks"].cpu().numpy()
     assert np.all(np.diff(lm) > 0)
     _, _, probes, _ = index.range_query(torch.from_numpy(data[lm]).cuda(), 4.0, 4)
@@ -102,3 +107,19 @@ def test_end_to_end_build(index, data):
     assert np.array_equal(is_lm, ~covered_earlier)
     assert np.all(first_cover < n)                   # every point in some (exact) ball
     assert np.array_equal(out["edges"].cpu().numpy(), oracle.edges(data, lm, ro, ri, 4.0))
+
+
+def test_tc_scan_on_ties_and_d128(bm):
+    """The tensor-core scan on a tie-heavy grid (pairs at exactly eps, decided in the FP64
+    recheck) and at d = 128 (the split's 256-wide point tiles), against the masked oracle."""
+    G = W.tiny_grid_cloud(6000, 3, 2, span=8, seed=42)
+    ig = bm.IvfIndex(torch.from_numpy(G).cuda(), nlist=16, iters=5, seed=1)
+    for path in ("tc", "fp32"):
+        off, ids, probes, _ = ig.range_query(torch.from_numpy(G[:500]).cuda(), 1.0, 3, path=path)
+        ro, ri = oracle.masked_range_query(G, G[:500], 1.0, ig.cell_of.cpu().numpy(), 16, probes.cpu().numpy())
+        assert np.array_equal(off.cpu().numpy(), ro) and np.array_equal(ids.cpu().numpy(), ri), path
+    X = W.make("iso-n20k-d128")
+    ix = bm.IvfIndex(torch.from_numpy(X).cuda(), nlist=32, iters=6, seed=2)
+    off, ids, probes, _ = ix.range_query(torch.from_numpy(X[::23]).cuda(), 14.0, 5, path="tc")
+    ro, ri = oracle.masked_range_query(X, X[::23], 14.0, ix.cell_of.cpu().numpy(), 32, probes.cpu().numpy())
+    assert np.array_equal(off.cpu().numpy(), ro) and np.array_equal(ids.cpu().numpy(), ri)
