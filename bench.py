@@ -39,7 +39,7 @@ UNIT = "evals/s"
 # rows x 10^6 points); a step's sweep reads every point's operands once whatever its
 # batch, so the figure holds for each launch of this workload (the automatic path runs
 # fp16 after the first step).  None where no capture of the current kernel exists.
-NCU_TRAFFIC = {("mix32-n1M-d64", "auto"): 164.9e6, ("mix32-n1M-d64", "tc16"): 164.9e6}
+NCU_TRAFFIC = {("mix32-n1M-d64", "auto"): 164.8e6, ("mix32-n1M-d64", "tc16"): 164.8e6}
 DTYPES = {"tc": "bf16x3-split/fp32-acc/fp64-recheck", "tc16": "f16-scaled/fp32-acc/fp64-recheck",
           "fp32": "f32/fp64-recheck", "auto": "f16-scaled or bf16x3-split/fp32-acc/fp64-recheck"}
 
