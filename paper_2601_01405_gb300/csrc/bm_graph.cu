@@ -46,12 +46,23 @@ __global__ void fill_i64_kernel(long long* p, long long n, long long v) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) p[i] = v;
 }
 
-// (row << 32 | point) -> (point << 32 | row): the transposed membership keys.
-__global__ void swap_keys_kernel(const unsigned long long* keys, long long nnz, unsigned long long* out) {
+// (row << 32 | point) at index e -> (point << 32 | e): sorted stably on the point alone,
+// these give every point's cover list in landmark order (e ascends with the landmark)
+// and, through e, where each membership sits in it.
+__global__ void point_index_keys_kernel(const unsigned long long* keys, long long nnz, unsigned long long* out) {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += stride) {
-        const unsigned long long k = keys[i];
-        out[i] = (k << 32) | (k >> 32);
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride)
+        out[e] = (keys[e] << 32) | (unsigned long long)e;
+}
+
+// tlist holds the membership index e at each cover-list position p: record tpos[e] = p and
+// replace it by e's landmark.
+__global__ void cover_from_index_kernel(const unsigned long long* keys, long long nnz, int* tlist, int* tpos) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride) {
+        const long long e = (long long)(unsigned)tlist[p];
+        tpos[e] = (int)p;
+        tlist[p] = (int)(keys[e] >> 32);
     }
 }
 
@@ -145,8 +156,8 @@ __global__ void unique_scatter_kernel(const unsigned long long* keys, long long 
 // from x's list) are not dereferenced: the kernel records them in *bad and
 // skips the entry.
 __global__ void nerve_bits_kernel(const unsigned long long* keys, const long long* moff, const long long* toff,
-                                  const int* tlist, long long nnz, long long n, int i0, int i1, long long W,
-                                  unsigned* bits, int* bad) {
+                                  const int* tlist, const int* tpos, long long nnz, long long n, int i0, int i1,
+                                  long long W, unsigned* bits, int* bad) {
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     const long long e0 = moff[i0], e1 = moff[i1];
@@ -167,8 +178,8 @@ __global__ void nerve_bits_kernel(const unsigned long long* keys, const long lon
             if (lane == 0) atomicOr(bad, 2);
             continue;
         }
-        const long long t = lower_bound_i32(tlist, b0, end, i);
-        if (t >= end || tlist[t] != i) {
+        const long long t = tpos[e];   // where membership e sits in x's cover list
+        if (t < b0 || t >= end || tlist[t] != i) {
             if (lane == 0) atomicOr(bad, 32);
             continue;
         }
@@ -203,9 +214,9 @@ __global__ void nerve_bits_kernel(const unsigned long long* keys, const long lon
 // atomics, and a heavy row never spreads its bits over L2.  Same input checks as
 // nerve_bits_kernel.
 __global__ void __launch_bounds__(512) nerve_rows_kernel(const unsigned long long* keys, const long long* moff,
-                                                         const long long* toff, const int* tlist, long long nnz,
-                                                         long long n, int i0, int i1, long long W, unsigned* bits,
-                                                         int* bad, int* next_row) {
+                                                         const long long* toff, const int* tlist, const int* tpos,
+                                                         long long nnz, long long n, int i0, int i1, long long W,
+                                                         unsigned* bits, int* bad, int* next_row) {
     extern __shared__ unsigned srow[];
     __shared__ int s_row;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -233,8 +244,8 @@ __global__ void __launch_bounds__(512) nerve_rows_kernel(const unsigned long lon
                 if (lane == 0) atomicOr(bad, 2);
                 continue;
             }
-            const long long t = lower_bound_i32(tlist, b0, end, (int)i);
-            if (t >= end || tlist[t] != (int)i) {
+            const long long t = tpos[e];   // where membership e sits in x's cover list
+            if (t < b0 || t >= end || tlist[t] != (int)i) {
                 if (lane == 0) atomicOr(bad, 32);
                 continue;
             }
@@ -458,20 +469,27 @@ cudaError_t launch_compact_segments(const unsigned long long* src, const unsigne
         }                                                              \
     } while (0)
 
-// Stage 1: point -> covering landmarks (transpose by a radix sort of swapped
-// keys), pairs per smaller landmark and their exclusive scan j.lpre (L + 1).
+// Stage 1: point -> covering landmarks (transpose by a stable radix sort of
+// (point, membership index) keys on the point bits: the memberships are in landmark
+// order, so each cover list comes out ascending), the position of every membership in
+// its cover list (j.tpos), pairs per smaller landmark and their exclusive scan j.lpre
+// (L + 1).
 bool edges_transpose(EdgeJob& j, Arena& ar, cudaStream_t s, Failure& f) {
     const long long nnz = j.nnz, n = j.n, L = j.L;
     unsigned long long *tk, *tk2;
     BM_ALLOC(tk, unsigned long long, nnz);
     BM_ALLOC(tk2, unsigned long long, nnz);
     note_launch();
-    swap_keys_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(j.keys, nnz, tk);
+    point_index_keys_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(j.keys, nnz, tk);
     BM_TRY(cudaGetLastError());
-    BM_TRY(radix_sort_u64(tk, tk2, nnz, digit_shifts(bits_for(L - 1), bits_for(n - 1)), ar, s, &j.tsorted));
+    BM_TRY(radix_sort_u64(tk, tk2, nnz, digit_shifts(0, bits_for(n - 1)), ar, s, &j.tsorted));
     BM_ALLOC(j.toff, long long, n + 1);
     BM_ALLOC(j.tlist, int, nnz);
+    BM_ALLOC(j.tpos, int, nnz);
     BM_TRY(launch_csr_from_sorted(j.tsorted, nnz, n, j.toff, j.tlist, s));
+    note_launch();
+    cover_from_index_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(j.keys, nnz, j.tlist, j.tpos);
+    BM_TRY(cudaGetLastError());
     unsigned long long* plc;
     BM_ALLOC(plc, unsigned long long, L + 1);
     BM_TRY(cudaMemsetAsync(plc, 0, sizeof(unsigned long long) * (L + 1), s));
@@ -539,12 +557,12 @@ bool edges_emit(EdgeJob& j, int i0, int i1, long long Pc, Arena& ar, cudaStream_
             const int per_sm = W * 4 <= 48 * 1024 ? 4 : (W * 4 <= 100 * 1024 ? 2 : 1);
             note_launch();
             nerve_rows_kernel<<<(unsigned)(device_sm_count() * per_sm), 512, (size_t)W * sizeof(unsigned), s>>>(
-                j.keys, j.moff, j.toff, j.tlist, j.nnz, n, i0, i1, W, j.bits, j.bad, next_row);
+                j.keys, j.moff, j.toff, j.tlist, j.tpos, j.nnz, n, i0, i1, W, j.bits, j.bad, next_row);
             BM_TRY(cudaGetLastError());
         } else {
             note_launch();
-            nerve_bits_kernel<<<grid_for(j.nnz * 32, 256), 256, 0, s>>>(j.keys, j.moff, j.toff, j.tlist, j.nnz, n, i0,
-                                                                         i1, W, j.bits, j.bad);
+            nerve_bits_kernel<<<grid_for(j.nnz * 32, 256), 256, 0, s>>>(j.keys, j.moff, j.toff, j.tlist, j.tpos, j.nnz,
+                                                                         n, i0, i1, W, j.bits, j.bad);
             BM_TRY(cudaGetLastError());
         }
         long long* cnt;
@@ -625,11 +643,13 @@ void edges_release(EdgeJob& j, Arena& ar) {
     ar.release(j.tsorted);
     ar.release(j.toff);
     ar.release(j.tlist);
+    ar.release(j.tpos);
     ar.release(j.lpre);
     ar.release(j.bad);
     j.tsorted = nullptr;
     j.toff = nullptr;
     j.tlist = nullptr;
+    j.tpos = nullptr;
     j.lpre = nullptr;
     j.bad = nullptr;
 }

@@ -354,6 +354,7 @@ struct EdgeJob {
     unsigned long long* tsorted = nullptr;     // swapped keys, sorted (stage 1 only)
     long long* toff = nullptr;                 // point -> covering landmarks (CSR)
     int* tlist = nullptr;
+    int* tpos = nullptr;                       // nnz: position of membership e (row-major) in tlist
     long long* lpre = nullptr;                 // L + 1: exclusive scan of the pairs per smaller landmark
     unsigned long long* sorted = nullptr;      // sort path: sorted pair keys of the chunk
     unsigned* bits = nullptr;                  // bitmap path: rows of the chunk, W words each
