@@ -104,6 +104,14 @@ __device__ __forceinline__ double exact_sqdist(const float* __restrict__ a,
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
+// Programmatic dependent launch: a kernel launched with launch_pdl may be scheduled while
+// its predecessor in the stream still runs; pdl_wait blocks until that predecessor has
+// completed and its memory operations are visible (a no-op for an ordinary launch), and
+// pdl_trigger lets the next kernel be scheduled once every block of this one has issued
+// it.  Step kernels call both first thing, before touching any global memory.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Warp-aggregated reservation of `cnt` slots in a global counter.  Must be
 // called by all 32 lanes of the warp.  Returns the lane's first slot.
 __device__ __forceinline__ unsigned long long warp_reserve(unsigned long long* counter, unsigned cnt) {

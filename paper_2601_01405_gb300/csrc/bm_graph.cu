@@ -378,6 +378,8 @@ __global__ void __launch_bounds__(256) compact_segments_kernel(
     const unsigned long long* seg_counts, const unsigned long long* band_seg_counts, int nseg,
     unsigned long long* dst, unsigned long long* band_dst, unsigned long long* count_out,
     unsigned long long* band_count_out, DeviceState* st, int overflow_bit, int check_done, int stop_on_overflow) {
+    pdl_wait();
+    pdl_trigger();
     if (check_done && st->done) return;
     __shared__ unsigned long long s_cnt[256];
     __shared__ unsigned long long s_pre, s_mine;
@@ -443,10 +445,9 @@ cudaError_t launch_compact_segments(const unsigned long long* src, const unsigne
     if (nseg <= 0) return cudaSuccess;
     if (nseg > 256) return cudaErrorInvalidValue;
     note_launch();
-    compact_segments_kernel<<<2 * nseg, 256, 0, s>>>(src, band_src, seg_cap, seg_counts, band_seg_counts, nseg, dst,
-                                                      band_dst, count_out, band_count_out, st, overflow_bit,
-                                                      check_done ? 1 : 0, stop_on_overflow ? 1 : 0);
-    return cudaGetLastError();
+    return launch_pdl(compact_segments_kernel, dim3(2 * nseg), dim3(256), 0, s, src, band_src, seg_cap, seg_counts,
+                      band_seg_counts, nseg, dst, band_dst, count_out, band_count_out, st, overflow_bit,
+                      check_done ? 1 : 0, stop_on_overflow ? 1 : 0);
 }
 
 #define BM_TRY(expr)                                                   \

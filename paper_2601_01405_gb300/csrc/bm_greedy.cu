@@ -33,6 +33,8 @@ __global__ void __launch_bounds__(kSelThreads) greedy_select_kernel(
     const __nv_bfloat16* __restrict__ H, const __nv_bfloat16* __restrict__ Lo,
     const __nv_bfloat16* __restrict__ Aug, int d_pad, __nv_bfloat16* cH, __nv_bfloat16* cLo,
     __nv_bfloat16* cAug) {
+    pdl_wait();
+    pdl_trigger();
     if (st->done) return;
     if (st->error & kErrTimeout) {  // a bounded wait expired in a previous step: stop the loop
         if (threadIdx.x == 0) st->done = 1;
@@ -126,6 +128,8 @@ __global__ void __launch_bounds__(256) greedy_gather_kernel(
     const unsigned* __restrict__ H, const unsigned* __restrict__ Lo, const unsigned short* __restrict__ Aug,
     int d_pad, unsigned* __restrict__ cH, unsigned* __restrict__ cLo, unsigned short* __restrict__ cAug,
     unsigned short one_bits) {
+    pdl_wait();
+    pdl_trigger();
     if (st->done) return;
     const int s = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (s >= st->cand_count) return;
@@ -162,6 +166,8 @@ __global__ void __launch_bounds__(1024) greedy_resolve_kernel(DeviceState* st, c
                                                              const int* cand_ids, int* ordinal,
                                                              int* landmarks, unsigned long long mem_cap,
                                                              int stage_words, int s_max) {
+    pdl_wait();
+    pdl_trigger();
     if (st->done) return;
     // the new memberships are a subset of this step's hits: stop before anything
     // is committed if they might not fit (the host grows the buffer and redoes the step)
@@ -281,6 +287,8 @@ __global__ void __launch_bounds__(256) greedy_apply_kernel(DeviceState* st, cons
                                                            unsigned long long step_cap, const int* ordinal,
                                                            unsigned* covered, unsigned long long* mem_keys,
                                                            unsigned long long mem_cap) {
+    pdl_wait();
+    pdl_trigger();
     if (st->done) return;
     const unsigned long long cnt = st->step_hits;
     if (cnt > step_cap) {
@@ -317,11 +325,11 @@ cudaError_t launch_greedy_select(const GreedyBuffers& g, const Prepared& pts, in
                                  cudaStream_t s) {
     const int words = S / 32;
     note_launch();
-    greedy_select_kernel<<<1, kSelThreads, 0, s>>>(
-        g.st, g.covered, pts.rows, S, g.slot_of, g.cand_ids, g.conflict, g.row_any, words, pts.x, pts.phi,
-        pts.d, const_cast<float*>(g.cand.x), g.cand.phi, want_tc ? 1 : 0,
-        pts.hi, pts.lo, pts.aug, pts.d_pad, g.cand.hi, g.cand.lo, g.cand.aug);
-    return cudaGetLastError();
+    return launch_pdl(greedy_select_kernel, dim3(1), dim3(kSelThreads), 0, s,
+        g.st, (const unsigned*)g.covered, pts.rows, S, g.slot_of, g.cand_ids, g.conflict, g.row_any, words,
+        (const float*)pts.x, (const float*)pts.phi, pts.d, const_cast<float*>(g.cand.x), g.cand.phi, want_tc ? 1 : 0,
+        (const __nv_bfloat16*)pts.hi, (const __nv_bfloat16*)pts.lo, (const __nv_bfloat16*)pts.aug, pts.d_pad,
+        g.cand.hi, g.cand.lo, g.cand.aug);
 }
 
 // Undo the bookkeeping of a step stopped by a buffer overflow so that the next
@@ -345,13 +353,13 @@ cudaError_t launch_greedy_rollback(const GreedyBuffers& g, cudaStream_t s) {
 
 cudaError_t launch_greedy_gather(const GreedyBuffers& g, const Prepared& pts, int S, bool want_tc, cudaStream_t s) {
     note_launch();
-    greedy_gather_kernel<<<(S + 7) / 8, 256, 0, s>>>(
-        g.st, g.cand_ids, pts.x, pts.phi, pts.d, const_cast<float*>(g.cand.x), g.cand.phi, want_tc ? 1 : 0,
+    return launch_pdl(greedy_gather_kernel, dim3((S + 7) / 8), dim3(256), 0, s,
+        (const DeviceState*)g.st, (const int*)g.cand_ids, (const float*)pts.x, (const float*)pts.phi, pts.d,
+        const_cast<float*>(g.cand.x), g.cand.phi, want_tc ? 1 : 0,
         reinterpret_cast<const unsigned*>(pts.hi), reinterpret_cast<const unsigned*>(pts.lo),
         reinterpret_cast<const unsigned short*>(pts.aug), pts.d_pad, reinterpret_cast<unsigned*>(g.cand.hi),
         reinterpret_cast<unsigned*>(g.cand.lo), reinterpret_cast<unsigned short*>(g.cand.aug),
         (unsigned short)(pts.prec == kPrecFp16 ? 0x3C00u : 0x3F80u));   // 1.0 in fp16 / bf16
-    return cudaGetLastError();
 }
 
 cudaError_t launch_greedy_resolve(const GreedyBuffers& g, int S, cudaStream_t s) {
@@ -367,9 +375,9 @@ cudaError_t launch_greedy_resolve(const GreedyBuffers& g, int S, cudaStream_t s)
         attr_set = true;
     }
     note_launch();
-    greedy_resolve_kernel<<<1, 1024, smem, s>>>(g.st, g.conflict, g.row_any, words, g.cand_ids, g.ordinal,
-                                               g.landmarks, g.mem_cap, (int)(smem / sizeof(unsigned)), S);
-    return cudaGetLastError();
+    return launch_pdl(greedy_resolve_kernel, dim3(1), dim3(1024), smem, s, g.st, (const unsigned*)g.conflict,
+                      (const unsigned*)g.row_any, words, (const int*)g.cand_ids, g.ordinal, g.landmarks, g.mem_cap,
+                      (int)(smem / sizeof(unsigned)), S);
 }
 
 // Loop condition of a greedy build run as a graph WHILE node: another step while
@@ -398,9 +406,9 @@ cudaError_t launch_greedy_continue(const GreedyBuffers& g, cudaGraphConditionalH
 
 cudaError_t launch_greedy_apply(const GreedyBuffers& g, cudaStream_t s) {
     note_launch();
-    greedy_apply_kernel<<<152 * 8, 256, 0, s>>>(g.st, g.step_keys, g.step_cap, g.ordinal, g.covered, g.mem_keys,
-                                                 g.mem_cap);
-    return cudaGetLastError();
+    return launch_pdl(greedy_apply_kernel, dim3(152 * 8), dim3(256), 0, s, g.st,
+                      (const unsigned long long*)g.step_keys, g.step_cap, (const int*)g.ordinal, g.covered,
+                      g.mem_keys, g.mem_cap);
 }
 
 }  // namespace bm

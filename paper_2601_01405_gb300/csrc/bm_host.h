@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "ballmapper.h"
@@ -43,6 +44,29 @@ private:
 };
 
 void device_free(const bm_options* opt, cudaStream_t s, void* p);
+
+// Launch with programmatic stream serialization (the kernel must begin with pdl_wait();
+// see bm_common.cuh), so that its launch overlaps the predecessor kernel's tail.  Inside a
+// stream capture the launch is an ordinary one.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusActive;   // unknown: take the ordinary launch
+    }
+    cfg.attrs = cs == cudaStreamCaptureStatusNone ? attr : nullptr;
+    cfg.numAttrs = cs == cudaStreamCaptureStatusNone ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
 
 // Kernel launches issued by the current thread (reported in bm_stats).
 extern thread_local long long g_kernel_launches;

@@ -51,6 +51,8 @@ __global__ void __launch_bounds__(256) band_recheck_kernel(
     unsigned long long* count, unsigned long long cap, const int* slot_of, unsigned* conflict, unsigned* row_any,
     int words, int check_done, int overflow_bit, int stop_on_overflow, int vec4, double c_lo, double c_hi,
     double abs_slack, const double* __restrict__ row_eps2) {
+    pdl_wait();
+    pdl_trigger();
     if (check_done && st->done) return;
     const unsigned long long nb_raw = st->band_n;
     const unsigned long long nb = nb_raw < band_cap ? nb_raw : band_cap;
@@ -130,12 +132,10 @@ cudaError_t launch_band_recheck(DeviceState* st, const unsigned long long* band,
     const double c_hi = (1.0 + g64) / (1.0 - g32) * (1.0 + std::ldexp(1.0, -50));
     const double abs_slack = d * std::ldexp(1.0, -125);
     note_launch();
-    band_recheck_kernel<<<device_sm_count() * 4, 256, 0, s>>>(st, band, band_cap, ax, bx, d, eps2, keys, count, cap,
-                                                             book.slot_of, book.conflict, book.row_any,
-                                                             book.conflict_words, check_done ? 1 : 0, overflow_bit,
-                                                             stop_on_overflow ? 1 : 0, vec4, c_lo, c_hi, abs_slack,
-                                                             row_eps2);
-    return cudaGetLastError();
+    return launch_pdl(band_recheck_kernel, dim3(device_sm_count() * 4), dim3(256), 0, s, st, band, band_cap, ax, bx, d,
+                      eps2, keys, count, cap, book.slot_of, book.conflict, book.row_any, book.conflict_words,
+                      check_done ? 1 : 0, overflow_bit, stop_on_overflow ? 1 : 0, vec4, c_lo, c_hi, abs_slack,
+                      row_eps2);
 }
 
 }  // namespace bm
