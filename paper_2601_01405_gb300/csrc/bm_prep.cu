@@ -27,6 +27,17 @@
 
 namespace bm {
 
+// One warp per group of 32 rows.  The coordinates are read coalesced (row by row, 32
+// columns at a time) and staged in shared memory, so that each lane then owns one row's
+// FP64 sum of squares: one FP64 multiply-add per coordinate and no cross-lane FP64
+// reduction (FP64 throughput is the limit of this kernel on GB300).  The bf16 split, phi
+// (FP64, rounded to float) and the augmentation row are written as before.
+constexpr int kPrepWarps = 8;
+
+__device__ __forceinline__ int aug_pos(int col, int a_side) {
+    return a_side ? col : (col < 3 ? col + 3 : (col < 6 ? col - 3 : col));
+}
+
 __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ x, long long rows, int d,
                                                    double eps2, const double* __restrict__ row_r2,
                                                    int a_side, int want_tc,
@@ -35,58 +46,77 @@ __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ x, 
                                                    __nv_bfloat16* __restrict__ lo,
                                                    __nv_bfloat16* __restrict__ aug, int d_pad,
                                                    unsigned* max_norm_bits, int* bad_flag) {
-    __shared__ float s_max[8];
+    __shared__ float tile[kPrepWarps][32][33];
+    __shared__ float s_max[kPrepWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int D = want_tc ? d_pad : d;   // columns summed (zeros past d) and, for the tiles, written
     float my_max = 0.f;
-    const long long warps_total = (long long)gridDim.x * 8;
-    for (long long r = (long long)blockIdx.x * 8 + warp; r < rows; r += warps_total) {
-        const float* xr = x + r * d;
+    bool bad = false;
+    const long long groups = (rows + 31) / 32;
+    for (long long gi = (long long)blockIdx.x * kPrepWarps + warp; gi < groups; gi += (long long)gridDim.x * kPrepWarps) {
+        const long long r0 = gi * 32;
         double s = 0.0;
-        bool bad = false;
-        for (int i = lane; i < (want_tc ? d_pad : d); i += 32) {
-            float v = i < d ? xr[i] : 0.f;
-            if (!isfinite(v)) bad = true;
-            s += (double)v * (double)v;
-            if (want_tc) {
-                __nv_bfloat16 h = __float2bfloat16_rn(v);
-                __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
-                hi[r * d_pad + i] = h;
-                lo[r * d_pad + i] = l;
+        for (int c0 = 0; c0 < D; c0 += 32) {
+            const int i = c0 + lane;
+            for (int rr = 0; rr < 32; ++rr) {
+                const long long r = r0 + rr;
+                float v = 0.f;
+                if (r < rows && i < d) {
+                    v = x[r * d + i];
+                    if (!isfinite(v)) bad = true;
+                }
+                if (want_tc && r < rows && i < D) {
+                    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+                    hi[r * d_pad + i] = h;
+                    lo[r * d_pad + i] = __float2bfloat16_rn(v - __bfloat162float(h));
+                }
+                tile[warp][rr][lane] = v;
             }
+            __syncwarp();
+#pragma unroll 8
+            for (int j = 0; j < 32; ++j) {
+                const double v = (double)tile[warp][lane][j];
+                s += v * v;
+            }
+            __syncwarp();
         }
+        const long long r = r0 + lane;
+        if (r < rows) {
+            // per-row radius (query side of a k-NN sweep): the whole r^2 on this side
+            const double phi = row_r2 ? 0.5 * s - 0.5 * row_r2[r] : 0.5 * s - 0.25 * eps2;
+            phi_out[r] = (float)phi;
+            if (want_tc) {
+                const __nv_bfloat16 p1 = __double2bfloat16(phi);
+                const double r1 = phi - (double)__bfloat162float(p1);
+                const __nv_bfloat16 p2 = __double2bfloat16(r1);
+                const double r2 = r1 - (double)__bfloat162float(p2);
+                const __nv_bfloat16 p3 = __double2bfloat16(r2);
+                const __nv_bfloat16 one = __float2bfloat16_rn(1.f);
+                const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+                // pos < 3: the -p pieces; 3 <= pos < 6: ones (A side layout; B side swaps halves);
+                // pos 6 on the A side: 1 against the points' +delta' (set_aug_delta)
+                __align__(16) __nv_bfloat16 a[16];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-        if (__any_sync(kFull, bad) && lane == 0) atomicExch(bad_flag, 1);
-        // per-row radius (query side of a k-NN sweep): the whole r^2 on this side
-        const double phi = row_r2 ? 0.5 * s - 0.5 * row_r2[r] : 0.5 * s - 0.25 * eps2;
-        if (lane == 0) phi_out[r] = (float)phi;
-        if (want_tc && lane < 16) {
-            const __nv_bfloat16 p1 = __double2bfloat16(phi);
-            const double r1 = phi - (double)__bfloat162float(p1);
-            const __nv_bfloat16 p2 = __double2bfloat16(r1);
-            const double r2 = r1 - (double)__bfloat162float(p2);
-            const __nv_bfloat16 p3 = __double2bfloat16(r2);
-            const __nv_bfloat16 one = __float2bfloat16_rn(1.f);
-            const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
-            __nv_bfloat16 v = zero;
-            const int pos = a_side ? lane : (lane < 3 ? lane + 3 : (lane < 6 ? lane - 3 : lane));
-            // pos < 3 : the -p pieces ; 3 <= pos < 6 : ones (A side layout; B side swaps halves)
-            if (pos == 0) v = __hneg(p1);
-            else if (pos == 1) v = __hneg(p2);
-            else if (pos == 2) v = __hneg(p3);
-            else if (pos < 6) v = one;
-            else if (pos == 6 && a_side) v = one;   // times the points' +delta' (set_aug_delta)
-            aug[r * 16 + lane] = v;
+                for (int col = 0; col < 16; ++col) {
+                    const int pos = aug_pos(col, a_side);
+                    a[col] = pos == 0 ? __hneg(p1) : pos == 1 ? __hneg(p2) : pos == 2 ? __hneg(p3)
+                           : pos < 6 ? one : (pos == 6 && a_side) ? one : zero;
+                }
+                uint4* dst = reinterpret_cast<uint4*>(aug + r * 16);
+                dst[0] = reinterpret_cast<const uint4*>(a)[0];
+                dst[1] = reinterpret_cast<const uint4*>(a)[1];
+            }
+            my_max = fmaxf(my_max, __fsqrt_ru(__double2float_ru(s)));   // an upper bound of the norm
         }
-        my_max = fmaxf(my_max, __double2float_ru(sqrt(s)));
     }
+    if (__any_sync(kFull, bad) && lane == 0) atomicExch(bad_flag, 1);
     // block max -> one atomic per block (norms are >= 0, so float bits order as unsigned)
     for (int o = 16; o > 0; o >>= 1) my_max = fmaxf(my_max, __shfl_xor_sync(kFull, my_max, o));
     if (lane == 0) s_max[warp] = my_max;
     __syncthreads();
     if (threadIdx.x == 0) {
         float m = 0.f;
-        for (int w = 0; w < 8; ++w) m = fmaxf(m, s_max[w]);
+        for (int w = 0; w < kPrepWarps; ++w) m = fmaxf(m, s_max[w]);
         atomicMax(max_norm_bits, __float_as_uint(m));
     }
 }
@@ -96,35 +126,54 @@ __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ x, 
 // phi_s = ||xs||^2 / 2 - eps^2 4^e / 4 (FP64), in the same positions as the bf16 block.
 // The scale 2^e keeps every operand and phi piece inside the fp16 range.
 __global__ void __launch_bounds__(256) prep16_kernel(const float* __restrict__ x, long long rows, int d, int d_pad,
-                                                     double scale, double eps2s, int a_side,
+                                                     int scale_exp, double eps2s, int a_side,
                                                      __half* __restrict__ hi, __half* __restrict__ aug) {
+    __shared__ float tile[kPrepWarps][32][33];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long warps_total = (long long)gridDim.x * 8;
-    for (long long r = (long long)blockIdx.x * 8 + warp; r < rows; r += warps_total) {
-        const float* xr = x + r * d;
-        double s = 0.0;
-        for (int i = lane; i < d_pad; i += 32) {
-            const double v = i < d ? (double)xr[i] * scale : 0.0;
-            s += v * v;
-            hi[r * d_pad + i] = __double2half(v);
+    const double scale = ldexp(1.0, scale_exp);
+    // x 2^e is exact in float (and so is its fp16 rounding) while 2^e is a normal float
+    const bool fscale = scale_exp >= -120 && scale_exp <= 120;
+    const float scalef = fscale ? ldexpf(1.f, scale_exp) : 1.f;
+    const long long groups = (rows + 31) / 32;
+    for (long long gi = (long long)blockIdx.x * kPrepWarps + warp; gi < groups; gi += (long long)gridDim.x * kPrepWarps) {
+        const long long r0 = gi * 32;
+        double s = 0.0;   // sum of x_i^2; the scaled sum is s 4^e, exactly
+        for (int c0 = 0; c0 < d_pad; c0 += 32) {
+            const int i = c0 + lane;
+            for (int rr = 0; rr < 32; ++rr) {
+                const long long r = r0 + rr;
+                const float v = (r < rows && i < d) ? x[r * d + i] : 0.f;
+                if (r < rows && i < d_pad)
+                    hi[r * d_pad + i] = fscale ? __float2half_rn(v * scalef) : __double2half((double)v * scale);
+                tile[warp][rr][lane] = v;
+            }
+            __syncwarp();
+#pragma unroll 8
+            for (int j = 0; j < 32; ++j) {
+                const double v = (double)tile[warp][lane][j];
+                s += v * v;
+            }
+            __syncwarp();
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-        if (lane < 16) {
-            const double phi = 0.5 * s - 0.25 * eps2s;
+        const long long r = r0 + lane;
+        if (r < rows) {
+            const double phi = 0.5 * (s * scale * scale) - 0.25 * eps2s;
             const __half p1 = __double2half(phi);
             const double r1 = phi - (double)__half2float(p1);
             const __half p2 = __double2half(r1);
             const double r2 = r1 - (double)__half2float(p2);
             const __half p3 = __double2half(r2);
-            __half v = __float2half_rn(0.f);
-            const int pos = a_side ? lane : (lane < 3 ? lane + 3 : (lane < 6 ? lane - 3 : lane));
-            if (pos == 0) v = __hneg(p1);
-            else if (pos == 1) v = __hneg(p2);
-            else if (pos == 2) v = __hneg(p3);
-            else if (pos < 6) v = __float2half_rn(1.f);
-            else if (pos == 6 && a_side) v = __float2half_rn(1.f);
-            aug[r * 16 + lane] = v;
+            const __half one = __float2half_rn(1.f), zero = __float2half_rn(0.f);
+            __align__(16) __half a[16];
+#pragma unroll
+            for (int col = 0; col < 16; ++col) {
+                const int pos = aug_pos(col, a_side);
+                a[col] = pos == 0 ? __hneg(p1) : pos == 1 ? __hneg(p2) : pos == 2 ? __hneg(p3)
+                       : pos < 6 ? one : (pos == 6 && a_side) ? one : zero;
+            }
+            uint4* dst = reinterpret_cast<uint4*>(aug + r * 16);
+            dst[0] = reinterpret_cast<const uint4*>(a)[0];
+            dst[1] = reinterpret_cast<const uint4*>(a)[1];
         }
     }
 }
@@ -132,13 +181,14 @@ __global__ void __launch_bounds__(256) prep16_kernel(const float* __restrict__ x
 cudaError_t launch_prep16(const float* x, long long rows, int d, double eps2, bool a_side, int scale_exp,
                           Prepared& p, cudaStream_t s) {
     if (rows == 0) return cudaSuccess;
-    long long blocks = (rows + 7) / 8;
+    long long blocks = (rows + 255) / 256;   // 8 warps of 32-row groups per block
     if (blocks > 152 * 16) blocks = 152 * 16;
     const double scale = ldexp(1.0, scale_exp);
     p.scale_exp = scale_exp;
     note_launch();
-    prep16_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, rows, d, p.d_pad, scale, eps2 * scale * scale, a_side ? 1 : 0,
-                                                   reinterpret_cast<__half*>(p.hi), reinterpret_cast<__half*>(p.aug));
+    prep16_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, rows, d, p.d_pad, scale_exp, eps2 * scale * scale,
+                                                   a_side ? 1 : 0, reinterpret_cast<__half*>(p.hi),
+                                                   reinterpret_cast<__half*>(p.aug));
     return cudaGetLastError();
 }
 
@@ -155,7 +205,7 @@ int fp16_scale_exp(double max_norm, double eps) {
 cudaError_t launch_prep(const float* x, long long rows, int d, double eps2, bool a_side, bool want_tc,
                         Prepared& out, unsigned* max_norm_bits, int* bad_flag, cudaStream_t s, const double* row_r2) {
     if (rows == 0) return cudaSuccess;
-    long long blocks = (rows + 7) / 8;
+    long long blocks = (rows + 255) / 256;   // 8 warps of 32-row groups per block
     if (blocks > 152 * 16) blocks = 152 * 16;
     note_launch();
     prep_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, rows, d, eps2, row_r2, a_side ? 1 : 0, want_tc ? 1 : 0,
