@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline sample")
     ap.add_argument("--dists-builds", type=int, default=1,
                     help="untimed builds per eps with reported distances (their measured error); 0: skip")
+    ap.add_argument("--other-configs", type=int, default=1,
+                    help="also time whole builds of the other configurations (1 rank, N = 1 only; 0: skip)")
     ap.add_argument("--kernel-probe", action="store_true",
                     help="time one distance-tile launch shape (a range query of --rows rows) and exit")
     ap.add_argument("--rows", type=int, default=1024, help="query rows of the kernel probe")
@@ -399,6 +401,9 @@ def run_ours(args):
                "h2d_bytes_per_step": int(n * d * 4 * len(eps_list)),
                "d2h_bytes_per_step": int(d2h // args.e2e_steps)}
 
+    if rank == 0 and ws == 1 and args.other_configs > 0 and args.workload == "mix32-n1M-d64":
+        extra["other_configs"] = _guarded(lambda: other_configs(args.path))
+
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_seconds > 0:
         r, ev, dt, rows, thr = oracle_rate(X, eps_list, args.cpu_seconds)
@@ -424,6 +429,47 @@ def run_ours(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def other_configs(path, reps=3):
+    """Whole builds of the other configurations, device-resident inputs: the median of the
+    library's CUDA-event total over reps builds after one warm-up, with the result sizes;
+    batched-256: the whole bm_build_batched call (CUDA events)."""
+    import statistics
+    import torch
+    from paper_2601_01405_gb300 import binding, workloads as W
+    out = []
+    for name in ("iso-n10k-d16", "roll-n2M-d128", "iso-n1M-d128"):
+        wl = W.WORKLOADS[name]
+        Xd = torch.from_numpy(W.make(name)).cuda()
+        for e in wl.eps:
+            binding.bm_build(Xd, e, path=path)
+            runs, g = [], None
+            for _ in range(reps):
+                g = binding.bm_build(Xd, e, path=path)
+                runs.append(g["stats"]["ms_total"])
+            out.append({"workload": name, "eps": e, "build_s": statistics.median(runs) / 1e3,
+                        "landmarks": int(g["landmarks"].numel()), "memberships": int(g["ids"].numel()),
+                        "edges": int(g["edges"].shape[0]),
+                        "path_used": {v: k for k, v in binding.PATHS.items()}.get(g["stats"]["path"])})
+            del g
+        del Xd
+    inst = W.batched_instances(count=256)
+    dev = [(torch.from_numpy(i.x).cuda(), i.eps) for i in inst]
+    binding.bm_build_batched(dev, path=path)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        res = binding.bm_build_batched(dev, path=path)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    out.append({"workload": "batched-256", "instances": len(inst), "build_s": statistics.median(ms) / 1e3,
+                "landmarks": int(sum(r["landmarks"].numel() for r in res)),
+                "memberships": int(sum(r["ids"].numel() for r in res))})
+    return out
 
 
 def run_kernel_probe(args):
