@@ -232,51 +232,62 @@ __global__ void __launch_bounds__(512) nerve_rows_kernel(const unsigned long lon
             if (threadIdx.x == 0) atomicOr(bad, 16);
             continue;
         }
-        for (long long e = e0 + warp; e < e1; e += nwarps) {
-            const unsigned long long key = keys[e];
-            const long long x = (long long)(key & 0xffffffffull);
-            if ((long long)(key >> 32) != i || x >= n) {
-                if (lane == 0) atomicOr(bad, 1);
-                continue;
-            }
-            const long long b0 = toff[x], end = toff[x + 1];
-            if (b0 < 0 || end > nnz || b0 >= end) {
-                if (lane == 0) atomicOr(bad, 2);
-                continue;
-            }
-            const long long t = tpos[e];   // where membership e sits in x's cover list
-            if (t < b0 || t >= end || tlist[t] != (int)i) {
-                if (lane == 0) atomicOr(bad, 32);
-                continue;
-            }
-            // four loads in flight per lane before the bits are combined
-            for (long long base = t + 1; base < end; base += 128) {
-                int jv[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const long long b = base + u * 32 + lane;
-                    jv[u] = b < end ? tlist[b] : 0;
+        // 32 memberships per warp at a time: their look-ups (the point, its cover list's
+        // extent, where i sits in it) are one load per lane, issued together; then the
+        // warp walks the 32 suffixes one after the other
+        for (long long eb = e0 + (long long)warp * 32; eb < e1; eb += (long long)nwarps * 32) {
+            const long long e = eb + lane;
+            long long t = 0, end = 0;
+            bool good = false;
+            if (e < e1) {
+                const unsigned long long key = keys[e];
+                const long long x = (long long)(key & 0xffffffffull);
+                if ((long long)(key >> 32) != i || x >= n) {
+                    atomicOr(bad, 1);
+                } else {
+                    const long long b0 = toff[x];
+                    end = toff[x + 1];
+                    if (b0 < 0 || end > nnz || b0 >= end) {
+                        atomicOr(bad, 2);
+                    } else {
+                        t = tpos[e];   // where membership e sits in x's cover list
+                        if (t < b0 || t >= end || tlist[t] != (int)i) atomicOr(bad, 32);
+                        else good = true;
+                    }
                 }
+            }
+            for (unsigned mm = __ballot_sync(kFull, good); mm; mm &= mm - 1) {
+                const int m = __ffs(mm) - 1;
+                const long long tm = __shfl_sync(kFull, t, m), endm = __shfl_sync(kFull, end, m);
+                // four loads in flight per lane before the bits are combined
+                for (long long base = tm + 1; base < endm; base += 128) {
+                    int jv[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (base + u * 32 >= end) break;   // warp-uniform
-                    const bool valid = base + u * 32 + lane < end;
-                    int j = jv[u];
-                    if (valid && (j <= (int)i || (long long)(j >> 5) >= W)) {
-                        atomicOr(bad, 4);
-                        j = 0;
+                    for (int u = 0; u < 4; ++u) {
+                        const long long b = base + u * 32 + lane;
+                        jv[u] = b < endm ? tlist[b] : 0;
                     }
-                    const bool ok = valid && j > (int)i;
-                    const int word = ok ? (j >> 5) : -1 - lane;
-                    unsigned acc = ok ? (1u << (j & 31)) : 0u;
 #pragma unroll
-                    for (int off = 1; off < 32; off <<= 1) {
-                        const unsigned v = __shfl_down_sync(kFull, acc, off);
-                        const int w = __shfl_down_sync(kFull, word, off);
-                        if (lane + off < 32 && w == word) acc |= v;
+                    for (int u = 0; u < 4; ++u) {
+                        if (base + u * 32 >= endm) break;   // warp-uniform
+                        const bool valid = base + u * 32 + lane < endm;
+                        int j = jv[u];
+                        if (valid && (j <= (int)i || (long long)(j >> 5) >= W)) {
+                            atomicOr(bad, 4);
+                            j = 0;
+                        }
+                        const bool ok = valid && j > (int)i;
+                        const int word = ok ? (j >> 5) : -1 - lane;
+                        unsigned acc = ok ? (1u << (j & 31)) : 0u;
+#pragma unroll
+                        for (int off = 1; off < 32; off <<= 1) {
+                            const unsigned v = __shfl_down_sync(kFull, acc, off);
+                            const int w = __shfl_down_sync(kFull, word, off);
+                            if (lane + off < 32 && w == word) acc |= v;
+                        }
+                        const int wprev = __shfl_up_sync(kFull, word, 1);
+                        if (ok && (lane == 0 || wprev != word)) atomicOr(&srow[word], acc);
                     }
-                    const int wprev = __shfl_up_sync(kFull, word, 1);
-                    if (ok && (lane == 0 || wprev != word)) atomicOr(&srow[word], acc);
                 }
             }
         }
