@@ -76,6 +76,20 @@ typedef enum {
                             * the path the build finished on. */
 } bm_path;
 
+/* Translation of the tensor-core operands.  D(q, x) is unchanged when every point and
+ * query moves by the same vector c, while the proven error band grows with the operands'
+ * norms (Sec. 3.2: the expanded form ||q||^2 + ||x||^2 - 2 q.x loses precision when the
+ * norms dwarf the distances).  The tensor-core tiles may therefore work on fl(x - c), c the
+ * mean of a sample of the points (up to 65,536 rows); results are identical either way
+ * (the FP64 recheck takes the original coordinates), only the band width changes. */
+typedef enum {
+    BM_CENTRE_AUTO = 0,    /* default: translate when the call has at least 65,536 points, takes a
+                            * tensor-core path without an inverted-file or graph index, and c shrinks
+                            * the sample's largest squared norm by 5 % or more */
+    BM_CENTRE_ALWAYS = 1,  /* translate whenever a tensor-core path without an index is taken */
+    BM_CENTRE_OFF = 2      /* never translate */
+} bm_centring;
+
 /* Allocation callbacks: return device (or, for host outputs, ignored) memory
  * of at least `bytes` bytes ordered on `stream`; NULL signals failure. */
 typedef void* (*bm_alloc_fn)(size_t bytes, void* stream, void* ctx);
@@ -97,7 +111,8 @@ typedef struct {
     int32_t want_dists;    /* bm_build, bm_range_query, bm_build_ivf, bm_ivf_range_query: 1 = also return
                               the distance of every stored pair (bm_csr.dists) and its measured error
                               (bm_stats.dist_max_rel_err); bm_build_batched rejects it (BM_ERR_ARG) */
-    int32_t reserved1;
+    int32_t centring;      /* bm_centring (bm_build, bm_range_query and bm_build_batched, per instance;
+                              other values: BM_ERR_ARG); the calls built on these follow it too */
 } bm_options;
 
 typedef struct {
@@ -118,7 +133,7 @@ typedef struct {
                                  D the FP64 squared distance in coordinate order (the CPU oracle's value);
                                  the rounding of sqrt(D) to float bounds it by 2^-24; 0 otherwise */
     int32_t truncated;        /* graph index: 1 when a query stopped at its visit cap */
-    int32_t reserved2;
+    int32_t centred;          /* 1 when the tensor-core operands were those of the translated points */
 } bm_stats;
 
 typedef struct {

@@ -24,6 +24,7 @@ LIB_PATH = os.path.join(_PKG, "lib", "libballmapper.so")
 BM_OK, BM_ERR_ARG, BM_ERR_CUDA, BM_ERR_NOMEM, BM_ERR_CAPACITY, BM_ERR_TIMEOUT, BM_ERR_UNSUPPORTED = range(7)
 BM_PATH_TC_SPLIT3, BM_PATH_FP32, BM_PATH_TC_FP16, BM_PATH_TC_AUTO = 0, 1, 2, 3
 PATHS = {"tc": BM_PATH_TC_SPLIT3, "fp32": BM_PATH_FP32, "tc16": BM_PATH_TC_FP16, "auto": BM_PATH_TC_AUTO}
+BM_CENTRE_AUTO, BM_CENTRE_ALWAYS, BM_CENTRE_OFF = 0, 1, 2
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
@@ -33,7 +34,7 @@ class bm_options(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("path", ctypes.c_int32), ("host_io", ctypes.c_int32),
                 ("batch", ctypes.c_int32), ("skip_edges", ctypes.c_int32), ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("want_dists", ctypes.c_int32),
-                ("reserved1", ctypes.c_int32)]
+                ("centring", ctypes.c_int32)]
 
 
 class bm_stats(ctypes.Structure):
@@ -43,7 +44,7 @@ class bm_stats(ctypes.Structure):
                 ("ms_edges", ctypes.c_double), ("ms_total", ctypes.c_double), ("band_delta", ctypes.c_float),
                 ("path", ctypes.c_int32), ("ms_sweep", ctypes.c_double), ("sweep_launches", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("recheck_rate", ctypes.c_double),
-                ("dist_max_rel_err", ctypes.c_double), ("truncated", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+                ("dist_max_rel_err", ctypes.c_double), ("truncated", ctypes.c_int32), ("centred", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -232,10 +233,14 @@ def _is_torch_cuda(x) -> bool:
     return isinstance(x, torch.Tensor) and x.is_cuda
 
 
+CENTRING = {"auto": BM_CENTRE_AUTO, "always": BM_CENTRE_ALWAYS, "off": BM_CENTRE_OFF}
+
+
 def _options(lib, path: str, batch: int, stream, host_io: bool, alloc: Optional[_TorchAllocator],
-             skip_edges: bool = False, want_dists: bool = False):
+             skip_edges: bool = False, want_dists: bool = False, centring: str = "auto"):
     opt = bm_options()
     lib.bm_options_init(ctypes.byref(opt))
+    opt.centring = CENTRING[centring]
     opt.skip_edges = 1 if skip_edges else 0
     opt.want_dists = 1 if want_dists else 0
     opt.path = PATHS[path]
@@ -273,12 +278,15 @@ def _as_input(x, d_expected=None):
     return (a.ctypes.data if a.size else None), a.shape[0], a.shape[1], a, True
 
 
-def bm_range_query(X, Q, eps: float, path: str = "auto", stream=None, want_dists: bool = False):
+def bm_range_query(X, Q, eps: float, path: str = "auto", stream=None, want_dists: bool = False,
+                   centring: str = "auto"):
     """Exact range query R_eps(q) for every row q of Q over the points X.
 
     Device tensors in -> torch CUDA tensors out; host arrays in -> numpy out.
     Returns (offsets int64 [m+1], ids int32 [nnz], stats dict); with want_dists,
-    (offsets, ids, stats, dists float32 [nnz]) where dists[e] = d(Q_row, X[ids[e]])."""
+    (offsets, ids, stats, dists float32 [nnz]) where dists[e] = d(Q_row, X[ids[e]]).
+    centring: "auto", "always" or "off" (bm_options.centring: whether the tensor-core
+    tiles take the points and queries translated by the points' sample mean)."""
     lib = load()
     px, n, d, kx, hx = _as_input(X)
     pq, m, dq, kq, hq = _as_input(Q)
@@ -289,7 +297,7 @@ def bm_range_query(X, Q, eps: float, path: str = "auto", stream=None, want_dists
     out = bm_csr()
     st = bm_stats()
     if hx:
-        opt = _options(lib, path, 0, stream, True, None, want_dists=want_dists)
+        opt = _options(lib, path, 0, stream, True, None, want_dists=want_dists, centring=centring)
         _check(lib, lib.bm_range_query(px, n, d, pq, m, ctypes.c_float(eps), ctypes.byref(opt), ctypes.byref(out),
                                        ctypes.byref(st)))
         try:
@@ -305,7 +313,8 @@ def bm_range_query(X, Q, eps: float, path: str = "auto", stream=None, want_dists
     import torch
     dev = kx.device
     alloc = _TorchAllocator(dev)
-    opt = _options(lib, path, 0, stream or _current_stream(dev), False, alloc, want_dists=want_dists)
+    opt = _options(lib, path, 0, stream or _current_stream(dev), False, alloc, want_dists=want_dists,
+                   centring=centring)
     _check(lib, lib.bm_range_query(px, n, d, pq, m, ctypes.c_float(eps), ctypes.byref(opt), ctypes.byref(out),
                                    ctypes.byref(st)))
     off = alloc.tensor(out.offsets, m + 1, torch.int64)
@@ -316,17 +325,18 @@ def bm_range_query(X, Q, eps: float, path: str = "auto", stream=None, want_dists
 
 
 def bm_build(X, eps: float, path: str = "auto", batch: int = 0, stream=None, skip_edges: bool = False,
-             want_dists: bool = False):
+             want_dists: bool = False, centring: str = "auto"):
     """Exact Ball Mapper: landmarks (greedy index order), CSR memberships, nerve edges.
 
     Device tensor in -> dict of torch CUDA tensors; host array in -> dict of numpy arrays.
     Keys: landmarks int32 [L], offsets int64 [L+1], ids int32 [nnz], edges int32 [E, 2], stats;
-    with want_dists also dists float32 [nnz] (distance of each member to its landmark)."""
+    with want_dists also dists float32 [nnz] (distance of each member to its landmark).
+    centring: "auto", "always" or "off" (bm_options.centring)."""
     lib = load()
     px, n, d, kx, host = _as_input(X)
     g = bm_graph()
     if host:
-        opt = _options(lib, path, batch, stream, True, None, skip_edges, want_dists)
+        opt = _options(lib, path, batch, stream, True, None, skip_edges, want_dists, centring)
         _check(lib, lib.bm_build(px, n, d, ctypes.c_float(eps), ctypes.byref(opt), ctypes.byref(g)))
         try:
             L, nnz, E = g.n_landmarks, g.members.nnz, g.n_edges
@@ -347,7 +357,7 @@ def bm_build(X, eps: float, path: str = "auto", batch: int = 0, stream=None, ski
     import torch
     dev = kx.device
     alloc = _TorchAllocator(dev)
-    opt = _options(lib, path, batch, stream or _current_stream(dev), False, alloc, skip_edges, want_dists)
+    opt = _options(lib, path, batch, stream or _current_stream(dev), False, alloc, skip_edges, want_dists, centring)
     _check(lib, lib.bm_build(px, n, d, ctypes.c_float(eps), ctypes.byref(opt), ctypes.byref(g)))
     return _graph_dict(alloc, g, want_dists)
 
@@ -470,7 +480,7 @@ def bm_occupancy_eps(X, k: int, path: str = "auto", stream=None):
 
 
 def bm_build_batched(instances, path: str = "auto", batch: int = 0, stream=None, skip_edges: bool = False,
-                     batches=None):
+                     batches=None, centring: str = "auto"):
     """Many independent exact builds in one call; the greedy loops of all instances
     run inside one CUDA graph.  instances: sequence of (X, eps), all CUDA tensors
     (results as torch tensors) or all host arrays (results as numpy arrays).
@@ -495,7 +505,7 @@ def bm_build_batched(instances, path: str = "auto", batch: int = 0, stream=None,
     outs = (bm_graph * max(count, 1))()
     statuses = (ctypes.c_int32 * max(count, 1))()
     if host:
-        opt = _options(lib, path, batch, stream, True, None, skip_edges)
+        opt = _options(lib, path, batch, stream, True, None, skip_edges, centring=centring)
         _check(lib, lib.bm_build_batched(arr_in, count, ctypes.byref(opt), outs, statuses))
 
         def arr(ptr, ctype, k):
@@ -517,7 +527,7 @@ def bm_build_batched(instances, path: str = "auto", batch: int = 0, stream=None,
     import torch
     dev = ins[0][3].device if count else torch.device("cuda", torch.cuda.current_device())
     alloc = _TorchAllocator(dev)
-    opt = _options(lib, path, batch, stream or _current_stream(dev), False, alloc, skip_edges)
+    opt = _options(lib, path, batch, stream or _current_stream(dev), False, alloc, skip_edges, centring=centring)
     _check(lib, lib.bm_build_batched(arr_in, count, ctypes.byref(opt), outs, statuses))
     res = []
     for g in outs[:count]:

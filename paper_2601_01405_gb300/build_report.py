@@ -20,6 +20,8 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--batch", type=int, default=0, help="largest greedy batch (0 = the library default)")
     ap.add_argument("--skip-edges", action="store_true")
+    ap.add_argument("--centring", choices=["auto", "always", "off"], default="auto",
+                    help="translation of the tensor-core operands (bm_options.centring)")
     a = ap.parse_args(argv)
 
     import torch
@@ -29,13 +31,14 @@ def main(argv=None):
     X = workloads.make(a.workload)
     Xd = torch.from_numpy(X).cuda()
     for eps in (a.eps or list(wl.eps)):
-        binding.bm_build(Xd, eps, path=a.path, batch=a.batch, skip_edges=a.skip_edges)
+        binding.bm_build(Xd, eps, path=a.path, batch=a.batch, skip_edges=a.skip_edges, centring=a.centring)
         torch.cuda.synchronize()
         runs = []
         out = None
         for _ in range(a.reps):
             out = None
-            out = binding.bm_build(Xd, eps, path=a.path, batch=a.batch, skip_edges=a.skip_edges)
+            out = binding.bm_build(Xd, eps, path=a.path, batch=a.batch, skip_edges=a.skip_edges,
+                                   centring=a.centring)
             torch.cuda.synchronize()
             runs.append(out["stats"])
         med = {k: statistics.median(r[k] for r in runs)
@@ -45,6 +48,7 @@ def main(argv=None):
                           "landmarks": int(out["landmarks"].numel()), "memberships": int(out["ids"].numel()),
                           "edges": int(out["edges"].shape[0]), "edge_pairs": st["edge_pairs"],
                           "greedy_steps": st["greedy_steps"], "band_pairs": st["band_pairs"],
+                          "band_delta": st["band_delta"], "centring": a.centring, "centred": st["centred"],
                           "path_used": {v: k for k, v in binding.PATHS.items()}.get(st["path"], st["path"]),
                           "distance_evals": st["distance_evals"], "tile_pairs": st["tile_pairs"],
                           "evals_per_s": st["distance_evals"] / (med["ms_total"] / 1e3), "median_ms": med,

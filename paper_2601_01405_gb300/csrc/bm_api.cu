@@ -149,6 +149,12 @@ bm_status validate_points(const float* X, long long n, int d, const char* name) 
     return BM_OK;
 }
 
+bm_status validate_centring(int c) {
+    if (c != BM_CENTRE_AUTO && c != BM_CENTRE_ALWAYS && c != BM_CENTRE_OFF)
+        return fail(BM_ERR_ARG, "centring must be BM_CENTRE_AUTO, BM_CENTRE_ALWAYS or BM_CENTRE_OFF");
+    return BM_OK;
+}
+
 bm_status validate_eps(float eps) {
     if (!std::isfinite(eps) || !(eps > 0.f)) return fail(BM_ERR_ARG, "eps must be finite and > 0");
     return BM_OK;
@@ -228,11 +234,13 @@ int prec_for(int path) {
 // bf16 split (kPrecSplit) here; the fp16 operands (kPrecFp16) only once the scale
 // is known (finish_fp16, after the norms have been read back).
 bm_status prepare(const float* x, long long rows, int d, double eps2, bool a_side, int prec, Arena& ar,
-                  unsigned* max_norm_bits, int* bad, cudaStream_t s, Prepared& p, const double* row_r2 = nullptr) {
+                  unsigned* max_norm_bits, int* bad, cudaStream_t s, Prepared& p, const double* row_r2 = nullptr,
+                  const float* centre = nullptr) {
     p.x = x;
     p.rows = rows;
     p.d = d;
     p.prec = prec;
+    p.centre = prec != kPrecNone ? centre : nullptr;
     const TileConfig tcfg = tile_config_for(d, prec == kPrecFp16 ? 1 : 3);
     p.d_pad = tcfg.d_pad;
     p.ck = tcfg.ck;
@@ -246,6 +254,26 @@ bm_status prepare(const float* x, long long rows, int d, double eps2, bool a_sid
     }
     if (prec == kPrecSplit) ALLOC(p.lo, __nv_bfloat16, std::max<long long>(rows, 1) * p.d_pad);
     TRY_CUDA(launch_prep(x, rows, d, eps2, a_side, prec == kPrecSplit, p, max_norm_bits, bad, s, row_r2));
+    return BM_OK;
+}
+
+// Centre of the tensor-core operands of a call over the points x (null: none), as
+// opt.centring asks; the device's choice lands in st->centred.  Lives in the call's arena.
+constexpr long long kCentreMinRows = 65536;
+
+bm_status operand_centre(const float* x, long long rows, int d, const bm_options& opt, DeviceState* st, Arena& ar,
+                         cudaStream_t s, const float** centre) {
+    *centre = nullptr;
+    if (opt.centring == BM_CENTRE_OFF || rows <= 0) return BM_OK;
+    if (opt.centring != BM_CENTRE_ALWAYS && rows < kCentreMinRows) return BM_OK;
+    float* c;
+    double* partial;
+    unsigned* maxima;
+    ALLOC(c, float, d);
+    ALLOC(partial, double, (long long)kCentreBlocks * d);
+    ALLOC(maxima, unsigned, 2);
+    TRY_CUDA(launch_centre(x, rows, d, opt.centring == BM_CENTRE_ALWAYS, partial, maxima, c, &st->centred, s));
+    *centre = c;
     return BM_OK;
 }
 
@@ -713,7 +741,8 @@ bm_status switch_path(GreedyCtx& c, Prepared& pts, Arena& ar, cudaStream_t s, in
         int* bad;
         ALLOC(bad, int, 1);
         TRY_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
-        bm_status rs = prepare(pts.x, pts.rows, pts.d, c.eps2, false, kPrecSplit, ar, &st->max_norm_bits, bad, s, p2);
+        bm_status rs = prepare(pts.x, pts.rows, pts.d, c.eps2, false, kPrecSplit, ar, &st->max_norm_bits, bad, s, p2,
+                               nullptr, pts.centre);
         if (rs != BM_OK) return rs;
         ar.release(pts.phi);
     } else {
@@ -907,7 +936,7 @@ bm_status range_core(const float* X, long long n, int d, const float* Q, long lo
     float* dists = nullptr;
     unsigned long long* err_dev = nullptr;
     double dist_err = 0.0;
-    int truncated = 0;
+    int truncated = 0, centred = 0;
     {
         Arena ar(&opt, s);
         const float* dX = (ivf || gidx) ? X : stage_input(X, n, d, host_io, ar, s, &rs);
@@ -930,9 +959,16 @@ bm_status range_core(const float* X, long long n, int d, const float* Q, long lo
             const int prec = tc ? prec_for(path) : kPrecNone;
             const float* bsrc = ivf ? (tc ? ivf->xpad : ivf->xperm) : dX;
             const long long brows = (ivf && tc) ? ivf->npad : n;
-            rs = prepare(bsrc, brows, d, eps2, false, prec, ar, &st->max_norm_bits, bad, s, px);
+            // the tensor-core tiles without an index may take translated operands (same centre
+            // for points and queries)
+            const float* centre = nullptr;
+            if (tc && !ivf) {
+                rs = operand_centre(dX, n, d, opt, st, ar, s, &centre);
+                if (rs != BM_OK) return rs;
+            }
+            rs = prepare(bsrc, brows, d, eps2, false, prec, ar, &st->max_norm_bits, bad, s, px, nullptr, centre);
             if (rs != BM_OK) return rs;
-            rs = prepare(dQ, m, d, eps2, true, prec, ar, &st->max_norm_q_bits, bad, s, pq, row_r2);
+            rs = prepare(dQ, m, d, eps2, true, prec, ar, &st->max_norm_q_bits, bad, s, pq, row_r2, centre);
             if (rs != BM_OK) return rs;
             int hbad = 0;
             unsigned hnorm[2] = {0u, 0u};
@@ -1017,6 +1053,7 @@ bm_status range_core(const float* X, long long n, int d, const float* Q, long lo
             pairs = h.tile_pairs;
             delta = h.delta;
             truncated = h.gidx_truncated;
+            centred = h.centred;
             unsigned long long* tmp;
             ALLOC(tmp, unsigned long long, std::max<long long>(nnz, 1));
             unsigned long long* sorted = nullptr;
@@ -1074,6 +1111,7 @@ bm_status range_core(const float* X, long long n, int d, const float* Q, long lo
         stats->recheck_rate = pairs ? (double)band / (double)pairs : 0.0;
         stats->dist_max_rel_err = dist_err;
         stats->truncated = truncated;
+        stats->centred = centred;
     }
     return BM_OK;
 }
@@ -1336,7 +1374,13 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
             TRY_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
             TRY_CUDA(cudaMemsetAsync(st, 0, sizeof(DeviceState), s));
             Prepared px;
-            rs = prepare(dX, n, d, eps2, false, tc ? prec_for(path) : kPrecNone, ar, &st->max_norm_bits, bad, s, px);
+            const float* centre = nullptr;   // translated tensor-core operands (not with an index)
+            if (tc && !ivf) {
+                rs = operand_centre(dX, n, d, opt, st, ar, s, &centre);
+                if (rs != BM_OK) return rs;
+            }
+            rs = prepare(dX, n, d, eps2, false, tc ? prec_for(path) : kPrecNone, ar, &st->max_norm_bits, bad, s, px,
+                         nullptr, centre);
             if (rs != BM_OK) return rs;
             // inverted-file mode: the cell-ordered copy of the points for the scan (phi for the
             // FP32 scan; the padded tensor-core operands otherwise)
@@ -1380,7 +1424,7 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
                 TRY_CUDA(launch_gather_rows(dX, landmarks, nL, d, qx, s));
                 Prepared pq;
                 rs = prepare(qx, nL, d, eps2, true, tc ? prec_for(path) : kPrecNone, ar, &st->max_norm_q_bits, bad, s,
-                             pq);
+                             pq, nullptr, centre);
                 if (rs != BM_OK) return rs;
                 const int sms = device_sm_count();
                 unsigned long long cap = (unsigned long long)std::max<long long>(4 * n, 1LL << 20);
@@ -1486,6 +1530,7 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
     g.stats.recheck_rate = fin.tile_pairs ? (double)fin.band_pairs / (double)fin.tile_pairs : 0.0;
     g.stats.dist_max_rel_err = dist_err;
     g.stats.truncated = fin.gidx_truncated;
+    g.stats.centred = fin.centred;
     *out = g;
     return BM_OK;
 }
@@ -1538,8 +1583,13 @@ bm_status batch_prep(BatchItem& it, const bm_instance& in, const bm_options& opt
     const float* dX = stage_input(in.X, in.n, in.d, opt.host_io != 0, ar, s, &rs);
     if (rs != BM_OK) return rs;
     it.st = st;
+    const float* centre = nullptr;
+    if (tc) {
+        rs = operand_centre(dX, in.n, in.d, opt, st, ar, s, &centre);
+        if (rs != BM_OK) return rs;
+    }
     rs = prepare(dX, in.n, in.d, it.eps2, false, tc ? prec_for(path) : kPrecNone, ar, &st->max_norm_bits, bad, s,
-                 it.px);
+                 it.px, nullptr, centre);
     if (rs != BM_OK) return rs;
     return BM_OK;
 }
@@ -1823,6 +1873,7 @@ bm_status build_batched(const bm_instance* inst, int count, const bm_options& op
         g.stats.candidates = (int64_t)fin.candidates;
         g.stats.edge_pairs = 0;   // witnessed pairs are counted for the whole batch only
         g.stats.band_delta = fin.delta;
+        g.stats.centred = fin.centred;
         g.stats.path = it.n ? it.gc.path : path;
         g.stats.kernel_launches = executed[i];
         outs[i] = g;
@@ -2003,6 +2054,8 @@ bm_status bm_range_query(const float* X, int64_t n, int32_t d, const float* Q, i
     if (vs != BM_OK) return vs;
     vs = validate_eps(eps);
     if (vs != BM_OK) return vs;
+    vs = validate_centring(opt.centring);
+    if (vs != BM_OK) return vs;
     vs = check_device(opt.path);
     if (vs != BM_OK) return vs;
     return range_core(X, n, d, Q, m, eps, opt, nullptr, 0, nullptr, out, stats);
@@ -2019,6 +2072,8 @@ bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_opt
     vs = validate_eps(eps);
     if (vs != BM_OK) return vs;
     vs = validate_batch(opt.batch, 8192);   // arguments first, then the device
+    if (vs != BM_OK) return vs;
+    vs = validate_centring(opt.centring);
     if (vs != BM_OK) return vs;
     vs = check_device(opt.path);
     if (vs != BM_OK) return vs;
@@ -2181,6 +2236,7 @@ bm_status bm_build_batched(const bm_instance* inst, int32_t count, const bm_opti
         }
     }
     bm_status vs = validate_batch(opt.batch, 2048);   // arguments first, then the device
+    if (vs == BM_OK) vs = validate_centring(opt.centring);
     if (vs != BM_OK) return vs;
     if (opt.want_dists) return fail(BM_ERR_ARG, "bm_build_batched does not return distances (want_dists)");
     vs = check_device(opt.path);

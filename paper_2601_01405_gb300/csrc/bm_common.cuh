@@ -43,7 +43,7 @@ struct DeviceState {
     int s_cur;                       // candidates requested by the current step
     int s_next;                      // candidates the next step requests (adapted to the survival rate)
     int gidx_truncated;              // a graph-index search stopped at its visit cap
-    int pad1;
+    int centred;                     // 1 when the tensor-core operands are those of translated rows
 };
 
 // One work item of the tensor-core tiles in table mode (the inverted-file scan): the

@@ -27,8 +27,9 @@ namespace {
 constexpr int kSelThreads = 1024;
 
 __global__ void __launch_bounds__(kSelThreads) greedy_select_kernel(
-    DeviceState* st, const unsigned* __restrict__ covered, long long n, int S, int* slot_of,
-    int* cand_ids, unsigned* conflict, unsigned* row_any, int words, const float* __restrict__ X,
+    DeviceState* st, const unsigned* __restrict__ covered, long long n, int S, int* __restrict__ slot_of,
+    int* __restrict__ cand_ids, unsigned* __restrict__ conflict, unsigned* __restrict__ row_any, int words,
+    const float* __restrict__ X,
     const float* __restrict__ phi, int d, float* cand_x, float* cand_phi, int want_tc,
     const __nv_bfloat16* __restrict__ H, const __nv_bfloat16* __restrict__ Lo,
     const __nv_bfloat16* __restrict__ Aug, int d_pad, __nv_bfloat16* cH, __nv_bfloat16* cLo,
@@ -50,7 +51,9 @@ __global__ void __launch_bounds__(kSelThreads) greedy_select_kernel(
     //    candidate slots), so only those are cleared
     const int prev = st->cand_count;
     const int prev_words = (prev + 31) >> 5;
+#pragma unroll 4
     for (int i = tid; i < prev; i += kSelThreads) slot_of[cand_ids[i]] = -1;
+#pragma unroll 4
     for (int k = tid; k < prev; k += kSelThreads)
         if ((row_any[k >> 5] >> (k & 31)) & 1u)
             for (int w = 0; w < prev_words; ++w) conflict[(size_t)k * words + w] = 0;
@@ -86,10 +89,13 @@ __global__ void __launch_bounds__(kSelThreads) greedy_select_kernel(
         int total;
         const int excl = block_exclusive_scan(__popc(bits), s_scan, total);
         int slot = found + excl;
-        while (bits && slot < S) {
+        while (bits && slot < S) {   // 3. register each candidate as it is found
             const int b = __ffs(bits) - 1;
             bits &= bits - 1;
-            cand_ids[slot++] = (int)(w * 32 + b);
+            const int id = (int)(w * 32 + b);
+            cand_ids[slot] = id;
+            slot_of[id] = slot;
+            ++slot;
         }
         __syncthreads();
         if (tid == 0) {
@@ -114,8 +120,7 @@ __global__ void __launch_bounds__(kSelThreads) greedy_select_kernel(
         if (found == 0) st->done = 1;
         else st->steps += 1;
     }
-    // 3. register the candidates (their rows are gathered by greedy_gather_kernel)
-    for (int s = tid; s < found; s += kSelThreads) slot_of[cand_ids[s]] = s;
+    // (the candidates' rows are gathered by greedy_gather_kernel)
 }
 
 // One warp per candidate: copy its float32 row, phi and, for the tensor-core

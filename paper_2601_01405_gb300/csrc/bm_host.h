@@ -91,6 +91,8 @@ struct Prepared {
     int ck = 0, nt = 0, bbuf = 0, astg = 0;   // tensor-core tile shape chosen for this d
     int prec = 0;                      // kPrecNone / kPrecSplit (bf16 hi, lo) / kPrecFp16 (fp16 in hi, no lo)
     int scale_exp = 0;                 // fp16: operands hold x * 2^scale_exp
+    const float* centre = nullptr;     // d floats (device) or null: the tensor-core operands, phi and the
+                                       // norms are those of fl(x - centre); x itself stays untranslated
 };
 constexpr int kPrecNone = 0, kPrecSplit = 1, kPrecFp16 = 2;
 
@@ -115,6 +117,13 @@ cudaError_t launch_prep(const float* x, long long rows, int d, double eps2, bool
                         const double* row_r2 = nullptr);
 cudaError_t launch_delta(DeviceState* st, int path, int d, int d_pad, double eps2, bool same_sets,
                          cudaStream_t s, int scale_exp = 0);
+// Centre of the tensor-core operands: the mean of a sample of the rows of x (d floats into
+// centre), set to 0 unless it shrinks the sample's largest squared norm by 5 % (force: kept
+// always); *centred (device) receives 1 when kept.  partial: kCentreBlocks * d doubles,
+// maxima: 2 unsigned (device scratch).
+constexpr int kCentreBlocks = 152;
+cudaError_t launch_centre(const float* x, long long rows, int d, bool force, double* partial, unsigned* maxima,
+                          float* centre, int* centred, cudaStream_t s);
 // fp16 operands of an already prepared set (hi, aug allocated as 2-byte arrays)
 cudaError_t launch_prep16(const float* x, long long rows, int d, double eps2, bool a_side, int scale_exp,
                           Prepared& p, cudaStream_t s);

@@ -18,7 +18,8 @@
 // with phi ~ p1 + p2 + p3 (three bf16 pieces of the FP64 value) and delta' the
 // band half-width rounded up to the operand type (written by set_aug_delta once
 // delta is known), so the accumulator holds v + delta' and the tiles classify by
-// its sign.
+// its sign.  The tensor-core operands may be those of the translated rows x - c
+// (launch_centre below); phi and the norms are then the translated rows' too.
 #include <cuda_fp16.h>
 
 #include <cmath>
@@ -41,6 +42,7 @@ __device__ __forceinline__ int aug_pos(int col, int a_side) {
 __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ x, long long rows, int d,
                                                    double eps2, const double* __restrict__ row_r2,
                                                    int a_side, int want_tc,
+                                                   const float* __restrict__ centre,
                                                    float* __restrict__ phi_out,
                                                    __nv_bfloat16* __restrict__ hi,
                                                    __nv_bfloat16* __restrict__ lo,
@@ -58,12 +60,14 @@ __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ x, 
         double s = 0.0;
         for (int c0 = 0; c0 < D; c0 += 32) {
             const int i = c0 + lane;
+            const float ci = (centre && i < d) ? centre[i] : 0.f;
             for (int rr = 0; rr < 32; ++rr) {
                 const long long r = r0 + rr;
                 float v = 0.f;
                 if (r < rows && i < d) {
                     v = x[r * d + i];
                     if (!isfinite(v)) bad = true;
+                    v = __fsub_rn(v, ci);   // x' = fl(x - c); exact when c = 0
                 }
                 if (want_tc && r < rows && i < D) {
                     const __nv_bfloat16 h = __float2bfloat16_rn(v);
@@ -121,12 +125,14 @@ __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ x, 
     }
 }
 
-// FP16 operands (BM_PATH_TC_FP16): xs = x 2^e (exact in FP64), hi = fp16(xs) rounded to
+// FP16 operands (BM_PATH_TC_FP16), of the translated rows x = fl(x_in - c) when a centre
+// is given: xs = x 2^e (exact in FP64), hi = fp16(xs) rounded to
 // nearest, and the augmentation block with three fp16 pieces of
 // phi_s = ||xs||^2 / 2 - eps^2 4^e / 4 (FP64), in the same positions as the bf16 block.
 // The scale 2^e keeps every operand and phi piece inside the fp16 range.
 __global__ void __launch_bounds__(256) prep16_kernel(const float* __restrict__ x, long long rows, int d, int d_pad,
                                                      int scale_exp, double eps2s, int a_side,
+                                                     const float* __restrict__ centre,
                                                      __half* __restrict__ hi, __half* __restrict__ aug) {
     __shared__ float tile[kPrepWarps][32][33];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -140,9 +146,10 @@ __global__ void __launch_bounds__(256) prep16_kernel(const float* __restrict__ x
         double s = 0.0;   // sum of x_i^2; the scaled sum is s 4^e, exactly
         for (int c0 = 0; c0 < d_pad; c0 += 32) {
             const int i = c0 + lane;
+            const float ci = (centre && i < d) ? centre[i] : 0.f;
             for (int rr = 0; rr < 32; ++rr) {
                 const long long r = r0 + rr;
-                const float v = (r < rows && i < d) ? x[r * d + i] : 0.f;
+                const float v = (r < rows && i < d) ? __fsub_rn(x[r * d + i], ci) : 0.f;
                 if (r < rows && i < d_pad)
                     hi[r * d_pad + i] = fscale ? __float2half_rn(v * scalef) : __double2half((double)v * scale);
                 tile[warp][rr][lane] = v;
@@ -187,7 +194,7 @@ cudaError_t launch_prep16(const float* x, long long rows, int d, double eps2, bo
     p.scale_exp = scale_exp;
     note_launch();
     prep16_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, rows, d, p.d_pad, scale_exp, eps2 * scale * scale,
-                                                   a_side ? 1 : 0, reinterpret_cast<__half*>(p.hi),
+                                                   a_side ? 1 : 0, p.centre, reinterpret_cast<__half*>(p.hi),
                                                    reinterpret_cast<__half*>(p.aug));
     return cudaGetLastError();
 }
@@ -209,8 +216,152 @@ cudaError_t launch_prep(const float* x, long long rows, int d, double eps2, bool
     if (blocks > 152 * 16) blocks = 152 * 16;
     note_launch();
     prep_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, rows, d, eps2, row_r2, a_side ? 1 : 0, want_tc ? 1 : 0,
-                                                 out.phi, out.hi, out.lo, out.aug, out.d_pad,
-                                                 max_norm_bits, bad_flag);
+                                                 want_tc ? out.centre : nullptr, out.phi, out.hi, out.lo, out.aug,
+                                                 out.d_pad, max_norm_bits, bad_flag);
+    return cudaGetLastError();
+}
+
+// ---- Translation of the tensor-core operands.
+// D(q, x) does not change when both sides move by the same c, while the proven band
+// half-width grows with the operands' norms (N_a N_b and |phi|, see below).  Data whose
+// mean lies far from the origin (the Swiss roll, for one) get a band several times wider
+// than their spread requires, so the tiles may take x' = fl(x - c) with c the mean of a
+// sample of the points.  The FP64 recheck keeps the original coordinates, so no decision
+// depends on c; the band bound charges the rounding of x - c.
+constexpr long long kCentreSample = 65536;
+
+// Row of sample k (m samples spread evenly over the rows; all rows when m = rows).
+__device__ __forceinline__ long long sample_row(long long k, long long m, long long rows) {
+    return (long long)(((unsigned long long)k * (unsigned long long)rows) / (unsigned long long)m);
+}
+
+// Block b sums its share of the sampled rows per column in FP64 (fixed partition, order
+// and reduction tree, so the centre is the same on every run).  Warp w of the block takes
+// rows k0 + w, k0 + w + 8, ...; lane l the columns c0 + l of each 32-column chunk, so each
+// row is read coalesced; the eight warp sums of a column are added in warp order.
+constexpr int kCentreWarps = 8;
+
+__global__ void __launch_bounds__(kCentreWarps * 32) centre_partial_kernel(const float* __restrict__ x, long long rows,
+                                                                          int d, long long m,
+                                                                          double* __restrict__ partial) {
+    __shared__ double s_sum[kCentreWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long k0 = (long long)blockIdx.x * m / gridDim.x, k1 = (long long)(blockIdx.x + 1) * m / gridDim.x;
+    for (int c0 = 0; c0 < d; c0 += 32) {
+        const int j = c0 + lane;
+        double s[4] = {0.0, 0.0, 0.0, 0.0};
+        long long k = k0 + warp;
+        for (; k + 3 * kCentreWarps < k1; k += 4 * kCentreWarps) {   // four rows in flight per lane
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = j < d ? x[sample_row(k + u * kCentreWarps, m, rows) * d + j] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s[u] += (double)v[u];
+        }
+        for (; k < k1; k += kCentreWarps) s[0] += j < d ? (double)x[sample_row(k, m, rows) * d + j] : 0.0;
+        s_sum[warp][lane] = (s[0] + s[1]) + (s[2] + s[3]);
+        __syncthreads();
+        if (warp == 0 && j < d) {
+            double t = 0.0;
+            for (int w = 0; w < kCentreWarps; ++w) t += s_sum[w][lane];
+            partial[(long long)blockIdx.x * d + j] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// c = the sample mean rounded to float (0 where it is not finite), one warp per column
+// (the block partials split over the lanes and added in a fixed tree); clears the two
+// maxima that centre_gain_kernel fills.
+__global__ void __launch_bounds__(256) centre_mean_kernel(const double* __restrict__ partial, int blocks, int d,
+                                                          long long m, float* __restrict__ centre,
+                                                          unsigned* maxima) {
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        maxima[0] = 0u;
+        maxima[1] = 0u;
+    }
+    if (j >= d) return;
+    double s = 0.0;
+    for (int b = lane; b < blocks; b += 32) s += partial[(long long)b * d + j];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    if (lane == 0) {
+        const float c = (float)(s / (double)m);
+        centre[j] = isfinite(c) ? c : 0.f;
+    }
+}
+
+// Largest squared norm over the sampled rows before (maxima[0]) and after (maxima[1])
+// the translation, in FP32: an estimate that only decides whether to translate (the band
+// bound uses the norms the prep kernels compute in FP64).  One warp per sampled row, one
+// atomic per block.
+__global__ void __launch_bounds__(256) centre_gain_kernel(const float* __restrict__ x, long long rows, int d,
+                                                          long long m, const float* __restrict__ centre,
+                                                          unsigned* maxima) {
+    __shared__ float s_max[2][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+    float m0 = 0.f, m1 = 0.f;
+    for (long long k = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < m; k += warps) {
+        const float* row = x + sample_row(k, m, rows) * d;
+        float s0 = 0.f, s1 = 0.f;
+        for (int j = lane; j < d; j += 32) {
+            const float v = row[j], t = v - centre[j];
+            s0 = fmaf(v, v, s0);
+            s1 = fmaf(t, t, s1);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_xor_sync(kFull, s0, o);
+            s1 += __shfl_xor_sync(kFull, s1, o);
+        }
+        m0 = fmaxf(m0, s0);
+        m1 = fmaxf(m1, s1);
+    }
+    if (lane == 0) {
+        s_max[0][warp] = m0;
+        s_max[1][warp] = m1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {   // squares are >= +0, so float bits order as unsigned
+        for (int w = 1; w < 8; ++w) {
+            m0 = fmaxf(m0, s_max[0][w]);
+            m1 = fmaxf(m1, s_max[1][w]);
+        }
+        atomicMax(&maxima[0], __float_as_uint(m0));
+        atomicMax(&maxima[1], __float_as_uint(m1));
+    }
+}
+
+// Keep c only where it shrinks the sample's largest squared norm by 5 % or more (always
+// when forced); otherwise c = 0.  *centred records the choice.
+__global__ void centre_decide_kernel(float* centre, int d, const unsigned* maxima, int force, int* centred) {
+    __shared__ int s_keep;
+    if (threadIdx.x == 0) {
+        const float n0 = __uint_as_float(maxima[0]), n1 = __uint_as_float(maxima[1]);
+        s_keep = force || (isfinite(n0) && n1 <= 0.95f * n0);
+        *centred = s_keep;
+    }
+    __syncthreads();
+    if (!s_keep)
+        for (int j = threadIdx.x; j < d; j += blockDim.x) centre[j] = 0.f;
+}
+
+cudaError_t launch_centre(const float* x, long long rows, int d, bool force, double* partial, unsigned* maxima,
+                          float* centre, int* centred, cudaStream_t s) {
+    if (rows <= 0) return cudaSuccess;
+    const long long m = rows < kCentreSample ? rows : kCentreSample;
+    note_launch();
+    centre_partial_kernel<<<kCentreBlocks, kCentreWarps * 32, 0, s>>>(x, rows, d, m, partial);
+    note_launch();
+    centre_mean_kernel<<<(unsigned)((d + 7) / 8), 256, 0, s>>>(partial, kCentreBlocks, d, m, centre, maxima);
+    if (!force) {
+        const long long blocks = (m + 7) / 8 < 152 * 16 ? (m + 7) / 8 : 152 * 16;   // ~4 sampled rows per warp
+        note_launch();
+        centre_gain_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, rows, d, m, centre, maxima);
+    }
+    note_launch();
+    centre_decide_kernel<<<1, 256, 0, s>>>(centre, d, maxima, force ? 1 : 0, centred);
     return cudaGetLastError();
 }
 
@@ -222,8 +373,8 @@ cudaError_t launch_prep(const float* x, long long rows, int d, double eps2, bool
 // (u = 2^-24); phi rounded to float (u |phi| each) and two subtractions (u |.| each).
 //     delta = 2 (d + 8) 2^-23 (N_a N_b + Phi_a + Phi_b)
 //
-// Tensor-core path: K = 3 d_pad + 6 accumulated terms (hi.hi, lo.hi, hi.lo and the six
-// phi-piece products), each exact in FP32; the accumulation order and rounding of
+// Tensor-core path: K = 3 d_pad + 7 accumulated terms (hi.hi, lo.hi, hi.lo, the six
+// phi-piece products and 1 x delta'), each exact in FP32; the accumulation order and rounding of
 // tcgen05 are not specified, so every one of the K-1 additions (and one alignment
 // truncation per term) is charged 2^-23 of the sum of magnitudes:
 //     |acc - T| <= 2 K 2^-23 (1.02 N_a N_b + 1.01 (Phi_a + Phi_b)).
@@ -236,10 +387,18 @@ cudaError_t launch_prep(const float* x, long long rows, int d, double eps2, bool
 // FP16 path (operands scaled by 2^e; N, Phi and delta in scaled units): with
 // hi = fp16(x), |x - hi| <= 2^-11 |x| + 2^-25 (normal / subnormal rounding), so
 // |q.x - hq.hx| <= 2^-10 (1 + 2^-10) N_a N_b + 2^-24 sqrt(d_pad) (N_a + N_b) + d_pad 2^-49;
-// products hq.hx are exact in FP32; K = d_pad + 6 accumulated terms charged as above;
+// products hq.hx are exact in FP32; K = d_pad + 7 accumulated terms charged as above;
 // three fp16 phi pieces: 2^-33 |phi| + 2^-25 each; FP64 phi: 2^-42 N^2.
 //     delta = 2 [E_rep + 2 K 2^-23 (1.002 N_a N_b + 1.001 (Phi_a + Phi_b) + 2^-24 sqrt(d_pad)(N_a + N_b))
 //                + 2^-33 (Phi_a + Phi_b) + 2^-22 + 2^-42 (N_a^2 + N_b^2)]
+//
+// Translated operands (both tensor-core paths): the tiles see x' = fl(x - c) on both
+// sides (c = 0: x' = x).  With e = x' - (x - c), |e_i| <= u |x'_i| / (1 - u) (u = 2^-24), so
+// the squared distance they approximate, D' = ||a' - b'||^2, differs from D by
+// |D' - D| <= 2 ||a' - b'|| (||e_a|| + ||e_b||) (1 + 3u) + (||e_a|| + ||e_b||)^2
+//          <= 2.0001 u (N_a + N_b)^2,
+// N the norms of the translated rows (the ones the prep kernels measure); v moves by half
+// of that, so both bounds add E_ctr = 1.01 2^-24 (N_a + N_b)^2 inside the brackets.
 // The bound itself, in the units of the operands (scaled by 2^scale_exp on the fp16
 // path); Na, Nb are the unscaled max norms.  Used by the device (delta_kernel) and by
 // the host's choice of path.
@@ -252,17 +411,19 @@ __host__ __device__ double band_halfwidth_core(int path, int d, int d_pad, doubl
     if (path == BM_PATH_FP32) {
         delta = 2.0 * (d + 8) * u23 * (Na * Nb + Pa + Pb);
     } else if (path == BM_PATH_TC_FP16) {
-        const double rd = sqrt((double)d_pad), K = d_pad + 6.0;
+        const double rd = sqrt((double)d_pad), K = d_pad + 7.0;
         const double u24 = u23 * 0.5;
         const double e_rep = ldexp(1.0 + ldexp(1.0, -10), -10) * Na * Nb + u24 * rd * (Na + Nb) + d_pad * ldexp(1.0, -49);
         const double e_acc = 2.0 * K * u23 * (1.002 * Na * Nb + 1.001 * (Pa + Pb) + u24 * rd * (Na + Nb));
         const double e_aug = ldexp(1.0, -33) * (Pa + Pb) + ldexp(1.0, -22);
         const double e_phi = ldexp(1.0, -42) * (Na * Na + Nb * Nb);
-        delta = 2.0 * (e_rep + e_acc + e_aug + e_phi);
+        const double e_ctr = 1.01 * u23 * 0.5 * (Na + Nb) * (Na + Nb);
+        delta = 2.0 * (e_rep + e_acc + e_aug + e_phi + e_ctr);
     } else {
-        const double K = 3.0 * d_pad + 6.0;
+        const double K = 3.0 * d_pad + 7.0;
+        const double e_ctr = 1.01 * u23 * 0.5 * (Na + Nb) * (Na + Nb);
         delta = 2.0 * (2.0 * K * u23 * (1.02 * Na * Nb + 1.01 * (Pa + Pb)) + 3.0 * u16 * Na * Nb +
-                       u23 * (Pa + Pb));
+                       u23 * (Pa + Pb) + e_ctr);
     }
     return delta + 1e-30;
 }

@@ -61,6 +61,7 @@ int main(void) {
     printf("%zu %zu %zu\n", offsetof(bm_options, alloc), offsetof(bm_stats, ms_prep), offsetof(bm_graph, edges));
     printf("%zu %zu %zu\n", offsetof(bm_options, want_dists), offsetof(bm_stats, dist_max_rel_err),
            offsetof(bm_csr, dists));
+    printf("%zu %zu\n", offsetof(bm_options, centring), offsetof(bm_stats, centred));
     return 0;
 }
 ''')
@@ -73,7 +74,7 @@ int main(void) {
            ctypes.sizeof(binding.bm_graph), binding.bm_graph.stats.offset,
            binding.bm_options.alloc.offset, binding.bm_stats.ms_prep.offset, binding.bm_graph.edges.offset,
            binding.bm_options.want_dists.offset, binding.bm_stats.dist_max_rel_err.offset,
-           binding.bm_csr.dists.offset]
+           binding.bm_csr.dists.offset, binding.bm_options.centring.offset, binding.bm_stats.centred.offset]
     assert got == exp
 
 
@@ -124,12 +125,35 @@ def test_binding_enums_match_header():
     """The binding's status and path constants equal the header's enum values, and every
     status has a string in the library."""
     text = open(os.path.join(ROOT, "include", "ballmapper.h")).read()
-    header = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(BM_(?:OK|ERR_\w+|PATH_\w+))\s*=\s*(\d+)", text)}
-    assert len(header) >= 11
+    header = {m.group(1): int(m.group(2))
+              for m in re.finditer(r"\b(BM_(?:OK|ERR_\w+|PATH_\w+|CENTRE_\w+))\s*=\s*(\d+)", text)}
+    assert len(header) >= 14
     for name, value in header.items():
         assert getattr(binding, name) == value, name
     _build.build()
     lib = binding.load()
     for name, value in header.items():
-        if not name.startswith("BM_PATH"):
+        if not name.startswith(("BM_PATH", "BM_CENTRE")):
             assert lib.bm_status_string(value), name
+
+
+def test_centring_mode_rejected_before_the_device():
+    """bm_options.centring takes the three bm_centring values; anything else is an
+    argument error raised before any device call."""
+    import numpy as np
+    _build.build()
+    lib = binding.load()
+    X = np.zeros((4, 2), dtype=np.float32)
+    px = X.ctypes.data_as(ctypes.c_void_p)
+    for bad in (-1, 3, 7):
+        opt = binding._options(lib, "auto", 0, None, True, None)
+        opt.centring = bad
+        g = binding.bm_graph()
+        st = lib.bm_build(px, 4, 2, ctypes.c_float(1.0), ctypes.byref(opt), ctypes.byref(g))
+        assert st == binding.BM_ERR_ARG
+        assert b"centring" in lib.bm_last_error()
+        out, stats = binding.bm_csr(), binding.bm_stats()
+        st = lib.bm_range_query(px, 4, 2, px, 4, ctypes.c_float(1.0), ctypes.byref(opt), ctypes.byref(out),
+                                ctypes.byref(stats))
+        assert st == binding.BM_ERR_ARG
+    assert binding.CENTRING == {"auto": 0, "always": 1, "off": 2}
