@@ -35,11 +35,12 @@ sys.path.insert(0, ROOT)
 METRIC = "Ball Mapper build s & distance evals/s (exact), TC split path vs plain FP32"
 UNIT = "evals/s"
 # DRAM bytes per tile-kernel launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# an ncu capture of the current fp16 kernel at the greedy's full batch (8192 candidate
+# an ncu capture of the current fp16 kernel at the greedy's full batch (16384 candidate
 # rows x 10^6 points); a step's sweep reads every point's operands once whatever its
-# batch, so the figure holds for each launch of this workload (the automatic path runs
-# fp16 after the first step).  None where no capture of the current kernel exists.
-NCU_TRAFFIC = {("mix32-n1M-d64", "auto"): 164.8e6, ("mix32-n1M-d64", "tc16"): 164.8e6}
+# batch, so the figure holds for each launch of this workload to within the query rows'
+# 160 B each (the automatic path runs fp16 after the first step).  None where no capture
+# of the current kernel exists.
+NCU_TRAFFIC = {("mix32-n1M-d64", "auto"): 166.1e6, ("mix32-n1M-d64", "tc16"): 166.1e6}
 DTYPES = {"tc": "bf16x3-split/fp32-acc/fp64-recheck", "tc16": "f16-scaled/fp32-acc/fp64-recheck",
           "fp32": "f32/fp64-recheck", "auto": "f16-scaled or bf16x3-split/fp32-acc/fp64-recheck"}
 

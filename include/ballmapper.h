@@ -99,8 +99,9 @@ typedef struct {
     void* stream;          /* cudaStream_t; NULL = legacy default stream */
     int32_t path;          /* bm_path */
     int32_t host_io;       /* 0: device pointers in and out; 1: host pointers in and out */
-    int32_t batch;         /* largest greedy batch (candidates per step), multiple of 32: 32..8192 for
-                              bm_build, 32..2048 for bm_build_batched; 0 = 8192 (bm_build).
+    int32_t batch;         /* largest greedy batch (candidates per step), multiple of 32: 32..16384 for
+                              bm_build and the index builds, 32..2048 for bm_build_batched;
+                              0 = 16384 (bm_build; 8192 for bm_build_ivf and bm_build_gidx).
                               The batch starts at min(batch, 256), doubles while 90 % of the
                               candidates become landmarks (99 % past 2048, 99.5 % past 4096) and
                               halves below 50 % (90 % past 2048). */

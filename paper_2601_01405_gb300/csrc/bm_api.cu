@@ -149,6 +149,10 @@ bm_status validate_points(const float* X, long long n, int d, const char* name) 
     return BM_OK;
 }
 
+// Largest greedy batch of a single build (the resolve kernel's conflict walk holds 16384
+// candidates).
+constexpr int kMaxBatch = 16384;
+
 bm_status validate_centring(int c) {
     if (c != BM_CENTRE_AUTO && c != BM_CENTRE_ALWAYS && c != BM_CENTRE_OFF)
         return fail(BM_ERR_ARG, "centring must be BM_CENTRE_AUTO, BM_CENTRE_ALWAYS or BM_CENTRE_OFF");
@@ -264,7 +268,7 @@ constexpr long long kCentreMinRows = 65536;
 bm_status operand_centre(const float* x, long long rows, int d, const bm_options& opt, DeviceState* st, Arena& ar,
                          cudaStream_t s, const float** centre) {
     *centre = nullptr;
-    if (opt.centring == BM_CENTRE_OFF || rows <= 0) return BM_OK;
+    if (opt.centring == BM_CENTRE_OFF || rows <= 0 || d > 512) return BM_OK;   // the tiles take d <= 512
     if (opt.centring != BM_CENTRE_ALWAYS && rows < kCentreMinRows) return BM_OK;
     float* c;
     double* partial;
@@ -1325,8 +1329,9 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
                       int ef = 0, long long max_visits = 0) {
     std::memset(out, 0, sizeof(*out));
     int S = opt.batch;
-    if (S == 0) S = 8192;
-    if (S < 32 || S > 8192 || S % 32) return fail(BM_ERR_ARG, "batch must be a multiple of 32 in [32, 8192]");
+    if (S == 0) S = (ivf || gidx) ? 8192 : kMaxBatch;
+    if (S < 32 || S > kMaxBatch || S % 32)
+        return fail(BM_ERR_ARG, "batch must be a multiple of 32 in [32, " + std::to_string(kMaxBatch) + "]");
     cudaStream_t s = (cudaStream_t)opt.stream;
     const bool host_io = opt.host_io != 0;
     const double eps2 = (double)eps * (double)eps;
@@ -2071,7 +2076,7 @@ bm_status bm_build(const float* X, int64_t n, int32_t d, float eps, const bm_opt
     if (vs != BM_OK) return vs;
     vs = validate_eps(eps);
     if (vs != BM_OK) return vs;
-    vs = validate_batch(opt.batch, 8192);   // arguments first, then the device
+    vs = validate_batch(opt.batch, kMaxBatch);   // arguments first, then the device
     if (vs != BM_OK) return vs;
     vs = validate_centring(opt.centring);
     if (vs != BM_OK) return vs;
@@ -2660,7 +2665,7 @@ bm_status bm_build_gidx(const bm_gidx* idx, float eps, int32_t ef, int64_t max_v
     if (vs == BM_OK) vs = validate_search(ef, &max_visits);
     if (vs != BM_OK) return vs;
     if (landmarks && (n_landmarks < 0 || n_landmarks > gx.n)) return fail(BM_ERR_ARG, "n_landmarks out of range");
-    vs = validate_batch(opt.batch, 8192);
+    vs = validate_batch(opt.batch, kMaxBatch);
     if (vs != BM_OK) return vs;
     vs = check_device(opt.path);
     if (vs != BM_OK) return vs;

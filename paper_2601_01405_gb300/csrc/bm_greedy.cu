@@ -159,13 +159,87 @@ __global__ void __launch_bounds__(256) greedy_gather_kernel(
 // the sweep; flagged rows are staged in shared memory (as many as fit; the rest
 // are read from global memory).  One warp then walks the flagged candidates in
 // index order: candidate k is a landmark iff no earlier landmark candidate
-// covers it (its bit is clear in the running 'killed' set, kLaneWords words per
-// lane: word lane + 32 h).  Finally every thread assigns ordinals in parallel,
+// covers it (its bit is clear in the running 'killed' set, up to 16 words per
+// lane: word lane + 32 h, as many as this step's batch needs).  Finally every thread assigns ordinals in parallel,
 // and the next step's batch size follows the survival rate (fewer wasted
 // candidate rows on dense data, larger batches where balls are small).
-constexpr int kMaxWords = 256;   // batches of up to 8192 candidates
-constexpr int kLaneWords = kMaxWords / 32;
+constexpr int kMaxWords = 512;   // batches of up to 16384 candidates
 
+// Warp 0 of the resolve: the flagged rows (a bit in row_any among the first c slots) in
+// index order into s_flag_row; returns their count.  H: words per lane, cw <= 32 H, so the
+// loops cover only the words this step's batch can use.
+template <int H>
+__device__ __forceinline__ int resolve_flags(const unsigned* row_any, int words, int c, int* s_flag_row, int lane) {
+    int base = 0;
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        const int w = lane + 32 * h;
+        unsigned a = w < words ? row_any[w] : 0u;
+        if (w * 32 >= c) a = 0u;
+        else if (w * 32 + 32 > c) a &= (1u << (c - w * 32)) - 1u;
+        const int cnt = __popc(a);
+        int x = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        const int first = base + x - cnt;
+        unsigned m = a;
+        int k = first;
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            s_flag_row[k++] = w * 32 + b;
+        }
+        base += __shfl_sync(kFull, x, 31);
+    }
+    return base;
+}
+
+// Warp 0 of the resolve: walk the flagged candidates in index order with the running
+// 'killed' set (word lane + 32 h in killed[h]), then the alive words and the alive count
+// before each word; returns the number of landmarks.
+template <int H>
+__device__ __forceinline__ int resolve_walk(const unsigned* conflict, int words, int c, int cw,
+                                            const int* s_flag_row, int nflag, const unsigned* s_rows, int staged,
+                                            unsigned* s_alive, int* s_rank_of_word, int lane) {
+    unsigned killed[H];
+#pragma unroll
+    for (int h = 0; h < H; ++h) killed[h] = 0u;
+    for (int f = 0; f < nflag; ++f) {
+        const int k = s_flag_row[f], w = k >> 5;
+        unsigned mine = killed[0];   // this lane's copy of word (w mod 32) + 32 h, h = w / 32
+#pragma unroll
+        for (int h = 1; h < H; ++h)
+            if ((w >> 5) == h) mine = killed[h];
+        const unsigned kw = __shfl_sync(kFull, mine, w & 31);
+        if ((kw >> (k & 31)) & 1u) continue;
+        const unsigned* row = f < staged ? s_rows + (size_t)f * cw : conflict + (size_t)k * words;
+#pragma unroll
+        for (int h = 0; h < H; ++h)
+            if (lane + 32 * h < cw) killed[h] |= row[lane + 32 * h];
+    }
+    int base = 0;
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        const int w = lane + 32 * h;
+        const unsigned valid = (w * 32 + 32 <= c) ? kFull : (w * 32 >= c ? 0u : ((1u << (c - w * 32)) - 1u));
+        const unsigned alive = ~killed[h] & valid;
+        s_alive[w] = alive;
+        const int cnt = __popc(alive);
+        int x = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        s_rank_of_word[w] = base + x - cnt;   // alive count before word w
+        base += __shfl_sync(kFull, x, 31);
+    }
+    return base;
+}
+
+// Dynamic shared memory: the flagged row ids (s_max ints), then the staged rows
+// (stage_words words).
 __global__ void __launch_bounds__(1024) greedy_resolve_kernel(DeviceState* st, const unsigned* conflict,
                                                              const unsigned* row_any, int words,
                                                              const int* cand_ids, int* ordinal,
@@ -183,39 +257,26 @@ __global__ void __launch_bounds__(1024) greedy_resolve_kernel(DeviceState* st, c
         }
         return;
     }
-    extern __shared__ unsigned s_rows[];   // staged flagged rows, cw words each (stage_words in all)
+    extern __shared__ unsigned s_dyn[];
+    int* s_flag_row = reinterpret_cast<int*>(s_dyn);   // flagged rows in index order (at most s_max)
+    unsigned* s_rows = s_dyn + s_max;                  // staged flagged rows, cw words each
     __shared__ int s_rank_of_word[kMaxWords + 1];
-    __shared__ int s_flag_row[kMaxWords * 32];
     __shared__ unsigned s_alive[kMaxWords];
     __shared__ int s_nflag;
     const int c = st->cand_count;
     const int cw = (c + 31) >> 5;   // words of a conflict row that can hold bits (slots < c)
+    const int H = cw <= 32 ? 1 : cw <= 64 ? 2 : cw <= 128 ? 4 : cw <= 256 ? 8 : 16;
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid < 32) {
-        int base = 0;
-#pragma unroll
-        for (int h = 0; h < kLaneWords; ++h) {
-            const int w = lane + 32 * h;
-            unsigned a = w < words ? row_any[w] : 0u;
-            if (w * 32 >= c) a = 0u;
-            else if (w * 32 + 32 > c) a &= (1u << (c - w * 32)) - 1u;
-            const int cnt = __popc(a);
-            int x = cnt;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(kFull, x, o);
-                if (lane >= o) x += y;
-            }
-            const int first = base + x - cnt;
-            unsigned m = a;
-            int k = first;
-            while (m) {
-                const int b = __ffs(m) - 1;
-                m &= m - 1;
-                s_flag_row[k++] = w * 32 + b;
-            }
-            base += __shfl_sync(kFull, x, 31);
+        int nf;
+        switch (H) {
+            case 1: nf = resolve_flags<1>(row_any, words, c, s_flag_row, lane); break;
+            case 2: nf = resolve_flags<2>(row_any, words, c, s_flag_row, lane); break;
+            case 4: nf = resolve_flags<4>(row_any, words, c, s_flag_row, lane); break;
+            case 8: nf = resolve_flags<8>(row_any, words, c, s_flag_row, lane); break;
+            default: nf = resolve_flags<16>(row_any, words, c, s_flag_row, lane); break;
         }
-        if (lane == 0) s_nflag = base;
+        if (lane == 0) s_nflag = nf;
     }
     __syncthreads();
     const int nflag = s_nflag;
@@ -227,39 +288,20 @@ __global__ void __launch_bounds__(1024) greedy_resolve_kernel(DeviceState* st, c
     }
     __syncthreads();
     if (tid < 32) {
-        unsigned killed[kLaneWords];
-#pragma unroll
-        for (int h = 0; h < kLaneWords; ++h) killed[h] = 0u;
-        for (int f = 0; f < nflag; ++f) {
-            const int k = s_flag_row[f], w = k >> 5;
-            unsigned mine = 0u;   // this lane's copy of word (w mod 32) + 32 h, h = w / 32
-#pragma unroll
-            for (int h = 0; h < kLaneWords; ++h)
-                if ((w >> 5) == h) mine = killed[h];
-            const unsigned kw = __shfl_sync(kFull, mine, w & 31);
-            if ((kw >> (k & 31)) & 1u) continue;
-            const unsigned* row = f < staged ? s_rows + (size_t)f * cw : conflict + (size_t)k * words;
-#pragma unroll
-            for (int h = 0; h < kLaneWords; ++h)
-                if (lane + 32 * h < cw) killed[h] |= row[lane + 32 * h];
+        int alive;
+        switch (H) {
+            case 1: alive = resolve_walk<1>(conflict, words, c, cw, s_flag_row, nflag, s_rows, staged, s_alive,
+                                            s_rank_of_word, lane); break;
+            case 2: alive = resolve_walk<2>(conflict, words, c, cw, s_flag_row, nflag, s_rows, staged, s_alive,
+                                            s_rank_of_word, lane); break;
+            case 4: alive = resolve_walk<4>(conflict, words, c, cw, s_flag_row, nflag, s_rows, staged, s_alive,
+                                            s_rank_of_word, lane); break;
+            case 8: alive = resolve_walk<8>(conflict, words, c, cw, s_flag_row, nflag, s_rows, staged, s_alive,
+                                            s_rank_of_word, lane); break;
+            default: alive = resolve_walk<16>(conflict, words, c, cw, s_flag_row, nflag, s_rows, staged, s_alive,
+                                              s_rank_of_word, lane); break;
         }
-        int base = 0;
-#pragma unroll
-        for (int h = 0; h < kLaneWords; ++h) {
-            const int w = lane + 32 * h;
-            const unsigned valid = (w * 32 + 32 <= c) ? kFull : (w * 32 >= c ? 0u : ((1u << (c - w * 32)) - 1u));
-            const unsigned alive = ~killed[h] & valid;
-            s_alive[w] = alive;
-            const int cnt = __popc(alive);
-            int x = cnt;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(kFull, x, o);
-                if (lane >= o) x += y;
-            }
-            s_rank_of_word[w] = base + x - cnt;   // alive count before word w
-            base += __shfl_sync(kFull, x, 31);
-        }
-        if (lane == 0) s_rank_of_word[kMaxWords] = base;
+        if (lane == 0) s_rank_of_word[kMaxWords] = alive;
     }
     __syncthreads();
     const int base_l = st->n_landmarks;
@@ -368,21 +410,24 @@ cudaError_t launch_greedy_gather(const GreedyBuffers& g, const Prepared& pts, in
 }
 
 cudaError_t launch_greedy_resolve(const GreedyBuffers& g, int S, cudaStream_t s) {
+    if (S > kMaxWords * 32) return cudaErrorInvalidValue;
     const int words = S / 32;
     constexpr size_t kStageBytes = 128 * 1024;
+    constexpr size_t kMaxSmem = kStageBytes + sizeof(int) * kMaxWords * 32;
     const size_t full = (size_t)S * words * sizeof(unsigned);   // every row of the largest batch
-    const size_t smem = full < kStageBytes ? full : kStageBytes;
+    const size_t stage = full < kStageBytes ? full : kStageBytes;
+    const size_t smem = sizeof(int) * (size_t)S + stage;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(greedy_resolve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kStageBytes);
+                                             (int)kMaxSmem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     note_launch();
     return launch_pdl(greedy_resolve_kernel, dim3(1), dim3(1024), smem, s, g.st, (const unsigned*)g.conflict,
                       (const unsigned*)g.row_any, words, (const int*)g.cand_ids, g.ordinal, g.landmarks, g.mem_cap,
-                      (int)(smem / sizeof(unsigned)), S);
+                      (int)(stage / sizeof(unsigned)), S);
 }
 
 // Loop condition of a greedy build run as a graph WHILE node: another step while

@@ -121,7 +121,7 @@ cudaError_t launch_delta(DeviceState* st, int path, int d, int d_pad, double eps
 // centre), set to 0 unless it shrinks the sample's largest squared norm by 5 % (force: kept
 // always); *centred (device) receives 1 when kept.  partial: kCentreBlocks * d doubles,
 // maxima: 2 unsigned (device scratch).
-constexpr int kCentreBlocks = 152;
+constexpr int kCentreBlocks = 152 * 8;
 cudaError_t launch_centre(const float* x, long long rows, int d, bool force, double* partial, unsigned* maxima,
                           float* centre, int* centred, cudaStream_t s);
 // fp16 operands of an already prepared set (hi, aug allocated as 2-byte arrays)

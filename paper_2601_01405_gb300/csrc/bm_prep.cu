@@ -236,37 +236,37 @@ __device__ __forceinline__ long long sample_row(long long k, long long m, long l
 }
 
 // Block b sums its share of the sampled rows per column in FP64 (fixed partition, order
-// and reduction tree, so the centre is the same on every run).  Warp w of the block takes
-// rows k0 + w, k0 + w + 8, ...; lane l the columns c0 + l of each 32-column chunk, so each
-// row is read coalesced; the eight warp sums of a column are added in warp order.
+// and reduction tree, so the centre is the same on every run; kCentreBlocks = 1216 blocks
+// leave ~54 of 65,536 sampled rows to a block).  Warp w of the block takes rows k0 + w,
+// k0 + w + 8, ...; lane l the columns 32 c + l of each row (all chunks of a row loaded
+// together, coalesced); the eight warp sums of a column are added in warp order.
 constexpr int kCentreWarps = 8;
+constexpr int kCentreChunks = 16;   // 32-column chunks: d <= 512 (the tensor-core tiles' limit)
 
 __global__ void __launch_bounds__(kCentreWarps * 32) centre_partial_kernel(const float* __restrict__ x, long long rows,
                                                                           int d, long long m,
                                                                           double* __restrict__ partial) {
-    __shared__ double s_sum[kCentreWarps][32];
+    __shared__ double s_sum[kCentreWarps][kCentreChunks * 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long k0 = (long long)blockIdx.x * m / gridDim.x, k1 = (long long)(blockIdx.x + 1) * m / gridDim.x;
-    for (int c0 = 0; c0 < d; c0 += 32) {
-        const int j = c0 + lane;
-        double s[4] = {0.0, 0.0, 0.0, 0.0};
-        long long k = k0 + warp;
-        for (; k + 3 * kCentreWarps < k1; k += 4 * kCentreWarps) {   // four rows in flight per lane
-            float v[4];
+    double acc[kCentreChunks];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) v[u] = j < d ? x[sample_row(k + u * kCentreWarps, m, rows) * d + j] : 0.f;
+    for (int c = 0; c < kCentreChunks; ++c) acc[c] = 0.0;
+    for (long long k = k0 + warp; k < k1; k += kCentreWarps) {   // every column of a row in flight at once
+        const float* row = x + sample_row(k, m, rows) * d;
+        float v[kCentreChunks];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) s[u] += (double)v[u];
-        }
-        for (; k < k1; k += kCentreWarps) s[0] += j < d ? (double)x[sample_row(k, m, rows) * d + j] : 0.0;
-        s_sum[warp][lane] = (s[0] + s[1]) + (s[2] + s[3]);
-        __syncthreads();
-        if (warp == 0 && j < d) {
-            double t = 0.0;
-            for (int w = 0; w < kCentreWarps; ++w) t += s_sum[w][lane];
-            partial[(long long)blockIdx.x * d + j] = t;
-        }
-        __syncthreads();
+        for (int c = 0; c < kCentreChunks; ++c) v[c] = c * 32 + lane < d ? row[c * 32 + lane] : 0.f;
+#pragma unroll
+        for (int c = 0; c < kCentreChunks; ++c) acc[c] += (double)v[c];
+    }
+#pragma unroll
+    for (int c = 0; c < kCentreChunks; ++c) s_sum[warp][c * 32 + lane] = acc[c];
+    __syncthreads();
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        double t = 0.0;
+        for (int w = 0; w < kCentreWarps; ++w) t += s_sum[w][j];
+        partial[(long long)blockIdx.x * d + j] = t;
     }
 }
 
@@ -350,6 +350,7 @@ __global__ void centre_decide_kernel(float* centre, int d, const unsigned* maxim
 cudaError_t launch_centre(const float* x, long long rows, int d, bool force, double* partial, unsigned* maxima,
                           float* centre, int* centred, cudaStream_t s) {
     if (rows <= 0) return cudaSuccess;
+    if (d > kCentreChunks * 32) return cudaErrorInvalidValue;
     const long long m = rows < kCentreSample ? rows : kCentreSample;
     note_launch();
     centre_partial_kernel<<<kCentreBlocks, kCentreWarps * 32, 0, s>>>(x, rows, d, m, partial);

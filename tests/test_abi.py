@@ -106,15 +106,15 @@ def test_tile_config_table_on_host():
 
 def test_batch_bounds_rejected_before_the_device():
     """The largest greedy batch is validated with the other arguments, before any device
-    call: bm_build takes multiples of 32 up to 8192, bm_build_batched up to 2048."""
+    call: bm_build takes multiples of 32 up to 16384, bm_build_batched up to 2048."""
     import numpy as np
     _build.build()
     X = np.zeros((4, 2), dtype=np.float32)
-    for bad in (16, 33, 8224, 16384):
+    for bad in (16, 33, 16416, 32768):
         with pytest.raises(binding.BallMapperError) as ei:
             binding.bm_build(X, 1.0, batch=bad)
         assert ei.value.status == binding.BM_ERR_ARG
-        assert "[32, 8192]" in str(ei.value)
+        assert "[32, 16384]" in str(ei.value)
     with pytest.raises(binding.BallMapperError) as ei:
         binding.bm_build_batched([(X, 1.0)], batch=4096)
     assert ei.value.status == binding.BM_ERR_ARG

@@ -108,7 +108,7 @@ def test_build_iso_n10k_d16(bm, path):
 
 
 @pytest.mark.parametrize("path", PATHS)
-@pytest.mark.parametrize("batch", [32, 96, 1024, 2048, 4096, 8192])
+@pytest.mark.parametrize("batch", [32, 96, 1024, 2048, 4096, 8192, 16384])
 def test_build_batch_sizes(bm, path, batch):
     X = W.isotropic(5003, 8, 10, seed=3)
     ref = oracle.build(X, 2.0)
@@ -134,6 +134,25 @@ def test_build_batch_8192_conflicts(bm, path):
     got = run_build(bm, X, 1.0, path, batch=8192)
     assert_same_graph(got, ref)
     assert got["stats"]["greedy_steps"] < 10   # 8 steps; a batch capped at 4096 takes 10
+
+
+@pytest.mark.parametrize("path", ["tc", "auto"])
+def test_build_batch_16384_conflicts(bm, path):
+    """The largest batch of a single build: isolated points with near copies planted
+    every 97th index, each within 16,000 positions of its original, so the batch grows to
+    16384 (the default) and in-batch conflicts fall across all 512 words of a conflict row."""
+    rng = np.random.default_rng(6)
+    n = 60000
+    X = np.round(rng.uniform(-1000.0, 1000.0, (n, 6)) * 16.0) / 16.0
+    for i in range(40, n, 97):
+        j = i - int(rng.integers(1, min(i, 16000) + 1))
+        X[i] = X[j] + rng.integers(-4, 5, 6) / 16.0   # within sqrt(6)/4 < 1 of X[j]
+    X = X.astype(np.float32)
+    ref = oracle.build(X, 1.0)
+    assert n - ref["landmarks"].size > 500
+    got = run_build(bm, X, 1.0, path)
+    assert_same_graph(got, ref)
+    assert got["stats"]["greedy_steps"] < 11   # 256, 512, ..., 16384, 16384, rest: 9 steps; capped at 8192: 12
 
 
 @pytest.mark.parametrize("path", PATHS)
