@@ -300,16 +300,12 @@ def bm_range_query(X, Q, eps: float, path: str = "auto", stream=None, want_dists
         opt = _options(lib, path, 0, stream, True, None, want_dists=want_dists, centring=centring)
         _check(lib, lib.bm_range_query(px, n, d, pq, m, ctypes.c_float(eps), ctypes.byref(opt), ctypes.byref(out),
                                        ctypes.byref(st)))
-        try:
-            off = np.ctypeslib.as_array((ctypes.c_int64 * (m + 1)).from_address(out.offsets)).copy()
-            ids = np.ctypeslib.as_array((ctypes.c_int32 * max(out.nnz, 1)).from_address(out.ids))[: out.nnz].copy()
-            dists = None
-            if want_dists:
-                dists = np.ctypeslib.as_array((ctypes.c_float * max(out.nnz, 1)).from_address(out.dists))[
-                    : out.nnz].copy()
-        finally:
-            lib.bm_csr_free(ctypes.byref(out), ctypes.byref(opt))
-        return (off, ids, st.as_dict(), dists) if want_dists else (off, ids, st.as_dict())
+        own = _HostResult(lib.bm_csr_free, bm_csr.from_buffer_copy(out), opt)
+        off = own.view(out.offsets, ctypes.c_int64, m + 1)
+        ids = own.view(out.ids, ctypes.c_int32, out.nnz)
+        if want_dists:
+            return off, ids, st.as_dict(), own.view(out.dists, ctypes.c_float, out.nnz)
+        return off, ids, st.as_dict()
     import torch
     dev = kx.device
     alloc = _TorchAllocator(dev)
@@ -338,22 +334,7 @@ def bm_build(X, eps: float, path: str = "auto", batch: int = 0, stream=None, ski
     if host:
         opt = _options(lib, path, batch, stream, True, None, skip_edges, want_dists, centring)
         _check(lib, lib.bm_build(px, n, d, ctypes.c_float(eps), ctypes.byref(opt), ctypes.byref(g)))
-        try:
-            L, nnz, E = g.n_landmarks, g.members.nnz, g.n_edges
-
-            def arr(ptr, ctype, count):
-                return np.ctypeslib.as_array((ctype * max(count, 1)).from_address(ptr))[:count].copy()
-
-            res = {"landmarks": arr(g.landmarks, ctypes.c_int32, L),
-                   "offsets": arr(g.members.offsets, ctypes.c_int64, L + 1),
-                   "ids": arr(g.members.ids, ctypes.c_int32, nnz),
-                   "edges": arr(g.edges, ctypes.c_int32, 2 * E).reshape(E, 2),
-                   "stats": g.stats.as_dict()}
-            if want_dists:
-                res["dists"] = arr(g.members.dists, ctypes.c_float, nnz)
-        finally:
-            lib.bm_graph_free(ctypes.byref(g), ctypes.byref(opt))
-        return res
+        return _host_graph(lib, g, opt, want_dists)
     import torch
     dev = kx.device
     alloc = _TorchAllocator(dev)
@@ -376,23 +357,37 @@ def _graph_dict(alloc, g, want_dists=False):
     return res
 
 
+class _HostResult:
+    """Owns the host buffers of one library result; the numpy arrays returned to the caller
+    are views of them, and the buffers go back to the library (bm_graph_free / bm_csr_free)
+    once the last view is gone."""
+
+    def __init__(self, free_fn, obj, opt):
+        self._free, self._obj, self._opt = free_fn, obj, opt
+
+    def view(self, ptr, ctype, count):
+        buf = (ctype * max(count, 1)).from_address(ptr)
+        buf._owner = self   # the array's base chain keeps the owner alive
+        return np.ctypeslib.as_array(buf)[:count]
+
+    def __del__(self):
+        try:
+            self._free(ctypes.byref(self._obj), ctypes.byref(self._opt))
+        except Exception:
+            pass
+
+
 def _host_graph(lib, g, opt, want_dists):
-    """A host bm_graph copied into numpy arrays, then released."""
-    try:
-        L, nnz, E = g.n_landmarks, g.members.nnz, g.n_edges
-
-        def arr(ptr, ctype, count):
-            return np.ctypeslib.as_array((ctype * max(count, 1)).from_address(ptr))[:count].copy()
-
-        res = {"landmarks": arr(g.landmarks, ctypes.c_int32, L),
-               "offsets": arr(g.members.offsets, ctypes.c_int64, L + 1),
-               "ids": arr(g.members.ids, ctypes.c_int32, nnz),
-               "edges": arr(g.edges, ctypes.c_int32, 2 * E).reshape(E, 2),
-               "stats": g.stats.as_dict()}
-        if want_dists:
-            res["dists"] = arr(g.members.dists, ctypes.c_float, nnz)
-    finally:
-        lib.bm_graph_free(ctypes.byref(g), ctypes.byref(opt))
+    """A host bm_graph as numpy arrays (views of the library's buffers, no copy)."""
+    own = _HostResult(lib.bm_graph_free, bm_graph.from_buffer_copy(g), opt)
+    L, nnz, E = g.n_landmarks, g.members.nnz, g.n_edges
+    res = {"landmarks": own.view(g.landmarks, ctypes.c_int32, L),
+           "offsets": own.view(g.members.offsets, ctypes.c_int64, L + 1),
+           "ids": own.view(g.members.ids, ctypes.c_int32, nnz),
+           "edges": own.view(g.edges, ctypes.c_int32, 2 * E).reshape(E, 2),
+           "stats": g.stats.as_dict()}
+    if want_dists:
+        res["dists"] = own.view(g.members.dists, ctypes.c_float, nnz)
     return res
 
 
@@ -507,23 +502,7 @@ def bm_build_batched(instances, path: str = "auto", batch: int = 0, stream=None,
     if host:
         opt = _options(lib, path, batch, stream, True, None, skip_edges, centring=centring)
         _check(lib, lib.bm_build_batched(arr_in, count, ctypes.byref(opt), outs, statuses))
-
-        def arr(ptr, ctype, k):
-            return np.ctypeslib.as_array((ctype * max(k, 1)).from_address(ptr))[:k].copy()
-
-        res = []
-        try:
-            for g in outs[:count]:
-                L, nnz, E = g.n_landmarks, g.members.nnz, g.n_edges
-                res.append({"landmarks": arr(g.landmarks, ctypes.c_int32, L),
-                            "offsets": arr(g.members.offsets, ctypes.c_int64, L + 1),
-                            "ids": arr(g.members.ids, ctypes.c_int32, nnz),
-                            "edges": arr(g.edges, ctypes.c_int32, 2 * E).reshape(E, 2),
-                            "stats": g.stats.as_dict()})
-        finally:
-            for k in range(count):
-                lib.bm_graph_free(ctypes.byref(outs[k]), ctypes.byref(opt))
-        return res
+        return [_host_graph(lib, outs[k], opt, False) for k in range(count)]
     import torch
     dev = ins[0][3].device if count else torch.device("cuda", torch.cuda.current_device())
     alloc = _TorchAllocator(dev)

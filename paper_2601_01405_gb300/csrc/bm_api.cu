@@ -1,5 +1,7 @@
 // bm_api.cu -- the C-ABI of libballmapper: argument checks, buffer management,
 // phase orchestration on the caller's stream, and error reporting.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -8,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -24,6 +27,75 @@ void device_free(const bm_options* opt, cudaStream_t s, void* p) {
     else cudaFreeAsync(p, s);
 }
 
+// Identifier of the current CUDA context (0 when the driver cannot report one).
+unsigned long long current_context_id() {
+    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (PFN_cuCtxGetCurrent_v4000)p;
+        else
+            cudaGetLastError();
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (PFN_cuCtxGetId_v12000)p;
+        else
+            cudaGetLastError();
+        looked_up = true;
+    }
+    if (!get_current || !get_id) return 0ull;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0ull;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0ull;
+    return id;
+}
+
+
+namespace {
+// The library's own stream-ordered pool per device (used when the caller gives no
+// allocator).  It keeps up to kPoolKeepBytes of freed memory mapped across
+// synchronisations, so that a call does not map its scratch afresh after the previous
+// call's memory went back to the driver (the default pool keeps nothing).  Keyed on the
+// context, like any device resource: a context created after a reset gets its own pool.
+constexpr unsigned long long kPoolKeepBytes = 8ull << 30;
+std::mutex g_pool_mu;
+std::vector<std::pair<unsigned long long, cudaMemPool_t>> g_pools;   // (context id, pool)
+
+cudaMemPool_t library_pool() {
+    const unsigned long long id = current_context_id();
+    if (id == 0) return nullptr;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (auto& e : g_pools)
+        if (e.first == id) return e.second;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    unsigned long long keep = kPoolKeepBytes;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    cudaGetLastError();
+    g_pools.emplace_back(id, pool);
+    return pool;
+}
+}  // namespace
+
 Arena::~Arena() {
     for (void* p : ptrs_) device_free(opt_, stream_, p);
     for (void* p : slabs_) device_free(opt_, stream_, p);
@@ -33,6 +105,11 @@ void* Arena::raw(size_t bytes) {
     void* p = nullptr;
     if (opt_ && opt_->alloc) {
         p = opt_->alloc(bytes, (void*)stream_, opt_->alloc_ctx);
+    } else if (cudaMemPool_t pool = library_pool()) {
+        if (cudaMallocFromPoolAsync(&p, bytes, pool, stream_) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
     } else if (cudaMallocAsync(&p, bytes, stream_) != cudaSuccess) {
         cudaGetLastError();
         p = nullptr;

@@ -44,6 +44,8 @@ private:
 };
 
 void device_free(const bm_options* opt, cudaStream_t s, void* p);
+// Identifier of the current CUDA context (0 when the driver cannot report one).
+unsigned long long current_context_id();
 
 // Launch with programmatic stream serialization (the kernel must begin with pdl_wait();
 // see bm_common.cuh), so that its launch overlaps the predecessor kernel's tail.  Inside a

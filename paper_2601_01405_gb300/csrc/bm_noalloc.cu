@@ -128,34 +128,6 @@ struct ScratchSlot {
 std::mutex g_setup_mutex;
 ScratchSlot g_slot[64] = {};
 
-// Identifier of the current CUDA context (0 when the driver cannot report one).
-unsigned long long current_context_id() {
-    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
-    static PFN_cuCtxGetId_v12000 get_id = nullptr;
-    static bool looked_up = false;
-    if (!looked_up) {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            get_current = (PFN_cuCtxGetCurrent_v4000)p;
-        else
-            cudaGetLastError();
-        p = nullptr;
-        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            get_id = (PFN_cuCtxGetId_v12000)p;
-        else
-            cudaGetLastError();
-        looked_up = true;
-    }
-    if (!get_current || !get_id) return 0ull;
-    CUcontext ctx = nullptr;
-    unsigned long long id = 0ull;
-    if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0ull;
-    return id;
-}
-
 }  // namespace
 
 // the library's thread-local error message (defined with the other entry points)
