@@ -370,7 +370,8 @@ bm_status finish_prep(DeviceState* st, int path, int d, double eps2, double eps,
         if (qry) TRY_CUDA(launch_prep16(qry->x, qry->rows, d, eps2, true, e, *qry, s));
     }
     TRY_CUDA(launch_delta(st, path, d, pts->d_pad, eps2, same_sets, s, e));
-    if (pts->prec != kPrecNone) TRY_CUDA(launch_set_aug_delta(st, *pts, s));
+    if (pts->prec != kPrecNone) TRY_CUDA(launch_set_aug_delta(st, *pts, eps2, false, s));
+    if (qry && qry->prec != kPrecNone) TRY_CUDA(launch_set_aug_delta(st, *qry, eps2, true, s));
     return BM_OK;
 }
 
@@ -867,7 +868,7 @@ bm_status switch_path(GreedyCtx& c, Prepared& pts, Arena& ar, cudaStream_t s, in
     cand.prec = pts.prec;
     cand.scale_exp = pts.scale_exp;
     TRY_CUDA(launch_delta(st, to, pts.d, pts.d_pad, c.eps2, true, s, e));
-    TRY_CUDA(launch_set_aug_delta(st, pts, s));
+    TRY_CUDA(launch_set_aug_delta(st, pts, c.eps2, false, s));
     c.path = to;
     c.switches.push_back(step);
     return BM_OK;
@@ -1071,7 +1072,10 @@ bm_status range_core(const float* X, long long n, int d, const float* Q, long lo
                     if ((double)df < dl) df = std::nextafter(df, INFINITY);
                     TRY_CUDA(cudaMemcpyAsync(&st->delta, &df, sizeof(float), cudaMemcpyHostToDevice, s));
                     TRY_CUDA(cudaStreamSynchronize(s));
-                    if (px.prec != kPrecNone) TRY_CUDA(launch_set_aug_delta(st, px, s));
+                    if (px.prec != kPrecNone) {
+                        TRY_CUDA(launch_set_aug_delta(st, px, eps2, false, s));
+                        TRY_CUDA(launch_set_aug_delta(st, pq, eps2, true, s, row_r2));
+                    }
                 } else {
                     rs = finish_prep(st, path, d, eps2, (double)eps, false, std::max(nx, nq), &px, &pq, s);
                     if (rs != BM_OK) return rs;
@@ -1488,7 +1492,7 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
                 std::memcpy(&nx, &hnorm, sizeof(float));
                 rs = finish_prep(st, path, d, eps2, (double)eps, true, nx, &px, nullptr, s);
                 if (rs != BM_OK) return rs;
-                if (b_pad) TRY_CUDA(launch_set_aug_delta(st, pperm, s));
+                if (b_pad) TRY_CUDA(launch_set_aug_delta(st, pperm, eps2, false, s));
             }
             tm.mark();  // 1: prep done
             unsigned long long step_cap = (unsigned long long)std::min<long long>((long long)S * n, 1LL << 22);
@@ -1508,6 +1512,7 @@ bm_status build_graph(const float* X, long long n, int d, float eps, const bm_op
                 rs = prepare(qx, nL, d, eps2, true, tc ? prec_for(path) : kPrecNone, ar, &st->max_norm_q_bits, bad, s,
                              pq, nullptr, centre);
                 if (rs != BM_OK) return rs;
+                if (tc) TRY_CUDA(launch_set_aug_delta(st, pq, eps2, true, s));   // the landmark rows' delta'
                 const int sms = device_sm_count();
                 unsigned long long cap = (unsigned long long)std::max<long long>(4 * n, 1LL << 20);
                 if (tc) cap = std::max<unsigned long long>(cap, (unsigned long long)sms * 4096);

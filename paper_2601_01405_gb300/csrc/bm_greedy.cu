@@ -125,14 +125,14 @@ __global__ void __launch_bounds__(kSelThreads) greedy_select_kernel(
 
 // One warp per candidate: copy its float32 row, phi and, for the tensor-core
 // paths, its 16-bit operand rows (bf16 hi and lo, or fp16 hi alone) and A-side
-// augmentation (the B-side row with the halves [0,3) and [3,6) swapped) into
+// augmentation (the B-side row with the halves [0,3) and [3,6) swapped and the point's
+// own delta'_row in column 6) into
 // the contiguous candidate operands.
 __global__ void __launch_bounds__(256) greedy_gather_kernel(
     const DeviceState* st, const int* __restrict__ cand_ids, const float* __restrict__ X,
     const float* __restrict__ phi, int d, float* __restrict__ cand_x, float* __restrict__ cand_phi, int want_tc,
     const unsigned* __restrict__ H, const unsigned* __restrict__ Lo, const unsigned short* __restrict__ Aug,
-    int d_pad, unsigned* __restrict__ cH, unsigned* __restrict__ cLo, unsigned short* __restrict__ cAug,
-    unsigned short one_bits) {
+    int d_pad, unsigned* __restrict__ cH, unsigned* __restrict__ cLo, unsigned short* __restrict__ cAug) {
     pdl_wait();
     pdl_trigger();
     if (st->done) return;
@@ -148,9 +148,11 @@ __global__ void __launch_bounds__(256) greedy_gather_kernel(
             if (Lo) cLo[(long long)s * w + i] = Lo[id * w + i];   // no lo half in fp16 mode
         }
         if (lane < 16) {
-            const int src = lane < 3 ? lane + 3 : (lane < 6 ? lane - 3 : lane);
-            // column 6: the candidates' 1 against the points' +delta'
-            cAug[(long long)s * 16 + lane] = lane == 6 ? one_bits : Aug[id * 16 + src];
+            // A-side layout from the point's B-side block: the halves [0,3) and [3,6) swapped,
+            // column 6 = the point's own +delta'_row (its column 7) against the points' 1,
+            // column 7 = 0
+            const int src = lane < 3 ? lane + 3 : (lane < 6 ? lane - 3 : (lane == 6 ? 7 : lane));
+            cAug[(long long)s * 16 + lane] = lane == 7 ? (unsigned short)0 : Aug[id * 16 + src];
         }
     }
 }
@@ -405,8 +407,7 @@ cudaError_t launch_greedy_gather(const GreedyBuffers& g, const Prepared& pts, in
         const_cast<float*>(g.cand.x), g.cand.phi, want_tc ? 1 : 0,
         reinterpret_cast<const unsigned*>(pts.hi), reinterpret_cast<const unsigned*>(pts.lo),
         reinterpret_cast<const unsigned short*>(pts.aug), pts.d_pad, reinterpret_cast<unsigned*>(g.cand.hi),
-        reinterpret_cast<unsigned*>(g.cand.lo), reinterpret_cast<unsigned short*>(g.cand.aug),
-        (unsigned short)(pts.prec == kPrecFp16 ? 0x3C00u : 0x3F80u));   // 1.0 in fp16 / bf16
+        reinterpret_cast<unsigned*>(g.cand.lo), reinterpret_cast<unsigned short*>(g.cand.aug));
 }
 
 cudaError_t launch_greedy_resolve(const GreedyBuffers& g, int S, cudaStream_t s) {

@@ -136,8 +136,12 @@ __host__ __device__ double band_halfwidth(int path, int d, int d_pad, double eps
 // The same bound for explicit bounds Pa, Pb on |phi| of the two sides (operand units)
 __host__ __device__ double band_halfwidth_core(int path, int d, int d_pad, double Na, double Nb, double Pa,
                                                double Pb);
-// +delta' into column 6 of a B-side (points) augmentation, after launch_delta
-cudaError_t launch_set_aug_delta(const DeviceState* st, Prepared& p, cudaStream_t s);
+// The per-row delta' entries of an augmentation (A side: column 6; B side: 1 in column 6,
+// the point's own delta'_row in column 7), once the points' maximum norm is in st.
+// eps2: the radius the set was prepared with (0 for the points of a k-NN sweep);
+// row_r2: a k-NN sweep's per-query squared radii (A side), else null.
+cudaError_t launch_set_aug_delta(const DeviceState* st, Prepared& p, double eps2, bool a_side, cudaStream_t s,
+                                 const double* row_r2 = nullptr);
 
 struct IvfIndex;
 struct GraphIndex;

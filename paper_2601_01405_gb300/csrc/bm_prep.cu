@@ -13,12 +13,12 @@
 // two bf16 values, x = hi + lo (hi = bf16(x), lo = bf16(x - hi)), and phi is
 // carried into the K dimension by a 16-wide augmentation block so that the
 // FP32 accumulator already holds v:
-//   B side (points):   aug = [1, 1, 1, -p1, -p2, -p3, delta', 0 ...]
-//   A side (queries):  aug = [-p1, -p2, -p3, 1, 1, 1, 1, 0 ...]
-// with phi ~ p1 + p2 + p3 (three bf16 pieces of the FP64 value) and delta' the
-// band half-width rounded up to the operand type (written by set_aug_delta once
-// delta is known), so the accumulator holds v + delta' and the tiles classify by
-// its sign.  The tensor-core operands may be those of the translated rows x - c
+//   B side (points):   aug = [1, 1, 1, -p1, -p2, -p3, 1, delta'_x, 0 ...]
+//   A side (queries):  aug = [-p1, -p2, -p3, 1, 1, 1, delta'_q, 0, 0 ...]
+// with phi ~ p1 + p2 + p3 (three bf16 pieces of the FP64 value) and delta'_q the query
+// row's band half-width rounded up to the operand type (set_aug_rows, once the points'
+// maximum norm is known; delta'_x, the same for a point, is what a greedy candidate
+// carries), so the accumulator holds v + delta'_q and the tiles classify by its sign.  The tensor-core operands may be those of the translated rows x - c
 // (launch_centre below); phi and the norms are then the translated rows' too.
 #include <cuda_fp16.h>
 
@@ -97,14 +97,20 @@ __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ x, 
                 const __nv_bfloat16 p3 = __double2bfloat16(r2);
                 const __nv_bfloat16 one = __float2bfloat16_rn(1.f);
                 const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+                const __nv_bfloat16 top = __ushort_as_bfloat16((unsigned short)0x7F7Fu);   // largest finite
                 // pos < 3: the -p pieces; 3 <= pos < 6: ones (A side layout; B side swaps halves);
-                // pos 6 on the A side: 1 against the points' +delta' (set_aug_delta)
+                // column 6: the query's +delta'_row (A side) against 1 (B side); column 7 (B side):
+                // the point's own delta'_row for the greedy's candidates.  Until set_aug_rows
+                // writes them, the delta' entries hold the largest finite value (every pair
+                // in the band: exact, only slow)
                 __align__(16) __nv_bfloat16 a[16];
 #pragma unroll
                 for (int col = 0; col < 16; ++col) {
                     const int pos = aug_pos(col, a_side);
                     a[col] = pos == 0 ? __hneg(p1) : pos == 1 ? __hneg(p2) : pos == 2 ? __hneg(p3)
-                           : pos < 6 ? one : (pos == 6 && a_side) ? one : zero;
+                           : pos < 6 ? one
+                           : pos == 6 ? (a_side ? top : one)
+                           : (pos == 7 && !a_side) ? top : zero;
                 }
                 uint4* dst = reinterpret_cast<uint4*>(aug + r * 16);
                 dst[0] = reinterpret_cast<const uint4*>(a)[0];
@@ -171,12 +177,15 @@ __global__ void __launch_bounds__(256) prep16_kernel(const float* __restrict__ x
             const double r2 = r1 - (double)__half2float(p2);
             const __half p3 = __double2half(r2);
             const __half one = __float2half_rn(1.f), zero = __float2half_rn(0.f);
+            const __half top = __ushort_as_half((unsigned short)0x7BFFu);   // largest finite
             __align__(16) __half a[16];
 #pragma unroll
             for (int col = 0; col < 16; ++col) {
                 const int pos = aug_pos(col, a_side);
                 a[col] = pos == 0 ? __hneg(p1) : pos == 1 ? __hneg(p2) : pos == 2 ? __hneg(p3)
-                       : pos < 6 ? one : (pos == 6 && a_side) ? one : zero;
+                       : pos < 6 ? one
+                       : pos == 6 ? (a_side ? top : one)
+                       : (pos == 7 && !a_side) ? top : zero;
             }
             uint4* dst = reinterpret_cast<uint4*>(aug + r * 16);
             dst[0] = reinterpret_cast<const uint4*>(a)[0];
@@ -215,9 +224,11 @@ cudaError_t launch_prep(const float* x, long long rows, int d, double eps2, bool
     long long blocks = (rows + 255) / 256;   // 8 warps of 32-row groups per block
     if (blocks > 152 * 16) blocks = 152 * 16;
     note_launch();
+    // out.centre is set for every tensor-core set (split or fp16): the norms and phi measured
+    // here must be those of the translated rows the tiles see
     prep_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, rows, d, eps2, row_r2, a_side ? 1 : 0, want_tc ? 1 : 0,
-                                                 want_tc ? out.centre : nullptr, out.phi, out.hi, out.lo, out.aug,
-                                                 out.d_pad, max_norm_bits, bad_flag);
+                                                 out.centre, out.phi, out.hi, out.lo, out.aug, out.d_pad,
+                                                 max_norm_bits, bad_flag);
     return cudaGetLastError();
 }
 
@@ -447,28 +458,65 @@ __global__ void delta_kernel(DeviceState* st, int path, int d, int d_pad, double
     st->delta = __double2float_ru(band_halfwidth(path, d, d_pad, eps2, Na, Nb, scale_exp));
 }
 
-// Column 6 of the points' augmentation: +delta' = delta rounded up to the operand type.
-__global__ void set_aug_delta_kernel(const DeviceState* st, long long rows, int fp16, unsigned short* aug) {
-    const float delta = st->delta;
-    unsigned short bits;
-    if (fp16) {
-        const __half h = __float2half_ru(delta);
-        bits = __half_as_ushort(h);
-    } else {
-        const __nv_bfloat16 b = __float2bfloat16_ru(delta);
-        bits = __bfloat16_as_ushort(b);
-    }
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += stride) aug[r * 16 + 6] = bits;
+// Band half-width of one query row: its own norm and |phi| against the points' maxima
+// (the bound above holds pair by pair with N_a the row's norm: every term is a product of
+// the two sides' magnitudes, and the points enter through their maxima only).  phi_f is
+// the row's phi rounded to float (the FP64 value lies within 2^-24 |phi_f| / (1 - 2^-24));
+// its squared norm is 2 phi + r2 (r2 = eps^2 / 2, or a k-NN row's own squared radius), so
+// N_a^2 <= 2 phi_f + 2^-22 |phi_f| + r2 and |phi| <= (1 + 2^-22) |phi_f|.  Unscaled inputs;
+// the result in the units of the operands (scaled by 2^scale_exp on the fp16 path).  The
+// bound is evaluated in FP64 row by row: read off as coefficients of N_a and N_a^2 it
+// would lose its low-order terms to cancellation when the norms are large.
+__device__ double band_halfwidth_row(int path, int d, int d_pad, double phi_f, double r2, double Nb, double Pb,
+                                     int scale_exp) {
+    const double sc = ldexp(1.0, scale_exp);
+    const double n2 = 2.0 * phi_f + ldexp(fabs(phi_f), -22) + r2;
+    const double Na = sqrt(fmax(n2, 0.0)) * (1.0 + ldexp(1.0, -40));
+    const double Pa = fabs(phi_f) * (1.0 + ldexp(1.0, -22));
+    return band_halfwidth_core(path, d, d_pad, Na * sc, Nb * sc, Pa * sc * sc, Pb * sc * sc);
 }
 
-cudaError_t launch_set_aug_delta(const DeviceState* st, Prepared& p, cudaStream_t s) {
-    if (p.rows == 0 || p.aug == nullptr) return cudaSuccess;
+// The delta' entries of an augmentation block once the points' maximum norm is known:
+// a query row (A side) gets +delta'_row in column 6; a point (B side) gets 1 in column 6 and
+// its own delta'_row in column 7 (what it carries as a greedy candidate; against the
+// queries' 0 in column 7 it adds nothing).  delta'_row = the row's half-width rounded up
+// to the operand type; the tiles compare the accumulator with 2 delta'_row, so every row
+// has the narrowest band its own norm allows.  row_r2 (queries of a k-NN sweep): each
+// row's squared radius, the points' side then prepared with eps^2 = 0.
+__global__ void set_aug_rows_kernel(const DeviceState* st, const float* __restrict__ phi,
+                                    const double* __restrict__ row_r2, long long rows, int path, int d, int d_pad,
+                                    double eps2, int scale_exp, int a_side, unsigned short* aug) {
+    const double Nb = (double)__uint_as_float(st->max_norm_bits);
+    const double Pb = fmax(Nb * Nb * 0.5 - 0.25 * eps2, 0.25 * eps2);
+    const bool fp16 = path == BM_PATH_TC_FP16;
+    const unsigned short one = fp16 ? __half_as_ushort(__float2half_rn(1.f))
+                                    : __bfloat16_as_ushort(__float2bfloat16_rn(1.f));
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += stride) {
+        const double r2 = row_r2 ? row_r2[r] : 0.5 * eps2;
+        const double dl = band_halfwidth_row(path, d, d_pad, (double)phi[r], r2, Nb, Pb, scale_exp);
+        const float df = __double2float_ru(dl);
+        const unsigned short bits = fp16 ? __half_as_ushort(__float2half_ru(df))
+                                         : __bfloat16_as_ushort(__float2bfloat16_ru(df));
+        if (a_side) {
+            aug[r * 16 + 6] = bits;
+        } else {
+            aug[r * 16 + 6] = one;
+            aug[r * 16 + 7] = bits;
+        }
+    }
+}
+
+cudaError_t launch_set_aug_delta(const DeviceState* st, Prepared& p, double eps2, bool a_side, cudaStream_t s,
+                                 const double* row_r2) {
+    if (p.rows == 0 || p.aug == nullptr || p.prec == kPrecNone) return cudaSuccess;
     long long blocks = (p.rows + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
+    const int path = p.prec == kPrecFp16 ? (int)BM_PATH_TC_FP16 : (int)BM_PATH_TC_SPLIT3;
     note_launch();
-    set_aug_delta_kernel<<<(unsigned)blocks, 256, 0, s>>>(st, p.rows, p.prec == kPrecFp16 ? 1 : 0,
-                                                          reinterpret_cast<unsigned short*>(p.aug));
+    set_aug_rows_kernel<<<(unsigned)blocks, 256, 0, s>>>(st, p.phi, row_r2, p.rows, path, p.d, p.d_pad, eps2,
+                                                         p.prec == kPrecFp16 ? p.scale_exp : 0, a_side ? 1 : 0,
+                                                         reinterpret_cast<unsigned short*>(p.aug));
     return cudaGetLastError();
 }
 

@@ -205,6 +205,7 @@ cudaError_t launch_sweep_tc(const SweepDesc& s, cudaStream_t stream, std::string
     args.items_count = s.tc_items_count;
     args.a_map = s.tc_a_map;
     args.b_ids = s.tc_b_ids;
+    args.a_aug_rows = reinterpret_cast<const unsigned short*>(s.a->aug);
     // fp16 with two K chunks keeps the whole query tile in one stage (a 64-wide chunk
     // only: d_pad = 128)
     const bool whole = fp16 && d_pad == 2 * CK && CK == 64;

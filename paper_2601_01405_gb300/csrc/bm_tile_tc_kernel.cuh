@@ -70,6 +70,8 @@ struct TcArgs {
     const long long* items_count;
     const int* a_map;
     const int* b_ids;
+    // the A operand's augmentation rows (16 entries each): column 6 holds each row's +delta'
+    const unsigned short* a_aug_rows;
 };
 
 struct Ctl {
@@ -538,13 +540,15 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
         constexpr int kChunks = NT / 64;            // 32-column loads per warp per tile
         const int quarter = warp & 3;
         const int half = (warp - 2) >> 2;
-        // The points' augmentation carries +delta' (delta rounded up to the operand type),
-        // so the accumulator holds acc = v + delta': acc < 0 (sign bit set) decides
-        // "not a member", acc > 2 delta' decides "member", the rest is the band.
-        const float delta = p.st->delta;
-        const float dprime = PROD == 3 ? __bfloat162float(__float2bfloat16_ru(delta))
-                                       : __half2float(__float2half_ru(delta));
-        const float hit_thr = 2.f * dprime;
+        // Column 6 of the query rows' augmentation carries +delta'_row (the row's band half-width
+        // rounded up to the operand type) against the points' 1, so the accumulator holds
+        // acc = v + delta'_row: acc < 0 (sign bit set) decides "not a member", acc > 2 delta'_row
+        // decides "member", the rest is the band.  The split tiles (dense, wide bands) read
+        // each row's delta'_row; the fp16 tiles take the threshold 2 delta' of the largest
+        // half-width instead (acc > 2 delta' >= 2 delta'_row is still a member, and their
+        // epilogue, the kernel's bottleneck, keeps no per-row load).
+        constexpr bool row_thr = PROD == 3;
+        const float thr_all = 2.f * __half2float(__float2half_ru(p.st->delta));
         const unsigned long long seg_off = seg_mode ? (unsigned long long)blockIdx.x * p.sink.seg_cap : 0ull;
         unsigned long long* seg_keys = p.sink.keys + seg_off;
         unsigned long long* band_keys = p.sink.band_keys + seg_off;
@@ -571,11 +575,13 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
             }
             const long long col_base = bt * NT + half * (NT / 2);
             for (long long at = at0; at < at1; ++at) {
+                const long long row = at * 128 + quarter * 32 + lane;
+                const bool row_ok = row < a_end;
+                // this row's threshold (split tiles), loaded before the wait for the accumulator
+                const unsigned short dbits = row_thr && row_ok ? p.a_aug_rows[row * 16 + 6] : (unsigned short)0;
                 const bool w = __all_sync(kFull, bar_wait(&ctl->t_full[t_buf], t_ph, abort_flag, gerr));
                 if (!w) { ok = false; break; }
                 fence_after();
-                const long long row = at * 128 + quarter * 32 + lane;
-                const bool row_ok = row < a_end;
                 // the query this A row holds (table mode) and the key's row part
                 const long long qid = table ? (row_ok ? (long long)p.a_map[row] : -1) : row;
                 const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + t_buf * NT + half * (NT / 2);
@@ -607,6 +613,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
                 // gathered with funnel shifts (bit i of the mask from register i); the sign
                 // of thr - acc is set exactly when acc > thr (a rounded difference keeps the
                 // sign of the exact one, and is +0 only when they are equal).
+                const float hit_thr = row_thr ? 2.f * __bfloat162float(__ushort_as_bfloat16(dbits)) : thr_all;
                 unsigned hitm[kChunks], bandm[kChunks];
                 unsigned nh = 0, nb = 0;
 #pragma unroll
