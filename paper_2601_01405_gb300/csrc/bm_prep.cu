@@ -263,13 +263,15 @@ __global__ void __launch_bounds__(kCentreWarps * 32) centre_partial_kernel(const
     double acc[kCentreChunks];
 #pragma unroll
     for (int c = 0; c < kCentreChunks; ++c) acc[c] = 0.0;
+    const int nch = (d + 31) >> 5;   // chunks that hold columns (FP64 adds only for those)
     for (long long k = k0 + warp; k < k1; k += kCentreWarps) {   // every column of a row in flight at once
         const float* row = x + sample_row(k, m, rows) * d;
         float v[kCentreChunks];
 #pragma unroll
-        for (int c = 0; c < kCentreChunks; ++c) v[c] = c * 32 + lane < d ? row[c * 32 + lane] : 0.f;
+        for (int c = 0; c < kCentreChunks; ++c) v[c] = c < nch && c * 32 + lane < d ? row[c * 32 + lane] : 0.f;
 #pragma unroll
-        for (int c = 0; c < kCentreChunks; ++c) acc[c] += (double)v[c];
+        for (int c = 0; c < kCentreChunks; ++c)
+            if (c < nch) acc[c] += (double)v[c];
     }
 #pragma unroll
     for (int c = 0; c < kCentreChunks; ++c) s_sum[warp][c * 32 + lane] = acc[c];
@@ -471,7 +473,7 @@ __device__ double band_halfwidth_row(int path, int d, int d_pad, double phi_f, d
                                      int scale_exp) {
     const double sc = ldexp(1.0, scale_exp);
     const double n2 = 2.0 * phi_f + ldexp(fabs(phi_f), -22) + r2;
-    const double Na = sqrt(fmax(n2, 0.0)) * (1.0 + ldexp(1.0, -40));
+    const double Na = (double)__fsqrt_ru(__double2float_ru(fmax(n2, 0.0)));   // rounded up (FP32: cheap)
     const double Pa = fabs(phi_f) * (1.0 + ldexp(1.0, -22));
     return band_halfwidth_core(path, d, d_pad, Na * sc, Nb * sc, Pa * sc * sc, Pb * sc * sc);
 }
