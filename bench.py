@@ -40,7 +40,7 @@ UNIT = "evals/s"
 # batch, so the figure holds for each launch of this workload to within the query rows'
 # 160 B each (the automatic path runs fp16 after the first step).  None where no capture
 # of the current kernel exists.
-NCU_TRAFFIC = {("mix32-n1M-d64", "auto"): 166.1e6, ("mix32-n1M-d64", "tc16"): 166.1e6}
+NCU_TRAFFIC = {("mix32-n1M-d64", "auto"): 166.5e6, ("mix32-n1M-d64", "tc16"): 166.5e6}
 DTYPES = {"tc": "bf16x3-split/fp32-acc/fp64-recheck", "tc16": "f16-scaled/fp32-acc/fp64-recheck",
           "fp32": "f32/fp64-recheck", "auto": "f16-scaled or bf16x3-split/fp32-acc/fp64-recheck"}
 
