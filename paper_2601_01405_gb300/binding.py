@@ -438,7 +438,7 @@ def bm_color(offsets, ids, f, stat: str = "mean", stream=None):
     return out[:rows]
 
 
-def bm_knn_dist(X, k: int, path: str = "auto", stream=None):
+def bm_knn_dist(X, k: int, path: str = "auto", stream=None, centring: str = "auto"):
     """Distance from every point to its k-th nearest neighbour, itself counted first
     (Sec. 6.1).  Device tensor in -> float64 CUDA tensor [n]; host array in -> numpy.
     Returns (kdist, stats)."""
@@ -447,18 +447,18 @@ def bm_knn_dist(X, k: int, path: str = "auto", stream=None):
     st = bm_stats()
     if host:
         out = np.empty(max(n, 1), dtype=np.float64)
-        opt = _options(lib, path, 0, stream, True, None)
+        opt = _options(lib, path, 0, stream, True, None, centring=centring)
         _check(lib, lib.bm_knn_dist(px, n, d, int(k), ctypes.byref(opt), out.ctypes.data, ctypes.byref(st)))
         return out[:n], st.as_dict()
     import torch
     out = torch.empty(max(n, 1), dtype=torch.float64, device=kx.device)
     alloc = _TorchAllocator(kx.device)
-    opt = _options(lib, path, 0, stream or _current_stream(kx.device), False, alloc)
+    opt = _options(lib, path, 0, stream or _current_stream(kx.device), False, alloc, centring=centring)
     _check(lib, lib.bm_knn_dist(px, n, d, int(k), ctypes.byref(opt), out.data_ptr(), ctypes.byref(st)))
     return out[:n], st.as_dict()
 
 
-def bm_occupancy_eps(X, k: int, path: str = "auto", stream=None):
+def bm_occupancy_eps(X, k: int, path: str = "auto", stream=None, centring: str = "auto"):
     """Target-occupancy scale (Sec. 6.1): median over the points of the k-th NN distance.
     Returns (eps as a Python float, stats)."""
     lib = load()
@@ -466,10 +466,10 @@ def bm_occupancy_eps(X, k: int, path: str = "auto", stream=None):
     st = bm_stats()
     eps = ctypes.c_double(0.0)
     if host:
-        opt = _options(lib, path, 0, stream, True, None)
+        opt = _options(lib, path, 0, stream, True, None, centring=centring)
     else:
         alloc = _TorchAllocator(kx.device)
-        opt = _options(lib, path, 0, stream or _current_stream(kx.device), False, alloc)
+        opt = _options(lib, path, 0, stream or _current_stream(kx.device), False, alloc, centring=centring)
     _check(lib, lib.bm_occupancy_eps(px, n, d, int(k), ctypes.byref(opt), ctypes.byref(eps), ctypes.byref(st)))
     return eps.value, st.as_dict()
 

@@ -143,3 +143,22 @@ def test_batched_translation(bm):
     for k, ((X, e), r) in enumerate(zip(inst, res)):
         assert_same_graph(to_np(r), oracle.build(X, e), k)
         assert r["stats"]["centred"] == 1
+
+
+@pytest.mark.parametrize("centring", ["always", "off"])
+def test_translated_knn_matches_oracle(bm, centring):
+    """The k-NN sweep (each row with its own squared radius) on translated operands."""
+    X = shifted(6000, 12, seed=13)
+    kd, st = bm.bm_knn_dist(cuda(X), 6, centring=centring)
+    torch.cuda.synchronize()
+    assert np.array_equal(kd.cpu().numpy(), oracle.kth_nn_dist(X, 6))
+    assert st["centred"] == (1 if centring == "always" else 0)
+
+
+def test_auto_translation_on_large_knn(bm):
+    """70,000 points far from the origin: the automatic mode translates the k-NN sweep."""
+    X = shifted(70_000, 8, seed=51, offset=9.0)
+    kd, st = bm.bm_knn_dist(cuda(X), 6)
+    torch.cuda.synchronize()
+    assert st["centred"] == 1
+    assert np.array_equal(kd.cpu().numpy(), oracle.kth_nn_dist(X, 6))
