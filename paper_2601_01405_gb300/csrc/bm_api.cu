@@ -359,8 +359,9 @@ bm_status operand_centre(const float* x, long long rows, int d, const bm_options
 }
 
 // After the norms are known on the host: fp16 operands at the chosen scale (fp16 path
-// only), the band half-width, and +delta' in the points' augmentation (tensor-core
-// paths).  pts: the B side (points); qry: the A side (queries), or null.
+// only), the band half-width, and the per-row delta' entries of both sides'
+// augmentation (tensor-core paths).  pts: the B side (points); qry: the A side
+// (queries), or null.
 bm_status finish_prep(DeviceState* st, int path, int d, double eps2, double eps, bool same_sets, float max_norm,
                       Prepared* pts, Prepared* qry, cudaStream_t s) {
     int e = 0;
@@ -814,7 +815,8 @@ bm_status greedy_enqueue_step(GreedyCtx& c, const Prepared& pts, Arena& ar, Swee
 // far ran elsewhere, e.g. in a graph).
 // Move a greedy in progress to another tensor-core representation: new operands
 // of the points (replacing the old ones), candidate operand rows to match, the new
-// band half-width and +delta'.  Every step is exact on either path.
+// band half-width and the points' per-row delta' entries.  Every step is exact on either
+// path.
 bm_status switch_path(GreedyCtx& c, Prepared& pts, Arena& ar, cudaStream_t s, int to, float max_norm, int step) {
     DeviceState* st = c.g.st;
     Prepared p2;

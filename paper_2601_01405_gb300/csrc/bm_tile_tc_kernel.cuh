@@ -9,9 +9,10 @@
 //     v = q.x - phi_q - phi_x = (eps^2 - D)/2,      phi = ||.||^2/2 - eps^2/4
 // as one FP32 accumulation in tensor memory:
 //     q.x ~ hi_q.hi_x + lo_q.hi_x + hi_q.lo_x      (bf16 split products, exact in FP32)
-//     - phi_q - phi_x                              (the 16-wide augmentation block)
-// Pairs with v > delta are members, v < -delta are not, and the band in
-// between is listed for the FP64 recheck kernel (verified range set, Sec. 5.3).
+//     - phi_q - phi_x + delta'_q                   (the 16-wide augmentation block)
+// with delta'_q the query row's own proven error bound (rounded up), so that pairs with
+// v > delta'_q are members, v < -delta'_q are not, and the band in between is listed for
+// the FP64 recheck kernel (verified range set, Sec. 5.3).
 //
 // Kernel organisation (one CTA per SM, persistent over work items):
 //   warp 0  TMA producer: one point tile (B, NT rows x all K) per work item,
@@ -608,8 +609,8 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_tc_kernel(const __grid_cons
                     }
                     continue;
                 }
-                // classification: per 32-column chunk a hit mask (acc > 2 delta') and a band
-                // mask (0 <= acc <= 2 delta'), bit i = column col0 + i.  Sign bits are
+                // classification: per 32-column chunk a hit mask (acc > hit_thr) and a band
+                // mask (0 <= acc <= hit_thr), bit i = column col0 + i.  Sign bits are
                 // gathered with funnel shifts (bit i of the mask from register i); the sign
                 // of thr - acc is set exactly when acc > thr (a rounded difference keeps the
                 // sign of the exact one, and is +0 only when they are equal).
