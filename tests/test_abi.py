@@ -157,3 +157,36 @@ def test_centring_mode_rejected_before_the_device():
                                 ctypes.byref(stats))
         assert st == binding.BM_ERR_ARG
     assert binding.CENTRING == {"auto": 0, "always": 1, "off": 2}
+
+
+def test_host_result_views_free_once_after_the_last_view():
+    """Host results are numpy views of the library's buffers: the buffers go back (one
+    free call) only when the last view is gone, and the views read the buffer in place."""
+    import gc
+    import numpy as np
+    calls = []
+
+    def fake_free(obj_ref, opt_ref):
+        calls.append(1)
+
+    buf = (ctypes.c_int32 * 8)(*range(8))
+    own = binding._HostResult(fake_free, binding.bm_csr(), binding.bm_options())
+    a = own.view(ctypes.addressof(buf), ctypes.c_int32, 5)
+    b = own.view(ctypes.addressof(buf) + 4 * 5, ctypes.c_int32, 3)
+    del own
+    gc.collect()
+    assert calls == [] and a.tolist() == [0, 1, 2, 3, 4] and b.tolist() == [5, 6, 7]
+    buf[1] = 42
+    assert a[1] == 42                      # a view, not a copy
+    del a
+    gc.collect()
+    assert calls == []                     # b still holds the buffers
+    del b
+    gc.collect()
+    assert calls == [1]
+    empty = binding._HostResult(fake_free, binding.bm_csr(), binding.bm_options()).view(
+        ctypes.addressof(buf), ctypes.c_int32, 0)
+    assert empty.shape == (0,)
+    del empty
+    gc.collect()
+    assert calls == [1, 1]
