@@ -244,8 +244,9 @@ __device__ __forceinline__ int resolve_walk(const unsigned* conflict, int words,
 // (stage_words words).
 __global__ void __launch_bounds__(1024) greedy_resolve_kernel(DeviceState* st, const unsigned* conflict,
                                                              const unsigned* row_any, int words,
-                                                             const int* cand_ids, int* ordinal,
-                                                             int* landmarks, unsigned long long mem_cap,
+                                                             const int* __restrict__ cand_ids,
+                                                             int* __restrict__ ordinal,
+                                                             int* __restrict__ landmarks, unsigned long long mem_cap,
                                                              int stage_words, int s_max) {
     pdl_wait();
     pdl_trigger();
@@ -307,12 +308,14 @@ __global__ void __launch_bounds__(1024) greedy_resolve_kernel(DeviceState* st, c
     }
     __syncthreads();
     const int base_l = st->n_landmarks;
-    for (int k = tid; k < c; k += blockDim.x) {
+#pragma unroll 4
+    for (int k = tid; k < c; k += blockDim.x) {   // the candidate id loads of four rounds in flight
+        const int id = cand_ids[k];
         const unsigned aw = s_alive[k >> 5];
         const bool a = (aw >> (k & 31)) & 1u;
         const int rank = s_rank_of_word[k >> 5] + __popc(aw & ((1u << (k & 31)) - 1u));
         ordinal[k] = a ? base_l + rank : -1;
-        if (a) landmarks[base_l + rank] = cand_ids[k];
+        if (a) landmarks[base_l + rank] = id;
     }
     __syncthreads();
     if (tid == 0) {
