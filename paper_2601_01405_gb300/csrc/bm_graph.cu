@@ -677,10 +677,11 @@ bool build_edges(const unsigned long long* keys, const long long* moff, long lon
     j.n = n;
     j.L = L;
     if (!edges_transpose(j, ar, s, f)) return false;
-    std::vector<long long> hpre((size_t)L + 1);
-    BM_TRY(cudaMemcpyAsync(hpre.data(), j.lpre, sizeof(long long) * (L + 1), cudaMemcpyDeviceToHost, s));
+    // the pair total first; the per-landmark prefix (8 (L + 1) bytes, 54 MB for a batch of
+    // 6.7M landmarks) comes to the host only where the sort path needs several chunks
+    long long P = 0;
+    BM_TRY(cudaMemcpyAsync(&P, j.lpre + L, sizeof(long long), cudaMemcpyDeviceToHost, s));
     BM_TRY(cudaStreamSynchronize(s));
-    const long long P = hpre[(size_t)L];
     out.pairs = P;
     if (P == 0) {
         edges_release(j, ar);
@@ -688,10 +689,22 @@ bool build_edges(const unsigned long long* keys, const long long* moff, long lon
     }
     j.bitmap = edges_choose_bitmap(L, P);
     std::vector<std::pair<int, int>> chunks;
+    std::vector<long long> cpre;   // pairs before each chunk's first landmark, then P
     if (j.bitmap) {
         const long long R = edges_bitmap_rows(L);
         for (long long i0 = 0; i0 < L; i0 += R) chunks.emplace_back((int)i0, (int)std::min(L, i0 + R));
+        cpre.resize(chunks.size() + 1);
+        for (size_t c = 0; c < chunks.size(); ++c)
+            BM_TRY(cudaMemcpyAsync(&cpre[c], j.lpre + chunks[c].first, sizeof(long long), cudaMemcpyDeviceToHost, s));
+        cpre[chunks.size()] = P;
+        BM_TRY(cudaStreamSynchronize(s));
+    } else if (P <= kEdgeChunkPairs) {
+        chunks.emplace_back(0, (int)L);
+        cpre = {0, P};
     } else {
+        std::vector<long long> hpre((size_t)L + 1);
+        BM_TRY(cudaMemcpyAsync(hpre.data(), j.lpre, sizeof(long long) * (L + 1), cudaMemcpyDeviceToHost, s));
+        BM_TRY(cudaStreamSynchronize(s));
         for (long long i0 = 0; i0 < L;) {
             // largest i1 with pairs(i0, i1) <= budget (at least one landmark)
             long long lo = i0 + 1, hi = L;
@@ -707,15 +720,17 @@ bool build_edges(const unsigned long long* keys, const long long* moff, long lon
                 return false;
             }
             chunks.emplace_back((int)i0, (int)i1);
+            cpre.push_back(hpre[(size_t)i0]);
             i0 = i1;
         }
+        cpre.push_back(P);
     }
     // per chunk: deduplicate, then append (chunks ascend in i)
     int* edges = nullptr;
     long long E = 0, cap = 0;
-    for (const auto& ch : chunks) {
-        const int i0 = ch.first, i1 = ch.second;
-        const long long Pc = hpre[(size_t)i1] - hpre[(size_t)i0];
+    for (size_t c = 0; c < chunks.size(); ++c) {
+        const int i0 = chunks[c].first, i1 = chunks[c].second;
+        const long long Pc = cpre[c + 1] - cpre[c];
         if (Pc == 0) continue;
         if (!edges_emit(j, i0, i1, Pc, ar, s, f)) return false;
         long long Ec = 0;
