@@ -93,7 +93,7 @@ typedef enum {
 /* Allocation callbacks: return device (or, for host outputs, ignored) memory
  * of at least `bytes` bytes ordered on `stream`; NULL signals failure.  Without them the
  * library allocates stream-ordered from a pool of its own per device and context, which
- * keeps up to 8 GiB of freed memory mapped for later calls (outputs handed to the caller
+ * keeps up to 64 GiB of freed memory mapped for later calls (outputs handed to the caller
  * return to it through bm_csr_free / bm_graph_free). */
 typedef void* (*bm_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*bm_free_fn)(void* ptr, void* stream, void* ctx);

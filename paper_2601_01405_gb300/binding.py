@@ -335,12 +335,12 @@ def bm_build(X, eps: float, path: str = "auto", batch: int = 0, stream=None, ski
         opt = _options(lib, path, batch, stream, True, None, skip_edges, want_dists, centring)
         _check(lib, lib.bm_build(px, n, d, ctypes.c_float(eps), ctypes.byref(opt), ctypes.byref(g)))
         return _host_graph(lib, g, opt, want_dists)
-    import torch
     dev = kx.device
-    alloc = _TorchAllocator(dev)
-    opt = _options(lib, path, batch, stream or _current_stream(dev), False, alloc, skip_edges, want_dists, centring)
+    # scratch and outputs from the library's own pool (no Python call per buffer); the
+    # outputs come back as zero-copy tensors that release them when the last one is gone
+    opt = _options(lib, path, batch, stream or _current_stream(dev), False, None, skip_edges, want_dists, centring)
     _check(lib, lib.bm_build(px, n, d, ctypes.c_float(eps), ctypes.byref(opt), ctypes.byref(g)))
-    return _graph_dict(alloc, g, want_dists)
+    return _device_graph(lib, g, opt, dev, want_dists)
 
 
 def _graph_dict(alloc, g, want_dists=False):
@@ -375,6 +375,57 @@ class _HostResult:
             self._free(ctypes.byref(self._obj), ctypes.byref(self._opt))
         except Exception:
             pass
+
+
+class _CudaSpan:
+    """__cuda_array_interface__ of a span of a library-owned device buffer (keeps its owner)."""
+
+    def __init__(self, owner, ptr, count, typestr):
+        self._owner = owner
+        self.__cuda_array_interface__ = {"shape": (int(count),), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None, "stream": None}
+
+
+class _DeviceResult:
+    """Owns the device buffers of one library result (allocated from the library's own
+    stream-ordered pool, with no call into Python per buffer); the torch tensors returned
+    are views of them, and the buffers go back to the library (bm_graph_free) once the last
+    tensor is gone."""
+
+    _TYPESTR = {"int32": "<i4", "int64": "<i8", "float32": "<f4"}
+
+    def __init__(self, free_fn, obj, opt, device):
+        self._free, self._obj, self._opt, self._device = free_fn, obj, opt, device
+
+    def tensor(self, ptr, count, dtype):
+        import torch
+        if count == 0 or not ptr:
+            return torch.empty(0, dtype=dtype, device=self._device)
+        span = _CudaSpan(self, ptr, count, self._TYPESTR[str(dtype).replace("torch.", "")])
+        t = torch.as_tensor(span, device=self._device)
+        t._bm_owner = span   # besides the storage's own reference to the span
+        return t
+
+    def __del__(self):
+        try:
+            self._free(ctypes.byref(self._obj), ctypes.byref(self._opt))
+        except Exception:
+            pass
+
+
+def _device_graph(lib, g, opt, device, want_dists=False):
+    """A device bm_graph from the library's pool as a dict of torch tensors (no copy)."""
+    import torch
+    own = _DeviceResult(lib.bm_graph_free, bm_graph.from_buffer_copy(g), opt, device)
+    L, nnz, E = g.n_landmarks, g.members.nnz, g.n_edges
+    res = {"landmarks": own.tensor(g.landmarks, L, torch.int32),
+           "offsets": own.tensor(g.members.offsets, L + 1, torch.int64),
+           "ids": own.tensor(g.members.ids, nnz, torch.int32),
+           "edges": own.tensor(g.edges, 2 * E, torch.int32).view(E, 2),
+           "stats": g.stats.as_dict()}
+    if want_dists:
+        res["dists"] = own.tensor(g.members.dists, nnz, torch.float32)
+    return res
 
 
 def _host_graph(lib, g, opt, want_dists):
@@ -505,18 +556,9 @@ def bm_build_batched(instances, path: str = "auto", batch: int = 0, stream=None,
         return [_host_graph(lib, outs[k], opt, False) for k in range(count)]
     import torch
     dev = ins[0][3].device if count else torch.device("cuda", torch.cuda.current_device())
-    alloc = _TorchAllocator(dev)
-    opt = _options(lib, path, batch, stream or _current_stream(dev), False, alloc, skip_edges, centring=centring)
+    opt = _options(lib, path, batch, stream or _current_stream(dev), False, None, skip_edges, centring=centring)
     _check(lib, lib.bm_build_batched(arr_in, count, ctypes.byref(opt), outs, statuses))
-    res = []
-    for g in outs[:count]:
-        L, nnz, E = g.n_landmarks, g.members.nnz, g.n_edges
-        res.append({"landmarks": alloc.tensor(g.landmarks, L, torch.int32),
-                    "offsets": alloc.tensor(g.members.offsets, L + 1, torch.int64),
-                    "ids": alloc.tensor(g.members.ids, nnz, torch.int32),
-                    "edges": alloc.tensor(g.edges, 2 * E, torch.int32).view(E, 2),
-                    "stats": g.stats.as_dict()})
-    return res
+    return [_device_graph(lib, outs[k], opt, dev) for k in range(count)]
 
 
 def tile_shapes():

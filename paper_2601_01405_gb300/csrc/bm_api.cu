@@ -62,7 +62,7 @@ namespace {
 // synchronisations, so that a call does not map its scratch afresh after the previous
 // call's memory went back to the driver (the default pool keeps nothing).  Keyed on the
 // context, like any device resource: a context created after a reset gets its own pool.
-constexpr unsigned long long kPoolKeepBytes = 8ull << 30;
+constexpr unsigned long long kPoolKeepBytes = 64ull << 30;
 std::mutex g_pool_mu;
 std::vector<std::pair<unsigned long long, cudaMemPool_t>> g_pools;   // (context id, pool)
 
