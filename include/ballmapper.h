@@ -299,6 +299,19 @@ BM_API bm_status bm_set_tile_config(int32_t d, const bm_tile_config* cfg);
  * depend on it. */
 BM_API int64_t bm_set_nerve_bitmap_bytes(int64_t bytes);
 
+/* The proven half-width of the error band (Sec. 3.2: the tiles evaluate
+ * v = q.x - phi_q - phi_x = (eps^2 - D)/2 from the expanded form, in FP32 on the
+ * tensor cores or the CUDA cores), in units of v: the library decides a pair on the
+ * tiles only where the accumulator lies farther than this from the decision point, and
+ * re-decides the rest in FP64.  path: BM_PATH_TC_SPLIT3, BM_PATH_TC_FP16 or BM_PATH_FP32;
+ * d: dimension; d_pad: the padded K extent of the tiles (bm_get_tile_config; d for the
+ * FP32 path); n_a, n_b: bounds on the norms of the query and point rows; phi_a, phi_b:
+ * bounds on their |phi| (on the fp16 path all four in the operands' scaled units).  The
+ * library uses it per query row (n_a, phi_a of the row) against the points' maxima.  Host
+ * function, no device needed; a negative or non-finite input gives a non-finite result. */
+BM_API double bm_band_halfwidth(int32_t path, int32_t d, int32_t d_pad, double n_a, double n_b, double phi_a,
+                                double phi_b);
+
 /* ---- Inverted-file index: the paper's non-exhaustive approximate oracle (Sec. 5.4;
  * nprobe cells searched per query, Sec. 6.1).  Points are grouped into nlist
  * k-means cells; a query examines only the points of its nprobe nearest cells

@@ -177,6 +177,9 @@ def load(path: str = LIB_PATH):
         lib.bm_occupancy_eps.restype = ctypes.c_int
         lib.bm_set_nerve_bitmap_bytes.argtypes = [ctypes.c_int64]
         lib.bm_set_nerve_bitmap_bytes.restype = ctypes.c_int64
+        lib.bm_band_halfwidth.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        lib.bm_band_halfwidth.restype = ctypes.c_double
         _lib = lib
         return lib
 
@@ -774,3 +777,10 @@ class GraphIndex:
             self.close()
         except Exception:
             pass
+
+
+def band_halfwidth(path: str, d: int, d_pad: int, n_a: float, n_b: float, phi_a: float, phi_b: float) -> float:
+    """The proven error-band half-width of a tile path (bm_band_halfwidth), in units of
+    v = (eps^2 - D)/2; path: "tc", "tc16" or "fp32"."""
+    return float(load().bm_band_halfwidth(PATHS[path], int(d), int(d_pad), float(n_a), float(n_b), float(phi_a),
+                                          float(phi_b)))

@@ -2281,6 +2281,11 @@ bm_status bm_occupancy_eps(const float* X, int64_t n, int32_t d, int32_t k, cons
 
 int64_t bm_set_nerve_bitmap_bytes(int64_t bytes) { return edges_set_bitmap_budget(bytes); }
 
+double bm_band_halfwidth(int32_t path, int32_t d, int32_t d_pad, double n_a, double n_b, double phi_a,
+                         double phi_b) {
+    return band_halfwidth_core(path, d, d_pad, n_a, n_b, phi_a, phi_b);
+}
+
 int32_t bm_tile_shapes(bm_tile_config* out, int32_t max) {
     std::vector<TileConfig> v(64);
     const int n = tile_shapes(v.data(), (int)v.size());
